@@ -1,0 +1,198 @@
+"""The PDXearch framework run block by block, one query at a time, in FP64.
+
+TEST INFRASTRUCTURE ONLY (see the package docstring).
+
+This follows the paper's description step by step; it is the reference for the
+*algorithm* (which vectors are pruned when, how many dimensions are visited),
+while ``oracle.knn`` is the reference for the exact *result*:
+
+* Sec. 4 PHASE 0 START: the first block is scanned without pruning; its
+  distances fill the max-heap and the k-th best becomes the threshold tau. When
+  a block holds fewer than k vectors the linear scan continues into the next
+  block(s) until k vectors have been seen (the paper is silent on this case).
+* Sec. 4 PHASE 1 WARMUP: dimensions are fetched in steps that start at
+  ``first_step`` (2) and double (2, 4, 8, ...), the last one clamped to the
+  remaining dimensions. After each step the partial distances of *all*
+  vectors of the block are updated and the pruning predicate is evaluated;
+  a vector that fails it is discarded for good but WARMUP keeps computing
+  its partial distance.
+* Sec. 4 PHASE 2 PRUNE: once the fraction of not-yet-pruned vectors of the
+  block is below ``selection_threshold`` (20%, Sec. 6.1) only the survivors
+  (the positions array) are computed; steps keep doubling. At the last
+  dimension the survivors are merged into the heap and tau tightens.
+* Sec. 5 PDX-BOND: the predicate is "partial distance > tau"; dimensions are
+  visited by decreasing |q_j - mu_j| where mu are the block's means
+  ("distance to means"), or by decreasing q_j ("decreasing", BOND's order),
+  or zone by zone: contiguous groups of ``zone_dims`` dimensions ranked by
+  sum_{j in zone} (q_j - mu_j)^2, dimensions inside a zone in storage order.
+  Ties in any ranking go to the lower dimension / zone index.
+* Sec. 2.3 ADSampling (on data rotated by a random orthogonal matrix, dims in
+  storage order): after d of D dimensions the vector is pruned when
+  partial * D / d > tau * (1 + eps0 / sqrt(d))^2 -- the hypothesis test on the
+  scaled partial distance with error bound eps0, written for squared distances.
+* Sec. 2.3 BSA_res (on PCA-projected data, dims in storage order): the
+  unvisited part of the distance is ||x_r||^2 + ||q_r||^2 - 2<x_r, q_r>; the
+  cross term is replaced by its error quantile m * s_d(q), with
+  s_d(q)^2 = sum_{j unvisited} lambda_j q_j^2 (lambda = PCA variances), capped
+  by the Cauchy-Schwarz bound ||x_r|| ||q_r||; prune when
+  partial + ||x_r||^2 + ||q_r||^2 - 2 min(m s_d, ||x_r|| ||q_r||) > tau.
+
+Returns the top-k plus per-query counters: values accumulated (the paper's
+pruning power is 1 - visited / (n*D)), vectors pruned, and the phase at which
+each block ended.
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field
+
+import numpy as np
+
+
+@dataclass
+class SearchStats:
+    values_visited: int = 0          # sum over vectors of dims accumulated
+    vectors_seen: int = 0
+    vectors_pruned: int = 0
+    prune_events: list = field(default_factory=list)   # (block, vector id, dims visited at prune)
+
+
+def visit_order(q, mu, order: str, zone_dims: int = 1):
+    """Order in which a block's dimensions are visited (Sec. 5)."""
+    d = q.shape[0]
+    if order == "sequential":
+        return np.arange(d)
+    if order == "decreasing":
+        # BOND: highest query value first; ties -> lower dim index
+        return np.lexsort((np.arange(d), -q))
+    if order != "dist_to_means":
+        raise ValueError(order)
+    score = (q - mu) ** 2
+    if zone_dims <= 1:
+        return np.lexsort((np.arange(d), -score))
+    nz = (d + zone_dims - 1) // zone_dims
+    zs = np.array([score[z * zone_dims:(z + 1) * zone_dims].sum() for z in range(nz)])
+    zorder = np.lexsort((np.arange(nz), -zs))
+    return np.concatenate([np.arange(z * zone_dims, min(d, (z + 1) * zone_dims)) for z in zorder])
+
+
+def step_schedule(d: int, first_step: int):
+    """Sizes of the fetching steps: first_step, doubling, last one clamped."""
+    out, pos, s = [], 0, max(1, first_step)
+    while pos < d:
+        t = min(s, d - pos)
+        out.append(t)
+        pos += t
+        s *= 2
+    return out
+
+
+class _Heap:
+    """Best-k list ordered by (distance, id)."""
+
+    def __init__(self, k):
+        self.k = k
+        self.items: list[tuple[float, int]] = []
+
+    def merge(self, dists, ids):
+        self.items.extend(zip((float(v) for v in dists), (int(i) for i in ids)))
+        self.items.sort()
+        del self.items[self.k:]
+
+    @property
+    def tau(self):
+        return self.items[-1][0] if len(self.items) == self.k else math.inf
+
+
+def pdxearch(x, q, k, blocks, pruner="bond", order="dist_to_means", zone_dims=1, first_step=2,
+             selection_threshold=0.20, eps0=2.1, bsa_m=None, bsa_lambda=None, tau0=None):
+    """One query. ``blocks`` is a list of int arrays (vector ids per PDXearch
+    block, visited in list order). ``x`` is [n][D]; returns (dists, ids, stats).
+    ``tau0`` optionally seeds the threshold (any k-th distance of k real
+    vectors keeps the search exact)."""
+    x = np.asarray(x, np.float64)
+    q = np.asarray(q, np.float64)
+    n, d = x.shape
+    heap = _Heap(k)
+    st = SearchStats()
+    seen = 0
+    started = tau0 is not None
+    tau_seed = math.inf if tau0 is None else float(tau0)
+    for bi, ids in enumerate(blocks):
+        ids = np.asarray(ids, np.int64)
+        if ids.size == 0:
+            continue
+        xb = x[ids]
+        if not started:
+            # START: linear scan until k vectors have been seen
+            full = ((xb - q) ** 2).sum(axis=1)
+            st.values_visited += ids.size * d
+            st.vectors_seen += ids.size
+            heap.merge(full, ids)
+            seen += ids.size
+            if seen >= k:
+                started = True
+            continue
+        tau = min(heap.tau, tau_seed)
+        if pruner in ("bond", "none"):
+            mu = xb.mean(axis=0)
+            dims = visit_order(q, mu, order, zone_dims)
+        else:
+            dims = np.arange(d)
+        partial = np.zeros(ids.size)
+        pruned = np.zeros(ids.size, bool)
+        positions = None          # None = WARMUP (all vectors), else PRUNE survivors
+        pos = 0
+        for s in step_schedule(d, first_step):
+            js = dims[pos:pos + s]
+            rows = np.arange(ids.size) if positions is None else positions
+            contrib = ((xb[np.ix_(rows, js)] - q[js]) ** 2).sum(axis=1)
+            partial[rows] += contrib
+            st.values_visited += rows.size * js.size
+            pos += s
+            if pos >= d:
+                break
+            test = _predicate(pruner, partial[rows], tau, pos, d, xb[rows], q, dims, pos, eps0, bsa_m, bsa_lambda)
+            newly = test & ~pruned[rows]
+            for r in rows[newly]:
+                st.prune_events.append((bi, int(ids[r]), pos))
+            pruned[rows] |= test
+            alive = np.flatnonzero(~pruned)
+            if alive.size == 0:
+                break
+            if positions is None and alive.size < selection_threshold * ids.size:
+                positions = alive
+            elif positions is not None:
+                positions = alive
+        st.vectors_seen += ids.size
+        st.vectors_pruned += int(pruned.sum())
+        alive = np.flatnonzero(~pruned)
+        if pos >= d and alive.size:
+            heap.merge(partial[alive], ids[alive])
+    items = heap.items + [(math.inf, -1)] * (k - len(heap.items))
+    return np.array([v for v, _ in items]), np.array([i for _, i in items], np.int64), st
+
+
+def _predicate(pruner, partial, tau, dvis, d, xrows, q, dims, pos, eps0, bsa_m, bsa_lambda):
+    if pruner == "none" or not math.isfinite(tau):
+        return np.zeros(partial.shape, bool)
+    if pruner == "bond":
+        return partial > tau
+    if pruner == "ads":
+        return partial * (d / dvis) > tau * (1.0 + eps0 / math.sqrt(dvis)) ** 2
+    if pruner == "bsa":
+        rest = dims[pos:]
+        rx2 = (xrows[:, rest] ** 2).sum(axis=1)
+        rq2 = float((q[rest] ** 2).sum())
+        s_d = math.sqrt(float((np.asarray(bsa_lambda, np.float64)[rest] * q[rest] ** 2).sum()))
+        cross = np.minimum(bsa_m * s_d, np.sqrt(rx2 * rq2))
+        return partial + rx2 + rq2 - 2.0 * cross > tau
+    raise ValueError(pruner)
+
+
+def partitions(n: int, partition_size: int):
+    """Exact-search blocks (Sec. 6.6): equal horizontal partitions of at most
+    ``partition_size`` vectors, in id order."""
+    nparts = max(1, -(-n // partition_size))
+    size = -(-n // nparts)
+    return [np.arange(p * size, min(n, (p + 1) * size)) for p in range(nparts)]
