@@ -1,0 +1,341 @@
+#!/usr/bin/env python
+"""Throughput of the PDX exact search (PDXearch + PDX-BOND) on GB300.
+
+A step is one exact top-10 search of the whole query batch (1,000 queries)
+over the 1M x 768 Gaussian-mixture collection, inputs resident in HBM. The
+JSON line reports queries/s, the roofline of the dominant kernel (the PDXearch
+scan) from live CUDA events and the kernel's own counters, the end-to-end
+rate through the C ABI with host buffers, the CPU oracle on the host cores,
+and the SM clocks seen during the timed region.
+
+Usage: python bench.py [--gpus N --steps K --warmup W --impl ours|reference]
+For N > 1 launch under torchrun: every rank holds a replica of the
+collection and searches its own batch of queries (weak scaling, no
+collective on the data path).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = ("queries/sec at exact top-10 (and recall@10=0.95 IVF); HBM GB/s vs peak; learned vs plain")
+WORKLOADS = {
+    "bond_exact_1m_d768": dict(k=10, pruner="bond"),
+    "plain_scan_10k_d128": dict(k=10, pruner="none"),
+}
+PROFILE_TRAFFIC = os.path.join(ROOT, "profiles", "traffic.json")
+
+
+def _env_int(name, default):
+    try:
+        return int(os.environ.get(name, default))
+    except ValueError:
+        return default
+
+
+class ClockSampler:
+    """nvidia-smi clocks/throttle reasons sampled every 200 ms in the background."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.QUERY}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                rows.append((float(parts[1]), float(parts[2]), parts[5:9]))
+            except ValueError:
+                continue
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for _, _, r in rows for i, v in enumerate(r) if v.lower().startswith("active")})
+        return {"sm_mhz": statistics.median(r[0] for r in rows), "sm_max_mhz": max(r[1] for r in rows),
+                "reasons": reasons, "samples": len(rows)}
+
+
+def _kernel_hash():
+    h = hashlib.sha256()
+    for f in ("pdx_search.cu", "pdx_internal.cuh"):
+        with open(os.path.join(ROOT, "paper_2503_04422_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def _traffic_per_launch(workload):
+    """DRAM bytes per scan launch from the committed ncu summary, if it was
+    taken on the current kernel source."""
+    try:
+        with open(PROFILE_TRAFFIC) as f:
+            t = json.load(f)
+    except (OSError, ValueError):
+        return None
+    e = t.get(workload)
+    if not e or e.get("kernel_hash") != _kernel_hash():
+        return None
+    return e.get("dram_bytes_per_launch")
+
+
+def _peak_hbm():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except (OSError, ValueError, KeyError):
+        return 6800.0, "fallback"
+
+
+def cpu_oracle_rate(x, q, k, budget_s=15.0, metric="l2"):
+    """FP64 oracle on the host cores over batches of queries until the budget
+    is spent. Returns (queries/s, threads, queries done)."""
+    from oracle import knn as ok
+    threads = ok.default_threads()
+    done, t0 = 0, time.perf_counter()
+    batch = max(threads, 8)
+    while True:
+        sel = q[(done % q.shape[0]):(done % q.shape[0]) + batch]
+        ok.knn(x, sel, k, metric, threads=threads)
+        done += sel.shape[0]
+        el = time.perf_counter() - t0
+        if el >= budget_s:
+            return done / el, threads, done
+
+
+def run_reference(args, rank, world):
+    """The oracle on the host cores: each step searches a bounded sample of the
+    same workload (a few queries against the full collection)."""
+    if rank != 0:
+        return
+    import pdx_synth
+    from oracle import knn as ok
+    ok.build()
+    spec = WORKLOADS[args.workload]
+    x, q = pdx_synth.make(args.workload)
+    threads = ok.default_threads()
+    per_step = max(threads, 8)
+    for s in range(args.warmup):
+        ok.knn(x, q[:per_step], spec["k"], threads=threads)
+    t0 = time.perf_counter()
+    done = 0
+    for s in range(args.steps):
+        sel = q[(s * per_step) % q.shape[0]:][:per_step]
+        ok.knn(x, sel, spec["k"], threads=threads)
+        done += sel.shape[0]
+    el = time.perf_counter() - t0
+    value = done / el
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "queries/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": args.workload, "n": x.shape[0], "d": x.shape[1], "k": spec["k"],
+                       "queries_per_step": per_step},
+            "cpu_baseline": {"value": value, "unit": "queries/s", "cores": threads, "kind": "oracle",
+                             "sample": f"{per_step} queries per step against all {x.shape[0]} vectors"},
+            "e2e": {"value": value, "unit": "queries/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args, rank, world, local_rank):
+    import numpy as np
+    import torch
+
+    import pdx_synth
+    from paper_2503_04422_gb300 import build as pbuild
+    pbuild.build()
+    from paper_2503_04422_gb300 import pdx
+
+    torch.cuda.set_device(local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    spec = WORKLOADS[args.workload]
+    k = spec["k"]
+    base_nq = pdx_synth.WORKLOADS[args.workload]["nq"]
+    x, q_all = pdx_synth.make(args.workload, nq=base_nq * world)
+    q = np.ascontiguousarray(q_all[rank * base_nq:(rank + 1) * base_nq])
+    n, d = x.shape
+    nq = q.shape[0]
+    ix = pdx.pdx_build_layout(torch.from_numpy(x).cuda())
+    torch.cuda.synchronize()
+    torch.cuda.empty_cache()
+    q_dev = torch.from_numpy(q).cuda()
+    od = torch.empty((nq, k), dtype=torch.float32, device="cuda")
+    oi = torch.empty((nq, k), dtype=torch.int64, device="cuda")
+    stats_dev = torch.zeros(16, dtype=torch.int64, device="cuda")
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")   # > 129 MB L2
+    opts = pdx.search_opts(pruner=spec["pruner"])
+    stream = torch.cuda.current_stream()
+
+    def step(ev_scan=None):
+        if ev_scan is not None:
+            opts.scan_event_start = ev_scan[0].cuda_event
+            opts.scan_event_stop = ev_scan[1].cuda_event
+            opts.stats_device = stats_dev.data_ptr()
+        else:
+            opts.scan_event_start = opts.scan_event_stop = opts.stats_device = None
+        pdx.pdx_search_exact(ix, q_dev, k, opts=opts, out=(od, oi))
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    K = args.steps
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+    ev_scan = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+    for a, b in ev_scan:          # torch creates event handles lazily: materialise them
+        a.record(stream)
+        b.record(stream)
+    clocks = ClockSampler(local_rank)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    stats_dev.zero_()
+    launches0 = pdx.pdx_kernel_launches()
+    clocks.start()
+    for i in range(K):
+        flush.zero_()                                   # L2 flush between timed steps (not timed)
+        ev[i][0].record(stream)
+        step(ev_scan[i])
+        ev[i][1].record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    launches = pdx.pdx_kernel_launches() - launches0
+    if dist:
+        dist.barrier()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    scan_ms = [a.elapsed_time(b) for a, b in ev_scan]
+    tot_ms = sum(step_ms)
+    st = stats_dev.cpu().numpy().astype(np.uint64)
+    if dist:
+        t = torch.tensor([tot_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        tot_ms = float(t.item())
+    ms_per_step = tot_ms / K
+    value = nq * world * K / (tot_ms / 1e3)
+
+    # roofline of the PDXearch scan: logical bytes it read per launch over its
+    # average event-timed duration
+    values_per_launch = float(st[0]) / K
+    bytes_per_launch = values_per_launch * 4.0
+    scan_avg_ms = sum(scan_ms) / K
+    achieved = bytes_per_launch / (scan_avg_ms / 1e3) / 1e9
+    peak, peak_kind = _peak_hbm()
+    traffic = _traffic_per_launch(args.workload)
+
+    # end to end through the C ABI with host (pinned) buffers
+    q_host = torch.from_numpy(q).pin_memory()
+    od_h = torch.empty((nq, k), dtype=torch.float32).pin_memory()
+    oi_h = torch.empty((nq, k), dtype=torch.int64).pin_memory()
+    opts.scan_event_start = opts.scan_event_stop = opts.stats_device = None
+    for _ in range(2):
+        pdx.pdx_search_exact(ix, q_host, k, opts=opts, out=(od_h, oi_h), stream=stream.cuda_stream)
+    e2e_ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+    torch.cuda.synchronize()
+    for i in range(K):
+        flush.zero_()
+        e2e_ev[i][0].record(stream)
+        pdx.pdx_search_exact(ix, q_host, k, opts=opts, out=(od_h, oi_h), stream=stream.cuda_stream)
+        e2e_ev[i][1].record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = sum(a.elapsed_time(b) for a, b in e2e_ev)
+    if dist:
+        t = torch.tensor([e2e_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_ms = float(t.item())
+    e2e_value = nq * world * K / (e2e_ms / 1e3)
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        rate, thr, done = cpu_oracle_rate(x, q, k, budget_s=args.cpu_budget)
+        cpu = {"value": rate, "unit": "queries/s", "cores": thr, "kind": "oracle",
+               "sample": f"{done} queries against all {n} vectors, FP64 brute force with full sort"}
+    if rank == 0:
+        pruned = float(st[2]) / max(1.0, float(st[1]))
+        line = {
+            "metric": METRIC, "value": value, "unit": "queries/s", "n_gpus": world, "steps": K,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": args.workload, "n": n, "d": d, "nq_per_gpu": nq, "k": k,
+                       "pruner": spec["pruner"], "order": "dist_to_means", "zone_dims": int(opts.zone_dims),
+                       "first_step": int(opts.first_step), "selection_threshold": round(float(opts.selection_threshold), 3),
+                       "start_vectors": int(opts.start_vectors),
+                       "l2": "collection 3.1 GB > L2; 256 MB L2 flush between timed steps (untimed)"},
+            "roofline": {"bound": "hbm", "kernel": "pdxsearch_kernel<BOND,L2>", "achieved": achieved,
+                         "peak": peak, "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,
+                         "traffic": traffic, "algorithmic_bytes_per_launch": bytes_per_launch,
+                         "scan_ms_avg": scan_avg_ms,
+                         "per_unit": {"bytes_per_query": bytes_per_launch / nq, "units_per_launch": nq}},
+            "pruning": {"values_visited_fraction": values_per_launch / (n * d * nq), "vectors_pruned_fraction": pruned},
+            "e2e": {"value": e2e_value, "unit": "queries/s", "h2d_bytes_per_step": nq * d * 4,
+                    "d2h_bytes_per_step": nq * k * 12},
+            "gpu_launches": int(launches),
+            "gpu_launches_per_step": launches / K,
+            "clocks": clk,
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="bond_exact_1m_d768", choices=sorted(WORKLOADS))
+    ap.add_argument("--cpu-budget", type=float, default=15.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "ours":
+        args.warmup = 3
+    rank = _env_int("RANK", 0)
+    world = _env_int("WORLD_SIZE", 1)
+    local_rank = _env_int("LOCAL_RANK", 0)
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+    else:
+        run_ours(args, rank, world, local_rank)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,236 @@
+/*
+ * pdx.h -- C ABI of the GB300 (sm_103a) PDX vector-search library.
+ *
+ * The library stores vectors in the PDX layout (Sec. 3 of "PDX: A Data Layout
+ * for Vector Similarity Search", Kuffo, Krippner, Boncz, SIGMOD'25): vectors
+ * are grouped in blocks of 64 and, inside a block, stored dimension by
+ * dimension (element (vector t, dimension j) of block b at
+ * data[(b*D + j)*64 + t]). Searches run the PDXearch framework (Sec. 4: START,
+ * WARMUP, PRUNE phases with doubling fetch steps) with the PDX-BOND (Sec. 5),
+ * ADSampling or BSA (Sec. 2.3) pruning predicates, and return the k nearest
+ * neighbours defined in Sec. 2.1.
+ *
+ * Conventions shared by every call:
+ *  - All functions are extern "C" and never throw. A non-OK status leaves a
+ *    thread-local message readable through pdx_last_error().
+ *  - Pointers to vectors, queries and outputs may be host or device memory of
+ *    the current device; the library tells them apart with
+ *    cudaPointerGetAttributes. The caller owns them; the library copies what
+ *    it needs and keeps no reference after the call returns.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = the legacy default
+ *    stream). With device outputs a search is asynchronous on `stream`; with
+ *    host outputs (or a non-NULL stats_out) it synchronises `stream` before
+ *    returning.
+ *  - Vectors and queries are row-major float32: x[i*d + j], q[i*d + j].
+ *  - Outputs are row-major [nq][k], best first: L2 and L1 ascending, IP
+ *    descending; equal distances are ordered by the lower vector id. A row
+ *    with fewer than k results is padded with id -1 and distance +inf
+ *    (-inf for IP).
+ *  - Search scratch memory is taken from the stream-ordered allocator
+ *    (cudaMallocAsync) and released on `stream` before the call returns, so
+ *    concurrent searches on the same index from different threads/streams are
+ *    safe. An index must not be freed while a search on it is in flight.
+ *  - Limits: 1 <= d <= 4096, 1 <= k <= 1024, n < 2^31.
+ */
+#ifndef PDX_H_
+#define PDX_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct pdx_index pdx_index; /* opaque; owns all of its device memory */
+
+typedef enum pdx_status {
+    PDX_OK = 0,
+    PDX_ERR_ARG = 1,          /* invalid argument; outputs untouched          */
+    PDX_ERR_OOM = 2,          /* device allocation failed                     */
+    PDX_ERR_CUDA = 3,         /* a CUDA call failed                           */
+    PDX_ERR_TIMEOUT = 4,      /* a bounded device wait ran out                */
+    PDX_ERR_UNSUPPORTED = 5   /* valid request this build does not implement  */
+} pdx_status;
+
+/* Sec. 2.1: squared Euclidean distance, inner product (similarity, larger is
+ * better), Manhattan distance; Listing 1 gives the three PDX kernels. */
+typedef enum pdx_metric { PDX_L2 = 0, PDX_IP = 1, PDX_L1 = 2 } pdx_metric;
+
+/* Storage type of the PDX blocks. BF16 / FP8-E4M3 storage keeps an FP32 copy
+ * for the final rerank; FP32 accumulation throughout. */
+typedef enum pdx_dtype { PDX_F32 = 0, PDX_BF16 = 1, PDX_FP8_E4M3 = 2 } pdx_dtype;
+
+/* Pruning predicates (Sec. 2.3 and Sec. 5). NONE is the PDX linear scan. */
+typedef enum pdx_pruner {
+    PDX_PRUNE_NONE = 0,
+    PDX_PRUNE_BOND = 1,        /* exact: partial distance > tau              */
+    PDX_PRUNE_ADSAMPLING = 2,  /* approximate: hypothesis test, eps0         */
+    PDX_PRUNE_BSA = 3          /* approximate: error quantile, multiplier m  */
+} pdx_pruner;
+
+/* Order in which PDX-BOND visits dimensions (Sec. 5, Fig. 6). */
+typedef enum pdx_order {
+    PDX_ORDER_DIST_TO_MEANS = 0, /* by |q_j - mu_j| of the block, descending */
+    PDX_ORDER_DECREASING = 1,    /* by q_j, descending (BOND's order)        */
+    PDX_ORDER_SEQUENTIAL = 2     /* storage order                            */
+} pdx_order;
+
+typedef struct pdx_build_opts {
+    uint32_t struct_size;      /* = sizeof(pdx_build_opts)                                */
+    pdx_metric metric;         /* metric the index will be searched with                   */
+    pdx_dtype storage;         /* block storage type (F32 only in this build for search)   */
+    uint32_t partition_size;   /* exact search: at most this many vectors per PDXearch
+                                  block, equal horizontal partitions (Sec. 6.6; 10000)    */
+    int32_t keep_fp32_rerank;  /* low-precision storage: keep an FP32 copy (default 1)     */
+} pdx_build_opts;
+
+typedef struct pdx_ivf_opts {
+    uint32_t struct_size;      /* = sizeof(pdx_ivf_opts)                                   */
+    pdx_build_opts base;       /* metric / storage; partition_size is ignored             */
+    uint32_t nlist;            /* number of IVF buckets (k-means centroids)               */
+    uint32_t kmeans_iters;     /* Lloyd iterations on the GPU                              */
+    uint32_t kmeans_sample;    /* vectors used to train (0 = all)                         */
+    uint64_t seed;             /* picks the initial centroids when none are given          */
+    pdx_pruner transform;      /* ADSAMPLING: rotate by `rotation`; BSA: PCA projection    */
+    const float *rotation;     /* ADSAMPLING: d*d orthogonal matrix, row-major; the stored
+                                  and query vectors become rotation * v. Caller-owned.    */
+    const float *init_centroids; /* optional nlist*d initial centroids (host or device)   */
+} pdx_ivf_opts;
+
+typedef struct pdx_search_stats {
+    uint64_t values_visited;   /* sum over (query, vector) of dimensions accumulated by the
+                                  PDXearch scan (Sec. 2.2: pruning power = 1 - this / (nq*n*D)) */
+    uint64_t vectors_scanned;  /* (query, vector) pairs touched by the scan                   */
+    uint64_t vectors_pruned;   /* pairs discarded before their last dimension                 */
+    uint64_t prune_phase_blocks; /* (query, 64-vector block) pairs that reached PRUNE         */
+    uint64_t candidates;       /* full distances offered to the top-k lists                   */
+    uint64_t work_items;       /* non-empty (query, block-group) work items                   */
+    uint64_t start_values;     /* values computed by the START scan (exact search)            */
+    uint64_t bytes_logical;    /* (values_visited + start_values) * element size; filled only
+                                  in stats_out                                               */
+    uint64_t reserved[8];
+} pdx_search_stats;
+
+typedef struct pdx_search_opts {
+    uint32_t struct_size;      /* = sizeof(pdx_search_opts)                                */
+    pdx_pruner pruner;         /* default BOND                                             */
+    pdx_order order;           /* PDX-BOND visit order (default DIST_TO_MEANS)             */
+    uint32_t zone_dims;        /* dimension-zone width (Sec. 5); 1 = per dimension         */
+    float selection_threshold; /* switch WARMUP -> PRUNE below this fraction (0.20)        */
+    float eps0;                /* ADSampling error bound (2.1)                             */
+    float bsa_m;               /* BSA multiplier m                                         */
+    uint32_t first_step;       /* first fetch step in dimensions (2); then doubling        */
+    uint32_t start_vectors;    /* exact search: vectors of the START scan (0 = one block)  */
+    uint32_t blocks_per_item;  /* 64-vector blocks per GPU work item (0 = automatic)       */
+    pdx_search_stats *stats_out; /* optional host pointer; filled after the search (the call
+                                  then synchronises `stream`)                               */
+    pdx_search_stats *stats_device; /* optional device pointer: the kernels add their counters
+                                  to its first seven fields asynchronously (caller zeroes it;
+                                  bytes_logical is not written)                              */
+    void *scan_event_start;    /* optional cudaEvent_t recorded on `stream` just before the
+                                  PDXearch scan kernel                                        */
+    void *scan_event_stop;     /* optional cudaEvent_t recorded just after it                 */
+} pdx_search_opts;
+
+typedef struct pdx_index_info {
+    int64_t n;                 /* vectors                                                  */
+    int32_t d;                 /* dimensions                                               */
+    int32_t nparts;            /* PDXearch blocks: partitions (exact) or buckets (IVF)     */
+    int64_t nblocks;           /* 64-vector storage blocks                                 */
+    pdx_metric metric;
+    pdx_dtype storage;
+    int32_t is_ivf;
+    int32_t unit_norm;         /* every stored vector has norm 1 (within 1e-5)             */
+    uint64_t device_bytes;     /* device memory owned by the index                         */
+} pdx_index_info;
+
+/* Internal arrays that pdx_index_copy_out can return (for inspection/tests). */
+typedef enum pdx_array {
+    PDX_ARRAY_BLOCKS = 0,      /* float32 [nblocks][d][64] PDX storage (zero padded)       */
+    PDX_ARRAY_IDS = 1,         /* int32 [nblocks*64] vector id per slot, -1 = padding      */
+    PDX_ARRAY_PART_BLOCKS = 2, /* int32 [nparts+1] first storage block of each part        */
+    PDX_ARRAY_MEANS = 3,       /* float32 [nparts][d] per-part dimension means (Sec. 3)    */
+    PDX_ARRAY_CENTROIDS = 4,   /* float32 [nparts][d] IVF centroids (transformed space)    */
+    PDX_ARRAY_ASSIGN = 5       /* int32 [n] IVF bucket of each vector                      */
+} pdx_array;
+
+/* Fill an options struct with the defaults named above. */
+void pdx_default_build_opts(pdx_build_opts *opts);
+void pdx_default_ivf_opts(pdx_ivf_opts *opts);
+void pdx_default_search_opts(pdx_search_opts *opts);
+
+/*
+ * pdx_build_layout -- exact-search index (Sec. 3, Sec. 6.6).
+ * Splits the n vectors x[n][d] (row-major float32, host or device) into
+ * ceil(n / partition_size) equal horizontal partitions in id order, stores
+ * each partition as consecutive 64-vector PDX blocks (its last block zero
+ * padded) and records per-partition dimension means (block metadata, Sec. 3).
+ * opts may be NULL (defaults). On success *out owns a new index; on failure
+ * *out is set to NULL. Errors: PDX_ERR_ARG (NULL pointers, n < 1, d outside
+ * [1,4096], bad opts), PDX_ERR_OOM, PDX_ERR_CUDA.
+ */
+pdx_status pdx_build_layout(const float *x, int64_t n, int32_t d, const pdx_build_opts *opts,
+                            void *stream, pdx_index **out);
+
+/*
+ * pdx_ivf_build -- IVF index whose buckets are PDX blocks (Sec. 2.1, Fig. 2).
+ * Optionally transforms the vectors first (ADSampling: the caller's random
+ * orthogonal rotation; BSA: PCA projection computed here), runs
+ * kmeans_iters Lloyd iterations on the GPU from init_centroids (or from
+ * nlist vectors picked with `seed`), assigns every vector to its nearest
+ * centroid (ties: lower bucket id), and lays each bucket out as PDX blocks.
+ * Errors as pdx_build_layout, plus PDX_ERR_ARG for nlist outside [1, n] or a
+ * missing rotation for ADSAMPLING.
+ */
+pdx_status pdx_ivf_build(const float *x, int64_t n, int32_t d, const pdx_ivf_opts *opts,
+                         void *stream, pdx_index **out);
+
+/*
+ * pdx_search_exact -- exact k-NN of nq queries q[nq][d] over an index built
+ * by pdx_build_layout (Sec. 2.1; PDX-BOND, Sec. 5, is exact). Writes
+ * out_dist[nq][k] (float32) and out_idx[nq][k] (int64 vector ids). opts may
+ * be NULL (PDX-BOND, distance-to-means order). pruner must be NONE or BOND
+ * (ADSampling/BSA are approximate and only offered over IVF). IP with BOND
+ * requires a unit-norm index (it is searched as L2, the same ranking).
+ * Errors: PDX_ERR_ARG (NULL pointers, nq < 0, k outside [1,1024], bad opts),
+ * PDX_ERR_UNSUPPORTED, PDX_ERR_OOM, PDX_ERR_CUDA. nq == 0 is a no-op.
+ */
+pdx_status pdx_search_exact(const pdx_index *index, const float *q, int64_t nq, int32_t k,
+                            const pdx_search_opts *opts, float *out_dist, int64_t *out_idx,
+                            void *stream);
+
+/*
+ * pdx_search_ivf -- approximate k-NN over an IVF index (Sec. 4, Fig. 4): finds
+ * the nprobe buckets whose centroids are nearest to each (transformed) query
+ * (ties: lower bucket id), then runs PDXearch over them, nearest bucket first,
+ * with the pruner in opts (BOND: exact within the probed buckets). Outputs
+ * as pdx_search_exact. Errors: as pdx_search_exact plus PDX_ERR_ARG for
+ * nprobe outside [1, nlist] or a pruner that needs a transform the index was
+ * not built with.
+ */
+pdx_status pdx_search_ivf(const pdx_index *index, const float *q, int64_t nq, int32_t k,
+                          int32_t nprobe, const pdx_search_opts *opts, float *out_dist,
+                          int64_t *out_idx, void *stream);
+
+/* Release an index and all of its device memory. NULL-safe. */
+void pdx_free(pdx_index *index);
+
+/* Number of CUDA kernels this process has launched through the library. */
+uint64_t pdx_kernel_launches(void);
+
+/* Message of the last non-OK status on this thread ("" if none). */
+const char *pdx_last_error(void);
+
+/* Sizes and flags of an index. */
+pdx_status pdx_index_info_get(const pdx_index *index, pdx_index_info *info);
+
+/* Copy one internal array (see pdx_array) to dst (host or device) of `bytes`
+ * bytes; PDX_ERR_ARG if bytes differs from the array's size. Synchronous. */
+pdx_status pdx_index_copy_out(const pdx_index *index, pdx_array which, void *dst, size_t bytes);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PDX_H_ */

@@ -130,3 +130,22 @@ def recall_at_k(truth_idx, found_idx) -> float:
     for t, f in zip(truth_idx, found_idx):
         tot += len(set(t.tolist()) & set(int(v) for v in f if v >= 0))
     return tot / (k * truth_idx.shape[0])
+
+
+def pair_distances(x, q, ids, metric: str = "l2"):
+    """delta(x[ids[r, c]], q[r]) in FP64 (Sec. 2.1); nan where ids < 0."""
+    x = np.asarray(x, np.float32)
+    q = np.asarray(q, np.float32)
+    ids = np.asarray(ids, np.int64)
+    out = np.full(ids.shape, np.nan)
+    for r in range(ids.shape[0]):
+        sel = ids[r] >= 0
+        v = x[ids[r][sel]].astype(np.float64)
+        qq = q[r].astype(np.float64)
+        if metric == "l2":
+            out[r, sel] = ((v - qq) ** 2).sum(axis=1)
+        elif metric == "ip":
+            out[r, sel] = (v * qq).sum(axis=1)
+        else:
+            out[r, sel] = np.abs(v - qq).sum(axis=1)
+    return out

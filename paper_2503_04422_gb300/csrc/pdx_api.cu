@@ -1,0 +1,582 @@
+// C ABI of libpdx: argument checks, memory management and the host-side
+// sequence of kernel launches for each call. See include/pdx.h.
+#include <algorithm>
+#include <atomic>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <cmath>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "pdx_internal.cuh"
+
+namespace pdx {
+
+static thread_local std::string g_err;
+static std::atomic<unsigned long long> g_launches{0};
+
+void count_launches(int n) { g_launches.fetch_add((unsigned long long)n, std::memory_order_relaxed); }
+
+void set_error(const char *fmt, ...) {
+    char buf[1024];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_err = buf;
+}
+
+static pdx_status cuda_status(cudaError_t e, const char *what, int line) {
+    set_error("%s failed: %s (pdx_api.cu:%d)", what, cudaGetErrorString(e), line);
+    return e == cudaErrorMemoryAllocation ? PDX_ERR_OOM : PDX_ERR_CUDA;
+}
+
+#define PDX_TRY(call)                                                                                            \
+    do {                                                                                                         \
+        cudaError_t e_ = (call);                                                                                 \
+        if (e_ != cudaSuccess) return ::pdx::cuda_status(e_, #call, __LINE__);                                 \
+    } while (0)
+
+static bool is_device_ptr(const void *p) {
+    cudaPointerAttributes a;
+    cudaError_t e = cudaPointerGetAttributes(&a, p);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+static int num_sms() {
+    static thread_local int dev_cached = -1, sms = 0;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev != dev_cached) {
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        dev_cached = dev;
+    }
+    return sms > 0 ? sms : 1;
+}
+
+// Stream-ordered scratch: one cudaMallocAsync for all regions of a call,
+// released on the same stream when the call returns.
+struct Scratch {
+    cudaStream_t st;
+    void *base = nullptr;
+    size_t off = 0, cap = 0;
+    explicit Scratch(cudaStream_t s) : st(s) {}
+    ~Scratch() {
+        if (base) cudaFreeAsync(base, st);
+    }
+    cudaError_t reserve(size_t bytes) {
+        cap = bytes;
+        if (bytes == 0) return cudaSuccess;
+        return cudaMallocAsync(&base, bytes, st);
+    }
+    template <class T>
+    T *take(size_t count) {
+        size_t bytes = (count * sizeof(T) + 255) & ~size_t(255);
+        T *p = reinterpret_cast<T *>(static_cast<char *>(base) + off);
+        off += bytes;
+        return p;
+    }
+};
+static size_t rup(size_t b) { return (b + 255) & ~size_t(255); }
+
+static void free_index(pdx_index *ix) {
+    if (!ix) return;
+    void *ptrs[] = {ix->data, ix->ids, ix->slot_of, ix->blk_cnt, ix->part_blk, ix->means, ix->centroids, ix->centroid_norms,
+                    ix->assign, ix->rot, ix->shift, ix->pca_var, ix->resid};
+    for (void *p : ptrs)
+        if (p) cudaFree(p);
+    delete[] ix->h_part_blk;
+    delete ix;
+}
+
+template <class T>
+static cudaError_t dalloc(pdx_index *ix, T **p, size_t count) {
+    size_t bytes = count * sizeof(T);
+    if (bytes == 0) bytes = sizeof(T);
+    cudaError_t e = cudaMalloc(reinterpret_cast<void **>(p), bytes);
+    if (e == cudaSuccess) ix->bytes += bytes;
+    return e;
+}
+
+// Lays out `rows` (vector ids, grouped by part) as PDX blocks: part p holds
+// rows[part_row[p] .. part_row[p+1]) in that order, in ceil(len/64) blocks.
+static pdx_status layout_parts(pdx_index *ix, const float *x_dev, const std::vector<int32_t> &rows,
+                               const std::vector<int64_t> &part_row, cudaStream_t st) {
+    const int nparts = (int)part_row.size() - 1;
+    std::vector<int32_t> part_blk(nparts + 1, 0);
+    for (int p = 0; p < nparts; ++p) {
+        int64_t len = part_row[p + 1] - part_row[p];
+        part_blk[p + 1] = part_blk[p] + (int32_t)((len + kBlock - 1) / kBlock);
+    }
+    const int64_t nblocks = part_blk[nparts];
+    std::vector<int32_t> ids((size_t)nblocks * kBlock, -1), cnt((size_t)(nblocks > 0 ? nblocks : 1), 0);
+    std::vector<int32_t> slot_of((size_t)ix->n, -1);
+    for (int p = 0; p < nparts; ++p) {
+        for (int64_t r = part_row[p]; r < part_row[p + 1]; ++r) {
+            int64_t local = r - part_row[p];
+            int64_t b = part_blk[p] + local / kBlock;
+            ids[(size_t)b * kBlock + local % kBlock] = rows[(size_t)r];
+            slot_of[(size_t)rows[(size_t)r]] = (int32_t)(b * kBlock + local % kBlock);
+            cnt[(size_t)b] += 1;
+        }
+    }
+    ix->nparts = nparts;
+    ix->nblocks = nblocks;
+    ix->h_part_blk = new (std::nothrow) int32_t[nparts + 1];
+    if (!ix->h_part_blk) {
+        set_error("host allocation failed");
+        return PDX_ERR_OOM;
+    }
+    std::memcpy(ix->h_part_blk, part_blk.data(), sizeof(int32_t) * (nparts + 1));
+    PDX_TRY(dalloc(ix, &ix->data, (size_t)nblocks * ix->d * kBlock));
+    PDX_TRY(dalloc(ix, &ix->ids, (size_t)nblocks * kBlock));
+    PDX_TRY(dalloc(ix, &ix->slot_of, (size_t)ix->n));
+    PDX_TRY(dalloc(ix, &ix->blk_cnt, (size_t)nblocks));
+    PDX_TRY(dalloc(ix, &ix->part_blk, (size_t)nparts + 1));
+    PDX_TRY(dalloc(ix, &ix->means, (size_t)nparts * ix->d));
+    PDX_TRY(cudaMemcpyAsync(ix->ids, ids.data(), ids.size() * 4, cudaMemcpyHostToDevice, st));
+    PDX_TRY(cudaMemcpyAsync(ix->slot_of, slot_of.data(), slot_of.size() * 4, cudaMemcpyHostToDevice, st));
+    PDX_TRY(cudaMemcpyAsync(ix->blk_cnt, cnt.data(), (size_t)nblocks * 4, cudaMemcpyHostToDevice, st));
+    PDX_TRY(cudaMemcpyAsync(ix->part_blk, part_blk.data(), part_blk.size() * 4, cudaMemcpyHostToDevice, st));
+    PDX_TRY(launch_to_pdx(x_dev, ix->d, ix->ids, nblocks, ix->data, st));
+    PDX_TRY(launch_part_means(ix->data, ix->blk_cnt, ix->part_blk, nparts, ix->d, ix->means, st));
+    // host vectors above are pageable: the copies have completed once the stream drains
+    PDX_TRY(cudaStreamSynchronize(st));
+    return PDX_OK;
+}
+
+static bool valid_metric(int m) { return m == PDX_L2 || m == PDX_IP || m == PDX_L1; }
+
+}  // namespace pdx
+
+using namespace pdx;
+
+extern "C" {
+
+void pdx_default_build_opts(pdx_build_opts *o) {
+    if (!o) return;
+    std::memset(o, 0, sizeof *o);
+    o->struct_size = sizeof *o;
+    o->metric = PDX_L2;
+    o->storage = PDX_F32;
+    o->partition_size = 10000;
+    o->keep_fp32_rerank = 1;
+}
+
+void pdx_default_ivf_opts(pdx_ivf_opts *o) {
+    if (!o) return;
+    std::memset(o, 0, sizeof *o);
+    o->struct_size = sizeof *o;
+    pdx_default_build_opts(&o->base);
+    o->nlist = 1024;
+    o->kmeans_iters = 10;
+    o->kmeans_sample = 0;
+    o->seed = 2503;
+    o->transform = PDX_PRUNE_NONE;
+}
+
+void pdx_default_search_opts(pdx_search_opts *o) {
+    if (!o) return;
+    std::memset(o, 0, sizeof *o);
+    o->struct_size = sizeof *o;
+    o->pruner = PDX_PRUNE_BOND;
+    o->order = PDX_ORDER_DIST_TO_MEANS;
+    o->zone_dims = 8;
+    o->selection_threshold = 0.20f;
+    o->eps0 = 2.1f;
+    o->bsa_m = 4.0f;
+    o->first_step = 2;
+    o->start_vectors = 4096;
+    o->blocks_per_item = 0;
+    o->stats_out = nullptr;
+}
+
+const char *pdx_last_error(void) { return g_err.c_str(); }
+
+uint64_t pdx_kernel_launches(void) { return g_launches.load(std::memory_order_relaxed); }
+
+void pdx_free(pdx_index *index) { free_index(index); }
+
+pdx_status pdx_index_info_get(const pdx_index *ix, pdx_index_info *info) {
+    if (!ix || !info) {
+        set_error("pdx_index_info_get: NULL argument");
+        return PDX_ERR_ARG;
+    }
+    info->n = ix->n;
+    info->d = ix->d;
+    info->nparts = ix->nparts;
+    info->nblocks = ix->nblocks;
+    info->metric = ix->metric;
+    info->storage = ix->storage;
+    info->is_ivf = ix->is_ivf;
+    info->unit_norm = ix->unit_norm;
+    info->device_bytes = ix->bytes;
+    return PDX_OK;
+}
+
+pdx_status pdx_index_copy_out(const pdx_index *ix, pdx_array which, void *dst, size_t bytes) {
+    if (!ix || !dst) {
+        set_error("pdx_index_copy_out: NULL argument");
+        return PDX_ERR_ARG;
+    }
+    const void *src = nullptr;
+    size_t need = 0;
+    switch (which) {
+    case PDX_ARRAY_BLOCKS: src = ix->data; need = (size_t)ix->nblocks * ix->d * kBlock * 4; break;
+    case PDX_ARRAY_IDS: src = ix->ids; need = (size_t)ix->nblocks * kBlock * 4; break;
+    case PDX_ARRAY_PART_BLOCKS: src = ix->part_blk; need = ((size_t)ix->nparts + 1) * 4; break;
+    case PDX_ARRAY_MEANS: src = ix->means; need = (size_t)ix->nparts * ix->d * 4; break;
+    case PDX_ARRAY_CENTROIDS: src = ix->centroids; need = (size_t)ix->nparts * ix->d * 4; break;
+    case PDX_ARRAY_ASSIGN: src = ix->assign; need = (size_t)ix->n * 4; break;
+    default: set_error("pdx_index_copy_out: unknown array %d", (int)which); return PDX_ERR_ARG;
+    }
+    if (!src) {
+        set_error("pdx_index_copy_out: array %d not present in this index", (int)which);
+        return PDX_ERR_ARG;
+    }
+    if (bytes != need) {
+        set_error("pdx_index_copy_out: array %d has %zu bytes, got %zu", (int)which, need, bytes);
+        return PDX_ERR_ARG;
+    }
+    PDX_TRY(cudaMemcpy(dst, src, need, cudaMemcpyDefault));
+    return PDX_OK;
+}
+
+pdx_status pdx_build_layout(const float *x, int64_t n, int32_t d, const pdx_build_opts *opts, void *stream,
+                            pdx_index **out) {
+    if (out) *out = nullptr;
+    if (!x || !out) {
+        set_error("pdx_build_layout: NULL x or out");
+        return PDX_ERR_ARG;
+    }
+    if (n < 1 || n >= (int64_t)1 << 31 || d < 1 || d > kMaxD) {
+        set_error("pdx_build_layout: n=%lld d=%d out of range", (long long)n, d);
+        return PDX_ERR_ARG;
+    }
+    pdx_build_opts o;
+    pdx_default_build_opts(&o);
+    if (opts) {
+        if (opts->struct_size < sizeof(pdx_build_opts)) {
+            set_error("pdx_build_layout: opts->struct_size %u < %zu", opts->struct_size, sizeof(pdx_build_opts));
+            return PDX_ERR_ARG;
+        }
+        o = *opts;
+    }
+    if (!valid_metric(o.metric) || (o.storage != PDX_F32 && o.storage != PDX_BF16 && o.storage != PDX_FP8_E4M3)) {
+        set_error("pdx_build_layout: bad metric %d or storage %d", (int)o.metric, (int)o.storage);
+        return PDX_ERR_ARG;
+    }
+    if (o.storage != PDX_F32) {
+        set_error("pdx_build_layout: only F32 storage is implemented");
+        return PDX_ERR_UNSUPPORTED;
+    }
+    if (o.partition_size == 0) o.partition_size = 10000;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    pdx_index *ix = new (std::nothrow) pdx_index();
+    if (!ix) {
+        set_error("host allocation failed");
+        return PDX_ERR_OOM;
+    }
+    ix->n = n;
+    ix->d = d;
+    ix->metric = o.metric;
+    ix->storage = o.storage;
+    cudaGetDevice(&ix->device);
+    pdx_status s = PDX_OK;
+    {
+        Scratch scr(st);
+        const float *xd = x;
+        if (!is_device_ptr(x)) {
+            cudaError_t e = scr.reserve(rup((size_t)n * d * 4));
+            if (e != cudaSuccess) { free_index(ix); return cuda_status(e, "cudaMallocAsync", __LINE__); }
+            float *tmp = scr.take<float>((size_t)n * d);
+            e = cudaMemcpyAsync(tmp, x, (size_t)n * d * 4, cudaMemcpyHostToDevice, st);
+            if (e != cudaSuccess) { free_index(ix); return cuda_status(e, "cudaMemcpyAsync", __LINE__); }
+            xd = tmp;
+        }
+        // Sec. 6.6: equal horizontal partitions of at most partition_size vectors
+        const int64_t nparts = (n + o.partition_size - 1) / o.partition_size;
+        const int64_t size = (n + nparts - 1) / nparts;
+        std::vector<int64_t> part_row((size_t)nparts + 1);
+        for (int64_t p = 0; p <= nparts; ++p) part_row[(size_t)p] = std::min<int64_t>(n, p * size);
+        std::vector<int32_t> rows((size_t)n);
+        for (int64_t i = 0; i < n; ++i) rows[(size_t)i] = (int32_t)i;
+        s = layout_parts(ix, xd, rows, part_row, st);
+        if (s == PDX_OK && o.metric == PDX_IP) {
+            int *flag = nullptr;
+            cudaError_t e = cudaMalloc(&flag, sizeof(int));
+            int one = 1;
+            if (e == cudaSuccess) e = cudaMemcpy(flag, &one, sizeof one, cudaMemcpyHostToDevice);
+            if (e == cudaSuccess) e = launch_unit_norm_check(xd, n, d, 1e-5f, flag, st);
+            if (e == cudaSuccess) e = cudaMemcpyAsync(&one, flag, sizeof one, cudaMemcpyDeviceToHost, st);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+            if (flag) cudaFree(flag);
+            if (e != cudaSuccess) s = cuda_status(e, "unit norm check", __LINE__);
+            ix->unit_norm = one;
+        }
+        if (s == PDX_OK) {
+            cudaError_t e = cudaStreamSynchronize(st);
+            if (e != cudaSuccess) s = cuda_status(e, "cudaStreamSynchronize", __LINE__);
+        }
+    }
+    if (s != PDX_OK) {
+        free_index(ix);
+        return s;
+    }
+    *out = ix;
+    return PDX_OK;
+}
+
+}  // extern "C"
+
+namespace pdx {
+
+struct SearchPlan {
+    int pruner;
+    int metric;      // metric the scan computes (IP on unit vectors is searched as L2)
+    int out_mode;    // 0: distance as ranked; 1: IP = -ranked value
+};
+
+static pdx_status check_search_args(const pdx_index *ix, const float *q, int64_t nq, int32_t k,
+                                    const pdx_search_opts *opts, float *out_dist, int64_t *out_idx,
+                                    pdx_search_opts *o, const char *fn) {
+    if (!ix || (nq > 0 && (!q || !out_dist || !out_idx))) {
+        set_error("%s: NULL argument", fn);
+        return PDX_ERR_ARG;
+    }
+    if (nq < 0 || nq >= (int64_t)1 << 31 || k < 1 || k > kMaxK) {
+        set_error("%s: nq=%lld k=%d out of range", fn, (long long)nq, k);
+        return PDX_ERR_ARG;
+    }
+    pdx_default_search_opts(o);
+    if (opts) {
+        if (opts->struct_size < sizeof(pdx_search_opts)) {
+            set_error("%s: opts->struct_size %u < %zu", fn, opts->struct_size, sizeof(pdx_search_opts));
+            return PDX_ERR_ARG;
+        }
+        *o = *opts;
+    }
+    if (o->pruner < PDX_PRUNE_NONE || o->pruner > PDX_PRUNE_BSA || o->order < PDX_ORDER_DIST_TO_MEANS ||
+        o->order > PDX_ORDER_SEQUENTIAL) {
+        set_error("%s: bad pruner %d or order %d", fn, (int)o->pruner, (int)o->order);
+        return PDX_ERR_ARG;
+    }
+    if (!(o->selection_threshold >= 0.f && o->selection_threshold <= 0.25f) || o->first_step < 1 ||
+        o->zone_dims < 1 || !(o->eps0 >= 0.f) || !(o->bsa_m >= 0.f)) {
+        set_error("%s: selection_threshold must be in [0, 0.25], first_step/zone_dims >= 1, eps0/bsa_m >= 0", fn);
+        return PDX_ERR_ARG;
+    }
+    return PDX_OK;
+}
+
+static pdx_status plan_metric(const pdx_index *ix, int pruner, SearchPlan *pl, const char *fn) {
+    pl->pruner = pruner;
+    pl->metric = ix->metric;
+    pl->out_mode = 0;
+    if (ix->metric == PDX_IP) {
+        if (pruner == PDX_PRUNE_NONE) {
+            pl->out_mode = 1;
+        } else if (ix->unit_norm) {
+            // unit-norm vectors: ||q - x||^2 = ||q||^2 + 1 - 2 q.x ranks like -q.x
+            pl->metric = PDX_L2;
+            pl->out_mode = 1;   // the refine step recomputes the inner product itself
+        } else {
+            set_error("%s: pruned inner-product search needs a unit-norm index", fn);
+            return PDX_ERR_UNSUPPORTED;
+        }
+    }
+    if (pl->metric == PDX_L1 && pruner > PDX_PRUNE_BOND) {
+        set_error("%s: ADSampling/BSA are defined for L2 only", fn);
+        return PDX_ERR_UNSUPPORTED;
+    }
+    return PDX_OK;
+}
+
+// Shared tail of both searches: scan items, merge the per-item lists, write
+// the outputs (to host through a staging buffer when needed).
+struct SearchIO {
+    const float *q_dev;
+    float *out_dist_dev;
+    int64_t *out_idx_dev;
+};
+
+}  // namespace pdx
+
+extern "C" pdx_status pdx_search_exact(const pdx_index *ix, const float *q, int64_t nq, int32_t k,
+                                       const pdx_search_opts *opts, float *out_dist, int64_t *out_idx,
+                                       void *stream) {
+    pdx_search_opts o;
+    pdx_status s = check_search_args(ix, q, nq, k, opts, out_dist, out_idx, &o, "pdx_search_exact");
+    if (s != PDX_OK) return s;
+    if (ix->is_ivf) {
+        set_error("pdx_search_exact: index was built by pdx_ivf_build");
+        return PDX_ERR_ARG;
+    }
+    if (o.pruner != PDX_PRUNE_NONE && o.pruner != PDX_PRUNE_BOND) {
+        set_error("pdx_search_exact: only NONE or BOND keep the search exact");
+        return PDX_ERR_ARG;
+    }
+    if (q && (q == out_dist || (const void *)q == (const void *)out_idx)) {
+        set_error("pdx_search_exact: outputs alias the queries");
+        return PDX_ERR_ARG;
+    }
+    SearchPlan pl;
+    s = plan_metric(ix, o.pruner, &pl, "pdx_search_exact");
+    if (s != PDX_OK) return s;
+    if (nq == 0) return PDX_OK;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const int d = ix->d;
+    const bool q_dev = is_device_ptr(q);
+    const bool o_dev = is_device_ptr(out_dist) && is_device_ptr(out_idx);
+    if (is_device_ptr(out_dist) != is_device_ptr(out_idx)) {
+        set_error("pdx_search_exact: out_dist and out_idx must both be host or both be device memory");
+        return PDX_ERR_ARG;
+    }
+    const int sms = num_sms();
+
+    // work items: (query, partition, block group); split partitions when
+    // there are too few (query, partition) pairs to fill the GPU
+    int max_blk = 0;
+    for (int p = 0; p < ix->nparts; ++p) max_blk = std::max(max_blk, ix->h_part_blk[p + 1] - ix->h_part_blk[p]);
+    int bpi = (int)o.blocks_per_item;
+    if (bpi <= 0) {
+        const int64_t target = (int64_t)sms * 64 * 3;
+        int64_t pairs = nq * (int64_t)ix->nparts;
+        int chunks = (int)std::min<int64_t>(max_blk, std::max<int64_t>(1, (target + pairs - 1) / pairs));
+        bpi = (max_blk + chunks - 1) / chunks;
+    }
+    if (bpi < 1) bpi = 1;
+    const int chunks = (max_blk + bpi - 1) / bpi;
+    const int nslots = ix->nparts * chunks;
+
+    const bool start = (pl.pruner != PDX_PRUNE_NONE);
+    int start_blk = 0;
+    if (start) {
+        int64_t sv = std::max<int64_t>(o.start_vectors, k);
+        start_blk = (int)std::min<int64_t>(ix->nblocks, (sv + kBlock - 1) / kBlock);
+    }
+    const int64_t Lstart = (int64_t)start_blk * kBlock;
+
+    Scratch scr(st);
+    size_t need = 0;
+    if (!q_dev) need += rup((size_t)nq * d * 4);
+    need += rup((size_t)nq * 4);                         // tau
+    need += rup((size_t)nq * nslots * k * 8);            // per-item lists
+    need += rup((size_t)nq * k * 8) * 3;                 // merged, refined, final top-k
+    if (start) need += rup((size_t)nq * Lstart * 8) + rup((size_t)nq * k * 8);
+    need += rup(C_COUNT * 8) + rup(8);
+    if (!o_dev) need += rup((size_t)nq * k * 4) + rup((size_t)nq * k * 8);
+    PDX_TRY(scr.reserve(need));
+    const float *qd = q;
+    if (!q_dev) {
+        float *t = scr.take<float>((size_t)nq * d);
+        PDX_TRY(cudaMemcpyAsync(t, q, (size_t)nq * d * 4, cudaMemcpyHostToDevice, st));
+        qd = t;
+    }
+    float *tau = scr.take<float>((size_t)nq);
+    uint64_t *cand = scr.take<uint64_t>((size_t)nq * nslots * k);
+    uint64_t *topk = scr.take<uint64_t>((size_t)nq * k);
+    uint64_t *refined = scr.take<uint64_t>((size_t)nq * k);
+    uint64_t *final_keys = scr.take<uint64_t>((size_t)nq * k);
+    uint64_t *skeys = start ? scr.take<uint64_t>((size_t)nq * Lstart) : nullptr;
+    uint64_t *stopk = start ? scr.take<uint64_t>((size_t)nq * k) : nullptr;
+    unsigned long long *counters = scr.take<unsigned long long>(C_COUNT);
+    int *work = scr.take<int>(2);
+    float *od = out_dist;
+    int64_t *oi = out_idx;
+    if (!o_dev) {
+        od = scr.take<float>((size_t)nq * k);
+        oi = scr.take<int64_t>((size_t)nq * k);
+    }
+    PDX_TRY(launch_fill_u32(reinterpret_cast<uint32_t *>(tau), 0xff800000u, nq, st));  // ordered +inf
+    PDX_TRY(cudaMemsetAsync(counters, 0, C_COUNT * 8, st));
+    PDX_TRY(cudaMemsetAsync(work, 0, 8, st));
+    // kernels accumulate into the caller's device stats when given, else into scratch
+    unsigned long long *kc = o.stats_device ? reinterpret_cast<unsigned long long *>(o.stats_device) : counters;
+    if (start) {
+        // START (Sec. 4): exact distances of the first start_vectors stored
+        // vectors give every query an initial k-th-best threshold
+        PDX_TRY(launch_dense_keys(qd, nq, ix->data, ix->ids, d, start_blk, pl.metric, skeys, st));
+        PDX_TRY(launch_select_k(skeys, nq, Lstart, k, stopk, st));
+        PDX_TRY(launch_tau_from_keys(stopk, nq, k, tau, st));
+        PDX_TRY(launch_add_u64(kc + C_START, (unsigned long long)nq * Lstart * d, st));
+    }
+    ScanParams p;
+    std::memset(&p, 0, sizeof p);
+    p.data = ix->data;
+    p.ids = ix->ids;
+    p.blk_cnt = ix->blk_cnt;
+    p.part_blk = ix->part_blk;
+    p.d = d;
+    p.q = qd;
+    p.nq = nq;
+    p.means = ix->means;
+    p.probes = nullptr;
+    p.nslots = nslots;
+    p.part0 = 0;
+    p.chunks_per_part = chunks;
+    p.blocks_per_item = bpi;
+    p.k = k;
+    p.tau = tau;
+    p.cand = cand;
+    p.counters = kc;
+    p.work_counter = work;
+    p.nitems = nq * (int64_t)nslots;
+    p.first_step = (int)o.first_step;
+    p.sel_count = std::min(kMaxSurv, (int)std::ceil(o.selection_threshold * kBlock) - 1);
+    if (p.sel_count < 0) p.sel_count = 0;
+    p.zone_dims = (int)o.zone_dims;
+    p.order = (int)o.order;
+    p.gamma = (float)d * 1.1920929e-7f;  // D * 2^-23
+    p.eps0 = o.eps0;
+    p.bsa_m = o.bsa_m;
+    if (o.scan_event_start) PDX_TRY(cudaEventRecord(static_cast<cudaEvent_t>(o.scan_event_start), st));
+    PDX_TRY(launch_scan(pl.pruner, pl.metric, p, sms, st));
+    if (o.scan_event_stop) PDX_TRY(cudaEventRecord(static_cast<cudaEvent_t>(o.scan_event_stop), st));
+    PDX_TRY(launch_select_k(cand, nq, (int64_t)nslots * k, k, topk, st));
+    PDX_TRY(launch_refine(topk, nq, k, qd, d, ix->data, ix->slot_of, ix->metric, refined, st));
+    PDX_TRY(launch_select_k(refined, nq, k, k, final_keys, st));
+    PDX_TRY(launch_write_out(final_keys, nq, k, pl.out_mode, qd, d, od, oi, st));
+    if (!o_dev) {
+        PDX_TRY(cudaMemcpyAsync(out_dist, od, (size_t)nq * k * 4, cudaMemcpyDeviceToHost, st));
+        PDX_TRY(cudaMemcpyAsync(out_idx, oi, (size_t)nq * k * 8, cudaMemcpyDeviceToHost, st));
+    }
+    if (o.stats_out) {
+        unsigned long long c[C_COUNT];
+        PDX_TRY(cudaMemcpyAsync(c, kc, sizeof c, cudaMemcpyDeviceToHost, st));
+        PDX_TRY(cudaStreamSynchronize(st));
+        pdx_search_stats *so = o.stats_out;
+        std::memset(so, 0, sizeof *so);
+        so->values_visited = c[C_VALUES];
+        so->vectors_scanned = c[C_SCANNED];
+        so->vectors_pruned = c[C_PRUNED];
+        so->prune_phase_blocks = c[C_PRUNE_BLOCKS];
+        so->candidates = c[C_CANDIDATES];
+        so->work_items = c[C_ITEMS];
+        so->start_values = c[C_START];
+        so->bytes_logical = (c[C_VALUES] + c[C_START]) * 4ull;
+    }
+    if (!o_dev) PDX_TRY(cudaStreamSynchronize(st));
+    return PDX_OK;
+}
+
+extern "C" pdx_status pdx_ivf_build(const float *x, int64_t n, int32_t d, const pdx_ivf_opts *opts, void *stream,
+                                    pdx_index **out) {
+    (void)x; (void)n; (void)d; (void)opts; (void)stream;
+    if (out) *out = nullptr;
+    set_error("pdx_ivf_build: not implemented in this build");
+    return PDX_ERR_UNSUPPORTED;
+}
+
+extern "C" pdx_status pdx_search_ivf(const pdx_index *ix, const float *q, int64_t nq, int32_t k, int32_t nprobe,
+                                     const pdx_search_opts *opts, float *out_dist, int64_t *out_idx, void *stream) {
+    (void)ix; (void)q; (void)nq; (void)k; (void)nprobe; (void)opts; (void)out_dist; (void)out_idx; (void)stream;
+    set_error("pdx_search_ivf: not implemented in this build");
+    return PDX_ERR_UNSUPPORTED;
+}

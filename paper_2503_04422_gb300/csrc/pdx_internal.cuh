@@ -1,0 +1,177 @@
+// Internal declarations shared by the CUDA translation units of libpdx.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "pdx.h"
+
+namespace pdx {
+
+// Sec. 3: vectors are grouped in blocks of 64 and stored dimension-major inside
+// a block; 64 is the paper's best block size (Table 4) and also two warps'
+// worth of 32-bit lanes, so one warp covers a block with one float4 per lane
+// per pair of dimensions.
+constexpr int kBlock = 64;
+constexpr int kMaxSurv = 16;   // PRUNE-phase survivors held in registers (selection <= 25%)
+constexpr int kMaxK = 1024;
+constexpr int kMaxD = 4096;
+
+// Device counters, in the order of the first fields of pdx_search_stats.
+enum Counter {
+    C_VALUES = 0, C_SCANNED, C_PRUNED, C_PRUNE_BLOCKS, C_CANDIDATES, C_ITEMS, C_START, C_COUNT
+};
+
+// Kernels launched through the library (host-side count).
+void count_launches(int n);
+inline cudaError_t counted(cudaError_t e) {
+    if (e == cudaSuccess) count_launches(1);
+    return e;
+}
+
+}  // namespace pdx
+
+// Opaque handle of the C ABI.
+struct pdx_index {
+    int64_t n = 0;
+    int32_t d = 0;
+    pdx_metric metric = PDX_L2;
+    pdx_dtype storage = PDX_F32;
+    int32_t is_ivf = 0;
+    int32_t unit_norm = 0;
+    int32_t nparts = 0;
+    int64_t nblocks = 0;
+    int device = 0;
+    pdx_pruner transform = PDX_PRUNE_NONE;  // IVF: ADSAMPLING rotation / BSA projection
+    // device arrays
+    float *data = nullptr;          // [nblocks][d][64]
+    int32_t *ids = nullptr;         // [nblocks*64]
+    int32_t *slot_of = nullptr;     // [n] storage slot (block*64 + lane) of each vector id
+    int32_t *blk_cnt = nullptr;     // [nblocks] valid lanes per block
+    int32_t *part_blk = nullptr;    // [nparts+1]
+    float *means = nullptr;         // [nparts][d]
+    float *centroids = nullptr;     // [nparts][d] (IVF)
+    float *centroid_norms = nullptr;// [nparts]
+    int32_t *assign = nullptr;      // [n] (IVF)
+    float *rot = nullptr;           // [d][d] query transform (row-major, q' = rot * (q - shift))
+    float *shift = nullptr;         // [d] (BSA: data mean)
+    float *pca_var = nullptr;       // [d] (BSA: variance of each projected dimension)
+    float *resid = nullptr;         // BSA: [nblocks][nchk][64] squared residual norms
+    int32_t bsa_nchk = 0;           // BSA: number of check points stored
+    int32_t bsa_first_step = 2;     // BSA: schedule the residual norms were taken for
+    // host mirrors
+    int32_t *h_part_blk = nullptr;  // [nparts+1]
+    uint64_t bytes = 0;
+};
+
+namespace pdx {
+
+void set_error(const char *fmt, ...);
+
+// ---- device helpers ----
+#ifdef __CUDACC__
+// Monotone map float -> uint32 (total order equal to the float order for
+// non-NaN values), so (distance, id) pairs sort as one uint64 key.
+__device__ __forceinline__ uint32_t f2o(float f) {
+    uint32_t u = __float_as_uint(f);
+    return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+__device__ __forceinline__ float o2f(uint32_t o) {
+    uint32_t u = (o & 0x80000000u) ? (o & 0x7fffffffu) : ~o;
+    return __uint_as_float(u);
+}
+__device__ __forceinline__ uint64_t make_key(float dist, int32_t id) {
+    return ((uint64_t)f2o(dist) << 32) | (uint32_t)id;
+}
+__device__ __forceinline__ float key_dist(uint64_t key) { return o2f((uint32_t)(key >> 32)); }
+__device__ __forceinline__ int32_t key_id(uint64_t key) { return (int32_t)(uint32_t)(key & 0xffffffffu); }
+#endif
+
+constexpr uint64_t kEmptyKey = ~0ull;
+
+// ---- launchers (each returns the launch's cudaError_t) ----
+cudaError_t launch_to_pdx(const float *x, int32_t d, const int32_t *ids, int64_t nblocks,
+                          float *data, cudaStream_t st);
+cudaError_t launch_part_means(const float *data, const int32_t *blk_cnt, const int32_t *part_blk,
+                              int32_t nparts, int32_t d, float *means, cudaStream_t st);
+cudaError_t launch_unit_norm_check(const float *x, int64_t n, int32_t d, float tol, int *flag,
+                                   cudaStream_t st);
+cudaError_t launch_fill_u32(uint32_t *p, uint32_t v, int64_t n, cudaStream_t st);
+cudaError_t launch_fill_u64(uint64_t *p, uint64_t v, int64_t n, cudaStream_t st);
+cudaError_t launch_add_u64(unsigned long long *p, unsigned long long v, cudaStream_t st);
+
+struct ScanParams {
+    const float *data;
+    const int32_t *ids;
+    const int32_t *blk_cnt;
+    const int32_t *part_blk;
+    int32_t d;
+    const float *q;            // [nq][d] (transformed for ADS/BSA)
+    int64_t nq;
+    const float *means;        // [nparts][d] (BOND order)
+    const int32_t *probes;     // [nq][nslots] part per slot, or null (slot -> part0 + slot/chunks)
+    int32_t nslots;            // items per query
+    int32_t part0;
+    int32_t chunks_per_part;   // exact search: block groups per partition
+    int32_t blocks_per_item;
+    int32_t k;
+    float *tau;                // [nq]
+    uint64_t *cand;            // [nq][nslots][k]
+    unsigned long long *counters;
+    int *work_counter;
+    int64_t nitems;
+    int32_t first_step;
+    int32_t sel_count;         // PRUNE when survivors <= sel_count
+    int32_t zone_dims;
+    int32_t order;
+    float gamma;               // relative slack covering FP32 rounding of partial sums
+    float eps0;
+    float bsa_m;
+    const float *qaux;         // BSA: [nq][nchk][2] (||q_r||^2, s_d(q)^2) per check point
+    const float *resid;        // BSA: [nblocks][nchk][64]
+    int32_t nchk;
+};
+cudaError_t launch_scan(int pruner, int metric, const ScanParams &p, int num_sms, cudaStream_t st);
+size_t scan_warp_smem(int d, int k, int zone_dims, int order);
+
+// START: exact distances of every query to the first `nvec` stored vectors,
+// as (distance, id) keys [nq][nvec_pad].
+cudaError_t launch_dense_keys(const float *q, int64_t nq, const float *data, const int32_t *ids,
+                              int32_t d, int32_t nblk, int metric, uint64_t *keys, cudaStream_t st);
+// Per-row k smallest keys of a [rows][L] array (sorted ascending) -> out [rows][k].
+cudaError_t launch_select_k(const uint64_t *keys, int64_t rows, int64_t L, int32_t k, uint64_t *out,
+                            cudaStream_t st);
+// tau[row] = distance of the k-th key of each row (or +inf).
+cudaError_t launch_tau_from_keys(const uint64_t *topk, int64_t rows, int32_t k, float *tau, cudaStream_t st);
+// Canonical distances of the selected results: recomputed in the natural
+// dimension order with a fixed reduction, in the index's metric, as keys.
+cudaError_t launch_refine(const uint64_t *topk, int64_t nq, int32_t k, const float *q, int32_t d,
+                          const float *data, const int32_t *slot_of, int metric, uint64_t *out, cudaStream_t st);
+// keys -> (float distance, int64 id) outputs. mode 0: dist as is; 1: IP = -dist;
+// 2: IP from L2 on unit vectors: (||q||^2 + 1 - L2) / 2.
+cudaError_t launch_write_out(const uint64_t *topk, int64_t nq, int32_t k, int mode, const float *q,
+                             int32_t d, float *out_dist, int64_t *out_idx, cudaStream_t st);
+
+// IVF
+cudaError_t launch_nearest_centroids(const float *x, int64_t n, int32_t d, const float *centroids,
+                                     const float *cnorm, int32_t nlist, int32_t *assign, float *best,
+                                     cudaStream_t st);
+cudaError_t launch_centroid_norms(const float *c, int32_t nlist, int32_t d, float *out, cudaStream_t st);
+cudaError_t launch_kmeans_update(const float *x, int64_t n, int32_t d, const int32_t *assign,
+                                 int32_t nlist, float *sums, int32_t *counts, float *centroids,
+                                 cudaStream_t st);
+cudaError_t launch_probe_keys(const float *q, int64_t nq, int32_t d, const float *centroids,
+                              int32_t nlist, uint64_t *keys, cudaStream_t st);
+cudaError_t launch_keys_to_parts(const uint64_t *topk, int64_t nq, int32_t nprobe, int32_t *probes,
+                                 cudaStream_t st);
+// y[rows][d] = (x[rows][d] - shift) * M^T   (M row-major d x d), FP32.
+cudaError_t launch_transform(const float *x, int64_t rows, int32_t d, const float *M, const float *shift,
+                             float *y, cudaStream_t st);
+cudaError_t launch_column_stats(const float *x, int64_t n, int32_t d, double *sum, double *cov,
+                                cudaStream_t st);
+cudaError_t launch_bsa_resid(const float *data, const int32_t *blk_cnt, int64_t nblocks, int32_t d,
+                             const int32_t *chk, int32_t nchk, float *resid, cudaStream_t st);
+cudaError_t launch_bsa_qaux(const float *q, int64_t nq, int32_t d, const float *var, const int32_t *chk,
+                            int32_t nchk, float *qaux, cudaStream_t st);
+
+}  // namespace pdx

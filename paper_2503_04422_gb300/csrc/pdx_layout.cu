@@ -1,0 +1,124 @@
+// Layout build (Sec. 3): N-ary rows -> PDX blocks, and block metadata.
+#include "pdx_internal.cuh"
+
+namespace pdx {
+
+// One CTA transposes a 64-vector x 32-dimension tile through shared memory:
+// rows are read 128 B at a time along dimensions (coalesced), and written
+// 256 B at a time along vectors (coalesced), which is the PDX order
+// data[(b*D + j)*64 + t]. Padding slots (id -1) are written as zeros.
+__global__ void __launch_bounds__(256) to_pdx_kernel(const float *__restrict__ x, int32_t d,
+                                                     const int32_t *__restrict__ ids,
+                                                     float *__restrict__ data) {
+    __shared__ float tile[kBlock][33];
+    const int64_t b = blockIdx.x;
+    const int j0 = blockIdx.y * 32;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int r = warp; r < kBlock; r += 8) {
+        int32_t id = ids[b * kBlock + r];
+        int j = j0 + lane;
+        float v = 0.f;
+        if (id >= 0 && j < d) v = x[(int64_t)id * d + j];
+        tile[r][lane] = v;
+    }
+    __syncthreads();
+    for (int jj = warp; jj < 32; jj += 8) {
+        int j = j0 + jj;
+        if (j >= d) break;
+        float *dst = data + ((b * d + j) * kBlock);
+        dst[lane] = tile[lane][jj];
+        dst[lane + 32] = tile[lane + 32][jj];
+    }
+}
+
+cudaError_t launch_to_pdx(const float *x, int32_t d, const int32_t *ids, int64_t nblocks, float *data,
+                          cudaStream_t st) {
+    if (nblocks == 0) return cudaSuccess;
+    dim3 grid((unsigned)nblocks, (unsigned)((d + 31) / 32));
+    to_pdx_kernel<<<grid, 256, 0, st>>>(x, d, ids, data);
+    return counted(cudaGetLastError());
+}
+
+// means[p][j] = average of dimension j over the valid vectors of part p
+// (block metadata, Sec. 3; used by PDX-BOND's distance-to-means order, Sec. 5).
+// One warp per (part, dimension): lanes cover the 64 slots of each block.
+__global__ void part_means_kernel(const float *__restrict__ data, const int32_t *__restrict__ blk_cnt,
+                                  const int32_t *__restrict__ part_blk, int32_t nparts, int32_t d,
+                                  float *__restrict__ means) {
+    const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (gw >= (int64_t)nparts * d) return;
+    const int p = (int)(gw / d), j = (int)(gw % d);
+    float s = 0.f;
+    int64_t cnt = 0;
+    for (int b = part_blk[p]; b < part_blk[p + 1]; ++b) {
+        const float *row = data + ((int64_t)b * d + j) * kBlock;
+        int c = blk_cnt[b];
+        if (lane < c) s += row[lane];
+        if (lane + 32 < c) s += row[lane + 32];
+        cnt += c;
+    }
+    for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) means[(int64_t)p * d + j] = cnt ? s / (float)cnt : 0.f;
+}
+
+cudaError_t launch_part_means(const float *data, const int32_t *blk_cnt, const int32_t *part_blk,
+                              int32_t nparts, int32_t d, float *means, cudaStream_t st) {
+    int64_t warps = (int64_t)nparts * d;
+    if (warps == 0) return cudaSuccess;
+    part_means_kernel<<<(unsigned)((warps * 32 + 255) / 256), 256, 0, st>>>(data, blk_cnt, part_blk, nparts,
+                                                                            d, means);
+    return counted(cudaGetLastError());
+}
+
+// flag is cleared when some row's squared norm differs from 1 by more than tol.
+__global__ void unit_norm_kernel(const float *__restrict__ x, int64_t n, int32_t d, float tol, int *flag) {
+    const int64_t row = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (row >= n) return;
+    float s = 0.f;
+    for (int j = lane; j < d; j += 32) {
+        float v = x[row * d + j];
+        s = fmaf(v, v, s);
+    }
+    for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0 && fabsf(s - 1.f) > tol) atomicExch(flag, 0);
+}
+
+cudaError_t launch_unit_norm_check(const float *x, int64_t n, int32_t d, float tol, int *flag,
+                                   cudaStream_t st) {
+    if (n == 0) return cudaSuccess;
+    unit_norm_kernel<<<(unsigned)((n * 32 + 255) / 256), 256, 0, st>>>(x, n, d, tol, flag);
+    return counted(cudaGetLastError());
+}
+
+__global__ void fill_u32_kernel(uint32_t *p, uint32_t v, int64_t n) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        p[i] = v;
+}
+__global__ void fill_u64_kernel(uint64_t *p, uint64_t v, int64_t n) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        p[i] = v;
+}
+
+cudaError_t launch_fill_u32(uint32_t *p, uint32_t v, int64_t n, cudaStream_t st) {
+    if (n <= 0) return cudaSuccess;
+    int64_t blocks = (n + 255) / 256;
+    fill_u32_kernel<<<(unsigned)(blocks < 4096 ? blocks : 4096), 256, 0, st>>>(p, v, n);
+    return counted(cudaGetLastError());
+}
+cudaError_t launch_fill_u64(uint64_t *p, uint64_t v, int64_t n, cudaStream_t st) {
+    if (n <= 0) return cudaSuccess;
+    int64_t blocks = (n + 255) / 256;
+    fill_u64_kernel<<<(unsigned)(blocks < 4096 ? blocks : 4096), 256, 0, st>>>(p, v, n);
+    return counted(cudaGetLastError());
+}
+
+__global__ void add_u64_kernel(unsigned long long *p, unsigned long long v) { atomicAdd(p, v); }
+
+cudaError_t launch_add_u64(unsigned long long *p, unsigned long long v, cudaStream_t st) {
+    add_u64_kernel<<<1, 1, 0, st>>>(p, v);
+    return counted(cudaGetLastError());
+}
+
+}  // namespace pdx

@@ -1,0 +1,759 @@
+// PDXearch on the GPU (Sec. 4) with the PDX-BOND (Sec. 5), ADSampling and
+// BSA (Sec. 2.3) predicates, over PDX blocks (Sec. 3, Listing 1).
+//
+// Work decomposition. A work item is (query, PDXearch block): a partition of
+// the exact index or a probed IVF bucket (optionally a contiguous group of its
+// 64-vector storage blocks). One warp runs one item at a time and pulls the
+// next from a global counter; items are numbered block-major, so the warps in
+// flight at any moment read the same few partitions for many queries and the
+// partition stays in L2 while they do. Inside an item the warp follows the
+// paper's phases for every 64-vector block:
+//   WARMUP: fetch dimensions in doubling steps for all 64 vectors (lane l holds
+//           vectors 4*(l&15)..+3 for the even or odd dimension of each pair, one
+//           float4 load per lane per pair of dimensions = 512 contiguous bytes
+//           per warp), evaluate the predicate on the partial distances, count
+//           survivors with warp ballots.
+//   PRUNE:  once survivors < selection_threshold * 64, keep only their
+//           positions (<= 16, in registers) and spread the dimensions of each
+//           step over the 32 lanes; per-survivor sums are warp-reduced.
+//   merge:  survivors' full distances go into the warp's sorted top-k list in
+//           shared memory; its k-th distance is the local threshold, published
+//           to the query's global threshold with an atomic min.
+// Any threshold that is the k-th distance of k real vectors bounds the final
+// k-th distance from above, so a stale or partially-tightened threshold never
+// prunes a true neighbour (only the amount of pruning depends on timing).
+// A relative slack gamma = D * 2^-23 on every threshold covers the rounding of
+// FP32 partial sums, so an FP32 partial that exceeds tau*(1+gamma) has an
+// exact partial above the exact tau.
+#include "pdx_internal.cuh"
+
+namespace pdx {
+
+enum { PR_NONE = 0, PR_BOND = 1, PR_ADS = 2, PR_BSA = 3 };
+enum { MT_L2 = 0, MT_IP = 1, MT_L1 = 2 };
+constexpr unsigned kFull = 0xffffffffu;
+
+template <int MET>
+__device__ __forceinline__ float term(float qv, float x, float acc) {
+    if (MET == MT_L2) {
+        float t = qv - x;
+        return fmaf(t, t, acc);
+    } else if (MET == MT_IP) {
+        return fmaf(qv, x, acc);
+    } else {
+        return acc + fabsf(qv - x);
+    }
+}
+
+// distance used for ranking (smaller is better)
+template <int MET>
+__device__ __forceinline__ float rank_dist(float acc) { return MET == MT_IP ? -acc : acc; }
+
+__device__ __forceinline__ float sel4(const float4 &v, int c) {
+    return c == 0 ? v.x : (c == 1 ? v.y : (c == 2 ? v.z : v.w));
+}
+
+__device__ __forceinline__ float slack(float tau, float gamma) { return tau + fabsf(tau) * gamma; }
+
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+    for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+    return v;
+}
+
+__device__ __forceinline__ int next_pow2(int v) {
+    int p = 1;
+    while (p < v) p <<= 1;
+    return p;
+}
+
+// Warp-wide ascending bitonic sort of n (power of two) keys in shared memory.
+__device__ void warp_bitonic_sort(uint64_t *s, int n, int lane) {
+    for (int size = 2; size <= n; size <<= 1) {
+        for (int stride = size >> 1; stride > 0; stride >>= 1) {
+            for (int i = lane; i < (n >> 1); i += 32) {
+                int lo = 2 * i - (i & (stride - 1));
+                int hi = lo + stride;
+                bool asc = (lo & size) == 0;
+                uint64_t a = s[lo], b = s[hi];
+                if ((a > b) == asc) {
+                    s[lo] = b;
+                    s[hi] = a;
+                }
+            }
+            __syncwarp();
+        }
+    }
+}
+
+// Insert `key` into the warp's ascending list (capacity k). Warp-uniform call.
+__device__ __forceinline__ void topk_insert(uint64_t *list, int &cnt, int k, uint64_t key, int lane) {
+    if (cnt == k && key >= list[k - 1]) return;
+    int pos = 0;
+    for (int base = 0; base < cnt; base += 32) {
+        int i = base + lane;
+        bool lt = (i < cnt) && (list[i] < key);
+        pos += __popc(__ballot_sync(kFull, lt));
+    }
+    int newcnt = cnt < k ? cnt + 1 : k;
+    int top = newcnt - 1;
+    for (int base = (top >> 5) << 5; base >= 0; base -= 32) {
+        int i = base + lane;
+        bool mv = (i > pos) && (i <= top);
+        uint64_t v = mv ? list[i - 1] : 0ull;
+        __syncwarp();
+        if (mv) list[i] = v;
+        __syncwarp();
+        if (base <= pos) break;
+    }
+    if (lane == 0) list[pos] = key;
+    __syncwarp();
+    cnt = newcnt;
+}
+
+struct WarpSmem {
+    uint64_t *sortbuf;  // [npad] (BOND order only)
+    uint16_t *ord;      // [d] dimension visited at position i
+    float *qo;          // [d] query value at position i
+    uint64_t *topk;     // [k]
+    int32_t *sv;        // [kMaxSurv] survivor slot indices
+    float *sp;          // [kMaxSurv] survivor partial distances
+};
+
+__host__ __device__ inline size_t align16(size_t v) { return (v + 15) & ~size_t(15); }
+
+__host__ __device__ inline int sort_units(int d, int zone_dims, int order, int pruner) {
+    if (pruner != PR_BOND || order == PDX_ORDER_SEQUENTIAL) return 0;
+    int z = (order == PDX_ORDER_DIST_TO_MEANS) ? (zone_dims < 1 ? 1 : zone_dims) : 1;
+    return (d + z - 1) / z;
+}
+
+__host__ __device__ inline int pow2_ceil(int v) {
+    int p = 1;
+    while (p < v) p <<= 1;
+    return p;
+}
+
+__host__ __device__ inline size_t warp_smem_bytes(int d, int k, int nunits) {
+    size_t s = 0;
+    if (nunits > 0) s += align16((size_t)pow2_ceil(nunits) * 8);
+    s += align16((size_t)d * 2);
+    s += align16((size_t)d * 4);
+    s += align16((size_t)k * 8);
+    s += align16(kMaxSurv * 4) * 2;
+    return s;
+}
+
+size_t scan_warp_smem(int d, int k, int zone_dims, int order) {
+    return warp_smem_bytes(d, k, sort_units(d, zone_dims, order, PR_BOND));
+}
+
+__device__ __forceinline__ WarpSmem carve(unsigned char *base, int d, int k, int nunits) {
+    WarpSmem w;
+    size_t o = 0;
+    w.sortbuf = nullptr;
+    if (nunits > 0) {
+        w.sortbuf = reinterpret_cast<uint64_t *>(base + o);
+        o += align16((size_t)pow2_ceil(nunits) * 8);
+    }
+    w.ord = reinterpret_cast<uint16_t *>(base + o);
+    o += align16((size_t)d * 2);
+    w.qo = reinterpret_cast<float *>(base + o);
+    o += align16((size_t)d * 4);
+    w.topk = reinterpret_cast<uint64_t *>(base + o);
+    o += align16((size_t)k * 8);
+    w.sv = reinterpret_cast<int32_t *>(base + o);
+    o += align16(kMaxSurv * 4);
+    w.sp = reinterpret_cast<float *>(base + o);
+    return w;
+}
+
+// Visit order of one (query, PDXearch block) item (Sec. 5): dimension zones
+// (contiguous groups of zone_dims dimensions) ranked by the summed squared
+// distance of the query to the block means, best zone first, dimensions in
+// storage order inside a zone; zone_dims = 1 is the per-dimension
+// distance-to-means order. DECREASING ranks single dimensions by the query
+// value. Ties go to the lower zone / dimension index.
+__device__ void build_order(const WarpSmem &w, const float *__restrict__ qrow, const float *__restrict__ mu,
+                            int d, int order, int zone_dims, int nunits, int lane) {
+    if (nunits == 0) {
+        for (int i = lane; i < d; i += 32) {
+            w.ord[i] = (uint16_t)i;
+            w.qo[i] = qrow[i];
+        }
+        __syncwarp();
+        return;
+    }
+    const int Z = (order == PDX_ORDER_DIST_TO_MEANS) ? (zone_dims < 1 ? 1 : zone_dims) : 1;
+    const int npad = pow2_ceil(nunits);
+    for (int u = lane; u < npad; u += 32) {
+        uint64_t key = kEmptyKey;
+        if (u < nunits) {
+            float sc = 0.f;
+            if (order == PDX_ORDER_DECREASING) {
+                sc = qrow[u];
+            } else {
+                int j1 = min(d, u * Z + Z);
+                for (int j = u * Z; j < j1; ++j) {
+                    float t = qrow[j] - mu[j];
+                    sc = fmaf(t, t, sc);
+                }
+            }
+            key = ((uint64_t)f2o(-sc) << 32) | (uint32_t)u;
+        }
+        w.sortbuf[u] = key;
+    }
+    __syncwarp();
+    warp_bitonic_sort(w.sortbuf, npad, lane);
+    const int lastlen = d - (nunits - 1) * Z;
+    int rlast = 0;
+    for (int r = lane; r < nunits; r += 32) {
+        if ((int)(w.sortbuf[r] & 0xffffffffu) == nunits - 1) rlast = r;
+    }
+    for (int o = 16; o; o >>= 1) rlast = max(rlast, __shfl_xor_sync(kFull, rlast, o));
+    for (int r = lane; r < nunits; r += 32) {
+        int z = (int)(w.sortbuf[r] & 0xffffffffu);
+        int off = r * Z - ((r > rlast) ? (Z - lastlen) : 0);
+        int len = (z == nunits - 1) ? lastlen : Z;
+        for (int t = 0; t < len; ++t) {
+            w.ord[off + t] = (uint16_t)(z * Z + t);
+            w.qo[off + t] = qrow[z * Z + t];
+        }
+    }
+    __syncwarp();
+}
+
+// Pruning predicate on a partial distance after `dv` of D dimensions
+// (true = discard). `thr` is the slack-widened threshold.
+template <int PR>
+__device__ __forceinline__ bool prune_test(float partial, float thr, int dv, int D, float eps0, float rx2,
+                                           float rq2, float sd2, float bsa_m) {
+    if (PR == PR_BOND) {
+        return partial > thr;  // Sec. 5: the partial distance is a lower bound
+    } else if (PR == PR_ADS) {
+        // Sec. 2.3 ADSampling: scaled partial vs tau * (1 + eps0/sqrt(d))^2
+        float r = 1.f + eps0 * rsqrtf((float)dv);
+        return partial * (float)D > thr * r * r * (float)dv;
+    } else if (PR == PR_BSA) {
+        // Sec. 2.3 BSA_res: error quantile of the residual cross term, capped
+        // by Cauchy-Schwarz
+        float cs = sqrtf(rx2 * rq2);
+        float cross = fminf(bsa_m * sqrtf(sd2), cs);
+        return partial + rx2 + rq2 - 2.f * cross > thr;
+    } else {
+        return false;
+    }
+}
+
+template <int PR, int MET>
+__global__ void __launch_bounds__(256) pdxsearch_kernel(ScanParams a) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int D = a.d;
+    const int nunits = sort_units(D, a.zone_dims, a.order, PR);
+    WarpSmem w = carve(smem + (size_t)warp * warp_smem_bytes(D, a.k, nunits), D, a.k, nunits);
+    const int h = lane >> 4, sl = lane & 15;
+    const int k = a.k;
+    const int chunks = a.chunks_per_part;
+    unsigned long long c_values = 0, c_scanned = 0, c_pruned = 0, c_pblocks = 0, c_cand = 0, c_items = 0;
+
+    while (true) {
+        unsigned long long wi = 0;
+        if (lane == 0) wi = atomicAdd(reinterpret_cast<unsigned long long *>(a.work_counter), 1ull);
+        wi = __shfl_sync(kFull, wi, 0);
+        if ((int64_t)wi >= a.nitems) break;
+        const int slot = (int)(wi / (unsigned long long)a.nq);
+        const int64_t qi = (int64_t)(wi % (unsigned long long)a.nq);
+        const int pr = slot / chunks, ch = slot % chunks;
+        const int part = a.probes ? a.probes[qi * (a.nslots / chunks) + pr] : a.part0 + pr;
+        uint64_t *out = a.cand + ((size_t)qi * a.nslots + slot) * k;
+        int b0 = 0, b1 = 0;
+        if (part >= 0) {
+            b0 = a.part_blk[part] + ch * a.blocks_per_item;
+            b1 = min(a.part_blk[part + 1], b0 + a.blocks_per_item);
+        }
+        if (b0 >= b1) {
+            for (int i = lane; i < k; i += 32) out[i] = kEmptyKey;
+            continue;
+        }
+        ++c_items;
+        const float *qrow = a.q + qi * D;
+        build_order(w, qrow, a.means ? a.means + (int64_t)part * D : nullptr, D, a.order, a.zone_dims, nunits,
+                    lane);
+        volatile uint32_t *tau_g_ptr = reinterpret_cast<volatile uint32_t *>(a.tau) + qi;
+        int cnt = 0;
+        float tau_loc = __int_as_float(0x7f800000);
+        const float *qaux = (PR == PR_BSA) ? a.qaux + qi * a.nchk * 2 : nullptr;
+
+        for (int b = b0; b < b1; ++b) {
+            const float *xb = a.data + (int64_t)b * D * kBlock;
+            const int nvalid = a.blk_cnt[b];
+            const float tau_g = o2f(*tau_g_ptr);
+            const float thr = slack(fminf(tau_loc, tau_g), a.gamma);
+            unsigned alive = 0;
+#pragma unroll
+            for (int c = 0; c < 4; ++c)
+                if (4 * sl + c < nvalid) alive |= 1u << c;
+            c_scanned += (lane == 0) ? nvalid : 0;
+            float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+            int pos = 0, step = (PR == PR_NONE) ? D : max(1, a.first_step);
+            int chk = 0;
+            int nsurv = -1;  // -1: still in WARMUP
+            float my_p = 0.f;
+            int my_v = 0;
+            // ---------------- WARMUP ----------------
+            while (pos < D) {
+                const int e = min(D, pos + step);
+                int i = pos;
+                for (; i + 8 <= e; i += 8) {
+                    float4 x[4];
+                    float qv[4];
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        int ii = i + 2 * u + h;
+                        int j = w.ord[ii];
+                        qv[u] = w.qo[ii];
+                        x[u] = __ldg(reinterpret_cast<const float4 *>(xb + j * kBlock) + sl);
+                    }
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        acc.x = term<MET>(qv[u], x[u].x, acc.x);
+                        acc.y = term<MET>(qv[u], x[u].y, acc.y);
+                        acc.z = term<MET>(qv[u], x[u].z, acc.z);
+                        acc.w = term<MET>(qv[u], x[u].w, acc.w);
+                    }
+                }
+                for (; i < e; i += 2) {
+                    int ii = i + h;
+                    if (ii < e) {
+                        int j = w.ord[ii];
+                        float qv = w.qo[ii];
+                        float4 x = __ldg(reinterpret_cast<const float4 *>(xb + j * kBlock) + sl);
+                        acc.x = term<MET>(qv, x.x, acc.x);
+                        acc.y = term<MET>(qv, x.y, acc.y);
+                        acc.z = term<MET>(qv, x.z, acc.z);
+                        acc.w = term<MET>(qv, x.w, acc.w);
+                    }
+                }
+                c_values += (lane == 0) ? (unsigned long long)(e - pos) * nvalid : 0ull;
+                pos = e;
+                step <<= 1;
+                if (PR == PR_NONE || pos >= D) break;
+                // predicate on all vectors of the block
+                const float4 f = make_float4(acc.x + __shfl_xor_sync(kFull, acc.x, 16),
+                                             acc.y + __shfl_xor_sync(kFull, acc.y, 16),
+                                             acc.z + __shfl_xor_sync(kFull, acc.z, 16),
+                                             acc.w + __shfl_xor_sync(kFull, acc.w, 16));
+                float rq2 = 0.f, sd2 = 0.f;
+                if (PR == PR_BSA) {
+                    rq2 = qaux[chk * 2];
+                    sd2 = qaux[chk * 2 + 1];
+                }
+#pragma unroll
+                for (int c = 0; c < 4; ++c) {
+                    float rx2 = 0.f;
+                    if (PR == PR_BSA) rx2 = a.resid[((int64_t)b * a.nchk + chk) * kBlock + 4 * sl + c];
+                    if (prune_test<PR>(sel4(f, c), thr, pos, D, a.eps0, rx2, rq2, sd2, a.bsa_m)) alive &= ~(1u << c);
+                }
+                ++chk;
+                unsigned m0 = __ballot_sync(kFull, alive & 1u) & 0xffffu;
+                unsigned m1 = __ballot_sync(kFull, alive & 2u) & 0xffffu;
+                unsigned m2 = __ballot_sync(kFull, alive & 4u) & 0xffffu;
+                unsigned m3 = __ballot_sync(kFull, alive & 8u) & 0xffffu;
+                int nalive = __popc(m0) + __popc(m1) + __popc(m2) + __popc(m3);
+                if (nalive == 0) {
+                    nsurv = 0;
+                    break;
+                }
+                if (nalive <= a.sel_count) {
+                    // PRUNE: positions array of the survivors, in slot order
+                    unsigned below = (1u << sl) - 1u;
+                    int before = __popc(m0 & below) + __popc(m1 & below) + __popc(m2 & below) + __popc(m3 & below);
+                    if (h == 0) {
+#pragma unroll
+                        for (int c = 0; c < 4; ++c) {
+                            if (alive & (1u << c)) {
+                                w.sv[before] = 4 * sl + c;
+                                w.sp[before] = sel4(f, c);
+                                ++before;
+                            }
+                        }
+                    }
+                    __syncwarp();
+                    nsurv = nalive;
+                    if (lane < nsurv) {
+                        my_v = w.sv[lane];
+                        my_p = w.sp[lane];
+                    }
+                    __syncwarp();
+                    ++c_pblocks;
+                    break;
+                }
+            }
+            // ---------------- PRUNE ----------------
+            if (nsurv > 0) {
+                int sv[kMaxSurv];
+#pragma unroll
+                for (int m = 0; m < kMaxSurv; ++m) sv[m] = __shfl_sync(kFull, my_v, m);
+                while (pos < D) {
+                    const int e = min(D, pos + step);
+                    float sacc[kMaxSurv];
+#pragma unroll
+                    for (int m = 0; m < kMaxSurv; ++m) sacc[m] = 0.f;
+                    for (int i = pos + lane; i < e; i += 32) {
+                        const float *row = xb + (int)w.ord[i] * kBlock;
+                        const float qv = w.qo[i];
+#pragma unroll
+                        for (int m = 0; m < kMaxSurv; ++m)
+                            if (m < nsurv) sacc[m] = term<MET>(qv, __ldg(row + sv[m]), sacc[m]);
+                    }
+#pragma unroll
+                    for (int m = 0; m < kMaxSurv; ++m) {
+                        if (m < nsurv) {
+                            float r = warp_sum(sacc[m]);
+                            if (lane == m) my_p += r;
+                        }
+                    }
+                    c_values += (lane == 0) ? (unsigned long long)(e - pos) * nsurv : 0ull;
+                    pos = e;
+                    step <<= 1;
+                    if (pos >= D) break;
+                    float rx2 = 0.f, rq2 = 0.f, sd2 = 0.f;
+                    if (PR == PR_BSA) {
+                        rq2 = qaux[chk * 2];
+                        sd2 = qaux[chk * 2 + 1];
+                        if (lane < nsurv) rx2 = a.resid[((int64_t)b * a.nchk + chk) * kBlock + my_v];
+                    }
+                    ++chk;
+                    bool keep = (lane < nsurv) && !prune_test<PR>(my_p, thr, pos, D, a.eps0, rx2, rq2, sd2, a.bsa_m);
+                    unsigned km = __ballot_sync(kFull, keep);
+                    int nn = __popc(km);
+                    if (nn < nsurv) {
+                        unsigned mm = km;
+                        for (int t = 0; t < lane && t < 32; ++t) mm &= mm - 1u;
+                        int src = (lane < nn) ? (__ffs(mm) - 1) : lane;
+                        my_p = __shfl_sync(kFull, my_p, src);
+                        my_v = __shfl_sync(kFull, my_v, src);
+#pragma unroll
+                        for (int m = 0; m < kMaxSurv; ++m) sv[m] = __shfl_sync(kFull, my_v, m);
+                        nsurv = nn;
+                        if (nsurv == 0) break;
+                    }
+                }
+            }
+            // ---------------- merge ----------------
+            int nfinal = 0;
+            if (nsurv < 0) {
+                // finished in WARMUP: every alive vector has its full distance
+                const float4 fm = make_float4(acc.x + __shfl_xor_sync(kFull, acc.x, 16),
+                                              acc.y + __shfl_xor_sync(kFull, acc.y, 16),
+                                              acc.z + __shfl_xor_sync(kFull, acc.z, 16),
+                                              acc.w + __shfl_xor_sync(kFull, acc.w, 16));
+                for (int c = 0; c < 4; ++c) {
+                    float dist = rank_dist<MET>(sel4(fm, c));
+                    bool cand = (h == 0) && (alive & (1u << c)) && (dist <= slack(o2f(*tau_g_ptr), a.gamma));
+                    unsigned cm = __ballot_sync(kFull, cand);
+                    while (cm) {
+                        int src = __ffs(cm) - 1;
+                        cm &= cm - 1u;
+                        float dd = __shfl_sync(kFull, dist, src);
+                        int v = 4 * src + c;
+                        uint64_t key = make_key(dd, a.ids[(int64_t)b * kBlock + v]);
+                        topk_insert(w.topk, cnt, k, key, lane);
+                        ++c_cand;
+                    }
+                }
+                unsigned m0 = __ballot_sync(kFull, alive & 1u) & 0xffffu;
+                unsigned m1 = __ballot_sync(kFull, alive & 2u) & 0xffffu;
+                unsigned m2 = __ballot_sync(kFull, alive & 4u) & 0xffffu;
+                unsigned m3 = __ballot_sync(kFull, alive & 8u) & 0xffffu;
+                nfinal = __popc(m0) + __popc(m1) + __popc(m2) + __popc(m3);
+            } else if (nsurv > 0) {
+                float dist = rank_dist<MET>(my_p);
+                bool cand = (lane < nsurv) && (dist <= slack(o2f(*tau_g_ptr), a.gamma));
+                unsigned cm = __ballot_sync(kFull, cand);
+                while (cm) {
+                    int src = __ffs(cm) - 1;
+                    cm &= cm - 1u;
+                    float dd = __shfl_sync(kFull, dist, src);
+                    int v = __shfl_sync(kFull, my_v, src);
+                    uint64_t key = make_key(dd, a.ids[(int64_t)b * kBlock + v]);
+                    topk_insert(w.topk, cnt, k, key, lane);
+                    ++c_cand;
+                }
+                nfinal = nsurv;
+            }
+            c_pruned += (lane == 0) ? (unsigned long long)(nvalid - nfinal) : 0ull;
+            if (cnt == k) {
+                float t = key_dist(w.topk[k - 1]);
+                if (t < tau_loc) {
+                    tau_loc = t;
+                    if (lane == 0 && f2o(t) < *tau_g_ptr) atomicMin(reinterpret_cast<unsigned *>(a.tau) + qi, f2o(t));
+                }
+            }
+        }
+        for (int i = lane; i < k; i += 32) out[i] = (i < cnt) ? w.topk[i] : kEmptyKey;
+        __syncwarp();
+    }
+    if (lane == 0 && a.counters) {
+        atomicAdd(a.counters + C_VALUES, c_values);
+        atomicAdd(a.counters + C_SCANNED, c_scanned);
+        atomicAdd(a.counters + C_PRUNED, c_pruned);
+        atomicAdd(a.counters + C_PRUNE_BLOCKS, c_pblocks);
+        atomicAdd(a.counters + C_CANDIDATES, c_cand);
+        atomicAdd(a.counters + C_ITEMS, c_items);
+    }
+}
+
+template <int PR, int MET>
+static cudaError_t launch_scan_t(const ScanParams &p, int num_sms, cudaStream_t st) {
+    const int nunits = sort_units(p.d, p.zone_dims, p.order, PR);
+    const size_t per_warp = warp_smem_bytes(p.d, p.k, nunits);
+    int warps = 8;
+    while (warps > 1 && per_warp * warps > 200 * 1024) warps >>= 1;
+    const size_t smem = per_warp * warps;
+    if (smem > 227 * 1024) return cudaErrorInvalidValue;
+    auto kern = pdxsearch_kernel<PR, MET>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, warps * 32, smem);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) per_sm = 1;
+    int64_t grid = (int64_t)num_sms * per_sm;
+    int64_t need = (p.nitems + warps - 1) / warps;
+    if (grid > need) grid = need;
+    if (grid < 1) grid = 1;
+    kern<<<(unsigned)grid, warps * 32, smem, st>>>(p);
+    return counted(cudaGetLastError());
+}
+
+cudaError_t launch_scan(int pruner, int metric, const ScanParams &p, int num_sms, cudaStream_t st) {
+    if (p.nitems == 0) return cudaSuccess;
+    switch (pruner) {
+    case PR_NONE:
+        if (metric == MT_IP) return launch_scan_t<PR_NONE, MT_IP>(p, num_sms, st);
+        if (metric == MT_L1) return launch_scan_t<PR_NONE, MT_L1>(p, num_sms, st);
+        return launch_scan_t<PR_NONE, MT_L2>(p, num_sms, st);
+    case PR_BOND:
+        if (metric == MT_L1) return launch_scan_t<PR_BOND, MT_L1>(p, num_sms, st);
+        return launch_scan_t<PR_BOND, MT_L2>(p, num_sms, st);
+    case PR_ADS:
+        return launch_scan_t<PR_ADS, MT_L2>(p, num_sms, st);
+    case PR_BSA:
+        return launch_scan_t<PR_BSA, MT_L2>(p, num_sms, st);
+    default:
+        return cudaErrorInvalidValue;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// START (Sec. 4, PHASE 0) for exact search: exact distances of a tile of 64
+// queries to one 64-vector block, fully over D, written as (distance, id) keys.
+// Each thread owns 4 queries x 4 vectors; the block's dimension slices are
+// already dimension-major in PDX order and are staged 32 dimensions at a time.
+template <int MET>
+__global__ void __launch_bounds__(256) dense_keys_kernel(const float *__restrict__ q, int64_t nq,
+                                                         const float *__restrict__ data,
+                                                         const int32_t *__restrict__ ids, int32_t d, int32_t nblk,
+                                                         uint64_t *__restrict__ keys) {
+    __shared__ __align__(16) float Qs[32][68];  // padded rows: fewer bank conflicts on the transposed store
+    __shared__ __align__(16) float Xs[32][64];
+    const int tid = threadIdx.x;
+    const int64_t q0 = (int64_t)blockIdx.x * 64;
+    const int b = blockIdx.y;
+    const int ty = tid >> 4, tx = tid & 15;
+    float acc[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
+    const float *xb = data + (int64_t)b * d * kBlock;
+    for (int j0 = 0; j0 < d; j0 += 32) {
+        for (int e = tid; e < 32 * 64; e += 256) {
+            int jj = e >> 6, t = e & 63;
+            Xs[jj][t] = (j0 + jj < d) ? xb[(int64_t)(j0 + jj) * kBlock + t] : 0.f;
+            int qq = e >> 5, j2 = e & 31;
+            int64_t qi = q0 + qq;
+            Qs[j2][qq] = (qi < nq && j0 + j2 < d) ? q[qi * d + j0 + j2] : 0.f;
+        }
+        __syncthreads();
+        const int jn = min(32, d - j0);
+        for (int jj = 0; jj < jn; ++jj) {
+            float4 av = *reinterpret_cast<const float4 *>(&Qs[jj][ty * 4]);
+            float4 bv = *reinterpret_cast<const float4 *>(&Xs[jj][tx * 4]);
+            float aa[4] = {av.x, av.y, av.z, av.w};
+            float bb[4] = {bv.x, bv.y, bv.z, bv.w};
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) acc[i][j] = term<MET>(aa[i], bb[j], acc[i][j]);
+        }
+        __syncthreads();
+    }
+    const int64_t L = (int64_t)nblk * kBlock;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        int64_t qi = q0 + ty * 4 + i;
+        if (qi >= nq) continue;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            int v = tx * 4 + j;
+            int32_t id = ids[(int64_t)b * kBlock + v];
+            keys[qi * L + (int64_t)b * kBlock + v] = (id >= 0) ? make_key(rank_dist<MET>(acc[i][j]), id) : kEmptyKey;
+        }
+    }
+}
+
+cudaError_t launch_dense_keys(const float *q, int64_t nq, const float *data, const int32_t *ids, int32_t d,
+                              int32_t nblk, int metric, uint64_t *keys, cudaStream_t st) {
+    if (nq == 0 || nblk == 0) return cudaSuccess;
+    dim3 grid((unsigned)((nq + 63) / 64), (unsigned)nblk);
+    if (metric == MT_IP)
+        dense_keys_kernel<MT_IP><<<grid, 256, 0, st>>>(q, nq, data, ids, d, nblk, keys);
+    else if (metric == MT_L1)
+        dense_keys_kernel<MT_L1><<<grid, 256, 0, st>>>(q, nq, data, ids, d, nblk, keys);
+    else
+        dense_keys_kernel<MT_L2><<<grid, 256, 0, st>>>(q, nq, data, ids, d, nblk, keys);
+    return counted(cudaGetLastError());
+}
+
+// ---------------------------------------------------------------------------
+// k smallest keys of each row: the row is consumed in chunks appended after the
+// running best kpad keys and the buffer is bitonic-sorted by the whole CTA.
+__global__ void __launch_bounds__(512) select_k_kernel(const uint64_t *__restrict__ keys, int64_t L, int32_t k,
+                                                       int32_t kpad, int32_t sb, uint64_t *__restrict__ out) {
+    extern __shared__ __align__(16) uint64_t buf[];
+    const int64_t row = blockIdx.x;
+    const uint64_t *src = keys + row * L;
+    const int tid = threadIdx.x, nt = blockDim.x;
+    for (int i = tid; i < kpad; i += nt) buf[i] = kEmptyKey;
+    const int chunk = sb - kpad;
+    for (int64_t off = 0; off < L; off += chunk) {
+        for (int i = tid; i < chunk; i += nt) buf[kpad + i] = (off + i < L) ? src[off + i] : kEmptyKey;
+        __syncthreads();
+        for (int size = 2; size <= sb; size <<= 1) {
+            for (int stride = size >> 1; stride > 0; stride >>= 1) {
+                for (int i = tid; i < (sb >> 1); i += nt) {
+                    int lo = 2 * i - (i & (stride - 1));
+                    int hi = lo + stride;
+                    bool asc = (lo & size) == 0;
+                    uint64_t x = buf[lo], y = buf[hi];
+                    if ((x > y) == asc) {
+                        buf[lo] = y;
+                        buf[hi] = x;
+                    }
+                }
+                __syncthreads();
+            }
+        }
+    }
+    for (int i = tid; i < k; i += nt) out[row * k + i] = buf[i];
+}
+
+cudaError_t launch_select_k(const uint64_t *keys, int64_t rows, int64_t L, int32_t k, uint64_t *out,
+                            cudaStream_t st) {
+    if (rows == 0) return cudaSuccess;
+    int kpad = pow2_ceil(k);
+    int64_t want = (int64_t)kpad + L;
+    int sb = pow2_ceil((int)(want < 8192 ? want : 8192));
+    if (sb < 2 * kpad) sb = 2 * kpad;
+    if (sb < 64) sb = 64;
+    size_t smem = (size_t)sb * 8;
+    cudaError_t e = cudaFuncSetAttribute(select_k_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    int threads = sb >= 1024 ? 512 : (sb / 2 < 32 ? 32 : sb / 2);
+    select_k_kernel<<<(unsigned)rows, threads, smem, st>>>(keys, L, k, kpad, sb, out);
+    return counted(cudaGetLastError());
+}
+
+__global__ void tau_from_keys_kernel(const uint64_t *topk, int64_t rows, int32_t k, float *tau) {
+    int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= rows) return;
+    uint64_t key = topk[r * k + k - 1];
+    uint32_t v = (key == kEmptyKey) ? f2o(__int_as_float(0x7f800000)) : f2o(key_dist(key));
+    reinterpret_cast<uint32_t *>(tau)[r] = v;
+}
+
+cudaError_t launch_tau_from_keys(const uint64_t *topk, int64_t rows, int32_t k, float *tau, cudaStream_t st) {
+    if (rows == 0) return cudaSuccess;
+    tau_from_keys_kernel<<<(unsigned)((rows + 255) / 256), 256, 0, st>>>(topk, rows, k, tau);
+    return counted(cudaGetLastError());
+}
+
+// One warp per (query, result): lanes take dimensions j = lane, lane+32, ...
+// of the vector's storage slot, then a fixed butterfly reduction. Identical
+// vectors therefore get bit-identical distances, whatever order the scan
+// visited their dimensions in, and ties order by id.
+template <int MET>
+__global__ void refine_kernel(const uint64_t *__restrict__ topk, int64_t nq, int32_t k, const float *__restrict__ q,
+                              int32_t d, const float *__restrict__ data, const int32_t *__restrict__ slot_of,
+                              uint64_t *__restrict__ out) {
+    const int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (w >= nq * k) return;
+    const int64_t row = w / k;
+    const uint64_t key = topk[w];
+    if (key == kEmptyKey) {
+        if (lane == 0) out[w] = kEmptyKey;
+        return;
+    }
+    const int32_t id = key_id(key);
+    const int32_t slot = slot_of[id];
+    const float *xb = data + (int64_t)(slot / kBlock) * d * kBlock + (slot % kBlock);
+    const float *qr = q + row * d;
+    float acc = 0.f;
+    for (int j = lane; j < d; j += 32) acc = term<MET>(qr[j], xb[(int64_t)j * kBlock], acc);
+    acc = warp_sum(acc);
+    if (lane == 0) out[w] = make_key(rank_dist<MET>(acc), id);
+}
+
+cudaError_t launch_refine(const uint64_t *topk, int64_t nq, int32_t k, const float *q, int32_t d, const float *data,
+                          const int32_t *slot_of, int metric, uint64_t *out, cudaStream_t st) {
+    int64_t warps = nq * k;
+    if (warps == 0) return cudaSuccess;
+    unsigned grid = (unsigned)((warps * 32 + 255) / 256);
+    if (metric == MT_IP)
+        refine_kernel<MT_IP><<<grid, 256, 0, st>>>(topk, nq, k, q, d, data, slot_of, out);
+    else if (metric == MT_L1)
+        refine_kernel<MT_L1><<<grid, 256, 0, st>>>(topk, nq, k, q, d, data, slot_of, out);
+    else
+        refine_kernel<MT_L2><<<grid, 256, 0, st>>>(topk, nq, k, q, d, data, slot_of, out);
+    return counted(cudaGetLastError());
+}
+
+__global__ void write_out_kernel(const uint64_t *topk, int64_t nq, int32_t k, int mode, const float *q, int32_t d,
+                                 float *out_dist, int64_t *out_idx) {
+    const int64_t row = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (row >= nq) return;
+    float qn = 0.f;
+    if (mode == 2) {
+        for (int j = lane; j < d; j += 32) qn = fmaf(q[row * d + j], q[row * d + j], qn);
+        qn = warp_sum(qn);
+    }
+    for (int i = lane; i < k; i += 32) {
+        uint64_t key = topk[row * k + i];
+        float dist;
+        int64_t id;
+        if (key == kEmptyKey) {
+            id = -1;
+            dist = (mode == 0) ? __int_as_float(0x7f800000) : __int_as_float(0xff800000);
+        } else {
+            id = key_id(key);
+            float kd = key_dist(key);
+            dist = (mode == 0) ? kd : (mode == 1) ? -kd : 0.5f * (qn + 1.f - kd);
+        }
+        out_dist[row * k + i] = dist;
+        out_idx[row * k + i] = id;
+    }
+}
+
+cudaError_t launch_write_out(const uint64_t *topk, int64_t nq, int32_t k, int mode, const float *q, int32_t d,
+                             float *out_dist, int64_t *out_idx, cudaStream_t st) {
+    if (nq == 0) return cudaSuccess;
+    write_out_kernel<<<(unsigned)((nq * 32 + 255) / 256), 256, 0, st>>>(topk, nq, k, mode, q, d, out_dist, out_idx);
+    return counted(cudaGetLastError());
+}
+
+}  // namespace pdx

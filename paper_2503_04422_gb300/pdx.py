@@ -1,0 +1,312 @@
+"""Thin Python binding of libpdx (include/pdx.h), argument marshalling only.
+
+Every call goes straight to the C ABI of the same name; all of the search runs
+in the library's CUDA kernels. Inputs may be torch tensors (CUDA or CPU) or
+numpy arrays: device tensors are passed as device pointers (asynchronous on
+the current torch stream), CPU data as host pointers (the library copies it
+and synchronises). If the shared library is missing this module raises; there
+is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libpdx.so")
+
+PDX_OK, PDX_ERR_ARG, PDX_ERR_OOM, PDX_ERR_CUDA, PDX_ERR_TIMEOUT, PDX_ERR_UNSUPPORTED = range(6)
+METRIC = {"l2": 0, "ip": 1, "l1": 2}
+DTYPE = {"f32": 0, "bf16": 1, "fp8": 2}
+PRUNER = {"none": 0, "bond": 1, "ads": 2, "adsampling": 2, "bsa": 3}
+ORDER = {"dist_to_means": 0, "decreasing": 1, "sequential": 2}
+ARRAY = {"blocks": 0, "ids": 1, "part_blocks": 2, "means": 3, "centroids": 4, "assign": 5}
+STATUS_NAMES = {0: "PDX_OK", 1: "PDX_ERR_ARG", 2: "PDX_ERR_OOM", 3: "PDX_ERR_CUDA", 4: "PDX_ERR_TIMEOUT",
+                5: "PDX_ERR_UNSUPPORTED"}
+
+
+class pdx_build_opts(ctypes.Structure):
+    _fields_ = [("struct_size", ctypes.c_uint32), ("metric", ctypes.c_int), ("storage", ctypes.c_int),
+                ("partition_size", ctypes.c_uint32), ("keep_fp32_rerank", ctypes.c_int32)]
+
+
+class pdx_ivf_opts(ctypes.Structure):
+    _fields_ = [("struct_size", ctypes.c_uint32), ("base", pdx_build_opts), ("nlist", ctypes.c_uint32),
+                ("kmeans_iters", ctypes.c_uint32), ("kmeans_sample", ctypes.c_uint32), ("seed", ctypes.c_uint64),
+                ("transform", ctypes.c_int), ("rotation", ctypes.c_void_p), ("init_centroids", ctypes.c_void_p)]
+
+
+class pdx_search_stats(ctypes.Structure):
+    _fields_ = [("values_visited", ctypes.c_uint64), ("vectors_scanned", ctypes.c_uint64),
+                ("vectors_pruned", ctypes.c_uint64), ("prune_phase_blocks", ctypes.c_uint64),
+                ("candidates", ctypes.c_uint64), ("work_items", ctypes.c_uint64),
+                ("start_values", ctypes.c_uint64), ("bytes_logical", ctypes.c_uint64),
+                ("reserved", ctypes.c_uint64 * 8)]
+    FIELDS = ("values_visited", "vectors_scanned", "vectors_pruned", "prune_phase_blocks", "candidates",
+              "work_items", "start_values", "bytes_logical")
+
+    def as_dict(self):
+        return {f: int(getattr(self, f)) for f, _ in self._fields_ if f != "reserved"}
+
+
+class pdx_search_opts(ctypes.Structure):
+    _fields_ = [("struct_size", ctypes.c_uint32), ("pruner", ctypes.c_int), ("order", ctypes.c_int),
+                ("zone_dims", ctypes.c_uint32), ("selection_threshold", ctypes.c_float), ("eps0", ctypes.c_float),
+                ("bsa_m", ctypes.c_float), ("first_step", ctypes.c_uint32), ("start_vectors", ctypes.c_uint32),
+                ("blocks_per_item", ctypes.c_uint32), ("stats_out", ctypes.POINTER(pdx_search_stats)),
+                ("stats_device", ctypes.c_void_p), ("scan_event_start", ctypes.c_void_p),
+                ("scan_event_stop", ctypes.c_void_p)]
+
+
+class pdx_index_info(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("d", ctypes.c_int32), ("nparts", ctypes.c_int32), ("nblocks", ctypes.c_int64),
+                ("metric", ctypes.c_int), ("storage", ctypes.c_int), ("is_ivf", ctypes.c_int32),
+                ("unit_norm", ctypes.c_int32), ("device_bytes", ctypes.c_uint64)]
+
+
+_lib = None
+_lock = threading.Lock()
+
+
+def lib():
+    """The loaded libpdx (raises if it has not been built)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise RuntimeError(f"libpdx is not built ({LIB_PATH} missing); run "
+                                   "paper_2503_04422_gb300.build.build() first")
+            L = ctypes.CDLL(LIB_PATH)
+            vp, i64, i32, sz = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_size_t
+            L.pdx_build_layout.argtypes = [vp, i64, i32, ctypes.POINTER(pdx_build_opts), vp, ctypes.POINTER(vp)]
+            L.pdx_ivf_build.argtypes = [vp, i64, i32, ctypes.POINTER(pdx_ivf_opts), vp, ctypes.POINTER(vp)]
+            L.pdx_search_exact.argtypes = [vp, vp, i64, i32, ctypes.POINTER(pdx_search_opts), vp, vp, vp]
+            L.pdx_search_ivf.argtypes = [vp, vp, i64, i32, i32, ctypes.POINTER(pdx_search_opts), vp, vp, vp]
+            L.pdx_free.argtypes = [vp]
+            L.pdx_free.restype = None
+            L.pdx_kernel_launches.restype = ctypes.c_uint64
+            L.pdx_kernel_launches.argtypes = []
+            L.pdx_last_error.restype = ctypes.c_char_p
+            L.pdx_last_error.argtypes = []
+            L.pdx_index_info_get.argtypes = [vp, ctypes.POINTER(pdx_index_info)]
+            L.pdx_index_copy_out.argtypes = [vp, ctypes.c_int, vp, sz]
+            L.pdx_default_build_opts.argtypes = [ctypes.POINTER(pdx_build_opts)]
+            L.pdx_default_ivf_opts.argtypes = [ctypes.POINTER(pdx_ivf_opts)]
+            L.pdx_default_search_opts.argtypes = [ctypes.POINTER(pdx_search_opts)]
+            for f in ("pdx_default_build_opts", "pdx_default_ivf_opts", "pdx_default_search_opts"):
+                getattr(L, f).restype = None
+            for f in ("pdx_build_layout", "pdx_ivf_build", "pdx_search_exact", "pdx_search_ivf",
+                      "pdx_index_info_get", "pdx_index_copy_out"):
+                getattr(L, f).restype = ctypes.c_int
+            _lib = L
+    return _lib
+
+
+class PdxError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = status
+        msg = lib().pdx_last_error().decode(errors="replace")
+        super().__init__(f"{where}: {STATUS_NAMES.get(status, status)}: {msg}")
+
+
+def _check(status: int, where: str):
+    if status != PDX_OK:
+        raise PdxError(status, where)
+
+
+def pdx_kernel_launches() -> int:
+    return int(lib().pdx_kernel_launches())
+
+
+def pdx_last_error() -> str:
+    return lib().pdx_last_error().decode(errors="replace")
+
+
+# ---------------------------------------------------------------- marshalling
+def _is_torch(a):
+    try:
+        import torch
+        return isinstance(a, torch.Tensor)
+    except ImportError:  # pragma: no cover
+        return False
+
+
+def _ptr_f32(a, name):
+    """(pointer, keepalive, is_cuda, shape) of a float32 C-contiguous array."""
+    if _is_torch(a):
+        import torch
+        if a.dtype != torch.float32:
+            raise TypeError(f"{name} must be float32")
+        a = a.contiguous()
+        return a.data_ptr(), a, a.is_cuda, tuple(a.shape)
+    a = np.ascontiguousarray(a, dtype=np.float32)
+    return a.ctypes.data, a, False, a.shape
+
+
+def _stream(is_cuda, stream):
+    if stream is not None:
+        return ctypes.c_void_p(int(stream))
+    if is_cuda:
+        import torch
+        return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    return ctypes.c_void_p(0)
+
+
+class Index:
+    """Owns a pdx_index*; freed with pdx_free when garbage collected."""
+
+    def __init__(self, handle: ctypes.c_void_p):
+        self.handle = handle
+
+    @property
+    def info(self) -> pdx_index_info:
+        inf = pdx_index_info()
+        _check(lib().pdx_index_info_get(self.handle, ctypes.byref(inf)), "pdx_index_info_get")
+        return inf
+
+    def copy_out(self, which: str):
+        inf = self.info
+        shapes = {
+            "blocks": ((inf.nblocks, inf.d, 64), np.float32), "ids": ((inf.nblocks * 64,), np.int32),
+            "part_blocks": ((inf.nparts + 1,), np.int32), "means": ((inf.nparts, inf.d), np.float32),
+            "centroids": ((inf.nparts, inf.d), np.float32), "assign": ((inf.n,), np.int32)}
+        shape, dt = shapes[which]
+        out = np.empty(shape, dt)
+        _check(lib().pdx_index_copy_out(self.handle, ARRAY[which], out.ctypes.data, out.nbytes), "pdx_index_copy_out")
+        return out
+
+    def free(self):
+        if self.handle:
+            lib().pdx_free(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def build_opts(metric="l2", storage="f32", partition_size=10000, keep_fp32_rerank=True) -> pdx_build_opts:
+    o = pdx_build_opts()
+    lib().pdx_default_build_opts(ctypes.byref(o))
+    o.metric = METRIC[metric]
+    o.storage = DTYPE[storage]
+    o.partition_size = partition_size
+    o.keep_fp32_rerank = int(bool(keep_fp32_rerank))
+    return o
+
+
+def search_opts(pruner="bond", order="dist_to_means", zone_dims=None, selection_threshold=None, eps0=None,
+                bsa_m=None, first_step=None, start_vectors=None, blocks_per_item=None) -> pdx_search_opts:
+    o = pdx_search_opts()
+    lib().pdx_default_search_opts(ctypes.byref(o))
+    o.pruner = PRUNER[pruner]
+    o.order = ORDER[order]
+    for name, v in (("zone_dims", zone_dims), ("selection_threshold", selection_threshold), ("eps0", eps0),
+                    ("bsa_m", bsa_m), ("first_step", first_step), ("start_vectors", start_vectors),
+                    ("blocks_per_item", blocks_per_item)):
+        if v is not None:
+            setattr(o, name, v)
+    return o
+
+
+def pdx_build_layout(x, metric="l2", partition_size=10000, storage="f32", stream=None) -> Index:
+    """Exact-search index over x [n][d] (Sec. 3, Sec. 6.6)."""
+    p, keep, cuda, shape = _ptr_f32(x, "x")
+    if len(shape) != 2:
+        raise ValueError("x must be [n][d]")
+    h = ctypes.c_void_p()
+    o = build_opts(metric, storage, partition_size)
+    _check(lib().pdx_build_layout(p, shape[0], shape[1], ctypes.byref(o), _stream(cuda, stream), ctypes.byref(h)),
+           "pdx_build_layout")
+    del keep
+    return Index(h)
+
+
+def pdx_ivf_build(x, nlist, metric="l2", kmeans_iters=10, kmeans_sample=0, seed=2503, transform="none",
+                  rotation=None, init_centroids=None, storage="f32", stream=None) -> Index:
+    """IVF index whose buckets are PDX blocks (Sec. 2.1, Fig. 2)."""
+    p, keep, cuda, shape = _ptr_f32(x, "x")
+    o = pdx_ivf_opts()
+    lib().pdx_default_ivf_opts(ctypes.byref(o))
+    o.base = build_opts(metric, storage)
+    o.nlist = nlist
+    o.kmeans_iters = kmeans_iters
+    o.kmeans_sample = kmeans_sample
+    o.seed = seed
+    o.transform = PRUNER[transform]
+    keeps = [keep]
+    if rotation is not None:
+        rp, rk, _, _ = _ptr_f32(rotation, "rotation")
+        o.rotation = rp
+        keeps.append(rk)
+    if init_centroids is not None:
+        cp, ck, _, _ = _ptr_f32(init_centroids, "init_centroids")
+        o.init_centroids = cp
+        keeps.append(ck)
+    h = ctypes.c_void_p()
+    _check(lib().pdx_ivf_build(p, shape[0], shape[1], ctypes.byref(o), _stream(cuda, stream), ctypes.byref(h)),
+           "pdx_ivf_build")
+    del keeps
+    return Index(h)
+
+
+def _outputs(nq, k, cuda, out):
+    if out is not None:
+        return out
+    if cuda:
+        import torch
+        return (torch.empty((nq, k), dtype=torch.float32, device="cuda"),
+                torch.empty((nq, k), dtype=torch.int64, device="cuda"))
+    return np.empty((nq, k), np.float32), np.empty((nq, k), np.int64)
+
+
+def _out_ptr(a):
+    return a.data_ptr() if _is_torch(a) else a.ctypes.data
+
+
+def pdx_search_exact(index: Index, q, k: int, opts: pdx_search_opts | None = None, out=None, stream=None,
+                     stats: bool = False, **kw):
+    """Exact k-NN (Sec. 2.1) with PDXearch + PDX-BOND (Sec. 4-5).
+    Returns (dist [nq][k], idx [nq][k]) and, with stats=True, a dict of counters."""
+    p, keep, cuda, shape = _ptr_f32(q, "q")
+    nq = shape[0]
+    o = opts if opts is not None else search_opts(**kw)
+    st = pdx_search_stats()
+    if stats:
+        o.stats_out = ctypes.pointer(st)
+    od, oi = _outputs(nq, k, cuda, out)
+    rc = lib().pdx_search_exact(index.handle, p, nq, k, ctypes.byref(o), _out_ptr(od), _out_ptr(oi),
+                                _stream(cuda, stream))
+    if stats:
+        o.stats_out = None
+    _check(rc, "pdx_search_exact")
+    del keep
+    return (od, oi, st.as_dict()) if stats else (od, oi)
+
+
+def pdx_search_ivf(index: Index, q, k: int, nprobe: int, opts: pdx_search_opts | None = None, out=None,
+                   stream=None, stats: bool = False, **kw):
+    """Approximate k-NN over an IVF index with PDXearch (Sec. 4)."""
+    p, keep, cuda, shape = _ptr_f32(q, "q")
+    nq = shape[0]
+    o = opts if opts is not None else search_opts(**kw)
+    st = pdx_search_stats()
+    if stats:
+        o.stats_out = ctypes.pointer(st)
+    od, oi = _outputs(nq, k, cuda, out)
+    rc = lib().pdx_search_ivf(index.handle, p, nq, k, nprobe, ctypes.byref(o), _out_ptr(od), _out_ptr(oi),
+                              _stream(cuda, stream))
+    if stats:
+        o.stats_out = None
+    _check(rc, "pdx_search_ivf")
+    del keep
+    return (od, oi, st.as_dict()) if stats else (od, oi)
+
+
+def pdx_free(index: Index):
+    index.free()
