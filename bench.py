@@ -172,6 +172,35 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+def _e2e(pdx, ix, q, k, opts, stream, flush, K, world, dist):
+    """Same search through the C ABI with pinned host buffers: the call copies
+    the queries in and the results out (and synchronises) inside the timed
+    region."""
+    import torch
+    nq, d = q.shape
+    q_host = torch.from_numpy(q).pin_memory()
+    od_h = torch.empty((nq, k), dtype=torch.float32).pin_memory()
+    oi_h = torch.empty((nq, k), dtype=torch.int64).pin_memory()
+    opts.scan_event_start = opts.scan_event_stop = opts.stats_device = None
+    for _ in range(2):
+        pdx.pdx_search_exact(ix, q_host, k, opts=opts, out=(od_h, oi_h), stream=stream.cuda_stream)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+    torch.cuda.synchronize()
+    for i in range(K):
+        flush.zero_()
+        ev[i][0].record(stream)
+        pdx.pdx_search_exact(ix, q_host, k, opts=opts, out=(od_h, oi_h), stream=stream.cuda_stream)
+        ev[i][1].record(stream)
+    torch.cuda.synchronize()
+    ms = sum(a.elapsed_time(b) for a, b in ev)
+    if dist:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    return {"value": nq * world * K / (ms / 1e3), "unit": "queries/s", "h2d_bytes_per_step": nq * d * 4,
+            "d2h_bytes_per_step": nq * k * 12}
+
+
 def run_ours(args, rank, world, local_rank):
     import numpy as np
     import torch
@@ -188,8 +217,8 @@ def run_ours(args, rank, world, local_rank):
         dist.init_process_group("nccl")
     spec = WORKLOADS[args.workload]
     k = spec["k"]
-    base_nq = pdx_synth.WORKLOADS[args.workload]["nq"]
-    x, q_all = pdx_synth.make(args.workload, nq=base_nq * world)
+    base_nq = args.nq or pdx_synth.WORKLOADS[args.workload]["nq"]
+    x, q_all = pdx_synth.make(args.workload, n=args.n, nq=base_nq * world)
     q = np.ascontiguousarray(q_all[rank * base_nq:(rank + 1) * base_nq])
     n, d = x.shape
     nq = q.shape[0]
@@ -260,26 +289,9 @@ def run_ours(args, rank, world, local_rank):
     traffic = _traffic_per_launch(args.workload)
 
     # end to end through the C ABI with host (pinned) buffers
-    q_host = torch.from_numpy(q).pin_memory()
-    od_h = torch.empty((nq, k), dtype=torch.float32).pin_memory()
-    oi_h = torch.empty((nq, k), dtype=torch.int64).pin_memory()
-    opts.scan_event_start = opts.scan_event_stop = opts.stats_device = None
-    for _ in range(2):
-        pdx.pdx_search_exact(ix, q_host, k, opts=opts, out=(od_h, oi_h), stream=stream.cuda_stream)
-    e2e_ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
-    torch.cuda.synchronize()
-    for i in range(K):
-        flush.zero_()
-        e2e_ev[i][0].record(stream)
-        pdx.pdx_search_exact(ix, q_host, k, opts=opts, out=(od_h, oi_h), stream=stream.cuda_stream)
-        e2e_ev[i][1].record(stream)
-    torch.cuda.synchronize()
-    e2e_ms = sum(a.elapsed_time(b) for a, b in e2e_ev)
-    if dist:
-        t = torch.tensor([e2e_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_ms = float(t.item())
-    e2e_value = nq * world * K / (e2e_ms / 1e3)
+    e2e = None
+    if not args.no_e2e:
+        e2e = _e2e(pdx, ix, q, k, opts, stream, flush, K, world, dist)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -303,8 +315,7 @@ def run_ours(args, rank, world, local_rank):
                          "scan_ms_avg": scan_avg_ms,
                          "per_unit": {"bytes_per_query": bytes_per_launch / nq, "units_per_launch": nq}},
             "pruning": {"values_visited_fraction": values_per_launch / (n * d * nq), "vectors_pruned_fraction": pruned},
-            "e2e": {"value": e2e_value, "unit": "queries/s", "h2d_bytes_per_step": nq * d * 4,
-                    "d2h_bytes_per_step": nq * k * 12},
+            "e2e": e2e,
             "gpu_launches": int(launches),
             "gpu_launches_per_step": launches / K,
             "clocks": clk,
@@ -325,6 +336,9 @@ def main():
     ap.add_argument("--workload", default="bond_exact_1m_d768", choices=sorted(WORKLOADS))
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--n", type=int, default=None, help="smaller collection (profiling); default = workload size")
+    ap.add_argument("--nq", type=int, default=None, help="queries per GPU; default = workload size")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3

@@ -337,13 +337,7 @@ pdx_status pdx_build_layout(const float *x, int64_t n, int32_t d, const pdx_buil
 
 namespace pdx {
 
-struct SearchPlan {
-    int pruner;
-    int metric;      // metric the scan computes (IP on unit vectors is searched as L2)
-    int out_mode;    // 0: distance as ranked; 1: IP = -ranked value
-};
-
-static pdx_status check_search_args(const pdx_index *ix, const float *q, int64_t nq, int32_t k,
+pdx_status check_search_args(const pdx_index *ix, const float *q, int64_t nq, int32_t k,
                                     const pdx_search_opts *opts, float *out_dist, int64_t *out_idx,
                                     pdx_search_opts *o, const char *fn) {
     if (!ix || (nq > 0 && (!q || !out_dist || !out_idx))) {
@@ -375,7 +369,7 @@ static pdx_status check_search_args(const pdx_index *ix, const float *q, int64_t
     return PDX_OK;
 }
 
-static pdx_status plan_metric(const pdx_index *ix, int pruner, SearchPlan *pl, const char *fn) {
+pdx_status plan_metric(const pdx_index *ix, int pruner, SearchPlan *pl, const char *fn) {
     pl->pruner = pruner;
     pl->metric = ix->metric;
     pl->out_mode = 0;

@@ -68,6 +68,16 @@ namespace pdx {
 
 void set_error(const char *fmt, ...);
 
+struct SearchPlan {
+    int pruner;
+    int metric;      // metric the scan computes (IP on unit vectors is searched as L2)
+    int out_mode;    // 0: distance as ranked; 1: IP = -ranked value
+};
+pdx_status check_search_args(const pdx_index *ix, const float *q, int64_t nq, int32_t k,
+                             const pdx_search_opts *opts, float *out_dist, int64_t *out_idx,
+                             pdx_search_opts *o, const char *fn);
+pdx_status plan_metric(const pdx_index *ix, int pruner, SearchPlan *pl, const char *fn);
+
 // ---- device helpers ----
 #ifdef __CUDACC__
 // Monotone map float -> uint32 (total order equal to the float order for

@@ -381,39 +381,32 @@ __global__ void __launch_bounds__(256) pdxsearch_kernel(ScanParams a) {
                     }
                     __syncwarp();
                     nsurv = nalive;
-                    if (lane < nsurv) {
-                        my_v = w.sv[lane];
-                        my_p = w.sp[lane];
-                    }
-                    __syncwarp();
                     ++c_pblocks;
                     break;
                 }
             }
             // ---------------- PRUNE ----------------
+            // Survivor m owns G = 32 / pow2(nsurv) consecutive lanes; its lanes
+            // stride over the step's dimensions, so all lanes stay busy for any
+            // mix of survivor count and step size, and a log2(G) shuffle tree
+            // reduces each survivor's step sum.
             if (nsurv > 0) {
-                int sv[kMaxSurv];
-#pragma unroll
-                for (int m = 0; m < kMaxSurv; ++m) sv[m] = __shfl_sync(kFull, my_v, m);
+                int G = 32 / pow2_ceil(nsurv);
+                int m = lane / G, g = lane % G;
+                if (m < nsurv) {
+                    my_v = w.sv[m];
+                    my_p = w.sp[m];
+                }
+                __syncwarp();
                 while (pos < D) {
                     const int e = min(D, pos + step);
-                    float sacc[kMaxSurv];
-#pragma unroll
-                    for (int m = 0; m < kMaxSurv; ++m) sacc[m] = 0.f;
-                    for (int i = pos + lane; i < e; i += 32) {
-                        const float *row = xb + (int)w.ord[i] * kBlock;
-                        const float qv = w.qo[i];
-#pragma unroll
-                        for (int m = 0; m < kMaxSurv; ++m)
-                            if (m < nsurv) sacc[m] = term<MET>(qv, __ldg(row + sv[m]), sacc[m]);
+                    float acc1 = 0.f;
+                    if (m < nsurv) {
+                        for (int i = pos + g; i < e; i += G)
+                            acc1 = term<MET>(w.qo[i], __ldg(xb + (int)w.ord[i] * kBlock + my_v), acc1);
                     }
-#pragma unroll
-                    for (int m = 0; m < kMaxSurv; ++m) {
-                        if (m < nsurv) {
-                            float r = warp_sum(sacc[m]);
-                            if (lane == m) my_p += r;
-                        }
-                    }
+                    for (int o = G >> 1; o; o >>= 1) acc1 += __shfl_xor_sync(kFull, acc1, o);
+                    my_p += acc1;
                     c_values += (lane == 0) ? (unsigned long long)(e - pos) * nsurv : 0ull;
                     pos = e;
                     step <<= 1;
@@ -422,23 +415,39 @@ __global__ void __launch_bounds__(256) pdxsearch_kernel(ScanParams a) {
                     if (PR == PR_BSA) {
                         rq2 = qaux[chk * 2];
                         sd2 = qaux[chk * 2 + 1];
-                        if (lane < nsurv) rx2 = a.resid[((int64_t)b * a.nchk + chk) * kBlock + my_v];
+                        if (m < nsurv) rx2 = a.resid[((int64_t)b * a.nchk + chk) * kBlock + my_v];
                     }
                     ++chk;
-                    bool keep = (lane < nsurv) && !prune_test<PR>(my_p, thr, pos, D, a.eps0, rx2, rq2, sd2, a.bsa_m);
-                    unsigned km = __ballot_sync(kFull, keep);
+                    bool keep = (m < nsurv) && !prune_test<PR>(my_p, thr, pos, D, a.eps0, rx2, rq2, sd2, a.bsa_m);
+                    unsigned km = __ballot_sync(kFull, keep && g == 0);   // one bit per survivor, at its lane m*G
                     int nn = __popc(km);
                     if (nn < nsurv) {
-                        unsigned mm = km;
-                        for (int t = 0; t < lane && t < 32; ++t) mm &= mm - 1u;
-                        int src = (lane < nn) ? (__ffs(mm) - 1) : lane;
-                        my_p = __shfl_sync(kFull, my_p, src);
-                        my_v = __shfl_sync(kFull, my_v, src);
-#pragma unroll
-                        for (int m = 0; m < kMaxSurv; ++m) sv[m] = __shfl_sync(kFull, my_v, m);
                         nsurv = nn;
-                        if (nsurv == 0) break;
+                        if (nn == 0) break;
+                        int Gn = 32 / pow2_ceil(nn);
+                        int mn = lane / Gn;
+                        unsigned mm = km;
+                        for (int t = 0; t < mn && t < nn; ++t) mm &= mm - 1u;
+                        int src = (mn < nn) ? (__ffs(mm) - 1) : lane;
+                        float np = __shfl_sync(kFull, my_p, src);
+                        int nv = __shfl_sync(kFull, my_v, src);
+                        if (mn < nn) {
+                            my_p = np;
+                            my_v = nv;
+                        }
+                        G = Gn;
+                        m = mn;
+                        g = lane % Gn;
                     }
+                }
+                // survivors' leaders hold (my_v, my_p) at lanes m*G; gather them
+                // to lanes 0..nsurv-1 for the merge below
+                if (nsurv > 0) {
+                    int src = lane * G;
+                    float np = __shfl_sync(kFull, my_p, src & 31);
+                    int nv = __shfl_sync(kFull, my_v, src & 31);
+                    my_p = np;
+                    my_v = nv;
                 }
             }
             // ---------------- merge ----------------
