@@ -213,6 +213,38 @@ pdx_status pdx_search_ivf(const pdx_index *index, const float *q, int64_t nq, in
                           int32_t nprobe, const pdx_search_opts *opts, float *out_dist,
                           int64_t *out_idx, void *stream);
 
+/*
+ * pdx_search_exact_noalloc -- pdx_search_exact for callers that must not
+ * allocate device memory during a search. The paper has no counterpart: this
+ * exists for hosts that hand the library a fixed memory budget. Examples are a
+ * plug-in running inside a process whose device memory is owned by another
+ * framework's caching allocator, or a latency-critical serving loop where an
+ * allocation (and the implicit synchronisation or pool growth it can cause)
+ * must never happen after start-up.
+ *
+ * The results and errors are those of pdx_search_exact, with these
+ * differences:
+ *  - q, out_dist and out_idx must be device memory (PDX_ERR_ARG otherwise);
+ *    nothing is staged through host memory.
+ *  - All scratch (thresholds, per-item candidate lists, START keys, counters)
+ *    lives in one file-scope __device__ array of 32 MiB that the library
+ *    declares statically. Every GPU that loads the library holds it until the
+ *    process exits. A search whose scratch would exceed 32 MiB returns
+ *    PDX_ERR_ARG and says how much it needed. Fewer queries per call or a
+ *    smaller start_vectors reduce it: about nq*(8*k*parts*groups + 8*start_vectors) bytes.
+ *  - The call allocates nothing. It makes no cudaMalloc/cudaFree and uses no
+ *    allocating library routine. The first call on a device looks up the
+ *    array's device address with cudaGetSymbolAddress, with that device
+ *    current. Make that first call before any stream capture.
+ *  - Every call on a device shares the one array, and each call overwrites it
+ *    (the call resets what must start from zero). Calls whose work overlaps
+ *    on the GPU (different streams, or host threads without ordering) race
+ *    on it and produce wrong results. Serialise them, e.g. on one stream.
+ */
+pdx_status pdx_search_exact_noalloc(const pdx_index *index, const float *q, int64_t nq, int32_t k,
+                                    const pdx_search_opts *opts, float *out_dist, int64_t *out_idx,
+                                    void *stream);
+
 /* Release an index and all of its device memory. NULL-safe. */
 void pdx_free(pdx_index *index);
 

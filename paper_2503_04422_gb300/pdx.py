@@ -310,3 +310,23 @@ def pdx_search_ivf(index: Index, q, k: int, nprobe: int, opts: pdx_search_opts |
 
 def pdx_free(index: Index):
     index.free()
+
+
+def pdx_search_exact_noalloc(index: Index, q, k: int, opts: pdx_search_opts | None = None, out=None,
+                             stream=None, **kw):
+    """pdx_search_exact with its scratch in the library's static 32 MiB device
+    array (no allocation during the call). q and the outputs must be CUDA
+    tensors; overlapping calls on one device race on the shared array."""
+    L = lib()
+    f = L.pdx_search_exact_noalloc
+    f.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32,
+                  ctypes.POINTER(pdx_search_opts), ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
+    f.restype = ctypes.c_int
+    p, keep, cuda, shape = _ptr_f32(q, "q")
+    nq = shape[0]
+    o = opts if opts is not None else search_opts(**kw)
+    od, oi = _outputs(nq, k, cuda, out)
+    _check(f(index.handle, p, nq, k, ctypes.byref(o), _out_ptr(od), _out_ptr(oi), _stream(cuda, stream)),
+           "pdx_search_exact_noalloc")
+    del keep
+    return od, oi
