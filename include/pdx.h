@@ -76,6 +76,17 @@ typedef enum pdx_order {
     PDX_ORDER_SEQUENTIAL = 2     /* storage order                            */
 } pdx_order;
 
+/* Whose means the distance-to-means order uses (Sec. 5 speaks of the block's
+ * statistics; the Fig. 6 caption of the collection's). Either keeps PDX-BOND
+ * exact: only the amount of pruning depends on the order. */
+typedef enum pdx_means_scope {
+    PDX_MEANS_BLOCK = 0,       /* per PDXearch block (partition / bucket)    */
+    PDX_MEANS_COLLECTION = 1,  /* of the whole collection                    */
+    PDX_MEANS_AUTO = 2         /* collection for exact search (its partitions
+                                  are arbitrary id ranges), block for IVF
+                                  (its buckets are clusters)                 */
+} pdx_means_scope;
+
 typedef struct pdx_build_opts {
     uint32_t struct_size;      /* = sizeof(pdx_build_opts)                                */
     pdx_metric metric;         /* metric the index will be searched with                   */
@@ -116,11 +127,14 @@ typedef struct pdx_search_opts {
     uint32_t struct_size;      /* = sizeof(pdx_search_opts)                                */
     pdx_pruner pruner;         /* default BOND                                             */
     pdx_order order;           /* PDX-BOND visit order (default DIST_TO_MEANS)             */
-    uint32_t zone_dims;        /* dimension-zone width (Sec. 5); 1 = per dimension         */
+    uint32_t zone_dims;        /* dimension-zone width (Sec. 5); 1 = per dimension; 0 = 1
+                                  with collection means, 8 with block means               */
     float selection_threshold; /* switch WARMUP -> PRUNE below this fraction (0.20)        */
     float eps0;                /* ADSampling error bound (2.1)                             */
     float bsa_m;               /* BSA multiplier m                                         */
-    uint32_t first_step;       /* first fetch step in dimensions (2); then doubling        */
+    uint32_t first_step;       /* first fetch step in dimensions, then doubling (default 4;
+                                  the paper's CPU setting is 2). BSA searches always use the
+                                  schedule their index stored residual norms for (4).      */
     uint32_t start_vectors;    /* exact search: vectors of the START scan (0 = one block)  */
     uint32_t blocks_per_item;  /* 64-vector blocks per GPU work item (0 = automatic)       */
     pdx_search_stats *stats_out; /* optional host pointer; filled after the search (the call
@@ -131,6 +145,10 @@ typedef struct pdx_search_opts {
     void *scan_event_start;    /* optional cudaEvent_t recorded on `stream` just before the
                                   PDXearch scan kernel                                        */
     void *scan_event_stop;     /* optional cudaEvent_t recorded just after it                 */
+    pdx_means_scope means_scope; /* distance-to-means order: block or collection means (AUTO) */
+    uint32_t ctas_per_sm;      /* resident scan CTAs per SM (0 = 3). The shared-memory carveout
+                                  is sized for exactly this many, and the rest of each SM's
+                                  on-chip memory serves as L1 for the loads in flight.     */
 } pdx_search_opts;
 
 typedef struct pdx_index_info {
@@ -152,7 +170,9 @@ typedef enum pdx_array {
     PDX_ARRAY_PART_BLOCKS = 2, /* int32 [nparts+1] first storage block of each part        */
     PDX_ARRAY_MEANS = 3,       /* float32 [nparts][d] per-part dimension means (Sec. 3)    */
     PDX_ARRAY_CENTROIDS = 4,   /* float32 [nparts][d] IVF centroids (transformed space)    */
-    PDX_ARRAY_ASSIGN = 5       /* int32 [n] IVF bucket of each vector                      */
+    PDX_ARRAY_ASSIGN = 5,      /* int32 [n] IVF bucket of each vector                      */
+    PDX_ARRAY_ROTATION = 6,    /* float32 [d][d] IVF transform applied to vectors/queries  */
+    PDX_ARRAY_VARIANCES = 7    /* float32 [d] BSA: variance of each projected dimension    */
 } pdx_array;
 
 /* Fill an options struct with the defaults named above. */

@@ -30,12 +30,15 @@ while ``oracle.knn`` is the reference for the exact *result*:
   storage order): after d of D dimensions the vector is pruned when
   partial * D / d > tau * (1 + eps0 / sqrt(d))^2 -- the hypothesis test on the
   scaled partial distance with error bound eps0, written for squared distances.
-* Sec. 2.3 BSA_res (on PCA-projected data, dims in storage order): the
-  unvisited part of the distance is ||x_r||^2 + ||q_r||^2 - 2<x_r, q_r>; the
-  cross term is replaced by its error quantile m * s_d(q), with
-  s_d(q)^2 = sum_{j unvisited} lambda_j q_j^2 (lambda = PCA variances), capped
-  by the Cauchy-Schwarz bound ||x_r|| ||q_r||; prune when
-  partial + ||x_r||^2 + ||q_r||^2 - 2 min(m s_d, ||x_r|| ||q_r||) > tau.
+* Sec. 2.3 BSA_res (on PCA-projected data, dims in storage order), pruned
+  when either test fires after d visited dimensions:
+  - Cauchy-Schwarz (exact): partial + (||x_r|| - ||q_r||)^2 > tau, since the
+    unvisited part ||x_r - q_r||^2 is at least (||x_r|| - ||q_r||)^2;
+  - error quantile: partial > tau * F(d) * (1 + m / sqrt(d))^2, where
+    F(d) = sum_{visited j} lambda_j / sum_j lambda_j is the fraction of the
+    collection's variance (lambda = PCA variances) in the visited dimensions,
+    so partial / F(d) estimates the full distance; m -> infinity leaves only
+    the exact test.
 
 Returns the top-k plus per-query counters: values accumulated (the paper's
 pruning power is 1 - visited / (n*D)), vectors pruned, and the phase at which
@@ -184,9 +187,11 @@ def _predicate(pruner, partial, tau, dvis, d, xrows, q, dims, pos, eps0, bsa_m, 
         rest = dims[pos:]
         rx2 = (xrows[:, rest] ** 2).sum(axis=1)
         rq2 = float((q[rest] ** 2).sum())
-        s_d = math.sqrt(float((np.asarray(bsa_lambda, np.float64)[rest] * q[rest] ** 2).sum()))
-        cross = np.minimum(bsa_m * s_d, np.sqrt(rx2 * rq2))
-        return partial + rx2 + rq2 - 2.0 * cross > tau
+        cs = partial + (np.sqrt(rx2) - math.sqrt(rq2)) ** 2 > tau
+        lam = np.asarray(bsa_lambda, np.float64)
+        frac = float(lam[dims[:pos]].sum() / lam.sum())
+        stat = partial > tau * frac * (1.0 + bsa_m / math.sqrt(dvis)) ** 2
+        return cs | stat
     raise ValueError(pruner)
 
 

@@ -75,20 +75,35 @@ struct Scratch {
         if (bytes == 0) return cudaSuccess;
         return cudaMallocAsync(&base, bytes, st);
     }
+    // Carves the next region; returns nullptr (and sets overflow) instead of
+    // handing out memory past the reservation.
+    bool overflow = false;
     template <class T>
     T *take(size_t count) {
         size_t bytes = (count * sizeof(T) + 255) & ~size_t(255);
+        if (off + bytes > cap || (!base && bytes)) {
+            overflow = true;
+            return nullptr;
+        }
         T *p = reinterpret_cast<T *>(static_cast<char *>(base) + off);
         off += bytes;
         return p;
     }
 };
+
+#define PDX_CHECK_SCRATCH(scr)                                                                          \
+    do {                                                                                                \
+        if ((scr).overflow) {                                                                           \
+            ::pdx::set_error("internal error: scratch layout exceeds its reservation (pdx_api.cu:%d)", __LINE__); \
+            return PDX_ERR_CUDA;                                                                        \
+        }                                                                                               \
+    } while (0)
 static size_t rup(size_t b) { return (b + 255) & ~size_t(255); }
 
 static void free_index(pdx_index *ix) {
     if (!ix) return;
-    void *ptrs[] = {ix->data, ix->ids, ix->slot_of, ix->blk_cnt, ix->part_blk, ix->means, ix->centroids, ix->centroid_norms,
-                    ix->assign, ix->rot, ix->shift, ix->pca_var, ix->resid};
+    void *ptrs[] = {ix->data, ix->ids, ix->slot_of, ix->blk_cnt, ix->part_blk, ix->means, ix->cmean, ix->centroids, ix->centroid_norms,
+                    ix->assign, ix->rot, ix->shift, ix->pca_var, ix->resid, ix->chk, ix->cdata, ix->cids};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     delete[] ix->h_part_blk;
@@ -146,6 +161,23 @@ static pdx_status layout_parts(pdx_index *ix, const float *x_dev, const std::vec
     PDX_TRY(cudaMemcpyAsync(ix->part_blk, part_blk.data(), part_blk.size() * 4, cudaMemcpyHostToDevice, st));
     PDX_TRY(launch_to_pdx(x_dev, ix->d, ix->ids, nblocks, ix->data, st));
     PDX_TRY(launch_part_means(ix->data, ix->blk_cnt, ix->part_blk, nparts, ix->d, ix->means, st));
+    // collection means = part means weighted by part sizes
+    {
+        std::vector<float> hm((size_t)nparts * ix->d);
+        PDX_TRY(cudaMemcpyAsync(hm.data(), ix->means, hm.size() * 4, cudaMemcpyDeviceToHost, st));
+        PDX_TRY(cudaStreamSynchronize(st));
+        std::vector<double> acc((size_t)ix->d, 0.0);
+        int64_t tot = 0;
+        for (int p = 0; p < nparts; ++p) {
+            int64_t len = part_row[p + 1] - part_row[p];
+            tot += len;
+            for (int j = 0; j < ix->d; ++j) acc[(size_t)j] += (double)hm[(size_t)p * ix->d + j] * (double)len;
+        }
+        std::vector<float> cm((size_t)ix->d);
+        for (int j = 0; j < ix->d; ++j) cm[(size_t)j] = tot ? (float)(acc[(size_t)j] / (double)tot) : 0.f;
+        PDX_TRY(dalloc(ix, &ix->cmean, (size_t)ix->d));
+        PDX_TRY(cudaMemcpyAsync(ix->cmean, cm.data(), cm.size() * 4, cudaMemcpyHostToDevice, st));
+    }
     // host vectors above are pageable: the copies have completed once the stream drains
     PDX_TRY(cudaStreamSynchronize(st));
     return PDX_OK;
@@ -187,11 +219,13 @@ void pdx_default_search_opts(pdx_search_opts *o) {
     o->struct_size = sizeof *o;
     o->pruner = PDX_PRUNE_BOND;
     o->order = PDX_ORDER_DIST_TO_MEANS;
-    o->zone_dims = 8;
+    o->zone_dims = 0;
     o->selection_threshold = 0.20f;
     o->eps0 = 2.1f;
-    o->bsa_m = 4.0f;
-    o->first_step = 2;
+    o->bsa_m = 1.0f;
+    o->first_step = 4;
+    o->means_scope = PDX_MEANS_AUTO;
+    o->ctas_per_sm = 0;
     o->start_vectors = 4096;
     o->blocks_per_item = 0;
     o->stats_out = nullptr;
@@ -234,6 +268,8 @@ pdx_status pdx_index_copy_out(const pdx_index *ix, pdx_array which, void *dst, s
     case PDX_ARRAY_MEANS: src = ix->means; need = (size_t)ix->nparts * ix->d * 4; break;
     case PDX_ARRAY_CENTROIDS: src = ix->centroids; need = (size_t)ix->nparts * ix->d * 4; break;
     case PDX_ARRAY_ASSIGN: src = ix->assign; need = (size_t)ix->n * 4; break;
+    case PDX_ARRAY_ROTATION: src = ix->rot; need = (size_t)ix->d * ix->d * 4; break;
+    case PDX_ARRAY_VARIANCES: src = ix->pca_var; need = (size_t)ix->d * 4; break;
     default: set_error("pdx_index_copy_out: unknown array %d", (int)which); return PDX_ERR_ARG;
     }
     if (!src) {
@@ -296,6 +332,7 @@ pdx_status pdx_build_layout(const float *x, int64_t n, int32_t d, const pdx_buil
             cudaError_t e = scr.reserve(rup((size_t)n * d * 4));
             if (e != cudaSuccess) { free_index(ix); return cuda_status(e, "cudaMallocAsync", __LINE__); }
             float *tmp = scr.take<float>((size_t)n * d);
+            if (!tmp) { free_index(ix); set_error("internal error: scratch layout"); return PDX_ERR_CUDA; }
             e = cudaMemcpyAsync(tmp, x, (size_t)n * d * 4, cudaMemcpyHostToDevice, st);
             if (e != cudaSuccess) { free_index(ix); return cuda_status(e, "cudaMemcpyAsync", __LINE__); }
             xd = tmp;
@@ -361,11 +398,21 @@ pdx_status check_search_args(const pdx_index *ix, const float *q, int64_t nq, in
         set_error("%s: bad pruner %d or order %d", fn, (int)o->pruner, (int)o->order);
         return PDX_ERR_ARG;
     }
-    if (!(o->selection_threshold >= 0.f && o->selection_threshold <= 0.25f) || o->first_step < 1 ||
-        o->zone_dims < 1 || !(o->eps0 >= 0.f) || !(o->bsa_m >= 0.f)) {
-        set_error("%s: selection_threshold must be in [0, 0.25], first_step/zone_dims >= 1, eps0/bsa_m >= 0", fn);
+    if (o->means_scope != PDX_MEANS_BLOCK && o->means_scope != PDX_MEANS_COLLECTION &&
+        o->means_scope != PDX_MEANS_AUTO) {
+        set_error("%s: bad means_scope %d", fn, (int)o->means_scope);
         return PDX_ERR_ARG;
     }
+    if (!(o->selection_threshold >= 0.f && o->selection_threshold <= 0.25f) || o->first_step < 1 ||
+        !(o->eps0 >= 0.f) || !(o->bsa_m >= 0.f) || o->ctas_per_sm > 32) {
+        set_error("%s: selection_threshold must be in [0, 0.25], first_step >= 1, eps0/bsa_m >= 0, "
+                  "ctas_per_sm <= 32", fn);
+        return PDX_ERR_ARG;
+    }
+    // resolve the automatic choices
+    if (o->means_scope == PDX_MEANS_AUTO) o->means_scope = ix->is_ivf ? PDX_MEANS_BLOCK : PDX_MEANS_COLLECTION;
+    if (o->zone_dims == 0) o->zone_dims = (o->means_scope == PDX_MEANS_COLLECTION) ? 1 : 8;
+    if (o->ctas_per_sm == 0) o->ctas_per_sm = 3;
     return PDX_OK;
 }
 
@@ -392,13 +439,28 @@ pdx_status plan_metric(const pdx_index *ix, int pruner, SearchPlan *pl, const ch
     return PDX_OK;
 }
 
-// Shared tail of both searches: scan items, merge the per-item lists, write
-// the outputs (to host through a staging buffer when needed).
-struct SearchIO {
-    const float *q_dev;
-    float *out_dist_dev;
-    int64_t *out_idx_dev;
-};
+// PDX-BOND visit orders: coarse zones against block means are sorted inside
+// the scan kernel; orders that do not depend on the block (collection means,
+// decreasing query value) are computed once per query; fine orders against
+// block means (more than kMaxSortUnits zones) once per (query, part rank).
+OrderPlan plan_orders(const pdx_index *ix, const pdx_search_opts &o, int pruner, int64_t nq, int parts_per_query) {
+    OrderPlan pl;
+    if (pruner != PDX_PRUNE_BOND || o.order == PDX_ORDER_SEQUENTIAL) return pl;
+    const int d = ix->d;
+    if (o.order == PDX_ORDER_DECREASING) {
+        pl.mode = 1;
+    } else if (o.means_scope == PDX_MEANS_COLLECTION) {
+        pl.mode = 0;
+    } else {
+        int z = o.zone_dims < 1 ? 1 : (int)o.zone_dims;
+        if ((d + z - 1) / z <= kMaxSortUnits) return pl;
+        pl.mode = 0;
+        pl.per_part = parts_per_query;
+    }
+    pl.rows = pl.per_part ? nq * pl.per_part : nq;
+    pl.bytes = (size_t)pl.rows * d * 2;
+    return pl;
+}
 
 }  // namespace pdx
 
@@ -456,9 +518,10 @@ extern "C" pdx_status pdx_search_exact(const pdx_index *ix, const float *q, int6
         start_blk = (int)std::min<int64_t>(ix->nblocks, (sv + kBlock - 1) / kBlock);
     }
     const int64_t Lstart = (int64_t)start_blk * kBlock;
+    const OrderPlan op = plan_orders(ix, o, pl.pruner, nq, ix->nparts);
 
     Scratch scr(st);
-    size_t need = 0;
+    size_t need = rup(op.bytes);
     if (!q_dev) need += rup((size_t)nq * d * 4);
     need += rup((size_t)nq * 4);                         // tau
     need += rup((size_t)nq * nslots * k * 8);            // per-item lists
@@ -470,6 +533,7 @@ extern "C" pdx_status pdx_search_exact(const pdx_index *ix, const float *q, int6
     const float *qd = q;
     if (!q_dev) {
         float *t = scr.take<float>((size_t)nq * d);
+        PDX_CHECK_SCRATCH(scr);
         PDX_TRY(cudaMemcpyAsync(t, q, (size_t)nq * d * 4, cudaMemcpyHostToDevice, st));
         qd = t;
     }
@@ -482,12 +546,17 @@ extern "C" pdx_status pdx_search_exact(const pdx_index *ix, const float *q, int6
     uint64_t *stopk = start ? scr.take<uint64_t>((size_t)nq * k) : nullptr;
     unsigned long long *counters = scr.take<unsigned long long>(C_COUNT);
     int *work = scr.take<int>(2);
+    uint16_t *qorder = op.rows ? scr.take<uint16_t>((size_t)op.rows * d) : nullptr;
     float *od = out_dist;
     int64_t *oi = out_idx;
     if (!o_dev) {
         od = scr.take<float>((size_t)nq * k);
         oi = scr.take<int64_t>((size_t)nq * k);
     }
+    PDX_CHECK_SCRATCH(scr);
+    if (op.rows)  // query preprocessing (Sec. 5): PDX-BOND visit orders
+        PDX_TRY(launch_order(qd, op.rows, d, op.per_part ? ix->means : ix->cmean, op.per_part, nullptr, op.mode,
+                             std::max(1, (int)o.zone_dims), qorder, st));
     PDX_TRY(launch_fill_u32(reinterpret_cast<uint32_t *>(tau), 0xff800000u, nq, st));  // ordered +inf
     PDX_TRY(cudaMemsetAsync(counters, 0, C_COUNT * 8, st));
     PDX_TRY(cudaMemsetAsync(work, 0, 8, st));
@@ -527,9 +596,12 @@ extern "C" pdx_status pdx_search_exact(const pdx_index *ix, const float *q, int6
     if (p.sel_count < 0) p.sel_count = 0;
     p.zone_dims = (int)o.zone_dims;
     p.order = (int)o.order;
+    p.ctas_per_sm = (int)o.ctas_per_sm;
     p.gamma = (float)d * 1.1920929e-7f;  // D * 2^-23
     p.eps0 = o.eps0;
     p.bsa_m = o.bsa_m;
+    p.qorder = qorder;
+    p.qorder_per_part = op.per_part;
     if (o.scan_event_start) PDX_TRY(cudaEventRecord(static_cast<cudaEvent_t>(o.scan_event_start), st));
     PDX_TRY(launch_scan(pl.pruner, pl.metric, p, sms, st));
     if (o.scan_event_stop) PDX_TRY(cudaEventRecord(static_cast<cudaEvent_t>(o.scan_event_stop), st));
@@ -560,17 +632,411 @@ extern "C" pdx_status pdx_search_exact(const pdx_index *ix, const float *q, int6
     return PDX_OK;
 }
 
+
+namespace pdx {
+
+// splitmix64: picks the initial k-means centroids from the seed
+static uint64_t splitmix64(uint64_t &st) {
+    uint64_t z = (st += 0x9E3779B97F4A7C15ull);
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+// Check points of the doubling fetch schedule (dimensions visited at each
+// prune test): first_step, first_step*3, ... strictly below d.
+static std::vector<int32_t> check_points(int d, int first_step) {
+    std::vector<int32_t> c;
+    int pos = 0, step = std::max(1, first_step);
+    while (true) {
+        pos = std::min(d, pos + step);
+        if (pos >= d) break;
+        c.push_back(pos);
+        step *= 2;
+    }
+    return c;
+}
+
+// PCA of the (sample of the) vectors for BSA: rot rows = eigenvectors of the
+// covariance by decreasing eigenvalue (ties: lower index), shift = mean,
+// var = eigenvalues (clamped at 0).
+static pdx_status build_pca(pdx_index *ix, const float *xd, int64_t m, cudaStream_t st) {
+    const int d = ix->d;
+    Scratch scr(st);
+    const size_t nwork = (size_t)d * d * 2 + 2 * (size_t)(d + 1) + (size_t)(d + 2);
+    size_t need = rup((size_t)d * 8) + 2 * rup((size_t)d * d * 8) + rup(nwork * 8);
+    PDX_TRY(scr.reserve(need));
+    double *sum = scr.take<double>(d);
+    double *A = scr.take<double>((size_t)d * d);
+    double *V = scr.take<double>((size_t)d * d);
+    double *work = scr.take<double>(nwork);
+    PDX_CHECK_SCRATCH(scr);
+    PDX_TRY(launch_column_stats(xd, m, d, sum, A, st));
+    std::vector<double> hs(d), hA((size_t)d * d);
+    PDX_TRY(cudaMemcpyAsync(hs.data(), sum, (size_t)d * 8, cudaMemcpyDeviceToHost, st));
+    PDX_TRY(cudaMemcpyAsync(hA.data(), A, (size_t)d * d * 8, cudaMemcpyDeviceToHost, st));
+    PDX_TRY(cudaStreamSynchronize(st));
+    std::vector<double> mean(d);
+    for (int j = 0; j < d; ++j) mean[j] = hs[j] / (double)m;
+    for (int i = 0; i < d; ++i)
+        for (int j = 0; j < d; ++j) hA[(size_t)i * d + j] = hA[(size_t)i * d + j] / (double)m - mean[i] * mean[j];
+    std::vector<double> eye((size_t)d * d, 0.0);
+    for (int i = 0; i < d; ++i) eye[(size_t)i * d + i] = 1.0;
+    PDX_TRY(cudaMemcpyAsync(A, hA.data(), hA.size() * 8, cudaMemcpyHostToDevice, st));
+    PDX_TRY(cudaMemcpyAsync(V, eye.data(), eye.size() * 8, cudaMemcpyHostToDevice, st));
+    PDX_TRY(jacobi_eigen(A, V, d, work, 10, st));
+    std::vector<double> hV((size_t)d * d);
+    PDX_TRY(cudaMemcpyAsync(hA.data(), A, hA.size() * 8, cudaMemcpyDeviceToHost, st));
+    PDX_TRY(cudaMemcpyAsync(hV.data(), V, hV.size() * 8, cudaMemcpyDeviceToHost, st));
+    PDX_TRY(cudaStreamSynchronize(st));
+    std::vector<int> order(d);
+    for (int i = 0; i < d; ++i) order[i] = i;
+    std::stable_sort(order.begin(), order.end(),
+                     [&](int a, int b) { return hA[(size_t)a * d + a] > hA[(size_t)b * d + b]; });
+    std::vector<float> rot((size_t)d * d), shift(d), var(d);
+    for (int r = 0; r < d; ++r) {
+        int c = order[r];
+        for (int j = 0; j < d; ++j) rot[(size_t)r * d + j] = (float)hV[(size_t)j * d + c];
+        var[r] = (float)std::max(0.0, hA[(size_t)c * d + c]);
+    }
+    for (int j = 0; j < d; ++j) shift[j] = (float)mean[j];
+    PDX_TRY(dalloc(ix, &ix->rot, (size_t)d * d));
+    PDX_TRY(dalloc(ix, &ix->shift, (size_t)d));
+    PDX_TRY(dalloc(ix, &ix->pca_var, (size_t)d));
+    PDX_TRY(cudaMemcpyAsync(ix->rot, rot.data(), rot.size() * 4, cudaMemcpyHostToDevice, st));
+    PDX_TRY(cudaMemcpyAsync(ix->shift, shift.data(), shift.size() * 4, cudaMemcpyHostToDevice, st));
+    PDX_TRY(cudaMemcpyAsync(ix->pca_var, var.data(), var.size() * 4, cudaMemcpyHostToDevice, st));
+    PDX_TRY(cudaStreamSynchronize(st));
+    return PDX_OK;
+}
+
+static pdx_status ivf_build_impl(pdx_index *ix, const float *x, const pdx_ivf_opts &o, cudaStream_t st) {
+    const int64_t n = ix->n;
+    const int d = ix->d;
+    const int nlist = (int)o.nlist;
+    Scratch scr(st);
+    const bool xdev = is_device_ptr(x);
+    const bool tr = o.transform != PDX_PRUNE_NONE;
+    const int64_t mtrain = (o.kmeans_sample > 0 && (int64_t)o.kmeans_sample < n) ? (int64_t)o.kmeans_sample : n;
+    size_t need = (xdev ? 0 : rup((size_t)n * d * 4)) + (tr ? rup((size_t)n * d * 4) : 0) +
+                  rup((size_t)nlist * d * 4) + rup((size_t)nlist * 4) + rup((size_t)n * 4) + rup((size_t)nlist * d * 4);
+    PDX_TRY(scr.reserve(need));
+    const float *xd = x;
+    if (!xdev) {
+        float *t = scr.take<float>((size_t)n * d);
+        PDX_CHECK_SCRATCH(scr);
+        PDX_TRY(cudaMemcpyAsync(t, x, (size_t)n * d * 4, cudaMemcpyHostToDevice, st));
+        xd = t;
+    }
+    // Sec. 2.3: ADSampling stores R x (random orthogonal R, given by the
+    // caller); BSA stores the PCA projection W^T (x - mean)
+    const float *xt = xd;
+    if (tr) {
+        float *t = scr.take<float>((size_t)n * d);
+        PDX_CHECK_SCRATCH(scr);
+        if (o.transform == PDX_PRUNE_ADSAMPLING) {
+            PDX_TRY(dalloc(ix, &ix->rot, (size_t)d * d));
+            PDX_TRY(cudaMemcpyAsync(ix->rot, o.rotation, (size_t)d * d * 4, cudaMemcpyDefault, st));
+            PDX_TRY(launch_transform(xd, n, d, ix->rot, nullptr, t, st));
+        } else {
+            pdx_status s = build_pca(ix, xd, std::min<int64_t>(n, 262144), st);
+            if (s != PDX_OK) return s;
+            PDX_TRY(launch_transform(xd, n, d, ix->rot, ix->shift, t, st));
+        }
+        xt = t;
+    }
+    // Lloyd's k-means (Sec. 2.1) on the first mtrain transformed vectors
+    float *sums = scr.take<float>((size_t)nlist * d);
+    int32_t *counts = scr.take<int32_t>((size_t)nlist);
+    int32_t *tassign = scr.take<int32_t>((size_t)n);
+    float *cinit = scr.take<float>((size_t)nlist * d);
+    PDX_CHECK_SCRATCH(scr);
+    PDX_TRY(dalloc(ix, &ix->centroids, (size_t)nlist * d));
+    if (o.init_centroids) {
+        PDX_TRY(cudaMemcpyAsync(cinit, o.init_centroids, (size_t)nlist * d * 4, cudaMemcpyDefault, st));
+        if (tr)
+            PDX_TRY(launch_transform(cinit, nlist, d, ix->rot, ix->shift, ix->centroids, st));
+        else
+            PDX_TRY(cudaMemcpyAsync(ix->centroids, cinit, (size_t)nlist * d * 4, cudaMemcpyDeviceToDevice, st));
+    } else {
+        // nlist distinct training vectors chosen by a seeded partial shuffle
+        std::vector<int64_t> pick((size_t)mtrain);
+        for (int64_t i = 0; i < mtrain; ++i) pick[(size_t)i] = i;
+        uint64_t sm = o.seed;
+        for (int c = 0; c < nlist; ++c) {
+            int64_t j = c + (int64_t)(splitmix64(sm) % (uint64_t)(mtrain - c));
+            std::swap(pick[(size_t)c], pick[(size_t)j]);
+            PDX_TRY(cudaMemcpyAsync(ix->centroids + (size_t)c * d, xt + (size_t)pick[(size_t)c] * d, (size_t)d * 4,
+                                    cudaMemcpyDeviceToDevice, st));
+        }
+    }
+    for (uint32_t it = 0; it < o.kmeans_iters; ++it) {
+        PDX_TRY(launch_nearest_centroids(xt, mtrain, d, ix->centroids, nullptr, nlist, tassign, nullptr, st));
+        PDX_TRY(launch_kmeans_update(xt, mtrain, d, tassign, nlist, sums, counts, ix->centroids, st));
+    }
+    PDX_TRY(dalloc(ix, &ix->assign, (size_t)n));
+    PDX_TRY(launch_nearest_centroids(xt, n, d, ix->centroids, nullptr, nlist, ix->assign, nullptr, st));
+    // buckets = PDXearch blocks (Fig. 2): vectors grouped by bucket, id order inside
+    std::vector<int32_t> ha((size_t)n);
+    PDX_TRY(cudaMemcpyAsync(ha.data(), ix->assign, (size_t)n * 4, cudaMemcpyDeviceToHost, st));
+    PDX_TRY(cudaStreamSynchronize(st));
+    std::vector<int64_t> part_row((size_t)nlist + 1, 0);
+    for (int64_t i = 0; i < n; ++i) part_row[(size_t)ha[(size_t)i] + 1] += 1;
+    for (int c = 0; c < nlist; ++c) part_row[(size_t)c + 1] += part_row[(size_t)c];
+    std::vector<int64_t> fill(part_row.begin(), part_row.end() - 1);
+    std::vector<int32_t> rows((size_t)n);
+    for (int64_t i = 0; i < n; ++i) rows[(size_t)fill[(size_t)ha[(size_t)i]]++] = (int32_t)i;
+    pdx_status s = layout_parts(ix, xt, rows, part_row, st);
+    if (s != PDX_OK) return s;
+    // centroids in PDX layout too (Sec. 6.4: the bucket search uses the PDX kernel)
+    ix->c_nblocks = (nlist + kBlock - 1) / kBlock;
+    std::vector<int32_t> cids((size_t)ix->c_nblocks * kBlock, -1);
+    for (int c = 0; c < nlist; ++c) cids[(size_t)c] = c;
+    PDX_TRY(dalloc(ix, &ix->cids, cids.size()));
+    PDX_TRY(dalloc(ix, &ix->cdata, (size_t)ix->c_nblocks * d * kBlock));
+    PDX_TRY(cudaMemcpyAsync(ix->cids, cids.data(), cids.size() * 4, cudaMemcpyHostToDevice, st));
+    PDX_TRY(launch_to_pdx(ix->centroids, d, ix->cids, ix->c_nblocks, ix->cdata, st));
+    if (o.transform == PDX_PRUNE_BSA) {
+        std::vector<int32_t> chk = check_points(d, ix->bsa_first_step);
+        ix->bsa_nchk = (int)chk.size();
+        if (ix->bsa_nchk > 0) {
+            PDX_TRY(dalloc(ix, &ix->chk, chk.size()));
+            PDX_TRY(dalloc(ix, &ix->resid, (size_t)ix->nblocks * ix->bsa_nchk * kBlock));
+            PDX_TRY(cudaMemcpyAsync(ix->chk, chk.data(), chk.size() * 4, cudaMemcpyHostToDevice, st));
+            PDX_TRY(launch_bsa_resid(ix->data, ix->blk_cnt, ix->nblocks, d, ix->chk, ix->bsa_nchk, ix->resid, st));
+        }
+    }
+    PDX_TRY(cudaStreamSynchronize(st));
+    return PDX_OK;
+}
+
+}  // namespace pdx
+
 extern "C" pdx_status pdx_ivf_build(const float *x, int64_t n, int32_t d, const pdx_ivf_opts *opts, void *stream,
                                     pdx_index **out) {
-    (void)x; (void)n; (void)d; (void)opts; (void)stream;
     if (out) *out = nullptr;
-    set_error("pdx_ivf_build: not implemented in this build");
-    return PDX_ERR_UNSUPPORTED;
+    if (!x || !out || !opts) {
+        set_error("pdx_ivf_build: NULL x, opts or out");
+        return PDX_ERR_ARG;
+    }
+    if (opts->struct_size < sizeof(pdx_ivf_opts)) {
+        set_error("pdx_ivf_build: opts->struct_size %u < %zu", opts->struct_size, sizeof(pdx_ivf_opts));
+        return PDX_ERR_ARG;
+    }
+    const pdx_ivf_opts o = *opts;
+    if (n < 1 || n >= (int64_t)1 << 31 || d < 1 || d > kMaxD || o.nlist < 1 || (int64_t)o.nlist > n) {
+        set_error("pdx_ivf_build: n=%lld d=%d nlist=%u out of range", (long long)n, d, o.nlist);
+        return PDX_ERR_ARG;
+    }
+    if (!valid_metric(o.base.metric) || o.transform < PDX_PRUNE_NONE || o.transform > PDX_PRUNE_BSA ||
+        o.transform == PDX_PRUNE_BOND) {
+        set_error("pdx_ivf_build: bad metric %d or transform %d", (int)o.base.metric, (int)o.transform);
+        return PDX_ERR_ARG;
+    }
+    if (o.kmeans_sample != 0 && o.kmeans_sample < o.nlist) {
+        set_error("pdx_ivf_build: kmeans_sample=%u must be 0 (all) or >= nlist=%u", o.kmeans_sample, o.nlist);
+        return PDX_ERR_ARG;
+    }
+    if (o.transform == PDX_PRUNE_ADSAMPLING && !o.rotation) {
+        set_error("pdx_ivf_build: ADSampling needs the caller's d*d orthogonal rotation");
+        return PDX_ERR_ARG;
+    }
+    if (o.base.storage != PDX_F32) {
+        set_error("pdx_ivf_build: only F32 storage is implemented");
+        return PDX_ERR_UNSUPPORTED;
+    }
+    if (o.transform != PDX_PRUNE_NONE && o.base.metric != PDX_L2) {
+        set_error("pdx_ivf_build: ADSampling/BSA transforms are defined for L2 only");
+        return PDX_ERR_UNSUPPORTED;
+    }
+    pdx_index *ix = new (std::nothrow) pdx_index();
+    if (!ix) {
+        set_error("host allocation failed");
+        return PDX_ERR_OOM;
+    }
+    ix->n = n;
+    ix->d = d;
+    ix->metric = o.base.metric;
+    ix->storage = o.base.storage;
+    ix->is_ivf = 1;
+    ix->transform = o.transform;
+    cudaGetDevice(&ix->device);
+    pdx_status s = ivf_build_impl(ix, x, o, static_cast<cudaStream_t>(stream));
+    if (s != PDX_OK) {
+        free_index(ix);
+        return s;
+    }
+    *out = ix;
+    return PDX_OK;
 }
 
 extern "C" pdx_status pdx_search_ivf(const pdx_index *ix, const float *q, int64_t nq, int32_t k, int32_t nprobe,
                                      const pdx_search_opts *opts, float *out_dist, int64_t *out_idx, void *stream) {
-    (void)ix; (void)q; (void)nq; (void)k; (void)nprobe; (void)opts; (void)out_dist; (void)out_idx; (void)stream;
-    set_error("pdx_search_ivf: not implemented in this build");
-    return PDX_ERR_UNSUPPORTED;
+    const char *fn = "pdx_search_ivf";
+    pdx_search_opts o;
+    pdx_status s = check_search_args(ix, q, nq, k, opts, out_dist, out_idx, &o, fn);
+    if (s != PDX_OK) return s;
+    if (!ix->is_ivf) {
+        set_error("%s: index was not built by pdx_ivf_build", fn);
+        return PDX_ERR_ARG;
+    }
+    if (nprobe < 1 || nprobe > ix->nparts || nprobe > 4096) {
+        set_error("%s: nprobe=%d outside [1, min(nlist=%d, 4096)]", fn, nprobe, ix->nparts);
+        return PDX_ERR_ARG;
+    }
+    if ((o.pruner == PDX_PRUNE_ADSAMPLING && ix->transform != PDX_PRUNE_ADSAMPLING) ||
+        (o.pruner == PDX_PRUNE_BSA && ix->transform != PDX_PRUNE_BSA)) {
+        set_error("%s: pruner %d needs an index built with that transform", fn, (int)o.pruner);
+        return PDX_ERR_ARG;
+    }
+    // BSA's residual norms were stored at the check points of one fetch
+    // schedule: a BSA search always uses that schedule
+    if (o.pruner == PDX_PRUNE_BSA) o.first_step = (uint32_t)ix->bsa_first_step;
+    if (q && (q == out_dist || (const void *)q == (const void *)out_idx)) {
+        set_error("%s: outputs alias the queries", fn);
+        return PDX_ERR_ARG;
+    }
+    SearchPlan pl;
+    s = plan_metric(ix, o.pruner, &pl, fn);
+    if (s != PDX_OK) return s;
+    if (nq == 0) return PDX_OK;
+    if (is_device_ptr(out_dist) != is_device_ptr(out_idx)) {
+        set_error("%s: out_dist and out_idx must both be host or both be device memory", fn);
+        return PDX_ERR_ARG;
+    }
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const int d = ix->d;
+    const bool q_dev = is_device_ptr(q);
+    const bool o_dev = is_device_ptr(out_dist);
+    const bool tr = ix->transform != PDX_PRUNE_NONE;
+    const int sms = num_sms();
+    const int64_t Lc = (int64_t)ix->c_nblocks * kBlock;
+    const int nchk = (o.pruner == PDX_PRUNE_BSA) ? ix->bsa_nchk : 0;
+    int max_blk = 0;
+    for (int p = 0; p < ix->nparts; ++p) max_blk = std::max(max_blk, ix->h_part_blk[p + 1] - ix->h_part_blk[p]);
+    const OrderPlan op = plan_orders(ix, o, pl.pruner, nq, nprobe);
+
+    Scratch scr(st);
+    size_t need = rup(op.bytes) + (q_dev ? 0 : rup((size_t)nq * d * 4)) + (tr ? rup((size_t)nq * d * 4) : 0) +
+                  rup((size_t)nq * Lc * 8) + rup((size_t)nq * nprobe * 8) + rup((size_t)nq * nprobe * 4) +
+                  rup((size_t)nq * 4) + rup((size_t)nq * nprobe * k * 8) + 3 * rup((size_t)nq * k * 8) +
+                  rup(C_COUNT * 8) + rup(16) + rup((size_t)nq * (nchk + 1) * 8) +
+                  (o_dev ? 0 : rup((size_t)nq * k * 4) + rup((size_t)nq * k * 8));
+    PDX_TRY(scr.reserve(need));
+    const float *qd = q;
+    if (!q_dev) {
+        float *t = scr.take<float>((size_t)nq * d);
+        PDX_CHECK_SCRATCH(scr);
+        PDX_TRY(cudaMemcpyAsync(t, q, (size_t)nq * d * 4, cudaMemcpyHostToDevice, st));
+        qd = t;
+    }
+    const float *qt = qd;
+    if (tr) {
+        float *t = scr.take<float>((size_t)nq * d);
+        PDX_CHECK_SCRATCH(scr);
+        PDX_TRY(launch_transform(qd, nq, d, ix->rot, ix->shift, t, st));
+        qt = t;
+    }
+    uint64_t *pkeys = scr.take<uint64_t>((size_t)nq * Lc);
+    uint64_t *ptopk = scr.take<uint64_t>((size_t)nq * nprobe);
+    int32_t *probes = scr.take<int32_t>((size_t)nq * nprobe);
+    float *tau = scr.take<float>((size_t)nq);
+    uint64_t *cand = scr.take<uint64_t>((size_t)nq * nprobe * k);
+    uint64_t *topk = scr.take<uint64_t>((size_t)nq * k);
+    uint64_t *refined = scr.take<uint64_t>((size_t)nq * k);
+    uint64_t *final_keys = scr.take<uint64_t>((size_t)nq * k);
+    unsigned long long *counters = scr.take<unsigned long long>(C_COUNT);
+    int *work = scr.take<int>(4);
+    float *qaux = scr.take<float>((size_t)nq * (nchk + 1) * 2);
+    uint16_t *qorder = op.rows ? scr.take<uint16_t>((size_t)op.rows * d) : nullptr;
+    float *od = out_dist;
+    int64_t *oi = out_idx;
+    if (!o_dev) {
+        od = scr.take<float>((size_t)nq * k);
+        oi = scr.take<int64_t>((size_t)nq * k);
+    }
+    PDX_CHECK_SCRATCH(scr);
+    // nearest buckets: PDX scan of the centroids, then the nprobe best per query
+    PDX_TRY(launch_dense_keys(qt, nq, ix->cdata, ix->cids, d, ix->c_nblocks, PDX_L2, pkeys, st));
+    PDX_TRY(launch_select_k(pkeys, nq, Lc, nprobe, ptopk, st));
+    PDX_TRY(launch_keys_to_parts(ptopk, nq, nprobe, probes, st));
+    if (nchk > 0) PDX_TRY(launch_bsa_qaux(qt, nq, d, ix->pca_var, ix->chk, nchk, qaux, st));
+    if (op.rows)  // PDX-BOND visit orders against the probed buckets' (or the collection's) means
+        PDX_TRY(launch_order(qt, op.rows, d, op.per_part ? ix->means : ix->cmean, op.per_part,
+                             op.per_part ? probes : nullptr, op.mode, std::max(1, (int)o.zone_dims), qorder, st));
+    PDX_TRY(launch_fill_u32(reinterpret_cast<uint32_t *>(tau), 0xff800000u, nq, st));
+    PDX_TRY(cudaMemsetAsync(counters, 0, C_COUNT * 8, st));
+    PDX_TRY(cudaMemsetAsync(work, 0, 16, st));
+    unsigned long long *kc = o.stats_device ? reinterpret_cast<unsigned long long *>(o.stats_device) : counters;
+    ScanParams p;
+    std::memset(&p, 0, sizeof p);
+    p.data = ix->data;
+    p.ids = ix->ids;
+    p.blk_cnt = ix->blk_cnt;
+    p.part_blk = ix->part_blk;
+    p.d = d;
+    p.q = qt;
+    p.nq = nq;
+    p.means = ix->means;
+    p.probes = probes;
+    p.nslots = nprobe;
+    p.chunks_per_part = 1;
+    p.blocks_per_item = std::max(1, max_blk);
+    p.k = k;
+    p.tau = tau;
+    p.cand = cand;
+    p.counters = kc;
+    p.first_step = (int)o.first_step;
+    p.sel_count = std::min(kMaxSurv, (int)std::ceil(o.selection_threshold * kBlock) - 1);
+    if (p.sel_count < 0) p.sel_count = 0;
+    p.zone_dims = (int)o.zone_dims;
+    p.order = (int)o.order;
+    p.ctas_per_sm = (int)o.ctas_per_sm;
+    p.gamma = (float)d * 1.1920929e-7f;
+    p.eps0 = o.eps0;
+    p.bsa_m = o.bsa_m;
+    p.qaux = qaux;
+    p.resid = ix->resid;
+    p.nchk = nchk;
+    p.qorder = qorder;
+    p.qorder_per_part = op.per_part;
+    if (o.scan_event_start) PDX_TRY(cudaEventRecord(static_cast<cudaEvent_t>(o.scan_event_start), st));
+    // START (Sec. 4): the nearest bucket of every query, starting from tau = +inf
+    p.slot0 = 0;
+    p.nitems = nq;
+    p.work_counter = work;
+    PDX_TRY(launch_scan(pl.pruner, pl.metric, p, sms, st));
+    // WARMUP/PRUNE over the remaining buckets with the thresholds START produced
+    if (nprobe > 1) {
+        p.slot0 = 1;
+        p.nitems = nq * (int64_t)(nprobe - 1);
+        p.work_counter = work + 2;
+        PDX_TRY(launch_scan(pl.pruner, pl.metric, p, sms, st));
+    }
+    if (o.scan_event_stop) PDX_TRY(cudaEventRecord(static_cast<cudaEvent_t>(o.scan_event_stop), st));
+    PDX_TRY(launch_select_k(cand, nq, (int64_t)nprobe * k, k, topk, st));
+    PDX_TRY(launch_refine(topk, nq, k, qt, d, ix->data, ix->slot_of, ix->metric, refined, st));
+    PDX_TRY(launch_select_k(refined, nq, k, k, final_keys, st));
+    PDX_TRY(launch_write_out(final_keys, nq, k, pl.out_mode, qt, d, od, oi, st));
+    if (!o_dev) {
+        PDX_TRY(cudaMemcpyAsync(out_dist, od, (size_t)nq * k * 4, cudaMemcpyDeviceToHost, st));
+        PDX_TRY(cudaMemcpyAsync(out_idx, oi, (size_t)nq * k * 8, cudaMemcpyDeviceToHost, st));
+    }
+    if (o.stats_out) {
+        unsigned long long c[C_COUNT];
+        PDX_TRY(cudaMemcpyAsync(c, kc, sizeof c, cudaMemcpyDeviceToHost, st));
+        PDX_TRY(cudaStreamSynchronize(st));
+        pdx_search_stats *so = o.stats_out;
+        std::memset(so, 0, sizeof *so);
+        so->values_visited = c[C_VALUES];
+        so->vectors_scanned = c[C_SCANNED];
+        so->vectors_pruned = c[C_PRUNED];
+        so->prune_phase_blocks = c[C_PRUNE_BLOCKS];
+        so->candidates = c[C_CANDIDATES];
+        so->work_items = c[C_ITEMS];
+        so->start_values = c[C_START];
+        so->bytes_logical = (c[C_VALUES] + c[C_START]) * 4ull;
+    }
+    if (!o_dev) PDX_TRY(cudaStreamSynchronize(st));
+    return PDX_OK;
 }

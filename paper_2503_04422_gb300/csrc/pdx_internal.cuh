@@ -16,6 +16,7 @@ constexpr int kBlock = 64;
 constexpr int kMaxSurv = 16;   // PRUNE-phase survivors held in registers (selection <= 25%)
 constexpr int kMaxK = 1024;
 constexpr int kMaxD = 4096;
+constexpr int kMaxSortUnits = 256;  // zone keys a scan warp sorts in-kernel (8 per lane)
 
 // Device counters, in the order of the first fields of pdx_search_stats.
 enum Counter {
@@ -50,6 +51,7 @@ struct pdx_index {
     int32_t *blk_cnt = nullptr;     // [nblocks] valid lanes per block
     int32_t *part_blk = nullptr;    // [nparts+1]
     float *means = nullptr;         // [nparts][d]
+    float *cmean = nullptr;         // [d] collection means
     float *centroids = nullptr;     // [nparts][d] (IVF)
     float *centroid_norms = nullptr;// [nparts]
     int32_t *assign = nullptr;      // [n] (IVF)
@@ -58,7 +60,11 @@ struct pdx_index {
     float *pca_var = nullptr;       // [d] (BSA: variance of each projected dimension)
     float *resid = nullptr;         // BSA: [nblocks][nchk][64] squared residual norms
     int32_t bsa_nchk = 0;           // BSA: number of check points stored
-    int32_t bsa_first_step = 2;     // BSA: schedule the residual norms were taken for
+    int32_t bsa_first_step = 4;     // BSA: fetch schedule the residual norms were taken for
+    int32_t *chk = nullptr;         // BSA: [bsa_nchk] dimensions visited at each check point
+    float *cdata = nullptr;         // IVF centroids in PDX layout [c_nblocks][d][64]
+    int32_t *cids = nullptr;        // [c_nblocks*64] bucket id per slot, -1 = padding
+    int32_t c_nblocks = 0;
     // host mirrors
     int32_t *h_part_blk = nullptr;  // [nparts+1]
     uint64_t bytes = 0;
@@ -122,6 +128,7 @@ struct ScanParams {
     const int32_t *probes;     // [nq][nslots] part per slot, or null (slot -> part0 + slot/chunks)
     int32_t nslots;            // items per query
     int32_t part0;
+    int32_t slot0;             // first slot this launch covers (item w -> slot slot0 + w / nq)
     int32_t chunks_per_part;   // exact search: block groups per partition
     int32_t blocks_per_item;
     int32_t k;
@@ -134,14 +141,31 @@ struct ScanParams {
     int32_t sel_count;         // PRUNE when survivors <= sel_count
     int32_t zone_dims;
     int32_t order;
+    int32_t ctas_per_sm;       // resident CTAs per SM the launch is shaped for
     float gamma;               // relative slack covering FP32 rounding of partial sums
     float eps0;
     float bsa_m;
+    const uint16_t *qorder;    // optional precomputed visit orders ([nq] or [nq][nparts] rows of d)
+    int32_t qorder_per_part;   // rows indexed by (query, part rank) instead of query
     const float *qaux;         // BSA: [nq][nchk][2] (||q_r||^2, s_d(q)^2) per check point
     const float *resid;        // BSA: [nblocks][nchk][64]
     int32_t nchk;
 };
 cudaError_t launch_scan(int pruner, int metric, const ScanParams &p, int num_sms, cudaStream_t st);
+// Visit orders for PDX-BOND (mode 0 distance to means with zones of Z, mode 1
+// decreasing query value); per_part > 0: one row per (query, part) with
+// means[part], else one row per query with means[0..d).
+cudaError_t launch_order(const float *q, int64_t rows, int32_t d, const float *means, int32_t per_part,
+                         const int32_t *row_part, int mode, int32_t Z, uint16_t *out, cudaStream_t st);
+
+// How a search gets its PDX-BOND visit orders (see plan_orders).
+struct OrderPlan {
+    int mode = -1;        // -1: none precomputed (in-kernel zones or storage order); 0: to means; 1: decreasing
+    int per_part = 0;     // >0: rows per query (one per part rank); 0: one row per query
+    int64_t rows = 0;
+    size_t bytes = 0;
+};
+OrderPlan plan_orders(const pdx_index *ix, const pdx_search_opts &o, int pruner, int64_t nq, int parts_per_query);
 size_t scan_warp_smem(int d, int k, int zone_dims, int order);
 
 // START: exact distances of every query to the first `nvec` stored vectors,
@@ -177,11 +201,13 @@ cudaError_t launch_keys_to_parts(const uint64_t *topk, int64_t nq, int32_t nprob
 // y[rows][d] = (x[rows][d] - shift) * M^T   (M row-major d x d), FP32.
 cudaError_t launch_transform(const float *x, int64_t rows, int32_t d, const float *M, const float *shift,
                              float *y, cudaStream_t st);
-cudaError_t launch_column_stats(const float *x, int64_t n, int32_t d, double *sum, double *cov,
+cudaError_t launch_column_stats(const float *x, int64_t n, int32_t d, double *sum, double *gram,
                                 cudaStream_t st);
 cudaError_t launch_bsa_resid(const float *data, const int32_t *blk_cnt, int64_t nblocks, int32_t d,
                              const int32_t *chk, int32_t nchk, float *resid, cudaStream_t st);
 cudaError_t launch_bsa_qaux(const float *q, int64_t nq, int32_t d, const float *var, const int32_t *chk,
                             int32_t nchk, float *qaux, cudaStream_t st);
+cudaError_t jacobi_eigen(double *A, double *V, int32_t dd, double *work, int sweeps, cudaStream_t st);
+cudaError_t launch_offdiag(const double *A, int32_t dd, double *out, cudaStream_t st);
 
 }  // namespace pdx

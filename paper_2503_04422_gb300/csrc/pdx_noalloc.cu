@@ -117,8 +117,9 @@ extern "C" pdx_status pdx_search_exact_noalloc(const pdx_index *ix, const float 
     }
     const int64_t Lstart = (int64_t)start_blk * kBlock;
 
+    const OrderPlan op = plan_orders(ix, o, pl.pruner, nq, ix->nparts);
     size_t need = r256((size_t)nq * 4) + r256((size_t)nq * nslots * k * 8) + 3 * r256((size_t)nq * k * 8) +
-                  r256(C_COUNT * 8) + r256(8);
+                  r256(C_COUNT * 8) + r256(8) + r256(op.bytes);
     if (start) need += r256((size_t)nq * Lstart * 8) + r256((size_t)nq * k * 8);
     if (need > kNoAllocScratchBytes) {
         set_error("%s: this search needs %zu bytes of scratch but the static array holds %zu; "
@@ -143,6 +144,7 @@ extern "C" pdx_status pdx_search_exact_noalloc(const pdx_index *ix, const float 
     int *work = reinterpret_cast<int *>(take(8));
     uint64_t *skeys = start ? reinterpret_cast<uint64_t *>(take((size_t)nq * Lstart * 8)) : nullptr;
     uint64_t *stopk = start ? reinterpret_cast<uint64_t *>(take((size_t)nq * k * 8)) : nullptr;
+    uint16_t *qorder = op.rows ? reinterpret_cast<uint16_t *>(take(op.bytes)) : nullptr;
 
 #define NOALLOC_TRY(call)                                                                             \
     do {                                                                                              \
@@ -155,6 +157,9 @@ extern "C" pdx_status pdx_search_exact_noalloc(const pdx_index *ix, const float 
 
     // the array keeps the previous call's contents: reset everything that must
     // start from a known value (thresholds, counters, the work counter)
+    if (op.rows)
+        NOALLOC_TRY(launch_order(q, op.rows, d, op.per_part ? ix->means : ix->cmean, op.per_part, nullptr, op.mode,
+                                 std::max(1, (int)o.zone_dims), qorder, st));
     NOALLOC_TRY(launch_fill_u32(reinterpret_cast<uint32_t *>(tau), 0xff800000u, nq, st));
     NOALLOC_TRY(cudaMemsetAsync(counters, 0, C_COUNT * 8, st));
     NOALLOC_TRY(cudaMemsetAsync(work, 0, 8, st));
@@ -189,9 +194,12 @@ extern "C" pdx_status pdx_search_exact_noalloc(const pdx_index *ix, const float 
     if (p.sel_count < 0) p.sel_count = 0;
     p.zone_dims = (int)o.zone_dims;
     p.order = (int)o.order;
+    p.ctas_per_sm = (int)o.ctas_per_sm;
     p.gamma = (float)d * 1.1920929e-7f;
     p.eps0 = o.eps0;
     p.bsa_m = o.bsa_m;
+    p.qorder = qorder;
+    p.qorder_per_part = op.per_part;
     if (o.scan_event_start) NOALLOC_TRY(cudaEventRecord(static_cast<cudaEvent_t>(o.scan_event_start), st));
     NOALLOC_TRY(launch_scan(pl.pruner, pl.metric, p, sms, st));
     if (o.scan_event_stop) NOALLOC_TRY(cudaEventRecord(static_cast<cudaEvent_t>(o.scan_event_stop), st));

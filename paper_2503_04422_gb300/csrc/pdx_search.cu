@@ -67,25 +67,6 @@ __device__ __forceinline__ int next_pow2(int v) {
     return p;
 }
 
-// Warp-wide ascending bitonic sort of n (power of two) keys in shared memory.
-__device__ void warp_bitonic_sort(uint64_t *s, int n, int lane) {
-    for (int size = 2; size <= n; size <<= 1) {
-        for (int stride = size >> 1; stride > 0; stride >>= 1) {
-            for (int i = lane; i < (n >> 1); i += 32) {
-                int lo = 2 * i - (i & (stride - 1));
-                int hi = lo + stride;
-                bool asc = (lo & size) == 0;
-                uint64_t a = s[lo], b = s[hi];
-                if ((a > b) == asc) {
-                    s[lo] = b;
-                    s[hi] = a;
-                }
-            }
-            __syncwarp();
-        }
-    }
-}
-
 // Insert `key` into the warp's ascending list (capacity k). Warp-uniform call.
 __device__ __forceinline__ void topk_insert(uint64_t *list, int &cnt, int k, uint64_t key, int lane) {
     if (cnt == k && key >= list[k - 1]) return;
@@ -112,21 +93,20 @@ __device__ __forceinline__ void topk_insert(uint64_t *list, int &cnt, int k, uin
 }
 
 struct WarpSmem {
-    uint64_t *sortbuf;  // [npad] (BOND order only)
     uint16_t *ord;      // [d] dimension visited at position i
-    float *qo;          // [d] query value at position i
+    float *qo;          // [d] query value of that dimension
     uint64_t *topk;     // [k]
     int32_t *sv;        // [kMaxSurv] survivor slot indices
     float *sp;          // [kMaxSurv] survivor partial distances
 };
 
-__host__ __device__ inline size_t align16(size_t v) { return (v + 15) & ~size_t(15); }
+// The scan kernel sorts at most kMaxSortUnits zone keys itself, in registers
+// (8 per lane); finer orders are computed once per query (or per query and
+// part) by order_kernel. Shared memory per warp is kept to 6 bytes per
+// dimension: the kernel's loads are latency-bound, and every byte of shared
+// memory is taken from the L1 that holds the lines of loads in flight.
 
-__host__ __device__ inline int sort_units(int d, int zone_dims, int order, int pruner) {
-    if (pruner != PR_BOND || order == PDX_ORDER_SEQUENTIAL) return 0;
-    int z = (order == PDX_ORDER_DIST_TO_MEANS) ? (zone_dims < 1 ? 1 : zone_dims) : 1;
-    return (d + z - 1) / z;
-}
+__host__ __device__ inline size_t align16(size_t v) { return (v + 15) & ~size_t(15); }
 
 __host__ __device__ inline int pow2_ceil(int v) {
     int p = 1;
@@ -134,28 +114,26 @@ __host__ __device__ inline int pow2_ceil(int v) {
     return p;
 }
 
-__host__ __device__ inline size_t warp_smem_bytes(int d, int k, int nunits) {
-    size_t s = 0;
-    if (nunits > 0) s += align16((size_t)pow2_ceil(nunits) * 8);
-    s += align16((size_t)d * 2);
-    s += align16((size_t)d * 4);
-    s += align16((size_t)k * 8);
-    s += align16(kMaxSurv * 4) * 2;
-    return s;
+// Number of zone keys the scan kernel sorts per work item (0 = order given).
+__host__ __device__ inline int sort_units(int d, int zone_dims, int order, int pruner, bool given) {
+    if (given || pruner != PR_BOND || order != PDX_ORDER_DIST_TO_MEANS) return 0;
+    int z = zone_dims < 1 ? 1 : zone_dims;
+    return (d + z - 1) / z;
+}
+
+__host__ __device__ inline size_t warp_smem_bytes(int d, int k) {
+    return align16((size_t)d * 2) + align16((size_t)d * 4) + align16((size_t)k * 8) + align16(kMaxSurv * 4) * 2;
 }
 
 size_t scan_warp_smem(int d, int k, int zone_dims, int order) {
-    return warp_smem_bytes(d, k, sort_units(d, zone_dims, order, PR_BOND));
+    (void)zone_dims;
+    (void)order;
+    return warp_smem_bytes(d, k);
 }
 
-__device__ __forceinline__ WarpSmem carve(unsigned char *base, int d, int k, int nunits) {
+__device__ __forceinline__ WarpSmem carve(unsigned char *base, int d, int k) {
     WarpSmem w;
     size_t o = 0;
-    w.sortbuf = nullptr;
-    if (nunits > 0) {
-        w.sortbuf = reinterpret_cast<uint64_t *>(base + o);
-        o += align16((size_t)pow2_ceil(nunits) * 8);
-    }
     w.ord = reinterpret_cast<uint16_t *>(base + o);
     o += align16((size_t)d * 2);
     w.qo = reinterpret_cast<float *>(base + o);
@@ -168,14 +146,62 @@ __device__ __forceinline__ WarpSmem carve(unsigned char *base, int d, int k, int
     return w;
 }
 
-// Visit order of one (query, PDXearch block) item (Sec. 5): dimension zones
-// (contiguous groups of zone_dims dimensions) ranked by the summed squared
-// distance of the query to the block means, best zone first, dimensions in
-// storage order inside a zone; zone_dims = 1 is the per-dimension
-// distance-to-means order. DECREASING ranks single dimensions by the query
-// value. Ties go to the lower zone / dimension index.
+// Ascending bitonic sort of 32*M keys held in registers, element e = t*32 + lane
+// in key[t]: strides >= 32 compare registers of the same lane, strides < 32
+// exchange with lane ^ stride.
+template <int M>
+__device__ __forceinline__ void reg_bitonic_sort(uint64_t (&key)[8], int lane) {
+#pragma unroll
+    for (int size = 2; size <= 32 * M; size <<= 1) {
+#pragma unroll
+        for (int stride = size >> 1; stride > 0; stride >>= 1) {
+            if (stride >= 32) {
+                const int ts = stride >> 5;
+#pragma unroll
+                for (int t = 0; t < M; ++t) {
+                    if ((t & ts) == 0) {
+                        const int e = t * 32 + lane;
+                        const bool asc = (e & size) == 0;
+                        uint64_t a = key[t], b = key[t ^ ts];
+                        if ((a > b) == asc) {
+                            key[t] = b;
+                            key[t ^ ts] = a;
+                        }
+                    }
+                }
+            } else {
+#pragma unroll
+                for (int t = 0; t < M; ++t) {
+                    const int e = t * 32 + lane;
+                    const bool asc = (e & size) == 0;
+                    const bool lower = (lane & stride) == 0;
+                    uint64_t other = __shfl_xor_sync(kFull, key[t], stride);
+                    uint64_t mn = key[t] < other ? key[t] : other;
+                    uint64_t mx = key[t] < other ? other : key[t];
+                    key[t] = (lower == asc) ? mn : mx;
+                }
+            }
+        }
+    }
+}
+
+// Visit order of one (query, PDXearch block) work item (Sec. 5).
+//  - given != null: a precomputed order (order_kernel) is copied in;
+//  - nunits > 0: dimension zones (zone_dims contiguous dimensions) ranked by
+//    sum over the zone of (q_j - mu_j)^2 against the block means, best zone
+//    first, storage order inside a zone, ties to the lower zone;
+//  - otherwise storage order.
 __device__ void build_order(const WarpSmem &w, const float *__restrict__ qrow, const float *__restrict__ mu,
-                            int d, int order, int zone_dims, int nunits, int lane) {
+                            const uint16_t *__restrict__ given, int d, int zone_dims, int nunits, int lane) {
+    if (given) {
+        for (int i = lane; i < d; i += 32) {
+            int j = given[i];
+            w.ord[i] = (uint16_t)j;
+            w.qo[i] = qrow[j];
+        }
+        __syncwarp();
+        return;
+    }
     if (nunits == 0) {
         for (int i = lane; i < d; i += 32) {
             w.ord[i] = (uint16_t)i;
@@ -184,40 +210,45 @@ __device__ void build_order(const WarpSmem &w, const float *__restrict__ qrow, c
         __syncwarp();
         return;
     }
-    const int Z = (order == PDX_ORDER_DIST_TO_MEANS) ? (zone_dims < 1 ? 1 : zone_dims) : 1;
-    const int npad = pow2_ceil(nunits);
-    for (int u = lane; u < npad; u += 32) {
-        uint64_t key = kEmptyKey;
+    const int Z = zone_dims < 1 ? 1 : zone_dims;
+    uint64_t key[8];
+#pragma unroll
+    for (int t = 0; t < 8; ++t) {
+        const int u = t * 32 + lane;
+        key[t] = kEmptyKey;
         if (u < nunits) {
             float sc = 0.f;
-            if (order == PDX_ORDER_DECREASING) {
-                sc = qrow[u];
-            } else {
-                int j1 = min(d, u * Z + Z);
-                for (int j = u * Z; j < j1; ++j) {
-                    float t = qrow[j] - mu[j];
-                    sc = fmaf(t, t, sc);
-                }
+            int j1 = min(d, u * Z + Z);
+            for (int j = u * Z; j < j1; ++j) {
+                float v = qrow[j] - mu[j];
+                sc = fmaf(v, v, sc);
             }
-            key = ((uint64_t)f2o(-sc) << 32) | (uint32_t)u;
+            key[t] = ((uint64_t)f2o(-sc) << 32) | (uint32_t)u;
         }
-        w.sortbuf[u] = key;
     }
-    __syncwarp();
-    warp_bitonic_sort(w.sortbuf, npad, lane);
+    const int m = (nunits + 31) >> 5;
+    if (m <= 1) reg_bitonic_sort<1>(key, lane);
+    else if (m <= 2) reg_bitonic_sort<2>(key, lane);
+    else if (m <= 4) reg_bitonic_sort<4>(key, lane);
+    else reg_bitonic_sort<8>(key, lane);
+    // rank r = t*32 + lane holds zone key[t]; rank of the last (shorter) zone
     const int lastlen = d - (nunits - 1) * Z;
     int rlast = 0;
-    for (int r = lane; r < nunits; r += 32) {
-        if ((int)(w.sortbuf[r] & 0xffffffffu) == nunits - 1) rlast = r;
-    }
+#pragma unroll
+    for (int t = 0; t < 8; ++t)
+        if (t * 32 + lane < nunits && (int)(key[t] & 0xffffffffu) == nunits - 1) rlast = t * 32 + lane;
     for (int o = 16; o; o >>= 1) rlast = max(rlast, __shfl_xor_sync(kFull, rlast, o));
-    for (int r = lane; r < nunits; r += 32) {
-        int z = (int)(w.sortbuf[r] & 0xffffffffu);
-        int off = r * Z - ((r > rlast) ? (Z - lastlen) : 0);
-        int len = (z == nunits - 1) ? lastlen : Z;
-        for (int t = 0; t < len; ++t) {
-            w.ord[off + t] = (uint16_t)(z * Z + t);
-            w.qo[off + t] = qrow[z * Z + t];
+#pragma unroll
+    for (int t = 0; t < 8; ++t) {
+        const int r = t * 32 + lane;
+        if (r < nunits) {
+            const int z = (int)(key[t] & 0xffffffffu);
+            const int off = r * Z - ((r > rlast) ? (Z - lastlen) : 0);
+            const int len = (z == nunits - 1) ? lastlen : Z;
+            for (int u = 0; u < len; ++u) {
+                w.ord[off + u] = (uint16_t)(z * Z + u);
+                w.qo[off + u] = qrow[z * Z + u];
+            }
         }
     }
     __syncwarp();
@@ -235,23 +266,33 @@ __device__ __forceinline__ bool prune_test(float partial, float thr, int dv, int
         float r = 1.f + eps0 * rsqrtf((float)dv);
         return partial * (float)D > thr * r * r * (float)dv;
     } else if (PR == PR_BSA) {
-        // Sec. 2.3 BSA_res: error quantile of the residual cross term, capped
-        // by Cauchy-Schwarz
-        float cs = sqrtf(rx2 * rq2);
-        float cross = fminf(bsa_m * sqrtf(sd2), cs);
-        return partial + rx2 + rq2 - 2.f * cross > thr;
+        // Sec. 2.3 BSA_res on PCA-projected data. Exact part (Cauchy-Schwarz):
+        // the unvisited distance is at least (||x_r|| - ||q_r||)^2. Error-
+        // quantile part: the visited PCA dimensions hold the fraction
+        // frac = F(d) of the collection's variance, so partial / F(d) estimates
+        // the full distance; it is tested against tau widened by (1 + m/sqrt(d))^2.
+        float g = sqrtf(rx2) - sqrtf(rq2);
+        if (partial + g * g > thr) return true;
+        float r = 1.f + bsa_m * rsqrtf((float)dv);
+        return partial > thr * sd2 * r * r;
     } else {
         return false;
     }
 }
 
+// Minimum resident CTAs per SM the register allocation must allow (a build-time
+// tuning knob; 1 leaves the compiler free).
+#ifndef PDX_SCAN_MIN_CTAS
+#define PDX_SCAN_MIN_CTAS 3
+#endif
+
 template <int PR, int MET>
-__global__ void __launch_bounds__(256) pdxsearch_kernel(ScanParams a) {
+__global__ void __launch_bounds__(256, PDX_SCAN_MIN_CTAS) pdxsearch_kernel(ScanParams a) {
     extern __shared__ __align__(16) unsigned char smem[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int D = a.d;
-    const int nunits = sort_units(D, a.zone_dims, a.order, PR);
-    WarpSmem w = carve(smem + (size_t)warp * warp_smem_bytes(D, a.k, nunits), D, a.k, nunits);
+    const int nunits = sort_units(D, a.zone_dims, a.order, PR, a.qorder != nullptr);
+    WarpSmem w = carve(smem + (size_t)warp * warp_smem_bytes(D, a.k), D, a.k);
     const int h = lane >> 4, sl = lane & 15;
     const int k = a.k;
     const int chunks = a.chunks_per_part;
@@ -262,7 +303,7 @@ __global__ void __launch_bounds__(256) pdxsearch_kernel(ScanParams a) {
         if (lane == 0) wi = atomicAdd(reinterpret_cast<unsigned long long *>(a.work_counter), 1ull);
         wi = __shfl_sync(kFull, wi, 0);
         if ((int64_t)wi >= a.nitems) break;
-        const int slot = (int)(wi / (unsigned long long)a.nq);
+        const int slot = a.slot0 + (int)(wi / (unsigned long long)a.nq);
         const int64_t qi = (int64_t)(wi % (unsigned long long)a.nq);
         const int pr = slot / chunks, ch = slot % chunks;
         const int part = a.probes ? a.probes[qi * (a.nslots / chunks) + pr] : a.part0 + pr;
@@ -278,8 +319,9 @@ __global__ void __launch_bounds__(256) pdxsearch_kernel(ScanParams a) {
         }
         ++c_items;
         const float *qrow = a.q + qi * D;
-        build_order(w, qrow, a.means ? a.means + (int64_t)part * D : nullptr, D, a.order, a.zone_dims, nunits,
-                    lane);
+        const uint16_t *given = nullptr;
+        if (a.qorder) given = a.qorder + (a.qorder_per_part ? (qi * (a.nslots / chunks) + pr) : qi) * (int64_t)D;
+        build_order(w, qrow, a.means ? a.means + (int64_t)part * D : nullptr, given, D, a.zone_dims, nunits, lane);
         volatile uint32_t *tau_g_ptr = reinterpret_cast<volatile uint32_t *>(a.tau) + qi;
         int cnt = 0;
         float tau_loc = __int_as_float(0x7f800000);
@@ -310,8 +352,8 @@ __global__ void __launch_bounds__(256) pdxsearch_kernel(ScanParams a) {
                     float qv[4];
 #pragma unroll
                     for (int u = 0; u < 4; ++u) {
-                        int ii = i + 2 * u + h;
-                        int j = w.ord[ii];
+                        const int ii = i + 2 * u + h;
+                        const int j = w.ord[ii];
                         qv[u] = w.qo[ii];
                         x[u] = __ldg(reinterpret_cast<const float4 *>(xb + j * kBlock) + sl);
                     }
@@ -326,8 +368,8 @@ __global__ void __launch_bounds__(256) pdxsearch_kernel(ScanParams a) {
                 for (; i < e; i += 2) {
                     int ii = i + h;
                     if (ii < e) {
-                        int j = w.ord[ii];
-                        float qv = w.qo[ii];
+                        const int j = w.ord[ii];
+                        const float qv = w.qo[ii];
                         float4 x = __ldg(reinterpret_cast<const float4 *>(xb + j * kBlock) + sl);
                         acc.x = term<MET>(qv, x.x, acc.x);
                         acc.y = term<MET>(qv, x.y, acc.y);
@@ -516,8 +558,9 @@ __global__ void __launch_bounds__(256) pdxsearch_kernel(ScanParams a) {
 
 template <int PR, int MET>
 static cudaError_t launch_scan_t(const ScanParams &p, int num_sms, cudaStream_t st) {
-    const int nunits = sort_units(p.d, p.zone_dims, p.order, PR);
-    const size_t per_warp = warp_smem_bytes(p.d, p.k, nunits);
+    const int nunits = sort_units(p.d, p.zone_dims, p.order, PR, p.qorder != nullptr);
+    if (nunits > kMaxSortUnits) return cudaErrorInvalidValue;
+    const size_t per_warp = warp_smem_bytes(p.d, p.k);
     int warps = 8;
     while (warps > 1 && per_warp * warps > 200 * 1024) warps >>= 1;
     const size_t smem = per_warp * warps;
@@ -525,10 +568,20 @@ static cudaError_t launch_scan_t(const ScanParams &p, int num_sms, cudaStream_t 
     auto kern = pdxsearch_kernel<PR, MET>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
+    // Shared-memory carveout sized for the requested number of resident CTAs
+    // (1 KB reserved per CTA); what remains of the SM's on-chip memory is L1,
+    // which holds the lines of the scan's loads in flight.
+    const int want = p.ctas_per_sm > 0 ? p.ctas_per_sm : 3;
+    int pct = (int)((want * (smem + 1024) * 100 + 228 * 1024 - 1) / (228 * 1024));
+    if (pct > 100) pct = 100;
+    if (pct < 1) pct = 1;
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, pct);
+    if (e != cudaSuccess) return e;
     int per_sm = 0;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, warps * 32, smem);
     if (e != cudaSuccess) return e;
     if (per_sm < 1) per_sm = 1;
+    if (per_sm > want) per_sm = want;
     int64_t grid = (int64_t)num_sms * per_sm;
     int64_t need = (p.nitems + warps - 1) / warps;
     if (grid > need) grid = need;
@@ -762,6 +815,91 @@ cudaError_t launch_write_out(const uint64_t *topk, int64_t nq, int32_t k, int mo
                              float *out_dist, int64_t *out_idx, cudaStream_t st) {
     if (nq == 0) return cudaSuccess;
     write_out_kernel<<<(unsigned)((nq * 32 + 255) / 256), 256, 0, st>>>(topk, nq, k, mode, q, d, out_dist, out_idx);
+    return counted(cudaGetLastError());
+}
+
+// ---------------------------------------------------------------------------
+// Query preprocessing for PDX-BOND (Sec. 5): the dimension visit order of each
+// row (a query, or a (query, part) pair when per_part > 0), computed once and
+// stored as uint16 dimension indices. mode 0: distance to the means (zones of
+// Z dimensions, score = sum (q_j - mu_j)^2); mode 1: decreasing query value.
+// One CTA per row sorts its keys (score descending, index ascending) with a
+// block-wide bitonic sort in shared memory.
+__global__ void __launch_bounds__(256) order_kernel(const float *__restrict__ q, int64_t rows, int32_t d,
+                                                    const float *__restrict__ means, int32_t per_part,
+                                                    const int32_t *__restrict__ row_part, int mode, int32_t Z,
+                                                    uint16_t *__restrict__ out) {
+    extern __shared__ __align__(16) uint64_t keys[];
+    const int64_t row = blockIdx.x;
+    if (row >= rows) return;
+    const int64_t qi = per_part > 0 ? row / per_part : row;
+    const float *qrow = q + qi * d;
+    int part = 0;
+    if (per_part > 0) part = row_part ? row_part[row] : (int)(row % per_part);
+    if (part < 0) part = 0;   // unused probe slot: any valid row of means
+    const float *mu = means + (int64_t)part * d;
+    const int nunits = (mode == 1) ? d : (d + Z - 1) / Z;
+    const int zz = (mode == 1) ? 1 : Z;
+    const int npad = pow2_ceil(nunits);
+    for (int u = threadIdx.x; u < npad; u += blockDim.x) {
+        uint64_t key = kEmptyKey;
+        if (u < nunits) {
+            float sc = 0.f;
+            if (mode == 1) {
+                sc = qrow[u];
+            } else {
+                int j1 = min(d, u * zz + zz);
+                for (int j = u * zz; j < j1; ++j) {
+                    float t = qrow[j] - mu[j];
+                    sc = fmaf(t, t, sc);
+                }
+            }
+            key = ((uint64_t)f2o(-sc) << 32) | (uint32_t)u;
+        }
+        keys[u] = key;
+    }
+    __syncthreads();
+    for (int size = 2; size <= npad; size <<= 1) {
+        for (int stride = size >> 1; stride > 0; stride >>= 1) {
+            for (int i = threadIdx.x; i < (npad >> 1); i += blockDim.x) {
+                int lo = 2 * i - (i & (stride - 1));
+                int hi = lo + stride;
+                bool asc = (lo & size) == 0;
+                uint64_t a = keys[lo], b = keys[hi];
+                if ((a > b) == asc) {
+                    keys[lo] = b;
+                    keys[hi] = a;
+                }
+            }
+            __syncthreads();
+        }
+    }
+    // expand zones: rank r's dimensions start at r*Z, shifted back by the
+    // shortfall of the last (shorter) zone when it ranks before r
+    __shared__ int rlast;
+    if (threadIdx.x == 0) rlast = 0;
+    __syncthreads();
+    for (int r = threadIdx.x; r < nunits; r += blockDim.x)
+        if ((int)(keys[r] & 0xffffffffu) == nunits - 1) rlast = r;
+    __syncthreads();
+    const int lastlen = d - (nunits - 1) * zz;
+    uint16_t *orow = out + row * (int64_t)d;
+    for (int r = threadIdx.x; r < nunits; r += blockDim.x) {
+        int z = (int)(keys[r] & 0xffffffffu);
+        int off = r * zz - ((r > rlast) ? (zz - lastlen) : 0);
+        int len = (z == nunits - 1) ? lastlen : zz;
+        for (int u = 0; u < len; ++u) orow[off + u] = (uint16_t)(z * zz + u);
+    }
+}
+
+cudaError_t launch_order(const float *q, int64_t rows, int32_t d, const float *means, int32_t per_part,
+                         const int32_t *row_part, int mode, int32_t Z, uint16_t *out, cudaStream_t st) {
+    if (rows == 0) return cudaSuccess;
+    const int nunits = (mode == 1) ? d : (d + Z - 1) / Z;
+    size_t smem = (size_t)pow2_ceil(nunits) * 8;
+    cudaError_t e = cudaFuncSetAttribute(order_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    order_kernel<<<(unsigned)rows, 256, smem, st>>>(q, rows, d, means, per_part, row_part, mode, Z, out);
     return counted(cudaGetLastError());
 }
 

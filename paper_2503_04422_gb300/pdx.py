@@ -23,7 +23,9 @@ METRIC = {"l2": 0, "ip": 1, "l1": 2}
 DTYPE = {"f32": 0, "bf16": 1, "fp8": 2}
 PRUNER = {"none": 0, "bond": 1, "ads": 2, "adsampling": 2, "bsa": 3}
 ORDER = {"dist_to_means": 0, "decreasing": 1, "sequential": 2}
-ARRAY = {"blocks": 0, "ids": 1, "part_blocks": 2, "means": 3, "centroids": 4, "assign": 5}
+MEANS = {"block": 0, "collection": 1, "auto": 2}
+ARRAY = {"blocks": 0, "ids": 1, "part_blocks": 2, "means": 3, "centroids": 4, "assign": 5, "rotation": 6,
+         "variances": 7}
 STATUS_NAMES = {0: "PDX_OK", 1: "PDX_ERR_ARG", 2: "PDX_ERR_OOM", 3: "PDX_ERR_CUDA", 4: "PDX_ERR_TIMEOUT",
                 5: "PDX_ERR_UNSUPPORTED"}
 
@@ -58,7 +60,8 @@ class pdx_search_opts(ctypes.Structure):
                 ("bsa_m", ctypes.c_float), ("first_step", ctypes.c_uint32), ("start_vectors", ctypes.c_uint32),
                 ("blocks_per_item", ctypes.c_uint32), ("stats_out", ctypes.POINTER(pdx_search_stats)),
                 ("stats_device", ctypes.c_void_p), ("scan_event_start", ctypes.c_void_p),
-                ("scan_event_stop", ctypes.c_void_p)]
+                ("scan_event_stop", ctypes.c_void_p), ("means_scope", ctypes.c_int),
+                ("ctas_per_sm", ctypes.c_uint32)]
 
 
 class pdx_index_info(ctypes.Structure):
@@ -172,7 +175,8 @@ class Index:
         shapes = {
             "blocks": ((inf.nblocks, inf.d, 64), np.float32), "ids": ((inf.nblocks * 64,), np.int32),
             "part_blocks": ((inf.nparts + 1,), np.int32), "means": ((inf.nparts, inf.d), np.float32),
-            "centroids": ((inf.nparts, inf.d), np.float32), "assign": ((inf.n,), np.int32)}
+            "centroids": ((inf.nparts, inf.d), np.float32), "assign": ((inf.n,), np.int32),
+            "rotation": ((inf.d, inf.d), np.float32), "variances": ((inf.d,), np.float32)}
         shape, dt = shapes[which]
         out = np.empty(shape, dt)
         _check(lib().pdx_index_copy_out(self.handle, ARRAY[which], out.ctypes.data, out.nbytes), "pdx_index_copy_out")
@@ -201,14 +205,17 @@ def build_opts(metric="l2", storage="f32", partition_size=10000, keep_fp32_reran
 
 
 def search_opts(pruner="bond", order="dist_to_means", zone_dims=None, selection_threshold=None, eps0=None,
-                bsa_m=None, first_step=None, start_vectors=None, blocks_per_item=None) -> pdx_search_opts:
+                bsa_m=None, first_step=None, start_vectors=None, blocks_per_item=None,
+                means_scope=None, ctas_per_sm=None) -> pdx_search_opts:
     o = pdx_search_opts()
     lib().pdx_default_search_opts(ctypes.byref(o))
     o.pruner = PRUNER[pruner]
     o.order = ORDER[order]
+    if means_scope is not None:
+        o.means_scope = MEANS[means_scope]
     for name, v in (("zone_dims", zone_dims), ("selection_threshold", selection_threshold), ("eps0", eps0),
                     ("bsa_m", bsa_m), ("first_step", first_step), ("start_vectors", start_vectors),
-                    ("blocks_per_item", blocks_per_item)):
+                    ("blocks_per_item", blocks_per_item), ("ctas_per_sm", ctas_per_sm)):
         if v is not None:
             setattr(o, name, v)
     return o

@@ -47,13 +47,13 @@ def test_struct_layouts_match_c(tmp_path):
         '#include <stdio.h>\n#include <stddef.h>\n#include "pdx.h"\n'
         "int main(void){printf(\"%zu %zu %zu %zu %zu %zu %zu\\n\", sizeof(pdx_build_opts), sizeof(pdx_ivf_opts),"
         " sizeof(pdx_search_opts), sizeof(pdx_search_stats), sizeof(pdx_index_info),"
-        " offsetof(pdx_search_opts, scan_event_stop), offsetof(pdx_ivf_opts, init_centroids));return 0;}\n")
+        " offsetof(pdx_search_opts, ctas_per_sm), offsetof(pdx_ivf_opts, init_centroids));return 0;}\n")
     exe = tmp_path / "sizes"
     subprocess.check_call(["gcc", "-I", os.path.join(ROOT, "include"), str(prog), "-o", str(exe)])
     got = [int(v) for v in subprocess.check_output([str(exe)]).split()]
     want = [ctypes.sizeof(P.pdx_build_opts), ctypes.sizeof(P.pdx_ivf_opts), ctypes.sizeof(P.pdx_search_opts),
             ctypes.sizeof(P.pdx_search_stats), ctypes.sizeof(P.pdx_index_info),
-            P.pdx_search_opts.scan_event_stop.offset, P.pdx_ivf_opts.init_centroids.offset]
+            P.pdx_search_opts.ctas_per_sm.offset, P.pdx_ivf_opts.init_centroids.offset]
     assert got == want
 
 
@@ -61,7 +61,7 @@ def test_defaults(L):
     o = P.pdx_search_opts()
     L.pdx_default_search_opts(ctypes.byref(o))
     assert o.struct_size == ctypes.sizeof(P.pdx_search_opts)
-    assert o.pruner == P.PRUNER["bond"] and o.first_step == 2
+    assert o.pruner == P.PRUNER["bond"] and o.first_step == 4 and o.means_scope == 2
     assert abs(o.selection_threshold - 0.20) < 1e-7 and abs(o.eps0 - 2.1) < 1e-6
     b = P.pdx_build_opts()
     L.pdx_default_build_opts(ctypes.byref(b))

@@ -189,3 +189,16 @@ def test_mixture_768_full_size_sampled(P, torch):
     torch.cuda.synchronize()
     rows = np.random.default_rng(1).choice(q.shape[0], size=6, replace=False)
     check_topk(x, q, 10, dist, idx, rows=rows)
+
+
+@pytest.mark.parametrize("scope,zone,d", [("collection", 1, 100), ("collection", 4, 300), ("block", 1, 300),
+                                          ("block", 2, 600)])
+def test_bond_precomputed_orders(P, torch, scope, zone, d):
+    # orders computed once per query (collection means) or per (query, part)
+    # (more zones than a warp sorts in-kernel) keep the search exact
+    x, q = pdx_synth.gaussian_mixture(pdx_synth.MixtureSpec(n=4000, d=d, nq=12, n_centres=10, seed=d + zone))
+    ix = P.pdx_build_layout(_dev(torch, x), partition_size=1000)
+    for order in ("dist_to_means", "decreasing"):
+        dist, idx = P.pdx_search_exact(ix, _dev(torch, q), 10, order=order, zone_dims=zone, means_scope=scope)
+        torch.cuda.synchronize()
+        check_topk(x, q, 10, dist, idx)
