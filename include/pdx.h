@@ -90,7 +90,10 @@ typedef enum pdx_means_scope {
 typedef struct pdx_build_opts {
     uint32_t struct_size;      /* = sizeof(pdx_build_opts)                                */
     pdx_metric metric;         /* metric the index will be searched with                   */
-    pdx_dtype storage;         /* block storage type (F32 only in this build for search)   */
+    pdx_dtype storage;         /* block storage type. BF16 / FP8_E4M3 blocks are scanned with
+                                  a lower bound widened by the per-element quantisation error,
+                                  and survivors are reranked from an FP32 copy of the vectors
+                                  that the index keeps (n*d*4 bytes); L2 and unit-norm IP  */
     uint32_t partition_size;   /* exact search: at most this many vectors per PDXearch
                                   block, equal horizontal partitions (Sec. 6.6; 10000)    */
     int32_t keep_fp32_rerank;  /* low-precision storage: keep an FP32 copy (default 1)     */
@@ -165,14 +168,16 @@ typedef struct pdx_index_info {
 
 /* Internal arrays that pdx_index_copy_out can return (for inspection/tests). */
 typedef enum pdx_array {
-    PDX_ARRAY_BLOCKS = 0,      /* float32 [nblocks][d][64] PDX storage (zero padded)       */
+    PDX_ARRAY_BLOCKS = 0,      /* float32 [nblocks][d][64] PDX storage (zero padded; F32)  */
     PDX_ARRAY_IDS = 1,         /* int32 [nblocks*64] vector id per slot, -1 = padding      */
     PDX_ARRAY_PART_BLOCKS = 2, /* int32 [nparts+1] first storage block of each part        */
     PDX_ARRAY_MEANS = 3,       /* float32 [nparts][d] per-part dimension means (Sec. 3)    */
     PDX_ARRAY_CENTROIDS = 4,   /* float32 [nparts][d] IVF centroids (transformed space)    */
     PDX_ARRAY_ASSIGN = 5,      /* int32 [n] IVF bucket of each vector                      */
     PDX_ARRAY_ROTATION = 6,    /* float32 [d][d] IVF transform applied to vectors/queries  */
-    PDX_ARRAY_VARIANCES = 7    /* float32 [d] BSA: variance of each projected dimension    */
+    PDX_ARRAY_VARIANCES = 7,   /* float32 [d] BSA: variance of each projected dimension    */
+    PDX_ARRAY_BLOCKS_LP = 8,   /* bf16 / fp8-e4m3 bits [nblocks][d][64] (storage != F32)   */
+    PDX_ARRAY_SCALES = 9       /* float32 [d] FP8 storage: per-dimension scale             */
 } pdx_array;
 
 /* Fill an options struct with the defaults named above. */

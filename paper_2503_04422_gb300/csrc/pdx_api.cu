@@ -102,7 +102,7 @@ static size_t rup(size_t b) { return (b + 255) & ~size_t(255); }
 
 static void free_index(pdx_index *ix) {
     if (!ix) return;
-    void *ptrs[] = {ix->data, ix->ids, ix->slot_of, ix->blk_cnt, ix->part_blk, ix->means, ix->cmean, ix->centroids, ix->centroid_norms,
+    void *ptrs[] = {ix->data, ix->data_lp, ix->scale, ix->xnary, ix->ids, ix->slot_of, ix->blk_cnt, ix->part_blk, ix->means, ix->cmean, ix->centroids, ix->centroid_norms,
                     ix->assign, ix->rot, ix->shift, ix->pca_var, ix->resid, ix->chk, ix->cdata, ix->cids};
     for (void *p : ptrs)
         if (p) cudaFree(p);
@@ -185,6 +185,40 @@ static pdx_status layout_parts(pdx_index *ix, const float *x_dev, const std::vec
 
 static bool valid_metric(int m) { return m == PDX_L2 || m == PDX_IP || m == PDX_L1; }
 
+static size_t elem_size(pdx_dtype t) { return t == PDX_F32 ? 4 : (t == PDX_BF16 ? 2 : 1); }
+
+// Low-precision storage: quantise the FP32 PDX blocks (BF16, or FP8-E4M3 with
+// per-dimension scales), keep the FP32 vectors by id (xrows, row-major) for the
+// START scan and the rerank, and release the FP32 blocks.
+static pdx_status finish_low_precision(pdx_index *ix, const float *xrows, cudaStream_t st) {
+    const int d = ix->d;
+    PDX_TRY(dalloc(ix, &ix->xnary, (size_t)ix->n * d));
+    PDX_TRY(cudaMemcpyAsync(ix->xnary, xrows, (size_t)ix->n * d * 4, cudaMemcpyDeviceToDevice, st));
+    unsigned *colmax = nullptr;
+    if (ix->storage == PDX_FP8_E4M3) {
+        PDX_TRY(dalloc(ix, &ix->scale, (size_t)d));
+        PDX_TRY(cudaMalloc(&colmax, (size_t)d * 4));
+        cudaError_t e = launch_fp8_scales(xrows, ix->n, d, colmax, ix->scale, st);
+        if (e != cudaSuccess) {
+            cudaFree(colmax);
+            return cuda_status(e, "launch_fp8_scales", __LINE__);
+        }
+    }
+    const size_t lp_bytes = (size_t)ix->nblocks * d * kBlock * elem_size(ix->storage);
+    cudaError_t e = cudaMalloc(&ix->data_lp, lp_bytes ? lp_bytes : 1);
+    if (e == cudaSuccess) {
+        ix->bytes += lp_bytes;
+        e = launch_quantize(ix->data, ix->nblocks, d, ix->storage, ix->scale, ix->data_lp, st);
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (colmax) cudaFree(colmax);
+    if (e != cudaSuccess) return cuda_status(e, "quantize", __LINE__);
+    cudaFree(ix->data);
+    ix->data = nullptr;
+    ix->bytes -= (size_t)ix->nblocks * d * kBlock * 4;
+    return PDX_OK;
+}
+
 }  // namespace pdx
 
 using namespace pdx;
@@ -263,6 +297,11 @@ pdx_status pdx_index_copy_out(const pdx_index *ix, pdx_array which, void *dst, s
     size_t need = 0;
     switch (which) {
     case PDX_ARRAY_BLOCKS: src = ix->data; need = (size_t)ix->nblocks * ix->d * kBlock * 4; break;
+    case PDX_ARRAY_BLOCKS_LP:
+        src = ix->data_lp;
+        need = (size_t)ix->nblocks * ix->d * kBlock * elem_size(ix->storage);
+        break;
+    case PDX_ARRAY_SCALES: src = ix->scale; need = (size_t)ix->d * 4; break;
     case PDX_ARRAY_IDS: src = ix->ids; need = (size_t)ix->nblocks * kBlock * 4; break;
     case PDX_ARRAY_PART_BLOCKS: src = ix->part_blk; need = ((size_t)ix->nparts + 1) * 4; break;
     case PDX_ARRAY_MEANS: src = ix->means; need = (size_t)ix->nparts * ix->d * 4; break;
@@ -308,8 +347,8 @@ pdx_status pdx_build_layout(const float *x, int64_t n, int32_t d, const pdx_buil
         set_error("pdx_build_layout: bad metric %d or storage %d", (int)o.metric, (int)o.storage);
         return PDX_ERR_ARG;
     }
-    if (o.storage != PDX_F32) {
-        set_error("pdx_build_layout: only F32 storage is implemented");
+    if (o.storage != PDX_F32 && o.metric == PDX_L1) {
+        set_error("pdx_build_layout: low-precision storage supports L2 (and unit-norm IP) only");
         return PDX_ERR_UNSUPPORTED;
     }
     if (o.partition_size == 0) o.partition_size = 10000;
@@ -361,6 +400,7 @@ pdx_status pdx_build_layout(const float *x, int64_t n, int32_t d, const pdx_buil
             cudaError_t e = cudaStreamSynchronize(st);
             if (e != cudaSuccess) s = cuda_status(e, "cudaStreamSynchronize", __LINE__);
         }
+        if (s == PDX_OK && o.storage != PDX_F32) s = finish_low_precision(ix, xd, st);
     }
     if (s != PDX_OK) {
         free_index(ix);
@@ -429,6 +469,16 @@ pdx_status plan_metric(const pdx_index *ix, int pruner, SearchPlan *pl, const ch
             pl->out_mode = 1;   // the refine step recomputes the inner product itself
         } else {
             set_error("%s: pruned inner-product search needs a unit-norm index", fn);
+            return PDX_ERR_UNSUPPORTED;
+        }
+    }
+    if (ix->storage != PDX_F32) {
+        // low-precision scans bound and rerank L2 distances
+        if (ix->metric == PDX_IP && ix->unit_norm) {
+            pl->metric = PDX_L2;
+            pl->out_mode = 1;
+        } else if (ix->metric != PDX_L2) {
+            set_error("%s: low-precision storage supports L2 and unit-norm IP only", fn);
             return PDX_ERR_UNSUPPORTED;
         }
     }
@@ -565,7 +615,13 @@ extern "C" pdx_status pdx_search_exact(const pdx_index *ix, const float *q, int6
     if (start) {
         // START (Sec. 4): exact distances of the first start_vectors stored
         // vectors give every query an initial k-th-best threshold
-        PDX_TRY(launch_dense_keys(qd, nq, ix->data, ix->ids, d, start_blk, pl.metric, skeys, st));
+        if (ix->storage == PDX_F32) {
+            PDX_TRY(launch_dense_keys(qd, nq, ix->data, ix->ids, d, start_blk, pl.metric, skeys, st));
+        } else {  // exact FP32 from the vectors' FP32 copy, so tau is a real k-th distance
+            const int32_t rows = (int32_t)std::min<int64_t>(ix->n, Lstart);
+            PDX_TRY(launch_fill_u64(skeys, kEmptyKey, nq * Lstart, st));
+            PDX_TRY(launch_dense_keys_rows(qd, nq, ix->xnary, rows, d, Lstart, skeys, st));
+        }
         PDX_TRY(launch_select_k(skeys, nq, Lstart, k, stopk, st));
         PDX_TRY(launch_tau_from_keys(stopk, nq, k, tau, st));
         PDX_TRY(launch_add_u64(kc + C_START, (unsigned long long)nq * Lstart * d, st));
@@ -573,6 +629,10 @@ extern "C" pdx_status pdx_search_exact(const pdx_index *ix, const float *q, int6
     ScanParams p;
     std::memset(&p, 0, sizeof p);
     p.data = ix->data;
+    p.data_lp = ix->data_lp;
+    p.storage = (int)ix->storage;
+    p.scale = ix->scale;
+    p.xnary = ix->xnary;
     p.ids = ix->ids;
     p.blk_cnt = ix->blk_cnt;
     p.part_blk = ix->part_blk;
@@ -606,7 +666,10 @@ extern "C" pdx_status pdx_search_exact(const pdx_index *ix, const float *q, int6
     PDX_TRY(launch_scan(pl.pruner, pl.metric, p, sms, st));
     if (o.scan_event_stop) PDX_TRY(cudaEventRecord(static_cast<cudaEvent_t>(o.scan_event_stop), st));
     PDX_TRY(launch_select_k(cand, nq, (int64_t)nslots * k, k, topk, st));
-    PDX_TRY(launch_refine(topk, nq, k, qd, d, ix->data, ix->slot_of, ix->metric, refined, st));
+    if (ix->storage == PDX_F32)
+        PDX_TRY(launch_refine(topk, nq, k, qd, d, ix->data, ix->slot_of, ix->metric, refined, st));
+    else
+        PDX_TRY(launch_refine_rows(topk, nq, k, qd, d, ix->xnary, ix->metric, refined, st));
     PDX_TRY(launch_select_k(refined, nq, k, k, final_keys, st));
     PDX_TRY(launch_write_out(final_keys, nq, k, pl.out_mode, qd, d, od, oi, st));
     if (!o_dev) {
@@ -626,7 +689,8 @@ extern "C" pdx_status pdx_search_exact(const pdx_index *ix, const float *q, int6
         so->candidates = c[C_CANDIDATES];
         so->work_items = c[C_ITEMS];
         so->start_values = c[C_START];
-        so->bytes_logical = (c[C_VALUES] + c[C_START]) * 4ull;
+        so->bytes_logical = c[C_VALUES] * elem_size(ix->storage) + c[C_START] * 4ull +
+                            (ix->storage == PDX_F32 ? 0ull : c[C_CANDIDATES] * (uint64_t)d * 4ull);
     }
     if (!o_dev) PDX_TRY(cudaStreamSynchronize(st));
     return PDX_OK;
@@ -807,6 +871,7 @@ static pdx_status ivf_build_impl(pdx_index *ix, const float *x, const pdx_ivf_op
         }
     }
     PDX_TRY(cudaStreamSynchronize(st));
+    if (ix->storage != PDX_F32) return finish_low_precision(ix, xt, st);
     return PDX_OK;
 }
 
@@ -841,8 +906,8 @@ extern "C" pdx_status pdx_ivf_build(const float *x, int64_t n, int32_t d, const 
         set_error("pdx_ivf_build: ADSampling needs the caller's d*d orthogonal rotation");
         return PDX_ERR_ARG;
     }
-    if (o.base.storage != PDX_F32) {
-        set_error("pdx_ivf_build: only F32 storage is implemented");
+    if (o.base.storage != PDX_F32 && o.base.metric == PDX_L1) {
+        set_error("pdx_ivf_build: low-precision storage supports L2 (and unit-norm IP) only");
         return PDX_ERR_UNSUPPORTED;
     }
     if (o.transform != PDX_PRUNE_NONE && o.base.metric != PDX_L2) {
@@ -971,6 +1036,10 @@ extern "C" pdx_status pdx_search_ivf(const pdx_index *ix, const float *q, int64_
     ScanParams p;
     std::memset(&p, 0, sizeof p);
     p.data = ix->data;
+    p.data_lp = ix->data_lp;
+    p.storage = (int)ix->storage;
+    p.scale = ix->scale;
+    p.xnary = ix->xnary;
     p.ids = ix->ids;
     p.blk_cnt = ix->blk_cnt;
     p.part_blk = ix->part_blk;
@@ -1015,7 +1084,10 @@ extern "C" pdx_status pdx_search_ivf(const pdx_index *ix, const float *q, int64_
     }
     if (o.scan_event_stop) PDX_TRY(cudaEventRecord(static_cast<cudaEvent_t>(o.scan_event_stop), st));
     PDX_TRY(launch_select_k(cand, nq, (int64_t)nprobe * k, k, topk, st));
-    PDX_TRY(launch_refine(topk, nq, k, qt, d, ix->data, ix->slot_of, ix->metric, refined, st));
+    if (ix->storage == PDX_F32)
+        PDX_TRY(launch_refine(topk, nq, k, qt, d, ix->data, ix->slot_of, ix->metric, refined, st));
+    else
+        PDX_TRY(launch_refine_rows(topk, nq, k, qt, d, ix->xnary, ix->metric, refined, st));
     PDX_TRY(launch_select_k(refined, nq, k, k, final_keys, st));
     PDX_TRY(launch_write_out(final_keys, nq, k, pl.out_mode, qt, d, od, oi, st));
     if (!o_dev) {
@@ -1035,7 +1107,8 @@ extern "C" pdx_status pdx_search_ivf(const pdx_index *ix, const float *q, int64_
         so->candidates = c[C_CANDIDATES];
         so->work_items = c[C_ITEMS];
         so->start_values = c[C_START];
-        so->bytes_logical = (c[C_VALUES] + c[C_START]) * 4ull;
+        so->bytes_logical = c[C_VALUES] * elem_size(ix->storage) + c[C_START] * 4ull +
+                            (ix->storage == PDX_F32 ? 0ull : c[C_CANDIDATES] * (uint64_t)d * 4ull);
     }
     if (!o_dev) PDX_TRY(cudaStreamSynchronize(st));
     return PDX_OK;

@@ -45,7 +45,10 @@ struct pdx_index {
     int device = 0;
     pdx_pruner transform = PDX_PRUNE_NONE;  // IVF: ADSAMPLING rotation / BSA projection
     // device arrays
-    float *data = nullptr;          // [nblocks][d][64]
+    float *data = nullptr;          // [nblocks][d][64] FP32 (absent for low-precision storage)
+    void *data_lp = nullptr;        // [nblocks][d][64] BF16 / FP8-E4M3 blocks
+    float *scale = nullptr;         // [d] FP8: per-dimension scale
+    float *xnary = nullptr;         // [n][d] FP32 vectors by id (low precision: START, rerank)
     int32_t *ids = nullptr;         // [nblocks*64]
     int32_t *slot_of = nullptr;     // [n] storage slot (block*64 + lane) of each vector id
     int32_t *blk_cnt = nullptr;     // [nblocks] valid lanes per block
@@ -117,7 +120,11 @@ cudaError_t launch_fill_u64(uint64_t *p, uint64_t v, int64_t n, cudaStream_t st)
 cudaError_t launch_add_u64(unsigned long long *p, unsigned long long v, cudaStream_t st);
 
 struct ScanParams {
-    const float *data;
+    const float *data;         // F32 PDX blocks
+    const void *data_lp;       // BF16 / FP8 PDX blocks (storage != F32)
+    int32_t storage;           // pdx_dtype of the blocks
+    const float *scale;        // FP8: per-dimension scale [d]
+    const float *xnary;        // low precision: FP32 vectors by id [n][d] for the rerank
     const int32_t *ids;
     const int32_t *blk_cnt;
     const int32_t *part_blk;
@@ -172,6 +179,14 @@ size_t scan_warp_smem(int d, int k, int zone_dims, int order);
 // as (distance, id) keys [nq][nvec_pad].
 cudaError_t launch_dense_keys(const float *q, int64_t nq, const float *data, const int32_t *ids,
                               int32_t d, int32_t nblk, int metric, uint64_t *keys, cudaStream_t st);
+// START over row-major FP32 vectors: keys[qi*ld + r] for r < nrows <= ld.
+cudaError_t launch_dense_keys_rows(const float *q, int64_t nq, const float *x, int32_t nrows, int32_t d, int64_t ld,
+                                   uint64_t *keys, cudaStream_t st);
+cudaError_t launch_refine_rows(const uint64_t *topk, int64_t nq, int32_t k, const float *q, int32_t d, const float *x,
+                               int metric, uint64_t *out, cudaStream_t st);
+cudaError_t launch_fp8_scales(const float *x, int64_t n, int32_t d, unsigned *colmax, float *scale, cudaStream_t st);
+cudaError_t launch_quantize(const float *data, int64_t nblocks, int32_t d, int storage, const float *scale, void *out,
+                            cudaStream_t st);
 // Per-row k smallest keys of a [rows][L] array (sorted ascending) -> out [rows][k].
 cudaError_t launch_select_k(const uint64_t *keys, int64_t rows, int64_t L, int32_t k, uint64_t *out,
                             cudaStream_t st);

@@ -1,4 +1,7 @@
 // Layout build (Sec. 3): N-ary rows -> PDX blocks, and block metadata.
+#include <cuda_bf16.h>
+#include <cuda_fp8.h>
+
 #include "pdx_internal.cuh"
 
 namespace pdx {
@@ -118,6 +121,59 @@ __global__ void add_u64_kernel(unsigned long long *p, unsigned long long v) { at
 
 cudaError_t launch_add_u64(unsigned long long *p, unsigned long long v, cudaStream_t st) {
     add_u64_kernel<<<1, 1, 0, st>>>(p, v);
+    return counted(cudaGetLastError());
+}
+
+// ---- low-precision storage ----
+// colmax[j] = max_i |x_ij| as float bits (non-negative floats order like their bits)
+__global__ void colmax_kernel(const float *__restrict__ x, int64_t n, int32_t d, unsigned *__restrict__ colmax) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= d) return;
+    float m = 0.f;
+    for (int64_t r = blockIdx.y; r < n; r += gridDim.y) m = fmaxf(m, fabsf(x[r * d + j]));
+    atomicMax(colmax + j, __float_as_uint(m));
+}
+
+// scale[j] = colmax[j] / 448 (the largest E4M3 magnitude), 1 for an all-zero column
+__global__ void fp8_scale_kernel(const unsigned *__restrict__ colmax, int32_t d, float *__restrict__ scale) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= d) return;
+    float m = __uint_as_float(colmax[j]);
+    scale[j] = m > 0.f ? m / 448.f : 1.f;
+}
+
+cudaError_t launch_fp8_scales(const float *x, int64_t n, int32_t d, unsigned *colmax, float *scale, cudaStream_t st) {
+    cudaError_t e = cudaMemsetAsync(colmax, 0, (size_t)d * 4, st);
+    if (e != cudaSuccess) return e;
+    dim3 g((unsigned)((d + 127) / 128), 256);
+    colmax_kernel<<<g, 128, 0, st>>>(x, n, d, colmax);
+    e = counted(cudaGetLastError());
+    if (e != cudaSuccess) return e;
+    fp8_scale_kernel<<<(unsigned)((d + 127) / 128), 128, 0, st>>>(colmax, d, scale);
+    return counted(cudaGetLastError());
+}
+
+// Element-wise quantisation of the FP32 PDX blocks: BF16 round-to-nearest-even,
+// or E4M3 (saturating, round-to-nearest-even) of x / scale[j].
+__global__ void quantize_kernel(const float *__restrict__ data, int64_t total, int32_t d, int storage,
+                                const float *__restrict__ scale, void *__restrict__ out) {
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
+        const float x = data[t];
+        if (storage == PDX_BF16) {
+            static_cast<uint16_t *>(out)[t] = __bfloat16_as_ushort(__float2bfloat16_rn(x));
+        } else {
+            const int j = (int)((t / kBlock) % d);
+            static_cast<uint8_t *>(out)[t] = (uint8_t)__nv_cvt_float_to_fp8(x / scale[j], __NV_SATFINITE, __NV_E4M3);
+        }
+    }
+}
+
+cudaError_t launch_quantize(const float *data, int64_t nblocks, int32_t d, int storage, const float *scale, void *out,
+                            cudaStream_t st) {
+    const int64_t total = nblocks * d * kBlock;
+    if (total == 0) return cudaSuccess;
+    int64_t blocks = (total + 255) / 256;
+    quantize_kernel<<<(unsigned)(blocks < 8192 ? blocks : 8192), 256, 0, st>>>(data, total, d, storage, scale, out);
     return counted(cudaGetLastError());
 }
 

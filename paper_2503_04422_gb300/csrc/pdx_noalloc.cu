@@ -165,7 +165,13 @@ extern "C" pdx_status pdx_search_exact_noalloc(const pdx_index *ix, const float 
     NOALLOC_TRY(cudaMemsetAsync(work, 0, 8, st));
     unsigned long long *kc = o.stats_device ? reinterpret_cast<unsigned long long *>(o.stats_device) : counters;
     if (start) {
-        NOALLOC_TRY(launch_dense_keys(q, nq, ix->data, ix->ids, d, start_blk, pl.metric, skeys, st));
+        if (ix->storage == PDX_F32) {
+            NOALLOC_TRY(launch_dense_keys(q, nq, ix->data, ix->ids, d, start_blk, pl.metric, skeys, st));
+        } else {
+            const int32_t rows = (int32_t)std::min<int64_t>(ix->n, Lstart);
+            NOALLOC_TRY(launch_fill_u64(skeys, kEmptyKey, nq * Lstart, st));
+            NOALLOC_TRY(launch_dense_keys_rows(q, nq, ix->xnary, rows, d, Lstart, skeys, st));
+        }
         NOALLOC_TRY(launch_select_k(skeys, nq, Lstart, k, stopk, st));
         NOALLOC_TRY(launch_tau_from_keys(stopk, nq, k, tau, st));
         NOALLOC_TRY(launch_add_u64(kc + C_START, (unsigned long long)nq * Lstart * d, st));
@@ -173,6 +179,10 @@ extern "C" pdx_status pdx_search_exact_noalloc(const pdx_index *ix, const float 
     ScanParams p;
     std::memset(&p, 0, sizeof p);
     p.data = ix->data;
+    p.data_lp = ix->data_lp;
+    p.storage = (int)ix->storage;
+    p.scale = ix->scale;
+    p.xnary = ix->xnary;
     p.ids = ix->ids;
     p.blk_cnt = ix->blk_cnt;
     p.part_blk = ix->part_blk;
@@ -204,7 +214,10 @@ extern "C" pdx_status pdx_search_exact_noalloc(const pdx_index *ix, const float 
     NOALLOC_TRY(launch_scan(pl.pruner, pl.metric, p, sms, st));
     if (o.scan_event_stop) NOALLOC_TRY(cudaEventRecord(static_cast<cudaEvent_t>(o.scan_event_stop), st));
     NOALLOC_TRY(launch_select_k(cand, nq, (int64_t)nslots * k, k, topk, st));
-    NOALLOC_TRY(launch_refine(topk, nq, k, q, d, ix->data, ix->slot_of, ix->metric, refined, st));
+    if (ix->storage == PDX_F32)
+        NOALLOC_TRY(launch_refine(topk, nq, k, q, d, ix->data, ix->slot_of, ix->metric, refined, st));
+    else
+        NOALLOC_TRY(launch_refine_rows(topk, nq, k, q, d, ix->xnary, ix->metric, refined, st));
     NOALLOC_TRY(launch_select_k(refined, nq, k, k, final_keys, st));
     NOALLOC_TRY(launch_write_out(final_keys, nq, k, pl.out_mode, q, d, out_dist, out_idx, st));
     if (o.stats_out) {
@@ -220,7 +233,8 @@ extern "C" pdx_status pdx_search_exact_noalloc(const pdx_index *ix, const float 
         so->candidates = c[C_CANDIDATES];
         so->work_items = c[C_ITEMS];
         so->start_values = c[C_START];
-        so->bytes_logical = (c[C_VALUES] + c[C_START]) * 4ull;
+        so->bytes_logical = c[C_VALUES] * (ix->storage == PDX_F32 ? 4ull : (ix->storage == PDX_BF16 ? 2ull : 1ull)) +
+                            c[C_START] * 4ull + (ix->storage == PDX_F32 ? 0ull : c[C_CANDIDATES] * (uint64_t)d * 4ull);
     }
 #undef NOALLOC_TRY
     return PDX_OK;

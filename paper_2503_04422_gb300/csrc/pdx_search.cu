@@ -25,6 +25,9 @@
 // A relative slack gamma = D * 2^-23 on every threshold covers the rounding of
 // FP32 partial sums, so an FP32 partial that exceeds tau*(1+gamma) has an
 // exact partial above the exact tau.
+#include <cuda_bf16.h>
+#include <cuda_fp8.h>
+
 #include "pdx_internal.cuh"
 
 namespace pdx {
@@ -42,6 +45,65 @@ __device__ __forceinline__ float term(float qv, float x, float acc) {
         return fmaf(qv, x, acc);
     } else {
         return acc + fabsf(qv - x);
+    }
+}
+
+// ---- storage types of the PDX blocks ----
+enum { ST_F32 = 0, ST_BF16 = 1, ST_FP8 = 2 };
+
+template <int ST> struct Elem;
+template <> struct Elem<ST_F32> {
+    using T = float;
+    static __device__ __forceinline__ float4 load4(const T *p) { return __ldg(reinterpret_cast<const float4 *>(p)); }
+    static __device__ __forceinline__ float load1(const T *p) { return __ldg(p); }
+};
+template <> struct Elem<ST_BF16> {
+    using T = uint16_t;
+    static __device__ __forceinline__ float4 load4(const T *p) {
+        uint2 v = __ldg(reinterpret_cast<const uint2 *>(p));
+        return make_float4(__uint_as_float(v.x << 16), __uint_as_float(v.x & 0xffff0000u), __uint_as_float(v.y << 16),
+                           __uint_as_float(v.y & 0xffff0000u));
+    }
+    static __device__ __forceinline__ float load1(const T *p) { return __uint_as_float((uint32_t)__ldg(p) << 16); }
+};
+template <> struct Elem<ST_FP8> {
+    using T = uint8_t;
+    static __device__ __forceinline__ float2 cvt2(uint32_t two) {
+        __half2_raw h = __nv_cvt_fp8x2_to_halfraw2((__nv_fp8x2_storage_t)(two & 0xffffu), __NV_E4M3);
+        return __half22float2(*reinterpret_cast<const __half2 *>(&h));
+    }
+    static __device__ __forceinline__ float4 load4(const T *p) {
+        uint32_t v = __ldg(reinterpret_cast<const unsigned int *>(p));
+        float2 a = cvt2(v), b = cvt2(v >> 16);
+        return make_float4(a.x, a.y, b.x, b.y);
+    }
+    static __device__ __forceinline__ float load1(const T *p) {
+        __half_raw h = __nv_cvt_fp8_to_halfraw((__nv_fp8_storage_t)__ldg(p), __NV_E4M3);
+        return __half2float(*reinterpret_cast<const __half *>(&h));
+    }
+};
+
+// One term of the distance. F32: the exact (q - x)^2 (or IP / L1 term).
+// Low-precision storage under an exact pruner (BOND, NONE): a lower bound of
+// (q - x)^2 from the stored x_hat and the per-element quantisation bound e
+// (|x - x_hat| <= e): max(0, |q - x_hat| - e)^2, with the float32 rounding of
+// |q - x_hat| (and of q / s for FP8) folded into a relative slack. For FP8 the
+// value is in units of the per-dimension scale s (qv = q/s, s2 = s^2).
+// Under an approximate pruner (ADSampling, BSA) the stored value is used as
+// is. Survivors of low-precision scans are reranked in FP32.
+template <int ST, bool LB>
+__device__ __forceinline__ float lp_term(float qv, float xh, float acc, float s2) {
+    if (ST == ST_F32 || !LB) {
+        float t = qv - xh;
+        return (ST == ST_FP8) ? fmaf(s2 * t, t, acc) : fmaf(t, t, acc);
+    } else if (ST == ST_BF16) {
+        float e = fmaxf(fabsf(xh) * 3.90625607e-3f, 4.6e-41f);           // |x_hat| 2^-8 (1+2^-20), 2^-134
+        float t = fabsf(qv - xh) * 0.99999976f - e;                      // (1 - 2^-22)
+        return t > 0.f ? fmaf(t, t, acc) : acc;
+    } else {
+        float e = fmaxf(fabsf(xh) * 6.25006e-2f, 9.765634e-4f);          // max(|c| 2^-4, 2^-10) (1+2^-20)
+        float t = fabsf(qv - xh) * 0.99999976f - e - fabsf(qv) * 2.3841858e-7f;
+        return t > 0.f ? fmaf(s2 * t, t, acc) : acc;
     }
 }
 
@@ -94,7 +156,8 @@ __device__ __forceinline__ void topk_insert(uint64_t *list, int &cnt, int k, uin
 
 struct WarpSmem {
     uint16_t *ord;      // [d] dimension visited at position i
-    float *qo;          // [d] query value of that dimension
+    float *qo;          // [d] query value of that dimension (FP8 storage: divided by its scale)
+    float *s2o;         // [d] FP8 storage: squared scale of that dimension
     uint64_t *topk;     // [k]
     int32_t *sv;        // [kMaxSurv] survivor slot indices
     float *sp;          // [kMaxSurv] survivor partial distances
@@ -121,23 +184,29 @@ __host__ __device__ inline int sort_units(int d, int zone_dims, int order, int p
     return (d + z - 1) / z;
 }
 
-__host__ __device__ inline size_t warp_smem_bytes(int d, int k) {
-    return align16((size_t)d * 2) + align16((size_t)d * 4) + align16((size_t)k * 8) + align16(kMaxSurv * 4) * 2;
+__host__ __device__ inline size_t warp_smem_bytes(int d, int k, bool scaled) {
+    return align16((size_t)d * 2) + align16((size_t)d * 4) * (scaled ? 2 : 1) + align16((size_t)k * 8) +
+           align16(kMaxSurv * 4) * 2;
 }
 
 size_t scan_warp_smem(int d, int k, int zone_dims, int order) {
     (void)zone_dims;
     (void)order;
-    return warp_smem_bytes(d, k);
+    return warp_smem_bytes(d, k, false);
 }
 
-__device__ __forceinline__ WarpSmem carve(unsigned char *base, int d, int k) {
+__device__ __forceinline__ WarpSmem carve(unsigned char *base, int d, int k, bool scaled) {
     WarpSmem w;
     size_t o = 0;
     w.ord = reinterpret_cast<uint16_t *>(base + o);
     o += align16((size_t)d * 2);
     w.qo = reinterpret_cast<float *>(base + o);
     o += align16((size_t)d * 4);
+    w.s2o = nullptr;
+    if (scaled) {
+        w.s2o = reinterpret_cast<float *>(base + o);
+        o += align16((size_t)d * 4);
+    }
     w.topk = reinterpret_cast<uint64_t *>(base + o);
     o += align16((size_t)k * 8);
     w.sv = reinterpret_cast<int32_t *>(base + o);
@@ -191,22 +260,28 @@ __device__ __forceinline__ void reg_bitonic_sort(uint64_t (&key)[8], int lane) {
 //    sum over the zone of (q_j - mu_j)^2 against the block means, best zone
 //    first, storage order inside a zone, ties to the lower zone;
 //  - otherwise storage order.
+__device__ __forceinline__ void put_dim(const WarpSmem &w, int i, int j, const float *__restrict__ qrow,
+                                        const float *__restrict__ scale) {
+    w.ord[i] = (uint16_t)j;
+    if (scale) {
+        float sj = scale[j];
+        w.qo[i] = qrow[j] / sj;
+        w.s2o[i] = sj * sj;
+    } else {
+        w.qo[i] = qrow[j];
+    }
+}
+
 __device__ void build_order(const WarpSmem &w, const float *__restrict__ qrow, const float *__restrict__ mu,
-                            const uint16_t *__restrict__ given, int d, int zone_dims, int nunits, int lane) {
+                            const uint16_t *__restrict__ given, const float *__restrict__ scale, int d, int zone_dims,
+                            int nunits, int lane) {
     if (given) {
-        for (int i = lane; i < d; i += 32) {
-            int j = given[i];
-            w.ord[i] = (uint16_t)j;
-            w.qo[i] = qrow[j];
-        }
+        for (int i = lane; i < d; i += 32) put_dim(w, i, given[i], qrow, scale);
         __syncwarp();
         return;
     }
     if (nunits == 0) {
-        for (int i = lane; i < d; i += 32) {
-            w.ord[i] = (uint16_t)i;
-            w.qo[i] = qrow[i];
-        }
+        for (int i = lane; i < d; i += 32) put_dim(w, i, i, qrow, scale);
         __syncwarp();
         return;
     }
@@ -245,10 +320,7 @@ __device__ void build_order(const WarpSmem &w, const float *__restrict__ qrow, c
             const int z = (int)(key[t] & 0xffffffffu);
             const int off = r * Z - ((r > rlast) ? (Z - lastlen) : 0);
             const int len = (z == nunits - 1) ? lastlen : Z;
-            for (int u = 0; u < len; ++u) {
-                w.ord[off + u] = (uint16_t)(z * Z + u);
-                w.qo[off + u] = qrow[z * Z + u];
-            }
+            for (int u = 0; u < len; ++u) put_dim(w, off + u, z * Z + u, qrow, scale);
         }
     }
     __syncwarp();
@@ -286,13 +358,28 @@ __device__ __forceinline__ bool prune_test(float partial, float thr, int dv, int
 #define PDX_SCAN_MIN_CTAS 3
 #endif
 
-template <int PR, int MET>
+// Exact FP32 L2 distance of one stored vector (row of the N-ary FP32 copy)
+// to the query; lanes take dimensions j = lane, lane + 32, ... (warp-uniform).
+__device__ __forceinline__ float rerank_l2(const float *__restrict__ xrow, const float *__restrict__ qrow, int D,
+                                          int lane) {
+    float acc = 0.f;
+    for (int j = lane; j < D; j += 32) {
+        float t = qrow[j] - __ldg(xrow + j);
+        acc = fmaf(t, t, acc);
+    }
+    return warp_sum(acc);
+}
+
+template <int PR, int MET, int ST>
 __global__ void __launch_bounds__(256, PDX_SCAN_MIN_CTAS) pdxsearch_kernel(ScanParams a) {
+    using ET = typename Elem<ST>::T;
+    constexpr bool kLB = (PR == PR_BOND || PR == PR_NONE);  // low-precision: prune on a lower bound
     extern __shared__ __align__(16) unsigned char smem[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int D = a.d;
     const int nunits = sort_units(D, a.zone_dims, a.order, PR, a.qorder != nullptr);
-    WarpSmem w = carve(smem + (size_t)warp * warp_smem_bytes(D, a.k), D, a.k);
+    WarpSmem w = carve(smem + (size_t)warp * warp_smem_bytes(D, a.k, ST == ST_FP8), D, a.k, ST == ST_FP8);
+    const ET *xbase = reinterpret_cast<const ET *>(ST == ST_F32 ? static_cast<const void *>(a.data) : a.data_lp);
     const int h = lane >> 4, sl = lane & 15;
     const int k = a.k;
     const int chunks = a.chunks_per_part;
@@ -321,14 +408,15 @@ __global__ void __launch_bounds__(256, PDX_SCAN_MIN_CTAS) pdxsearch_kernel(ScanP
         const float *qrow = a.q + qi * D;
         const uint16_t *given = nullptr;
         if (a.qorder) given = a.qorder + (a.qorder_per_part ? (qi * (a.nslots / chunks) + pr) : qi) * (int64_t)D;
-        build_order(w, qrow, a.means ? a.means + (int64_t)part * D : nullptr, given, D, a.zone_dims, nunits, lane);
+        build_order(w, qrow, a.means ? a.means + (int64_t)part * D : nullptr, given,
+                    (ST == ST_FP8) ? a.scale : nullptr, D, a.zone_dims, nunits, lane);
         volatile uint32_t *tau_g_ptr = reinterpret_cast<volatile uint32_t *>(a.tau) + qi;
         int cnt = 0;
         float tau_loc = __int_as_float(0x7f800000);
         const float *qaux = (PR == PR_BSA) ? a.qaux + qi * a.nchk * 2 : nullptr;
 
         for (int b = b0; b < b1; ++b) {
-            const float *xb = a.data + (int64_t)b * D * kBlock;
+            const ET *xb = xbase + (int64_t)b * D * kBlock;
             const int nvalid = a.blk_cnt[b];
             const float tau_g = o2f(*tau_g_ptr);
             const float thr = slack(fminf(tau_loc, tau_g), a.gamma);
@@ -349,20 +437,28 @@ __global__ void __launch_bounds__(256, PDX_SCAN_MIN_CTAS) pdxsearch_kernel(ScanP
                 int i = pos;
                 for (; i + 8 <= e; i += 8) {
                     float4 x[4];
-                    float qv[4];
+                    float qv[4], s2[4];
 #pragma unroll
                     for (int u = 0; u < 4; ++u) {
                         const int ii = i + 2 * u + h;
                         const int j = w.ord[ii];
                         qv[u] = w.qo[ii];
-                        x[u] = __ldg(reinterpret_cast<const float4 *>(xb + j * kBlock) + sl);
+                        s2[u] = (ST == ST_FP8) ? w.s2o[ii] : 1.f;
+                        x[u] = Elem<ST>::load4(xb + j * kBlock + 4 * sl);
                     }
 #pragma unroll
                     for (int u = 0; u < 4; ++u) {
-                        acc.x = term<MET>(qv[u], x[u].x, acc.x);
-                        acc.y = term<MET>(qv[u], x[u].y, acc.y);
-                        acc.z = term<MET>(qv[u], x[u].z, acc.z);
-                        acc.w = term<MET>(qv[u], x[u].w, acc.w);
+                        if (ST == ST_F32) {
+                            acc.x = term<MET>(qv[u], x[u].x, acc.x);
+                            acc.y = term<MET>(qv[u], x[u].y, acc.y);
+                            acc.z = term<MET>(qv[u], x[u].z, acc.z);
+                            acc.w = term<MET>(qv[u], x[u].w, acc.w);
+                        } else {
+                            acc.x = lp_term<ST, kLB>(qv[u], x[u].x, acc.x, s2[u]);
+                            acc.y = lp_term<ST, kLB>(qv[u], x[u].y, acc.y, s2[u]);
+                            acc.z = lp_term<ST, kLB>(qv[u], x[u].z, acc.z, s2[u]);
+                            acc.w = lp_term<ST, kLB>(qv[u], x[u].w, acc.w, s2[u]);
+                        }
                     }
                 }
                 for (; i < e; i += 2) {
@@ -370,11 +466,19 @@ __global__ void __launch_bounds__(256, PDX_SCAN_MIN_CTAS) pdxsearch_kernel(ScanP
                     if (ii < e) {
                         const int j = w.ord[ii];
                         const float qv = w.qo[ii];
-                        float4 x = __ldg(reinterpret_cast<const float4 *>(xb + j * kBlock) + sl);
-                        acc.x = term<MET>(qv, x.x, acc.x);
-                        acc.y = term<MET>(qv, x.y, acc.y);
-                        acc.z = term<MET>(qv, x.z, acc.z);
-                        acc.w = term<MET>(qv, x.w, acc.w);
+                        const float4 x = Elem<ST>::load4(xb + j * kBlock + 4 * sl);
+                        if (ST == ST_F32) {
+                            acc.x = term<MET>(qv, x.x, acc.x);
+                            acc.y = term<MET>(qv, x.y, acc.y);
+                            acc.z = term<MET>(qv, x.z, acc.z);
+                            acc.w = term<MET>(qv, x.w, acc.w);
+                        } else {
+                            const float s2 = (ST == ST_FP8) ? w.s2o[ii] : 1.f;
+                            acc.x = lp_term<ST, kLB>(qv, x.x, acc.x, s2);
+                            acc.y = lp_term<ST, kLB>(qv, x.y, acc.y, s2);
+                            acc.z = lp_term<ST, kLB>(qv, x.z, acc.z, s2);
+                            acc.w = lp_term<ST, kLB>(qv, x.w, acc.w, s2);
+                        }
                     }
                 }
                 c_values += (lane == 0) ? (unsigned long long)(e - pos) * nvalid : 0ull;
@@ -444,8 +548,13 @@ __global__ void __launch_bounds__(256, PDX_SCAN_MIN_CTAS) pdxsearch_kernel(ScanP
                     const int e = min(D, pos + step);
                     float acc1 = 0.f;
                     if (m < nsurv) {
-                        for (int i = pos + g; i < e; i += G)
-                            acc1 = term<MET>(w.qo[i], __ldg(xb + (int)w.ord[i] * kBlock + my_v), acc1);
+                        for (int i = pos + g; i < e; i += G) {
+                            const float xv = Elem<ST>::load1(xb + (int)w.ord[i] * kBlock + my_v);
+                            if (ST == ST_F32)
+                                acc1 = term<MET>(w.qo[i], xv, acc1);
+                            else
+                                acc1 = lp_term<ST, kLB>(w.qo[i], xv, acc1, (ST == ST_FP8) ? w.s2o[i] : 1.f);
+                        }
                     }
                     for (int o = G >> 1; o; o >>= 1) acc1 += __shfl_xor_sync(kFull, acc1, o);
                     my_p += acc1;
@@ -509,7 +618,9 @@ __global__ void __launch_bounds__(256, PDX_SCAN_MIN_CTAS) pdxsearch_kernel(ScanP
                         cm &= cm - 1u;
                         float dd = __shfl_sync(kFull, dist, src);
                         int v = 4 * src + c;
-                        uint64_t key = make_key(dd, a.ids[(int64_t)b * kBlock + v]);
+                        const int id = a.ids[(int64_t)b * kBlock + v];
+                        if (ST != ST_F32) dd = rerank_l2(a.xnary + (int64_t)id * D, qrow, D, lane);  // exact FP32
+                        uint64_t key = make_key(dd, id);
                         topk_insert(w.topk, cnt, k, key, lane);
                         ++c_cand;
                     }
@@ -528,7 +639,9 @@ __global__ void __launch_bounds__(256, PDX_SCAN_MIN_CTAS) pdxsearch_kernel(ScanP
                     cm &= cm - 1u;
                     float dd = __shfl_sync(kFull, dist, src);
                     int v = __shfl_sync(kFull, my_v, src);
-                    uint64_t key = make_key(dd, a.ids[(int64_t)b * kBlock + v]);
+                    const int id = a.ids[(int64_t)b * kBlock + v];
+                    if (ST != ST_F32) dd = rerank_l2(a.xnary + (int64_t)id * D, qrow, D, lane);  // exact FP32
+                    uint64_t key = make_key(dd, id);
                     topk_insert(w.topk, cnt, k, key, lane);
                     ++c_cand;
                 }
@@ -556,16 +669,16 @@ __global__ void __launch_bounds__(256, PDX_SCAN_MIN_CTAS) pdxsearch_kernel(ScanP
     }
 }
 
-template <int PR, int MET>
+template <int PR, int MET, int ST>
 static cudaError_t launch_scan_t(const ScanParams &p, int num_sms, cudaStream_t st) {
     const int nunits = sort_units(p.d, p.zone_dims, p.order, PR, p.qorder != nullptr);
     if (nunits > kMaxSortUnits) return cudaErrorInvalidValue;
-    const size_t per_warp = warp_smem_bytes(p.d, p.k);
+    const size_t per_warp = warp_smem_bytes(p.d, p.k, ST == ST_FP8);
     int warps = 8;
     while (warps > 1 && per_warp * warps > 200 * 1024) warps >>= 1;
     const size_t smem = per_warp * warps;
     if (smem > 227 * 1024) return cudaErrorInvalidValue;
-    auto kern = pdxsearch_kernel<PR, MET>;
+    auto kern = pdxsearch_kernel<PR, MET, ST>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     // Shared-memory carveout sized for the requested number of resident CTAs
@@ -590,20 +703,37 @@ static cudaError_t launch_scan_t(const ScanParams &p, int num_sms, cudaStream_t 
     return counted(cudaGetLastError());
 }
 
+template <int ST>
+static cudaError_t launch_scan_lp(int pruner, const ScanParams &p, int num_sms, cudaStream_t st) {
+    switch (pruner) {
+    case PR_NONE: return launch_scan_t<PR_NONE, MT_L2, ST>(p, num_sms, st);
+    case PR_BOND: return launch_scan_t<PR_BOND, MT_L2, ST>(p, num_sms, st);
+    case PR_ADS: return launch_scan_t<PR_ADS, MT_L2, ST>(p, num_sms, st);
+    case PR_BSA: return launch_scan_t<PR_BSA, MT_L2, ST>(p, num_sms, st);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
 cudaError_t launch_scan(int pruner, int metric, const ScanParams &p, int num_sms, cudaStream_t st) {
     if (p.nitems == 0) return cudaSuccess;
+    if (p.storage != ST_F32) {
+        // low-precision storage: L2 only (lower bound / FP32 rerank are L2)
+        if (metric != MT_L2) return cudaErrorInvalidValue;
+        return p.storage == ST_BF16 ? launch_scan_lp<ST_BF16>(pruner, p, num_sms, st)
+                                    : launch_scan_lp<ST_FP8>(pruner, p, num_sms, st);
+    }
     switch (pruner) {
     case PR_NONE:
-        if (metric == MT_IP) return launch_scan_t<PR_NONE, MT_IP>(p, num_sms, st);
-        if (metric == MT_L1) return launch_scan_t<PR_NONE, MT_L1>(p, num_sms, st);
-        return launch_scan_t<PR_NONE, MT_L2>(p, num_sms, st);
+        if (metric == MT_IP) return launch_scan_t<PR_NONE, MT_IP, ST_F32>(p, num_sms, st);
+        if (metric == MT_L1) return launch_scan_t<PR_NONE, MT_L1, ST_F32>(p, num_sms, st);
+        return launch_scan_t<PR_NONE, MT_L2, ST_F32>(p, num_sms, st);
     case PR_BOND:
-        if (metric == MT_L1) return launch_scan_t<PR_BOND, MT_L1>(p, num_sms, st);
-        return launch_scan_t<PR_BOND, MT_L2>(p, num_sms, st);
+        if (metric == MT_L1) return launch_scan_t<PR_BOND, MT_L1, ST_F32>(p, num_sms, st);
+        return launch_scan_t<PR_BOND, MT_L2, ST_F32>(p, num_sms, st);
     case PR_ADS:
-        return launch_scan_t<PR_ADS, MT_L2>(p, num_sms, st);
+        return launch_scan_t<PR_ADS, MT_L2, ST_F32>(p, num_sms, st);
     case PR_BSA:
-        return launch_scan_t<PR_BSA, MT_L2>(p, num_sms, st);
+        return launch_scan_t<PR_BSA, MT_L2, ST_F32>(p, num_sms, st);
     default:
         return cudaErrorInvalidValue;
     }
@@ -665,6 +795,63 @@ __global__ void __launch_bounds__(256) dense_keys_kernel(const float *__restrict
             keys[qi * L + (int64_t)b * kBlock + v] = (id >= 0) ? make_key(rank_dist<MET>(acc[i][j]), id) : kEmptyKey;
         }
     }
+}
+
+// START on row-major FP32 vectors (the low-precision indexes' FP32 copy):
+// keys[qi][r] = (exact distance of row r, id r) for the first nrows rows.
+__global__ void __launch_bounds__(256) dense_keys_rows_kernel(const float *__restrict__ q, int64_t nq,
+                                                              const float *__restrict__ x, int32_t nrows, int32_t d,
+                                                              int64_t ld, uint64_t *__restrict__ keys) {
+    __shared__ __align__(16) float Qs[32][68];
+    __shared__ __align__(16) float Xs[32][68];
+    const int tid = threadIdx.x, ty = tid >> 4, tx = tid & 15;
+    const int64_t q0 = (int64_t)blockIdx.x * 64;
+    const int r0 = blockIdx.y * 64;
+    float acc[4][4] = {};
+    for (int j0 = 0; j0 < d; j0 += 32) {
+        for (int e = tid; e < 64 * 32; e += 256) {
+            int rr = e >> 5, jj = e & 31;
+            int j = j0 + jj;
+            int64_t qi = q0 + rr;
+            Qs[jj][rr] = (qi < nq && j < d) ? q[qi * d + j] : 0.f;
+            int r = r0 + rr;
+            Xs[jj][rr] = (r < nrows && j < d) ? x[(int64_t)r * d + j] : 0.f;
+        }
+        __syncthreads();
+        const int jn = min(32, d - j0);
+        for (int jj = 0; jj < jn; ++jj) {
+            float4 av = *reinterpret_cast<const float4 *>(&Qs[jj][ty * 4]);
+            float4 bv = *reinterpret_cast<const float4 *>(&Xs[jj][tx * 4]);
+            float aa[4] = {av.x, av.y, av.z, av.w}, bb[4] = {bv.x, bv.y, bv.z, bv.w};
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    float t = aa[i] - bb[j];
+                    acc[i][j] = fmaf(t, t, acc[i][j]);
+                }
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        int64_t qi = q0 + ty * 4 + i;
+        if (qi >= nq) continue;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            int r = r0 + tx * 4 + j;
+            if (r < ld) keys[qi * ld + r] = (r < nrows) ? make_key(acc[i][j], r) : kEmptyKey;
+        }
+    }
+}
+
+cudaError_t launch_dense_keys_rows(const float *q, int64_t nq, const float *x, int32_t nrows, int32_t d, int64_t ld,
+                                   uint64_t *keys, cudaStream_t st) {
+    if (nq == 0 || nrows == 0) return cudaSuccess;
+    if (nrows > ld) return cudaErrorInvalidValue;
+    dim3 grid((unsigned)((nq + 63) / 64), (unsigned)((nrows + 63) / 64));
+    dense_keys_rows_kernel<<<grid, 256, 0, st>>>(q, nq, x, nrows, d, ld, keys);
+    return counted(cudaGetLastError());
 }
 
 cudaError_t launch_dense_keys(const float *q, int64_t nq, const float *data, const int32_t *ids, int32_t d,
@@ -768,6 +955,40 @@ __global__ void refine_kernel(const uint64_t *__restrict__ topk, int64_t nq, int
     for (int j = lane; j < d; j += 32) acc = term<MET>(qr[j], xb[(int64_t)j * kBlock], acc);
     acc = warp_sum(acc);
     if (lane == 0) out[w] = make_key(rank_dist<MET>(acc), id);
+}
+
+// Canonical distances from row-major FP32 vectors (low-precision indexes).
+template <int MET>
+__global__ void refine_rows_kernel(const uint64_t *__restrict__ topk, int64_t nq, int32_t k, const float *__restrict__ q,
+                                   int32_t d, const float *__restrict__ x, uint64_t *__restrict__ out) {
+    const int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (w >= nq * k) return;
+    const int64_t row = w / k;
+    const uint64_t key = topk[w];
+    if (key == kEmptyKey) {
+        if (lane == 0) out[w] = kEmptyKey;
+        return;
+    }
+    const int32_t id = key_id(key);
+    const float *xr = x + (int64_t)id * d;
+    const float *qr = q + row * d;
+    float acc = 0.f;
+    for (int j = lane; j < d; j += 32) acc = term<MET>(qr[j], xr[j], acc);
+    acc = warp_sum(acc);
+    if (lane == 0) out[w] = make_key(rank_dist<MET>(acc), id);
+}
+
+cudaError_t launch_refine_rows(const uint64_t *topk, int64_t nq, int32_t k, const float *q, int32_t d, const float *x,
+                               int metric, uint64_t *out, cudaStream_t st) {
+    int64_t warps = nq * k;
+    if (warps == 0) return cudaSuccess;
+    unsigned grid = (unsigned)((warps * 32 + 255) / 256);
+    if (metric == MT_IP)
+        refine_rows_kernel<MT_IP><<<grid, 256, 0, st>>>(topk, nq, k, q, d, x, out);
+    else
+        refine_rows_kernel<MT_L2><<<grid, 256, 0, st>>>(topk, nq, k, q, d, x, out);
+    return counted(cudaGetLastError());
 }
 
 cudaError_t launch_refine(const uint64_t *topk, int64_t nq, int32_t k, const float *q, int32_t d, const float *data,

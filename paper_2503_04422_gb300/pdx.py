@@ -25,7 +25,7 @@ PRUNER = {"none": 0, "bond": 1, "ads": 2, "adsampling": 2, "bsa": 3}
 ORDER = {"dist_to_means": 0, "decreasing": 1, "sequential": 2}
 MEANS = {"block": 0, "collection": 1, "auto": 2}
 ARRAY = {"blocks": 0, "ids": 1, "part_blocks": 2, "means": 3, "centroids": 4, "assign": 5, "rotation": 6,
-         "variances": 7}
+         "variances": 7, "blocks_lp": 8, "scales": 9}
 STATUS_NAMES = {0: "PDX_OK", 1: "PDX_ERR_ARG", 2: "PDX_ERR_OOM", 3: "PDX_ERR_CUDA", 4: "PDX_ERR_TIMEOUT",
                 5: "PDX_ERR_UNSUPPORTED"}
 
@@ -176,7 +176,9 @@ class Index:
             "blocks": ((inf.nblocks, inf.d, 64), np.float32), "ids": ((inf.nblocks * 64,), np.int32),
             "part_blocks": ((inf.nparts + 1,), np.int32), "means": ((inf.nparts, inf.d), np.float32),
             "centroids": ((inf.nparts, inf.d), np.float32), "assign": ((inf.n,), np.int32),
-            "rotation": ((inf.d, inf.d), np.float32), "variances": ((inf.d,), np.float32)}
+            "rotation": ((inf.d, inf.d), np.float32), "variances": ((inf.d,), np.float32),
+            "blocks_lp": ((inf.nblocks, inf.d, 64), np.uint16 if inf.storage == 1 else np.uint8),
+            "scales": ((inf.d,), np.float32)}
         shape, dt = shapes[which]
         out = np.empty(shape, dt)
         _check(lib().pdx_index_copy_out(self.handle, ARRAY[which], out.ctypes.data, out.nbytes), "pdx_index_copy_out")
