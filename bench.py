@@ -33,6 +33,7 @@ METRIC = ("queries/sec at exact top-10 (and recall@10=0.95 IVF); HBM GB/s vs pea
 WORKLOADS = {
     "bond_exact_1m_d768": dict(k=10, pruner="bond"),
     "plain_scan_10k_d128": dict(k=10, pruner="none"),
+    "ivf_1m_d960": dict(k=10, pruner="ads", nlist=1024),
 }
 PROFILE_TRAFFIC = os.path.join(ROOT, "profiles", "traffic.json")
 
@@ -222,7 +223,7 @@ def run_ours(args, rank, world, local_rank):
     q = np.ascontiguousarray(q_all[rank * base_nq:(rank + 1) * base_nq])
     n, d = x.shape
     nq = q.shape[0]
-    ix = pdx.pdx_build_layout(torch.from_numpy(x).cuda())
+    ix = pdx.pdx_build_layout(torch.from_numpy(x).cuda(), storage=args.storage)
     torch.cuda.synchronize()
     torch.cuda.empty_cache()
     q_dev = torch.from_numpy(q).cuda()
@@ -282,11 +283,14 @@ def run_ours(args, rank, world, local_rank):
     # roofline of the PDXearch scan: logical bytes it read per launch over its
     # average event-timed duration
     values_per_launch = float(st[0]) / K
-    bytes_per_launch = values_per_launch * 4.0
+    esize = {"f32": 4.0, "bf16": 2.0, "fp8": 1.0}[args.storage]
+    # logical bytes of the scan: values visited x element size, plus the FP32
+    # rerank rows of low-precision candidates
+    bytes_per_launch = values_per_launch * esize + (0.0 if args.storage == "f32" else float(st[4]) / K * d * 4.0)
     scan_avg_ms = sum(scan_ms) / K
     achieved = bytes_per_launch / (scan_avg_ms / 1e3) / 1e9
     peak, peak_kind = _peak_hbm()
-    traffic = _traffic_per_launch(args.workload)
+    traffic = _traffic_per_launch(args.workload) if args.storage == "f32" else None
 
     # end to end through the C ABI with host (pinned) buffers
     e2e = None
@@ -303,13 +307,15 @@ def run_ours(args, rank, world, local_rank):
         line = {
             "metric": METRIC, "value": value, "unit": "queries/s", "n_gpus": world, "steps": K,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": args.workload, "n": n, "d": d, "nq_per_gpu": nq, "k": k,
-                       "pruner": spec["pruner"], "order": "dist_to_means", "zone_dims": int(opts.zone_dims),
+            "vs_baseline": None, "dtype": args.storage, "data": "synthetic",
+            "config": {"workload": args.workload, "n": n, "d": d, "nq_per_gpu": nq, "k": k, "storage": args.storage,
+                       "pruner": spec["pruner"], "order": "dist_to_means",
+                       "means": "collection (automatic for exact search)", "zone_dims": "1 (automatic)",
                        "first_step": int(opts.first_step), "selection_threshold": round(float(opts.selection_threshold), 3),
-                       "start_vectors": int(opts.start_vectors),
+                       "start_vectors": int(opts.start_vectors), "ctas_per_sm": "3 (automatic)",
                        "l2": "collection 3.1 GB > L2; 256 MB L2 flush between timed steps (untimed)"},
-            "roofline": {"bound": "hbm", "kernel": "pdxsearch_kernel<BOND,L2>", "achieved": achieved,
+            "roofline": {"bound": "hbm", "kernel": f"pdxsearch_kernel<BOND,L2,{args.storage.upper()}>",
+                         "achieved": achieved,
                          "peak": peak, "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,
                          "traffic": traffic, "algorithmic_bytes_per_launch": bytes_per_launch,
                          "scan_ms_avg": scan_avg_ms,
@@ -327,6 +333,98 @@ def run_ours(args, rank, world, local_rank):
         dist.destroy_process_group()
 
 
+def run_ivf(args, rank, world, local_rank):
+    """IVF search (Sec. 6.3-6.4 setting): 1M x 960 rotated Gaussian mixture,
+    nlist = 1024, 10,000 queries, k = 10. For each pruner the nprobe sweep
+    8..128 runs, and the line reports queries/s at the smallest nprobe whose
+    recall@10 (against the FP64 oracle on a sample of queries) is >= 0.95."""
+    import numpy as np
+    import torch
+
+    import pdx_synth
+    from oracle import knn as ok
+    from paper_2503_04422_gb300 import build as pbuild
+    pbuild.build()
+    ok.build()
+    from paper_2503_04422_gb300 import pdx
+
+    torch.cuda.set_device(local_rank)
+    spec = WORKLOADS[args.workload]
+    k, nlist = spec["k"], spec["nlist"]
+    nq = args.nq or pdx_synth.WORKLOADS[args.workload]["nq"]
+    x, q = pdx_synth.make(args.workload, n=args.n, nq=nq)
+    n, d = x.shape
+    rng = np.random.default_rng(2503)
+    sample = np.sort(rng.choice(nq, size=min(nq, args.recall_queries), replace=False))
+    truth = ok.knn(x, q[sample], k)[1]
+    xd = torch.from_numpy(x).cuda()
+    qd = torch.from_numpy(q).cuda()
+    od = torch.empty((nq, k), dtype=torch.float32, device="cuda")
+    oi = torch.empty((nq, k), dtype=torch.int64, device="cuda")
+    stats_dev = torch.zeros(16, dtype=torch.int64, device="cuda")
+    results = {}
+    pruners = [p.strip() for p in args.pruners.split(",")]
+    transforms = {"ads": "ads", "bsa": "bsa", "bond": "none", "none": "none"}
+    built = {}
+    for pruner in pruners:
+        tr = transforms[pruner]
+        if tr not in built:
+            rot = pdx_synth.random_orthogonal(d, 77) if tr == "ads" else None
+            t0 = time.perf_counter()
+            built[tr] = pdx.pdx_ivf_build(xd, nlist=nlist, kmeans_iters=10, kmeans_sample=min(n, 256 * nlist),
+                                          transform=tr, rotation=rot, storage=args.storage)
+            torch.cuda.synchronize()
+            build_s = time.perf_counter() - t0
+        ix = built[tr]
+        rows = []
+        for nprobe in (8, 16, 32, 64, 128):
+            opts = pdx.search_opts(pruner=pruner)
+            for _ in range(args.warmup):
+                pdx.pdx_search_ivf(ix, qd, k, nprobe, opts=opts, out=(od, oi))
+            ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+            evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+            for a_, b_ in evs:
+                a_.record()
+                b_.record()
+            stats_dev.zero_()
+            torch.cuda.synchronize()
+            for i in range(args.steps):
+                opts.scan_event_start, opts.scan_event_stop = evs[i][0].cuda_event, evs[i][1].cuda_event
+                opts.stats_device = stats_dev.data_ptr()
+                ev[i][0].record()
+                pdx.pdx_search_ivf(ix, qd, k, nprobe, opts=opts, out=(od, oi))
+                ev[i][1].record()
+            torch.cuda.synchronize()
+            ms = sum(a_.elapsed_time(b_) for a_, b_ in ev) / args.steps
+            scan_ms = sum(a_.elapsed_time(b_) for a_, b_ in evs) / args.steps
+            st = stats_dev.cpu().numpy().astype(np.float64)
+            rec = ok.recall_at_k(truth, oi.cpu().numpy()[sample])
+            esize = {"f32": 4.0, "bf16": 2.0, "fp8": 1.0}[args.storage]
+            byts = st[0] / args.steps * esize + (0.0 if args.storage == "f32" else st[4] / args.steps * d * 4.0)
+            rows.append(dict(nprobe=nprobe, qps=nq / (ms / 1e3), ms=ms, recall=rec, scan_ms=scan_ms,
+                             scan_gbs=byts / (scan_ms / 1e3) / 1e9,
+                             visited_fraction=st[0] / args.steps / (nq * nprobe * (n / nlist) * d)))
+            print(json.dumps({"pruner": pruner, **rows[-1]}), file=sys.stderr, flush=True)
+        ok_rows = [r for r in rows if r["recall"] >= 0.95]
+        results[pruner] = dict(at_recall_095=(ok_rows[0] if ok_rows else None), sweep=rows)
+    main_p = pruners[0]
+    best = results[main_p]["at_recall_095"] or results[main_p]["sweep"][-1]
+    peak, peak_kind = _peak_hbm()
+    line = {"metric": METRIC, "value": best["qps"], "unit": "queries/s", "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": best["ms"], "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": args.storage, "data": "synthetic",
+            "config": {"workload": args.workload, "n": n, "d": d, "nq": nq, "k": k, "nlist": nlist,
+                       "pruner": main_p, "storage": args.storage, "nprobe": best["nprobe"],
+                       "recall@10": best["recall"], "recall_queries": int(sample.size),
+                       "l2": "collection 3.8 GB > L2"},
+            "roofline": {"bound": "hbm", "kernel": f"pdxsearch_kernel<{main_p.upper()},L2>", "achieved": best["scan_gbs"],
+                         "peak": peak, "peak_kind": peak_kind, "unit": "GB/s", "frac": best["scan_gbs"] / peak,
+                         "traffic": None},
+            "pruners": {p: r["at_recall_095"] for p, r in results.items()},
+            "sweeps": {p: r["sweep"] for p, r in results.items()}}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -339,6 +437,9 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--n", type=int, default=None, help="smaller collection (profiling); default = workload size")
     ap.add_argument("--nq", type=int, default=None, help="queries per GPU; default = workload size")
+    ap.add_argument("--storage", default="f32", choices=["f32", "bf16", "fp8"])
+    ap.add_argument("--pruners", default="ads,bsa,bond", help="IVF workload: pruners to sweep")
+    ap.add_argument("--recall-queries", type=int, default=200, help="IVF workload: queries checked by the oracle")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3
@@ -347,6 +448,8 @@ def main():
     local_rank = _env_int("LOCAL_RANK", 0)
     if args.impl == "reference":
         run_reference(args, rank, world)
+    elif args.workload.startswith("ivf"):
+        run_ivf(args, rank, world, local_rank)
     else:
         run_ours(args, rank, world, local_rank)
 

@@ -270,6 +270,57 @@ pdx_status pdx_search_exact_noalloc(const pdx_index *index, const float *q, int6
                                     const pdx_search_opts *opts, float *out_dist, int64_t *out_idx,
                                     void *stream);
 
+/*
+ * Batched serving (no counterpart in the paper, which answers one query at a
+ * time on one thread): a server answers exact k-NN batches of 1..max_batch
+ * queries against any of `count` exact indexes (collections of uneven size and
+ * dimensionality). Each (collection, power-of-two batch bucket) pair is
+ * prepared on first use. The search is captured as a CUDA graph and replayed
+ * afterwards (use_graphs). Its launch shape (resident scan CTAs per SM, first
+ * fetch step, START size) is first chosen by timing candidates on that first
+ * batch (autotune). Exact results are identical for every candidate. Tuning
+ * results persist in the JSON file tune_cache (optional).
+ *
+ * The server owns one device workspace sized for its largest plan, plus
+ * staging buffers and a private stream. Calls are serialised internally;
+ * `stream` orders a call after the caller's prior work, and the caller's
+ * stream waits for the results. Host outputs make the call synchronous.
+ * Indexes must outlive the server.
+ */
+typedef struct pdx_server pdx_server;
+
+typedef struct pdx_server_opts {
+    uint32_t struct_size;      /* = sizeof(pdx_server_opts)                                */
+    int32_t k;                 /* neighbours per query (1..1024)                            */
+    int32_t max_batch;         /* largest batch a call may pass (1..65536)                  */
+    int32_t use_graphs;        /* capture each (collection, bucket) search in a CUDA graph  */
+    int32_t autotune;          /* time candidate launch shapes on first use                 */
+    const char *tune_cache;    /* optional JSON file of tuning results (read and written)   */
+    pdx_search_opts search;    /* base options; pruner NONE or BOND                         */
+} pdx_server_opts;
+
+typedef struct pdx_server_info_t {
+    int32_t collections;
+    int32_t max_bucket;
+    uint64_t workspace_bytes;
+    uint64_t graph_launches;   /* batches served by replaying a graph                       */
+    uint64_t direct_launches;  /* batches served by direct launches                         */
+    uint64_t tunings;          /* (collection, bucket) pairs tuned by timing                */
+    int32_t entries_ready;
+} pdx_server_info_t;
+
+void pdx_default_server_opts(pdx_server_opts *opts);
+/* Errors: PDX_ERR_ARG (NULL/empty, IVF index, k or max_batch out of range, an
+ * approximate pruner), PDX_ERR_OOM, PDX_ERR_CUDA. */
+pdx_status pdx_server_create(const pdx_index *const *indexes, int32_t count, const pdx_server_opts *opts,
+                             pdx_server **out);
+/* Exact top-k of nq (1..max_batch) queries q[nq][d] of collection `collection`;
+ * outputs as pdx_search_exact. Errors: PDX_ERR_ARG, PDX_ERR_CUDA. */
+pdx_status pdx_server_search(pdx_server *server, int32_t collection, const float *q, int64_t nq, float *out_dist,
+                             int64_t *out_idx, void *stream);
+pdx_status pdx_server_info(const pdx_server *server, pdx_server_info_t *info);
+void pdx_server_free(pdx_server *server); /* NULL-safe */
+
 /* Release an index and all of its device memory. NULL-safe. */
 void pdx_free(pdx_index *index);
 

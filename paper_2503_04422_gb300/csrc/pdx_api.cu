@@ -28,6 +28,11 @@ void set_error(const char *fmt, ...) {
     g_err = buf;
 }
 
+pdx_status cuda_status_ext(cudaError_t e, const char *what) {
+    set_error("%s failed: %s", what, cudaGetErrorString(e));
+    return e == cudaErrorMemoryAllocation ? PDX_ERR_OOM : PDX_ERR_CUDA;
+}
+
 static pdx_status cuda_status(cudaError_t e, const char *what, int line) {
     set_error("%s failed: %s (pdx_api.cu:%d)", what, cudaGetErrorString(e), line);
     return e == cudaErrorMemoryAllocation ? PDX_ERR_OOM : PDX_ERR_CUDA;
@@ -514,38 +519,11 @@ OrderPlan plan_orders(const pdx_index *ix, const pdx_search_opts &o, int pruner,
 
 }  // namespace pdx
 
-extern "C" pdx_status pdx_search_exact(const pdx_index *ix, const float *q, int64_t nq, int32_t k,
-                                       const pdx_search_opts *opts, float *out_dist, int64_t *out_idx,
-                                       void *stream) {
-    pdx_search_opts o;
-    pdx_status s = check_search_args(ix, q, nq, k, opts, out_dist, out_idx, &o, "pdx_search_exact");
-    if (s != PDX_OK) return s;
-    if (ix->is_ivf) {
-        set_error("pdx_search_exact: index was built by pdx_ivf_build");
-        return PDX_ERR_ARG;
-    }
-    if (o.pruner != PDX_PRUNE_NONE && o.pruner != PDX_PRUNE_BOND) {
-        set_error("pdx_search_exact: only NONE or BOND keep the search exact");
-        return PDX_ERR_ARG;
-    }
-    if (q && (q == out_dist || (const void *)q == (const void *)out_idx)) {
-        set_error("pdx_search_exact: outputs alias the queries");
-        return PDX_ERR_ARG;
-    }
-    SearchPlan pl;
-    s = plan_metric(ix, o.pruner, &pl, "pdx_search_exact");
-    if (s != PDX_OK) return s;
-    if (nq == 0) return PDX_OK;
-    cudaStream_t st = static_cast<cudaStream_t>(stream);
-    const int d = ix->d;
-    const bool q_dev = is_device_ptr(q);
-    const bool o_dev = is_device_ptr(out_dist) && is_device_ptr(out_idx);
-    if (is_device_ptr(out_dist) != is_device_ptr(out_idx)) {
-        set_error("pdx_search_exact: out_dist and out_idx must both be host or both be device memory");
-        return PDX_ERR_ARG;
-    }
-    const int sms = num_sms();
+namespace pdx {
 
+// Launch shape and scratch layout of an exact search (no allocation).
+pdx_status exact_plan(const pdx_index *ix, int64_t nq, int32_t k, const pdx_search_opts &o, const SearchPlan &pl,
+                      int sms, ExactPlan *ep) {
     // work items: (query, partition, block group); split partitions when
     // there are too few (query, partition) pairs to fill the GPU
     int max_blk = 0;
@@ -553,78 +531,81 @@ extern "C" pdx_status pdx_search_exact(const pdx_index *ix, const float *q, int6
     int bpi = (int)o.blocks_per_item;
     if (bpi <= 0) {
         const int64_t target = (int64_t)sms * 64 * 3;
-        int64_t pairs = nq * (int64_t)ix->nparts;
+        int64_t pairs = std::max<int64_t>(1, nq * (int64_t)ix->nparts);
         int chunks = (int)std::min<int64_t>(max_blk, std::max<int64_t>(1, (target + pairs - 1) / pairs));
         bpi = (max_blk + chunks - 1) / chunks;
     }
     if (bpi < 1) bpi = 1;
-    const int chunks = (max_blk + bpi - 1) / bpi;
-    const int nslots = ix->nparts * chunks;
-
-    const bool start = (pl.pruner != PDX_PRUNE_NONE);
-    int start_blk = 0;
-    if (start) {
+    ep->bpi = bpi;
+    ep->chunks = (max_blk + bpi - 1) / bpi;
+    ep->nslots = ix->nparts * ep->chunks;
+    ep->start = (pl.pruner != PDX_PRUNE_NONE);
+    ep->start_blk = 0;
+    if (ep->start) {
         int64_t sv = std::max<int64_t>(o.start_vectors, k);
-        start_blk = (int)std::min<int64_t>(ix->nblocks, (sv + kBlock - 1) / kBlock);
+        ep->start_blk = (int)std::min<int64_t>(ix->nblocks, (sv + kBlock - 1) / kBlock);
     }
-    const int64_t Lstart = (int64_t)start_blk * kBlock;
-    const OrderPlan op = plan_orders(ix, o, pl.pruner, nq, ix->nparts);
+    ep->Lstart = (int64_t)ep->start_blk * kBlock;
+    ep->op = plan_orders(ix, o, pl.pruner, nq, ix->nparts);
+    size_t b = rup((size_t)nq * 4)                              // tau
+               + rup((size_t)nq * ep->nslots * k * 8)           // per-item lists
+               + 3 * rup((size_t)nq * k * 8)                    // merged, refined, final top-k
+               + rup(C_COUNT * 8) + rup(8)                      // counters, work counter
+               + rup(ep->op.bytes);                             // visit orders
+    if (ep->start) b += rup((size_t)nq * ep->Lstart * 8) + rup((size_t)nq * k * 8);
+    ep->bytes = b;
+    return PDX_OK;
+}
 
-    Scratch scr(st);
-    size_t need = rup(op.bytes);
-    if (!q_dev) need += rup((size_t)nq * d * 4);
-    need += rup((size_t)nq * 4);                         // tau
-    need += rup((size_t)nq * nslots * k * 8);            // per-item lists
-    need += rup((size_t)nq * k * 8) * 3;                 // merged, refined, final top-k
-    if (start) need += rup((size_t)nq * Lstart * 8) + rup((size_t)nq * k * 8);
-    need += rup(C_COUNT * 8) + rup(8);
-    if (!o_dev) need += rup((size_t)nq * k * 4) + rup((size_t)nq * k * 8);
-    PDX_TRY(scr.reserve(need));
-    const float *qd = q;
-    if (!q_dev) {
-        float *t = scr.take<float>((size_t)nq * d);
-        PDX_CHECK_SCRATCH(scr);
-        PDX_TRY(cudaMemcpyAsync(t, q, (size_t)nq * d * 4, cudaMemcpyHostToDevice, st));
-        qd = t;
+// All launches of an exact search on `st`, with scratch carved from
+// `scratch` (ep.bytes, 256-byte aligned). Allocates nothing and does not
+// synchronise, so it can be captured in a CUDA graph (without scan events).
+pdx_status exact_run(const pdx_index *ix, const float *qd, int64_t nq, int32_t k, const pdx_search_opts &o,
+                     const SearchPlan &pl, const ExactPlan &ep, unsigned char *scratch, float *od, int64_t *oi,
+                     unsigned long long **counters_out, int sms, cudaStream_t st) {
+    const int d = ix->d;
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        unsigned char *p = scratch + off;
+        off += rup(bytes);
+        return p;
+    };
+    float *tau = reinterpret_cast<float *>(take((size_t)nq * 4));
+    uint64_t *cand = reinterpret_cast<uint64_t *>(take((size_t)nq * ep.nslots * k * 8));
+    uint64_t *topk = reinterpret_cast<uint64_t *>(take((size_t)nq * k * 8));
+    uint64_t *refined = reinterpret_cast<uint64_t *>(take((size_t)nq * k * 8));
+    uint64_t *final_keys = reinterpret_cast<uint64_t *>(take((size_t)nq * k * 8));
+    unsigned long long *counters = reinterpret_cast<unsigned long long *>(take(C_COUNT * 8));
+    int *work = reinterpret_cast<int *>(take(8));
+    uint16_t *qorder = ep.op.rows ? reinterpret_cast<uint16_t *>(take(ep.op.bytes)) : nullptr;
+    uint64_t *skeys = ep.start ? reinterpret_cast<uint64_t *>(take((size_t)nq * ep.Lstart * 8)) : nullptr;
+    uint64_t *stopk = ep.start ? reinterpret_cast<uint64_t *>(take((size_t)nq * k * 8)) : nullptr;
+    if (off > ep.bytes) {
+        set_error("internal error: exact-search scratch layout exceeds its plan");
+        return PDX_ERR_CUDA;
     }
-    float *tau = scr.take<float>((size_t)nq);
-    uint64_t *cand = scr.take<uint64_t>((size_t)nq * nslots * k);
-    uint64_t *topk = scr.take<uint64_t>((size_t)nq * k);
-    uint64_t *refined = scr.take<uint64_t>((size_t)nq * k);
-    uint64_t *final_keys = scr.take<uint64_t>((size_t)nq * k);
-    uint64_t *skeys = start ? scr.take<uint64_t>((size_t)nq * Lstart) : nullptr;
-    uint64_t *stopk = start ? scr.take<uint64_t>((size_t)nq * k) : nullptr;
-    unsigned long long *counters = scr.take<unsigned long long>(C_COUNT);
-    int *work = scr.take<int>(2);
-    uint16_t *qorder = op.rows ? scr.take<uint16_t>((size_t)op.rows * d) : nullptr;
-    float *od = out_dist;
-    int64_t *oi = out_idx;
-    if (!o_dev) {
-        od = scr.take<float>((size_t)nq * k);
-        oi = scr.take<int64_t>((size_t)nq * k);
-    }
-    PDX_CHECK_SCRATCH(scr);
-    if (op.rows)  // query preprocessing (Sec. 5): PDX-BOND visit orders
-        PDX_TRY(launch_order(qd, op.rows, d, op.per_part ? ix->means : ix->cmean, op.per_part, nullptr, op.mode,
-                             std::max(1, (int)o.zone_dims), qorder, st));
+    if (ep.op.rows)  // query preprocessing (Sec. 5): PDX-BOND visit orders
+        PDX_TRY(launch_order(qd, ep.op.rows, d, ep.op.per_part ? ix->means : ix->cmean, ep.op.per_part, nullptr,
+                             ep.op.mode, std::max(1, (int)o.zone_dims), qorder, st));
     PDX_TRY(launch_fill_u32(reinterpret_cast<uint32_t *>(tau), 0xff800000u, nq, st));  // ordered +inf
     PDX_TRY(cudaMemsetAsync(counters, 0, C_COUNT * 8, st));
     PDX_TRY(cudaMemsetAsync(work, 0, 8, st));
     // kernels accumulate into the caller's device stats when given, else into scratch
     unsigned long long *kc = o.stats_device ? reinterpret_cast<unsigned long long *>(o.stats_device) : counters;
-    if (start) {
+    if (counters_out) *counters_out = kc;
+    if (ep.start) {
         // START (Sec. 4): exact distances of the first start_vectors stored
         // vectors give every query an initial k-th-best threshold
         if (ix->storage == PDX_F32) {
-            PDX_TRY(launch_dense_keys(qd, nq, ix->data, ix->ids, d, start_blk, pl.metric, skeys, st));
+            PDX_TRY(launch_dense_keys(qd, nq, ix->data, ix->ids, d, ep.start_blk, pl.metric, skeys, st));
         } else {  // exact FP32 from the vectors' FP32 copy, so tau is a real k-th distance
-            const int32_t rows = (int32_t)std::min<int64_t>(ix->n, Lstart);
-            PDX_TRY(launch_fill_u64(skeys, kEmptyKey, nq * Lstart, st));
-            PDX_TRY(launch_dense_keys_rows(qd, nq, ix->xnary, rows, d, Lstart, skeys, st));
+            const int32_t rows = (int32_t)std::min<int64_t>(ix->n, ep.Lstart);
+            PDX_TRY(launch_fill_u64(skeys, kEmptyKey, nq * ep.Lstart, st));
+            PDX_TRY(launch_dense_keys_rows(qd, nq, ix->xnary, rows, d, ep.Lstart, skeys, st));
         }
-        PDX_TRY(launch_select_k(skeys, nq, Lstart, k, stopk, st));
+        PDX_TRY(launch_select_k(skeys, nq, ep.Lstart, k, stopk, st));
         PDX_TRY(launch_tau_from_keys(stopk, nq, k, tau, st));
-        PDX_TRY(launch_add_u64(kc + C_START, (unsigned long long)nq * Lstart * d, st));
+        PDX_TRY(launch_add_u64(kc + C_START, (unsigned long long)nq * ep.Lstart * d, st));
     }
     ScanParams p;
     std::memset(&p, 0, sizeof p);
@@ -641,16 +622,16 @@ extern "C" pdx_status pdx_search_exact(const pdx_index *ix, const float *q, int6
     p.nq = nq;
     p.means = ix->means;
     p.probes = nullptr;
-    p.nslots = nslots;
+    p.nslots = ep.nslots;
     p.part0 = 0;
-    p.chunks_per_part = chunks;
-    p.blocks_per_item = bpi;
+    p.chunks_per_part = ep.chunks;
+    p.blocks_per_item = ep.bpi;
     p.k = k;
     p.tau = tau;
     p.cand = cand;
     p.counters = kc;
     p.work_counter = work;
-    p.nitems = nq * (int64_t)nslots;
+    p.nitems = nq * (int64_t)ep.nslots;
     p.first_step = (int)o.first_step;
     p.sel_count = std::min(kMaxSurv, (int)std::ceil(o.selection_threshold * kBlock) - 1);
     if (p.sel_count < 0) p.sel_count = 0;
@@ -661,17 +642,97 @@ extern "C" pdx_status pdx_search_exact(const pdx_index *ix, const float *q, int6
     p.eps0 = o.eps0;
     p.bsa_m = o.bsa_m;
     p.qorder = qorder;
-    p.qorder_per_part = op.per_part;
+    p.qorder_per_part = ep.op.per_part;
     if (o.scan_event_start) PDX_TRY(cudaEventRecord(static_cast<cudaEvent_t>(o.scan_event_start), st));
     PDX_TRY(launch_scan(pl.pruner, pl.metric, p, sms, st));
     if (o.scan_event_stop) PDX_TRY(cudaEventRecord(static_cast<cudaEvent_t>(o.scan_event_stop), st));
-    PDX_TRY(launch_select_k(cand, nq, (int64_t)nslots * k, k, topk, st));
+    PDX_TRY(launch_select_k(cand, nq, (int64_t)ep.nslots * k, k, topk, st));
     if (ix->storage == PDX_F32)
         PDX_TRY(launch_refine(topk, nq, k, qd, d, ix->data, ix->slot_of, ix->metric, refined, st));
     else
         PDX_TRY(launch_refine_rows(topk, nq, k, qd, d, ix->xnary, ix->metric, refined, st));
     PDX_TRY(launch_select_k(refined, nq, k, k, final_keys, st));
     PDX_TRY(launch_write_out(final_keys, nq, k, pl.out_mode, qd, d, od, oi, st));
+    return PDX_OK;
+}
+
+void fill_stats(pdx_search_stats *so, const unsigned long long *c, const pdx_index *ix) {
+    std::memset(so, 0, sizeof *so);
+    so->values_visited = c[C_VALUES];
+    so->vectors_scanned = c[C_SCANNED];
+    so->vectors_pruned = c[C_PRUNED];
+    so->prune_phase_blocks = c[C_PRUNE_BLOCKS];
+    so->candidates = c[C_CANDIDATES];
+    so->work_items = c[C_ITEMS];
+    so->start_values = c[C_START];
+    so->bytes_logical = c[C_VALUES] * elem_size(ix->storage) + c[C_START] * 4ull +
+                        (ix->storage == PDX_F32 ? 0ull : c[C_CANDIDATES] * (uint64_t)ix->d * 4ull);
+}
+
+pdx_status exact_check(const pdx_index *ix, const float *q, int64_t nq, int32_t k, const pdx_search_opts *opts,
+                       float *out_dist, int64_t *out_idx, pdx_search_opts *o, SearchPlan *pl, const char *fn) {
+    pdx_status s = check_search_args(ix, q, nq, k, opts, out_dist, out_idx, o, fn);
+    if (s != PDX_OK) return s;
+    if (ix->is_ivf) {
+        set_error("%s: index was built by pdx_ivf_build", fn);
+        return PDX_ERR_ARG;
+    }
+    if (o->pruner != PDX_PRUNE_NONE && o->pruner != PDX_PRUNE_BOND) {
+        set_error("%s: only NONE or BOND keep the search exact", fn);
+        return PDX_ERR_ARG;
+    }
+    if (q && (q == out_dist || (const void *)q == (const void *)out_idx)) {
+        set_error("%s: outputs alias the queries", fn);
+        return PDX_ERR_ARG;
+    }
+    return plan_metric(ix, o->pruner, pl, fn);
+}
+
+}  // namespace pdx
+
+extern "C" pdx_status pdx_search_exact(const pdx_index *ix, const float *q, int64_t nq, int32_t k,
+                                       const pdx_search_opts *opts, float *out_dist, int64_t *out_idx,
+                                       void *stream) {
+    const char *fn = "pdx_search_exact";
+    pdx_search_opts o;
+    SearchPlan pl;
+    pdx_status s = exact_check(ix, q, nq, k, opts, out_dist, out_idx, &o, &pl, fn);
+    if (s != PDX_OK) return s;
+    if (nq == 0) return PDX_OK;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const int d = ix->d;
+    const bool q_dev = is_device_ptr(q);
+    const bool o_dev = is_device_ptr(out_dist) && is_device_ptr(out_idx);
+    if (is_device_ptr(out_dist) != is_device_ptr(out_idx)) {
+        set_error("%s: out_dist and out_idx must both be host or both be device memory", fn);
+        return PDX_ERR_ARG;
+    }
+    const int sms = num_sms();
+    ExactPlan ep;
+    s = exact_plan(ix, nq, k, o, pl, sms, &ep);
+    if (s != PDX_OK) return s;
+    Scratch scr(st);
+    size_t need = ep.bytes;
+    if (!q_dev) need += rup((size_t)nq * d * 4);
+    if (!o_dev) need += rup((size_t)nq * k * 4) + rup((size_t)nq * k * 8);
+    PDX_TRY(scr.reserve(need));
+    unsigned char *work = scr.take<unsigned char>(ep.bytes);
+    const float *qd = q;
+    float *qs = q_dev ? nullptr : scr.take<float>((size_t)nq * d);
+    float *od = out_dist;
+    int64_t *oi = out_idx;
+    if (!o_dev) {
+        od = scr.take<float>((size_t)nq * k);
+        oi = scr.take<int64_t>((size_t)nq * k);
+    }
+    PDX_CHECK_SCRATCH(scr);
+    if (!q_dev) {
+        PDX_TRY(cudaMemcpyAsync(qs, q, (size_t)nq * d * 4, cudaMemcpyHostToDevice, st));
+        qd = qs;
+    }
+    unsigned long long *kc = nullptr;
+    s = exact_run(ix, qd, nq, k, o, pl, ep, work, od, oi, &kc, sms, st);
+    if (s != PDX_OK) return s;
     if (!o_dev) {
         PDX_TRY(cudaMemcpyAsync(out_dist, od, (size_t)nq * k * 4, cudaMemcpyDeviceToHost, st));
         PDX_TRY(cudaMemcpyAsync(out_idx, oi, (size_t)nq * k * 8, cudaMemcpyDeviceToHost, st));
@@ -680,22 +741,11 @@ extern "C" pdx_status pdx_search_exact(const pdx_index *ix, const float *q, int6
         unsigned long long c[C_COUNT];
         PDX_TRY(cudaMemcpyAsync(c, kc, sizeof c, cudaMemcpyDeviceToHost, st));
         PDX_TRY(cudaStreamSynchronize(st));
-        pdx_search_stats *so = o.stats_out;
-        std::memset(so, 0, sizeof *so);
-        so->values_visited = c[C_VALUES];
-        so->vectors_scanned = c[C_SCANNED];
-        so->vectors_pruned = c[C_PRUNED];
-        so->prune_phase_blocks = c[C_PRUNE_BLOCKS];
-        so->candidates = c[C_CANDIDATES];
-        so->work_items = c[C_ITEMS];
-        so->start_values = c[C_START];
-        so->bytes_logical = c[C_VALUES] * elem_size(ix->storage) + c[C_START] * 4ull +
-                            (ix->storage == PDX_F32 ? 0ull : c[C_CANDIDATES] * (uint64_t)d * 4ull);
+        fill_stats(o.stats_out, c, ix);
     }
     if (!o_dev) PDX_TRY(cudaStreamSynchronize(st));
     return PDX_OK;
 }
-
 
 namespace pdx {
 

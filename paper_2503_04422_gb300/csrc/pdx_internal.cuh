@@ -76,6 +76,7 @@ struct pdx_index {
 namespace pdx {
 
 void set_error(const char *fmt, ...);
+pdx_status cuda_status_ext(cudaError_t e, const char *what);
 
 struct SearchPlan {
     int pruner;
@@ -173,6 +174,25 @@ struct OrderPlan {
     size_t bytes = 0;
 };
 OrderPlan plan_orders(const pdx_index *ix, const pdx_search_opts &o, int pruner, int64_t nq, int parts_per_query);
+
+// Exact search split into planning (launch shape, scratch bytes) and running
+// (launches only, on caller-provided scratch: no allocation, no sync).
+struct ExactPlan {
+    int bpi = 1, chunks = 1, nslots = 0;
+    bool start = false;
+    int start_blk = 0;
+    int64_t Lstart = 0;
+    OrderPlan op;
+    size_t bytes = 0;
+};
+pdx_status exact_check(const pdx_index *ix, const float *q, int64_t nq, int32_t k, const pdx_search_opts *opts,
+                       float *out_dist, int64_t *out_idx, pdx_search_opts *o, SearchPlan *pl, const char *fn);
+pdx_status exact_plan(const pdx_index *ix, int64_t nq, int32_t k, const pdx_search_opts &o, const SearchPlan &pl,
+                      int sms, ExactPlan *ep);
+pdx_status exact_run(const pdx_index *ix, const float *qd, int64_t nq, int32_t k, const pdx_search_opts &o,
+                     const SearchPlan &pl, const ExactPlan &ep, unsigned char *scratch, float *od, int64_t *oi,
+                     unsigned long long **counters_out, int sms, cudaStream_t st);
+void fill_stats(pdx_search_stats *so, const unsigned long long *c, const pdx_index *ix);
 size_t scan_warp_smem(int d, int k, int zone_dims, int order);
 
 // START: exact distances of every query to the first `nvec` stored vectors,

@@ -339,3 +339,81 @@ def pdx_search_exact_noalloc(index: Index, q, k: int, opts: pdx_search_opts | No
            "pdx_search_exact_noalloc")
     del keep
     return od, oi
+
+
+# ---------------------------------------------------------------- serving
+class pdx_server_opts(ctypes.Structure):
+    _fields_ = [("struct_size", ctypes.c_uint32), ("k", ctypes.c_int32), ("max_batch", ctypes.c_int32),
+                ("use_graphs", ctypes.c_int32), ("autotune", ctypes.c_int32), ("tune_cache", ctypes.c_char_p),
+                ("search", pdx_search_opts)]
+
+
+class pdx_server_info_t(ctypes.Structure):
+    _fields_ = [("collections", ctypes.c_int32), ("max_bucket", ctypes.c_int32), ("workspace_bytes", ctypes.c_uint64),
+                ("graph_launches", ctypes.c_uint64), ("direct_launches", ctypes.c_uint64), ("tunings", ctypes.c_uint64),
+                ("entries_ready", ctypes.c_int32)]
+
+
+def _server_lib():
+    L = lib()
+    if not getattr(L, "_server_ready", False):
+        vp = ctypes.c_void_p
+        L.pdx_default_server_opts.argtypes = [ctypes.POINTER(pdx_server_opts)]
+        L.pdx_default_server_opts.restype = None
+        L.pdx_server_create.argtypes = [ctypes.POINTER(vp), ctypes.c_int32, ctypes.POINTER(pdx_server_opts),
+                                        ctypes.POINTER(vp)]
+        L.pdx_server_create.restype = ctypes.c_int
+        L.pdx_server_search.argtypes = [vp, ctypes.c_int32, vp, ctypes.c_int64, vp, vp, vp]
+        L.pdx_server_search.restype = ctypes.c_int
+        L.pdx_server_info.argtypes = [vp, ctypes.POINTER(pdx_server_info_t)]
+        L.pdx_server_info.restype = ctypes.c_int
+        L.pdx_server_free.argtypes = [vp]
+        L.pdx_server_free.restype = None
+        L._server_ready = True
+    return L
+
+
+class Server:
+    """Batched exact search over several collections (pdx_server_*)."""
+
+    def __init__(self, indexes, k=10, max_batch=4096, use_graphs=True, autotune=True, tune_cache=None, **search_kw):
+        L = _server_lib()
+        o = pdx_server_opts()
+        L.pdx_default_server_opts(ctypes.byref(o))
+        o.k, o.max_batch, o.use_graphs, o.autotune = k, max_batch, int(use_graphs), int(autotune)
+        self._cache = tune_cache.encode() if tune_cache else None
+        o.tune_cache = self._cache
+        o.search = search_opts(**search_kw)
+        self.indexes = list(indexes)          # keep the indexes alive
+        self.k = k
+        arr = (ctypes.c_void_p * len(self.indexes))(*[ix.handle.value if hasattr(ix.handle, "value") else ix.handle
+                                                      for ix in self.indexes])
+        h = ctypes.c_void_p()
+        _check(L.pdx_server_create(arr, len(self.indexes), ctypes.byref(o), ctypes.byref(h)), "pdx_server_create")
+        self.handle = h
+
+    def search(self, collection: int, q, out=None, stream=None):
+        L = _server_lib()
+        p, keep, cuda, shape = _ptr_f32(q, "q")
+        od, oi = _outputs(shape[0], self.k, cuda, out)
+        _check(L.pdx_server_search(self.handle, collection, p, shape[0], _out_ptr(od), _out_ptr(oi),
+                                   _stream(cuda, stream)), "pdx_server_search")
+        del keep
+        return od, oi
+
+    @property
+    def info(self):
+        inf = pdx_server_info_t()
+        _check(_server_lib().pdx_server_info(self.handle, ctypes.byref(inf)), "pdx_server_info")
+        return {f: getattr(inf, f) for f, _ in inf._fields_}
+
+    def free(self):
+        if self.handle:
+            _server_lib().pdx_server_free(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass

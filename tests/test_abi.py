@@ -47,13 +47,15 @@ def test_struct_layouts_match_c(tmp_path):
         '#include <stdio.h>\n#include <stddef.h>\n#include "pdx.h"\n'
         "int main(void){printf(\"%zu %zu %zu %zu %zu %zu %zu\\n\", sizeof(pdx_build_opts), sizeof(pdx_ivf_opts),"
         " sizeof(pdx_search_opts), sizeof(pdx_search_stats), sizeof(pdx_index_info),"
-        " offsetof(pdx_search_opts, ctas_per_sm), offsetof(pdx_ivf_opts, init_centroids));return 0;}\n")
+        " offsetof(pdx_search_opts, ctas_per_sm), offsetof(pdx_ivf_opts, init_centroids));"
+        "printf(\"%zu %zu\\n\", sizeof(pdx_server_opts), sizeof(pdx_server_info_t));return 0;}\n")
     exe = tmp_path / "sizes"
     subprocess.check_call(["gcc", "-I", os.path.join(ROOT, "include"), str(prog), "-o", str(exe)])
     got = [int(v) for v in subprocess.check_output([str(exe)]).split()]
     want = [ctypes.sizeof(P.pdx_build_opts), ctypes.sizeof(P.pdx_ivf_opts), ctypes.sizeof(P.pdx_search_opts),
             ctypes.sizeof(P.pdx_search_stats), ctypes.sizeof(P.pdx_index_info),
-            P.pdx_search_opts.ctas_per_sm.offset, P.pdx_ivf_opts.init_centroids.offset]
+            P.pdx_search_opts.ctas_per_sm.offset, P.pdx_ivf_opts.init_centroids.offset,
+            ctypes.sizeof(P.pdx_server_opts), ctypes.sizeof(P.pdx_server_info_t)]
     assert got == want
 
 
