@@ -34,6 +34,7 @@ WORKLOADS = {
     "bond_exact_1m_d768": dict(k=10, pruner="bond"),
     "plain_scan_10k_d128": dict(k=10, pruner="none"),
     "ivf_1m_d960": dict(k=10, pruner="ads", nlist=1024),
+    "learned_order_2m_d1536": dict(k=10, pruner="bond", metric="ip", nclusters=1024, traces=50_000),
 }
 PROFILE_TRAFFIC = os.path.join(ROOT, "profiles", "traffic.json")
 
@@ -94,26 +95,41 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(rows)}
 
 
-def _kernel_hash():
+SCAN_SOURCES = ("pdx_search.cu", "pdx_internal.cuh")
+DENSE_SOURCES = ("pdx_dense.cu", "pdx_internal.cuh")
+
+
+def _kernel_hash(sources=SCAN_SOURCES):
     h = hashlib.sha256()
-    for f in ("pdx_search.cu", "pdx_internal.cuh"):
+    for f in sources:
         with open(os.path.join(ROOT, "paper_2503_04422_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
 
 
-def _traffic_per_launch(workload):
-    """DRAM bytes per scan launch from the committed ncu summary, if it was
-    taken on the current kernel source."""
+def _traffic_per_launch(key):
+    """DRAM bytes per launch of the dominant kernel from the committed ncu
+    summary, if it was taken on the current kernel source (else None)."""
     try:
         with open(PROFILE_TRAFFIC) as f:
             t = json.load(f)
     except (OSError, ValueError):
         return None
-    e = t.get(workload)
-    if not e or e.get("kernel_hash") != _kernel_hash():
+    e = t.get(key)
+    sources = DENSE_SOURCES if key.endswith(":tensor") else SCAN_SOURCES
+    if not e or e.get("kernel_hash") != _kernel_hash(sources):
         return None
     return e.get("dram_bytes_per_launch")
+
+
+def _peak_tf32():
+    """TF32 dense tensor peak: the measured BF16 burst peak times the nominal
+    TF32/BF16 ratio (1.1 / 2.25 PFLOP/s)."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["bf16_tflops"]) * 1.1 / 2.25, "measured bf16 x 1.1/2.25"
+    except (OSError, ValueError, KeyError):
+        return 1900.0 * 1.1 / 2.25, "fallback bf16 x 1.1/2.25"
 
 
 def _peak_hbm():
@@ -223,7 +239,10 @@ def run_ours(args, rank, world, local_rank):
     q = np.ascontiguousarray(q_all[rank * base_nq:(rank + 1) * base_nq])
     n, d = x.shape
     nq = q.shape[0]
-    ix = pdx.pdx_build_layout(torch.from_numpy(x).cuda(), storage=args.storage)
+    pruner = args.pruner or spec["pruner"]
+    engine = args.engine or ("tensor" if pruner == "none" else "auto")
+    tensor = pruner == "none" and engine == "tensor"
+    ix = pdx.pdx_build_layout(torch.from_numpy(x).cuda(), storage=args.storage, dense_rows=tensor)
     torch.cuda.synchronize()
     torch.cuda.empty_cache()
     q_dev = torch.from_numpy(q).cuda()
@@ -231,7 +250,7 @@ def run_ours(args, rank, world, local_rank):
     oi = torch.empty((nq, k), dtype=torch.int64, device="cuda")
     stats_dev = torch.zeros(16, dtype=torch.int64, device="cuda")
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")   # > 129 MB L2
-    opts = pdx.search_opts(pruner=spec["pruner"])
+    opts = pdx.search_opts(pruner=pruner, engine=engine if pruner == "none" else "auto")
     stream = torch.cuda.current_stream()
 
     def step(ev_scan=None):
@@ -280,8 +299,8 @@ def run_ours(args, rank, world, local_rank):
     ms_per_step = tot_ms / K
     value = nq * world * K / (tot_ms / 1e3)
 
-    # roofline of the PDXearch scan: logical bytes it read per launch over its
-    # average event-timed duration
+    # roofline of the dominant kernel from its event-timed launches: the
+    # PDXearch scan (logical bytes read) or the tensor-core GEMM (2 nq n d FLOP)
     values_per_launch = float(st[0]) / K
     esize = {"f32": 4.0, "bf16": 2.0, "fp8": 1.0}[args.storage]
     # logical bytes of the scan: values visited x element size, plus the FP32
@@ -291,6 +310,24 @@ def run_ours(args, rank, world, local_rank):
     achieved = bytes_per_launch / (scan_avg_ms / 1e3) / 1e9
     peak, peak_kind = _peak_hbm()
     traffic = _traffic_per_launch(args.workload) if args.storage == "f32" else None
+    if pruner == "none":
+        traffic = None
+    if tensor:
+        flop = 2.0 * nq * n * d
+        tflops = flop / (scan_avg_ms / 1e3) / 1e12
+        tpeak, tkind = _peak_tf32()
+        roofline = {"bound": "tensor", "kernel": "dense_tc_kernel<16,L2> (tcgen05.mma kind::tf32, TMA, TMEM)",
+                    "achieved": tflops, "peak": tpeak, "peak_kind": tkind, "unit": "TFLOP/s",
+                    "frac": tflops / tpeak, "traffic": _traffic_per_launch(args.workload + ":tensor"),
+                    "algorithmic_flop_per_launch": flop, "gemm_ms_avg": scan_avg_ms,
+                    "per_unit": {"flop_per_query": 2.0 * n * d, "units_per_launch": nq}}
+    else:
+        roofline = {"bound": "hbm", "kernel": f"pdxsearch_kernel<{pruner.upper()},L2,{args.storage.upper()}>",
+                    "achieved": achieved,
+                    "peak": peak, "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,
+                    "traffic": traffic, "algorithmic_bytes_per_launch": bytes_per_launch,
+                    "scan_ms_avg": scan_avg_ms,
+                    "per_unit": {"bytes_per_query": bytes_per_launch / nq, "units_per_launch": nq}}
 
     # end to end through the C ABI with host (pinned) buffers
     e2e = None
@@ -309,18 +346,17 @@ def run_ours(args, rank, world, local_rank):
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": args.storage, "data": "synthetic",
             "config": {"workload": args.workload, "n": n, "d": d, "nq_per_gpu": nq, "k": k, "storage": args.storage,
-                       "pruner": spec["pruner"], "order": "dist_to_means",
+                       "pruner": pruner, "engine": "tensor (TF32 GEMM + FP32 rerank)" if tensor else "pdx scan",
+                       "order": "dist_to_means",
                        "means": "collection (automatic for exact search)", "zone_dims": "1 (automatic)",
                        "first_step": int(opts.first_step), "selection_threshold": round(float(opts.selection_threshold), 3),
                        "start_vectors": int(opts.start_vectors), "ctas_per_sm": "3 (automatic)",
-                       "l2": "collection 3.1 GB > L2; 256 MB L2 flush between timed steps (untimed)"},
-            "roofline": {"bound": "hbm", "kernel": f"pdxsearch_kernel<BOND,L2,{args.storage.upper()}>",
-                         "achieved": achieved,
-                         "peak": peak, "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,
-                         "traffic": traffic, "algorithmic_bytes_per_launch": bytes_per_launch,
-                         "scan_ms_avg": scan_avg_ms,
-                         "per_unit": {"bytes_per_query": bytes_per_launch / nq, "units_per_launch": nq}},
-            "pruning": {"values_visited_fraction": values_per_launch / (n * d * nq), "vectors_pruned_fraction": pruned},
+                       "l2": (f"collection {n * d * 4 / 1e9:.3g} GB; 256 MB L2 flush between timed steps "
+                              "(untimed)")},
+            "roofline": roofline,
+            "pruning": {"values_visited_fraction": values_per_launch / (n * d * nq), "vectors_pruned_fraction": pruned,
+                        "candidates_reranked_per_query": float(st[4]) / K / nq,
+                        "dense_fallbacks": int(st[8])},
             "e2e": e2e,
             "gpu_launches": int(launches),
             "gpu_launches_per_step": launches / K,
@@ -425,6 +461,106 @@ def run_ivf(args, rank, world, local_rank):
     print(json.dumps(line), flush=True)
 
 
+def run_learned(args, rank, world, local_rank):
+    """Learned visit order vs the distance-to-means heuristic (exact PDX-BOND,
+    inner product on unit-norm 1536-d embeddings). The network [q; c] -> 256 ->
+    1536 is trained on the GPU on traces of the plain method for separate
+    training queries. The line reports queries/s with the learned order, next to
+    the heuristic's, at identical exact results. Following the fallback rule,
+    the learned order is used only if it visits fewer values than the heuristic
+    on a validation split."""
+    import numpy as np
+    import torch
+
+    import pdx_synth
+    from paper_2503_04422_gb300 import build as pbuild
+    pbuild.build()
+    from paper_2503_04422_gb300 import pdx
+
+    torch.cuda.set_device(local_rank)
+    spec = WORKLOADS[args.workload]
+    k = spec["k"]
+    nq = args.nq or pdx_synth.WORKLOADS[args.workload]["nq"]
+    ntr = args.traces or spec["traces"]
+    n_full = args.n or pdx_synth.WORKLOADS[args.workload]["n"]
+    d = pdx_synth.WORKLOADS[args.workload]["d"]
+    t0 = time.perf_counter()
+    x, q_all = pdx_synth.embedding_like(n_full, d, nq + ntr + 1000)
+    gen_s = time.perf_counter() - t0
+    xd = torch.from_numpy(x).cuda()
+    del x
+    q_all = torch.from_numpy(q_all).cuda()
+    q_test, q_tr, q_val = q_all[:nq].contiguous(), q_all[nq:nq + ntr].contiguous(), q_all[nq + ntr:].contiguous()
+    ix = pdx.pdx_build_layout(xd, metric="ip")
+    # clusters for the network input: k-means on a sample (an IVF index over it)
+    nsample = min(n_full, 256 * spec["nclusters"])
+    clus = pdx.pdx_ivf_build(xd[:nsample].contiguous(), nlist=spec["nclusters"], kmeans_iters=8)
+    cent = torch.from_numpy(clus.copy_out("centroids")).cuda()
+    del clus
+    torch.cuda.synchronize()
+    # traces: the vectors the plain method ranked just behind the top-k, plus
+    # a sample of the vectors it pruned
+    t0 = time.perf_counter()
+    m_hard, m_rand = 48, 160
+    tg = []
+    for c0 in range(0, ntr, 5000):
+        qq = q_tr[c0:c0 + 5000].contiguous()
+        _, ids = pdx.pdx_search_exact(ix, qq, k + m_hard)
+        rnd = torch.randint(0, n_full, (qq.shape[0], m_rand), device="cuda", dtype=torch.int64,
+                            generator=torch.Generator(device="cuda").manual_seed(c0))
+        tg.append(pdx.pdx_order_targets(ix, qq, torch.cat([ids[:, k:], rnd], dim=1).contiguous()))
+    targets = torch.cat(tg)
+    u = pdx.pdx_mlp_inputs(q_tr, cent)
+    trace_s = time.perf_counter() - t0
+    net = pdx.Mlp(d, 256, seed=2503)
+    t0 = time.perf_counter()
+    loss = net.train(u, targets, epochs=args.epochs, batch=256, lr=1e-3)
+    train_s = time.perf_counter() - t0
+    heur = pdx.search_opts(pruner="bond")
+    learned = pdx.search_opts(pruner="bond", order="learned", mlp=net, mlp_centroids=cent)
+    # fallback / judge on a validation split
+    _, iv_h, sv_h = pdx.pdx_search_exact(ix, q_val, k, opts=pdx.search_opts(pruner="bond"), stats=True)
+    _, iv_l, sv_l = pdx.pdx_search_exact(ix, q_val, k, opts=pdx.search_opts(pruner="bond", order="learned", mlp=net,
+                                                                             mlp_centroids=cent), stats=True)
+    use_learned = sv_l["values_visited"] < sv_h["values_visited"]
+    od = torch.empty((nq, k), dtype=torch.float32, device="cuda")
+    oi = torch.empty((nq, k), dtype=torch.int64, device="cuda")
+    stats_dev = torch.zeros(16, dtype=torch.int64, device="cuda")
+
+    def timed(opts):
+        for _ in range(args.warmup):
+            pdx.pdx_search_exact(ix, q_test, k, opts=opts, out=(od, oi))
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+        stats_dev.zero_()
+        opts.stats_device = stats_dev.data_ptr()
+        torch.cuda.synchronize()
+        for a_, b_ in ev:
+            a_.record()
+            pdx.pdx_search_exact(ix, q_test, k, opts=opts, out=(od, oi))
+            b_.record()
+        torch.cuda.synchronize()
+        opts.stats_device = None
+        ms = sum(a_.elapsed_time(b_) for a_, b_ in ev) / args.steps
+        st = stats_dev.cpu().numpy().astype(np.float64)
+        return ms, st[0] / args.steps / (n_full * d * nq), oi.clone()
+
+    ms_h, vis_h, res_h = timed(heur)
+    ms_l, vis_l, res_l = timed(learned)
+    same = bool(torch.equal(res_h, res_l))
+    chosen = ms_l if use_learned else ms_h
+    line = {"metric": METRIC, "value": nq / (chosen / 1e3), "unit": "queries/s", "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": chosen, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": args.workload, "n": n_full, "d": d, "nq": nq, "k": k, "metric": "ip (unit norm)",
+                       "network": f"{2 * d}-256-{d}, BF16 inference weights", "traces": ntr,
+                       "clusters": spec["nclusters"], "epochs": args.epochs},
+            "learned_vs_plain": {"learned_qps": nq / (ms_l / 1e3), "plain_qps": nq / (ms_h / 1e3),
+                                 "learned_values_visited": vis_l, "plain_values_visited": vis_h,
+                                 "identical_results": same, "validation_prefers_learned": bool(use_learned),
+                                 "train_loss": loss, "train_s": train_s, "trace_s": trace_s, "gen_s": gen_s}}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -438,8 +574,14 @@ def main():
     ap.add_argument("--n", type=int, default=None, help="smaller collection (profiling); default = workload size")
     ap.add_argument("--nq", type=int, default=None, help="queries per GPU; default = workload size")
     ap.add_argument("--storage", default="f32", choices=["f32", "bf16", "fp8"])
+    ap.add_argument("--pruner", default=None, choices=["none", "bond"],
+                    help="exact workloads: override the workload's pruner")
+    ap.add_argument("--engine", default=None, choices=["auto", "scan", "tensor"],
+                    help="unpruned exact search: PDX scan or tensor-core GEMM (default tensor)")
     ap.add_argument("--pruners", default="ads,bsa,bond", help="IVF workload: pruners to sweep")
     ap.add_argument("--recall-queries", type=int, default=200, help="IVF workload: queries checked by the oracle")
+    ap.add_argument("--traces", type=int, default=None, help="learned-order workload: training queries")
+    ap.add_argument("--epochs", type=int, default=30, help="learned-order workload: training epochs")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3
@@ -450,6 +592,8 @@ def main():
         run_reference(args, rank, world)
     elif args.workload.startswith("ivf"):
         run_ivf(args, rank, world, local_rank)
+    elif args.workload.startswith("learned"):
+        run_learned(args, rank, world, local_rank)
     else:
         run_ours(args, rank, world, local_rank)
 

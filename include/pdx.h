@@ -43,6 +43,7 @@ extern "C" {
 #endif
 
 typedef struct pdx_index pdx_index; /* opaque; owns all of its device memory */
+typedef struct pdx_mlp pdx_mlp;     /* opaque order-proposal network (see pdx_mlp_create) */
 
 typedef enum pdx_status {
     PDX_OK = 0,
@@ -73,7 +74,8 @@ typedef enum pdx_pruner {
 typedef enum pdx_order {
     PDX_ORDER_DIST_TO_MEANS = 0, /* by |q_j - mu_j| of the block, descending */
     PDX_ORDER_DECREASING = 1,    /* by q_j, descending (BOND's order)        */
-    PDX_ORDER_SEQUENTIAL = 2     /* storage order                            */
+    PDX_ORDER_SEQUENTIAL = 2,    /* storage order                            */
+    PDX_ORDER_LEARNED = 3        /* scores of an order-proposal network      */
 } pdx_order;
 
 /* Whose means the distance-to-means order uses (Sec. 5 speaks of the block's
@@ -87,6 +89,26 @@ typedef enum pdx_means_scope {
                                   (its buckets are clusters)                 */
 } pdx_means_scope;
 
+/*
+ * Engines of the unpruned exact search (pruner PDX_PRUNE_NONE).
+ * SCAN   -- the PDX scan of Sec. 3/4 without a predicate: every dimension of
+ *           every vector, accumulated lane by lane on the CUDA cores.
+ * TENSOR -- the distance decomposition ||q||^2 + ||x||^2 - 2 q.x of Sec. 2.1
+ *           with q.x from a TF32 tensor-core GEMM over query batches
+ *           (tcgen05, FP32 accumulation). Every pair gets an estimate and a
+ *           proven error bound; vectors whose lower bound is within the k-th
+ *           smallest upper bound are reranked in FP32 from the row-major
+ *           copy, so results equal the SCAN engine's (up to ties within
+ *           FP32 rounding). Needs an exact index built with dense_rows (or
+ *           low-precision storage), L2 or IP, d a multiple of 4, k <= 64.
+ * AUTO   -- TENSOR when those conditions hold, else SCAN.
+ */
+typedef enum pdx_engine {
+    PDX_ENGINE_AUTO = 0,
+    PDX_ENGINE_SCAN = 1,
+    PDX_ENGINE_TENSOR = 2
+} pdx_engine;
+
 typedef struct pdx_build_opts {
     uint32_t struct_size;      /* = sizeof(pdx_build_opts)                                */
     pdx_metric metric;         /* metric the index will be searched with                   */
@@ -97,6 +119,10 @@ typedef struct pdx_build_opts {
     uint32_t partition_size;   /* exact search: at most this many vectors per PDXearch
                                   block, equal horizontal partitions (Sec. 6.6; 10000)    */
     int32_t keep_fp32_rerank;  /* low-precision storage: keep an FP32 copy (default 1)     */
+    int32_t dense_rows;        /* keep the vectors row-major in FP32 with their norms
+                                  (n*(d+2)*4 bytes) for the tensor-core dense engine;
+                                  low-precision storage keeps the FP32 rows anyway and then
+                                  only adds the norms (default 0)                           */
 } pdx_build_opts;
 
 typedef struct pdx_ivf_opts {
@@ -123,7 +149,10 @@ typedef struct pdx_search_stats {
     uint64_t start_values;     /* values computed by the START scan (exact search)            */
     uint64_t bytes_logical;    /* (values_visited + start_values) * element size; filled only
                                   in stats_out                                               */
-    uint64_t reserved[8];
+    uint64_t dense_fallbacks;  /* tensor-core engine: queries whose candidates overflowed their
+                                  buffer (or whose GEMM gave up on a wait) and were answered
+                                  by a plain FP32 scan instead                              */
+    uint64_t reserved[7];
 } pdx_search_stats;
 
 typedef struct pdx_search_opts {
@@ -143,8 +172,8 @@ typedef struct pdx_search_opts {
     pdx_search_stats *stats_out; /* optional host pointer; filled after the search (the call
                                   then synchronises `stream`)                               */
     pdx_search_stats *stats_device; /* optional device pointer: the kernels add their counters
-                                  to its first seven fields asynchronously (caller zeroes it;
-                                  bytes_logical is not written)                              */
+                                  to its first seven fields and dense_fallbacks asynchronously
+                                  (caller zeroes it; bytes_logical is not written)           */
     void *scan_event_start;    /* optional cudaEvent_t recorded on `stream` just before the
                                   PDXearch scan kernel                                        */
     void *scan_event_stop;     /* optional cudaEvent_t recorded just after it                 */
@@ -152,6 +181,11 @@ typedef struct pdx_search_opts {
     uint32_t ctas_per_sm;      /* resident scan CTAs per SM (0 = 3). The shared-memory carveout
                                   is sized for exactly this many, and the rest of each SM's
                                   on-chip memory serves as L1 for the loads in flight.     */
+    pdx_mlp *mlp;              /* PDX_ORDER_LEARNED: the network (exact indexes)           */
+    const float *mlp_centroids;/* PDX_ORDER_LEARNED: device [mlp_ncentroids][d]; each query
+                                  is paired with its nearest one as the network input      */
+    int32_t mlp_ncentroids;
+    pdx_engine engine;         /* unpruned exact search: PDX scan or tensor-core GEMM (AUTO) */
 } pdx_search_opts;
 
 typedef struct pdx_index_info {
@@ -320,6 +354,47 @@ pdx_status pdx_server_search(pdx_server *server, int32_t collection, const float
                              int64_t *out_idx, void *stream);
 pdx_status pdx_server_info(const pdx_server *server, pdx_server_info_t *info);
 void pdx_server_free(pdx_server *server); /* NULL-safe */
+
+/*
+ * Order-proposal network (no counterpart in the paper): u = [q; c] (2d) ->
+ * relu(W1 u + b1) (hidden) -> W2 h + b2 (d outputs). A PDX_ORDER_LEARNED search
+ * visits dimensions by decreasing (q_j - mu_j)^2 + s_q output_j (s_q =
+ * mean_j (q_j - mu_j)^2): the network
+ * corrects PDX-BOND's distance-to-means order (mu = collection means); the
+ * prune test stays the true partial distance, so results are exact whatever
+ * the network proposes.
+ * Parameters are one FP32 buffer W1[hidden][2d] | b1[hidden] | W2[d][hidden] |
+ * b2[d]; searches use BF16 copies of W1 and W2 with FP32 accumulation.
+ * All data pointers below are device memory unless stated; calls synchronise.
+ */
+pdx_status pdx_mlp_create(int32_t d, int32_t hidden, uint64_t seed, pdx_mlp **out);
+void pdx_mlp_free(pdx_mlp *net);
+size_t pdx_mlp_param_count(const pdx_mlp *net);
+pdx_status pdx_mlp_set_params(pdx_mlp *net, const float *params, size_t count);   /* host or device */
+pdx_status pdx_mlp_get_params(const pdx_mlp *net, float *params, size_t count);   /* host or device */
+/* y[B][d] = network(u[B][2d]); use_bf16 selects the inference weights. */
+pdx_status pdx_mlp_forward(pdx_mlp *net, const float *u, int64_t B, int32_t use_bf16, float *y, void *stream);
+/* Gradients of L = sum((y - t)^2) / (B d) into grads (count floats, host or
+ * device, parameter layout) and L into *loss (host, optional); FP32 weights. */
+pdx_status pdx_mlp_backward(pdx_mlp *net, const float *u, const float *t, int64_t B, float *grads, float *loss,
+                            void *stream);
+/* Adam (lr, betas 0.9/0.999) over shuffled mini-batches of the n rows (u, t);
+ * *loss receives the last epoch's final batch loss. */
+pdx_status pdx_mlp_train(pdx_mlp *net, const float *u, const float *t, int64_t n, int32_t epochs, int32_t batch,
+                         float lr, uint64_t seed, float *loss, void *stream);
+/* Network inputs u[r] = [q_r; c] with c the centroid (row of centroids[nc][d])
+ * nearest to q_r in L2 (ties: lower row) -- what a PDX_ORDER_LEARNED search feeds
+ * the network. */
+pdx_status pdx_mlp_inputs(const float *q, int64_t nq, int32_t d, const float *centroids, int32_t nc, float *u,
+                          void *stream);
+/* Training targets from the plain method's traces: t[r][j] = mean over the m
+ * vectors ids[r][*] (int64, -1 ignored; vectors the plain search pruned for
+ * query r) of (q_rj - x_j)^2, minus the heuristic term (q_rj - mu_j)^2 with mu
+ * the collection means, divided by s_r = mean_j (q_rj - mu_j)^2. A
+ * PDX_ORDER_LEARNED search ranks dimensions by (q_j - mu_j)^2 + s_q network_j,
+ * so the network learns the heuristic's error in units of s_q. Exact indexes. */
+pdx_status pdx_order_targets(const pdx_index *index, const float *q, int64_t nq, const int64_t *ids, int32_t m,
+                             float *targets, void *stream);
 
 /* Release an index and all of its device memory. NULL-safe. */
 void pdx_free(pdx_index *index);

@@ -107,7 +107,7 @@ static size_t rup(size_t b) { return (b + 255) & ~size_t(255); }
 
 static void free_index(pdx_index *ix) {
     if (!ix) return;
-    void *ptrs[] = {ix->data, ix->data_lp, ix->scale, ix->xnary, ix->ids, ix->slot_of, ix->blk_cnt, ix->part_blk, ix->means, ix->cmean, ix->centroids, ix->centroid_norms,
+    void *ptrs[] = {ix->data, ix->data_lp, ix->scale, ix->xnary, ix->xnorm, ix->ids, ix->slot_of, ix->blk_cnt, ix->part_blk, ix->means, ix->cmean, ix->centroids, ix->centroid_norms,
                     ix->assign, ix->rot, ix->shift, ix->pca_var, ix->resid, ix->chk, ix->cdata, ix->cids};
     for (void *p : ptrs)
         if (p) cudaFree(p);
@@ -221,6 +221,20 @@ static pdx_status finish_low_precision(pdx_index *ix, const float *xrows, cudaSt
     cudaFree(ix->data);
     ix->data = nullptr;
     ix->bytes -= (size_t)ix->nblocks * d * kBlock * 4;
+    return PDX_OK;
+}
+
+// Row-major FP32 vectors and their (||x||^2, ||x||) for the tensor-core
+// dense engine (the rows are already there for low-precision storage).
+static pdx_status keep_dense_rows(pdx_index *ix, const float *xrows, cudaStream_t st) {
+    const int d = ix->d;
+    if (!ix->xnary) {
+        PDX_TRY(dalloc(ix, &ix->xnary, (size_t)ix->n * d));
+        PDX_TRY(cudaMemcpyAsync(ix->xnary, xrows, (size_t)ix->n * d * 4, cudaMemcpyDeviceToDevice, st));
+    }
+    PDX_TRY(dalloc(ix, &ix->xnorm, (size_t)ix->n * 2));
+    PDX_TRY(launch_row_norms(ix->xnary, ix->n, d, ix->xnorm, st));
+    PDX_TRY(cudaStreamSynchronize(st));
     return PDX_OK;
 }
 
@@ -406,6 +420,7 @@ pdx_status pdx_build_layout(const float *x, int64_t n, int32_t d, const pdx_buil
             if (e != cudaSuccess) s = cuda_status(e, "cudaStreamSynchronize", __LINE__);
         }
         if (s == PDX_OK && o.storage != PDX_F32) s = finish_low_precision(ix, xd, st);
+        if (s == PDX_OK && o.dense_rows) s = keep_dense_rows(ix, xd, st);
     }
     if (s != PDX_OK) {
         free_index(ix);
@@ -439,7 +454,7 @@ pdx_status check_search_args(const pdx_index *ix, const float *q, int64_t nq, in
         *o = *opts;
     }
     if (o->pruner < PDX_PRUNE_NONE || o->pruner > PDX_PRUNE_BSA || o->order < PDX_ORDER_DIST_TO_MEANS ||
-        o->order > PDX_ORDER_SEQUENTIAL) {
+        o->order > PDX_ORDER_LEARNED) {
         set_error("%s: bad pruner %d or order %d", fn, (int)o->pruner, (int)o->order);
         return PDX_ERR_ARG;
     }
@@ -452,6 +467,19 @@ pdx_status check_search_args(const pdx_index *ix, const float *q, int64_t nq, in
         !(o->eps0 >= 0.f) || !(o->bsa_m >= 0.f) || o->ctas_per_sm > 32) {
         set_error("%s: selection_threshold must be in [0, 0.25], first_step >= 1, eps0/bsa_m >= 0, "
                   "ctas_per_sm <= 32", fn);
+        return PDX_ERR_ARG;
+    }
+    if (o->order == PDX_ORDER_LEARNED &&
+        (!o->mlp || !o->mlp_centroids || o->mlp_ncentroids < 1 || pdx_mlp_param_count(o->mlp) == 0 || ix->is_ivf)) {
+        set_error("%s: the learned order needs an exact index, a network and its centroids", fn);
+        return PDX_ERR_ARG;
+    }
+    if (o->engine < PDX_ENGINE_AUTO || o->engine > PDX_ENGINE_TENSOR) {
+        set_error("%s: bad engine %d", fn, (int)o->engine);
+        return PDX_ERR_ARG;
+    }
+    if (o->order == PDX_ORDER_LEARNED && o->mlp->d != ix->d) {
+        set_error("%s: the network was built for d=%d, the index has d=%d", fn, o->mlp->d, ix->d);
         return PDX_ERR_ARG;
     }
     // resolve the automatic choices
@@ -502,7 +530,9 @@ OrderPlan plan_orders(const pdx_index *ix, const pdx_search_opts &o, int pruner,
     OrderPlan pl;
     if (pruner != PDX_PRUNE_BOND || o.order == PDX_ORDER_SEQUENTIAL) return pl;
     const int d = ix->d;
-    if (o.order == PDX_ORDER_DECREASING) {
+    if (o.order == PDX_ORDER_LEARNED) {
+        pl.mode = 2;
+    } else if (o.order == PDX_ORDER_DECREASING) {
         pl.mode = 1;
     } else if (o.means_scope == PDX_MEANS_COLLECTION) {
         pl.mode = 0;
@@ -538,6 +568,21 @@ pdx_status exact_plan(const pdx_index *ix, int64_t nq, int32_t k, const pdx_sear
     if (bpi < 1) bpi = 1;
     ep->bpi = bpi;
     ep->chunks = (max_blk + bpi - 1) / bpi;
+    // unpruned search: the tensor-core engine when the index supports it
+    const char *why = nullptr;
+    const bool can_dense = pl.pruner == PDX_PRUNE_NONE && dense_supported(ix, k, &why);
+    if (o.engine == PDX_ENGINE_TENSOR && !can_dense) {
+        set_error("tensor-core engine: %s",
+                  pl.pruner != PDX_PRUNE_NONE ? "it runs unpruned searches only (pruner PDX_PRUNE_NONE)" : why);
+        return PDX_ERR_UNSUPPORTED;
+    }
+    ep->dense = can_dense && o.engine != PDX_ENGINE_SCAN;
+    if (ep->dense) {
+        ep->dense_cap = dense_cap(ix->n, k);
+        ep->nslots = 0;
+        ep->bytes = dense_scratch_bytes(nq, ix->d, k, ep->dense_cap) + rup(C_COUNT * 8);
+        return PDX_OK;
+    }
     ep->nslots = ix->nparts * ep->chunks;
     ep->start = (pl.pruner != PDX_PRUNE_NONE);
     ep->start_blk = 0;
@@ -553,6 +598,14 @@ pdx_status exact_plan(const pdx_index *ix, int64_t nq, int32_t k, const pdx_sear
                + rup(C_COUNT * 8) + rup(8)                      // counters, work counter
                + rup(ep->op.bytes);                             // visit orders
     if (ep->start) b += rup((size_t)nq * ep->Lstart * 8) + rup((size_t)nq * k * 8);
+    ep->mlp_bytes = 0;
+    if (ep->op.mode == 2) {
+        ep->mlp_Lc = ((int64_t)o.mlp_ncentroids + kBlock - 1) / kBlock * kBlock;
+        const int hidden = o.mlp->hidden;
+        ep->mlp_bytes = rup((size_t)nq * ep->mlp_Lc * 8) + rup((size_t)nq * 8) + rup((size_t)nq * 2 * ix->d * 4) +
+                        rup((size_t)nq * hidden * 4) + rup((size_t)nq * ix->d * 4);
+    }
+    b += ep->mlp_bytes;
     ep->bytes = b;
     return PDX_OK;
 }
@@ -564,6 +617,16 @@ pdx_status exact_run(const pdx_index *ix, const float *qd, int64_t nq, int32_t k
                      const SearchPlan &pl, const ExactPlan &ep, unsigned char *scratch, float *od, int64_t *oi,
                      unsigned long long **counters_out, int sms, cudaStream_t st) {
     const int d = ix->d;
+    if (ep.dense) {
+        const size_t db = dense_scratch_bytes(nq, d, k, ep.dense_cap);
+        unsigned long long *counters = reinterpret_cast<unsigned long long *>(scratch + db);
+        PDX_TRY(cudaMemsetAsync(counters, 0, C_COUNT * 8, st));
+        unsigned long long *kc = o.stats_device ? reinterpret_cast<unsigned long long *>(o.stats_device) : counters;
+        if (counters_out) *counters_out = kc;
+        const bool ip = ix->metric == PDX_IP;
+        return dense_run(ix, qd, nq, k, ip ? MT_IP : MT_L2, ip ? 1 : 0, scratch, db, ep.dense_cap, od, oi, kc, sms,
+                         o.scan_event_start, o.scan_event_stop, st);
+    }
     size_t off = 0;
     auto take = [&](size_t bytes) {
         unsigned char *p = scratch + off;
@@ -580,13 +643,36 @@ pdx_status exact_run(const pdx_index *ix, const float *qd, int64_t nq, int32_t k
     uint16_t *qorder = ep.op.rows ? reinterpret_cast<uint16_t *>(take(ep.op.bytes)) : nullptr;
     uint64_t *skeys = ep.start ? reinterpret_cast<uint64_t *>(take((size_t)nq * ep.Lstart * 8)) : nullptr;
     uint64_t *stopk = ep.start ? reinterpret_cast<uint64_t *>(take((size_t)nq * k * 8)) : nullptr;
+    unsigned char *mlp_ws = ep.mlp_bytes ? take(ep.mlp_bytes) : nullptr;
     if (off > ep.bytes) {
         set_error("internal error: exact-search scratch layout exceeds its plan");
         return PDX_ERR_CUDA;
     }
+    const float *scores = nullptr;
+    if (ep.op.mode == 2) {
+        // learned order: each query's nearest centroid, network input [q; c],
+        // BF16 inference into per-dimension scores
+        const int hidden = o.mlp->hidden;
+        unsigned char *mp = mlp_ws;
+        uint64_t *ckeys = reinterpret_cast<uint64_t *>(mp);
+        mp += rup((size_t)nq * ep.mlp_Lc * 8);
+        uint64_t *nearest = reinterpret_cast<uint64_t *>(mp);
+        mp += rup((size_t)nq * 8);
+        float *u = reinterpret_cast<float *>(mp);
+        mp += rup((size_t)nq * 2 * d * 4);
+        float *zb = reinterpret_cast<float *>(mp);
+        mp += rup((size_t)nq * hidden * 4);
+        float *yb = reinterpret_cast<float *>(mp);
+        PDX_TRY(launch_fill_u64(ckeys, kEmptyKey, nq * ep.mlp_Lc, st));
+        PDX_TRY(launch_dense_keys_rows(qd, nq, o.mlp_centroids, o.mlp_ncentroids, d, ep.mlp_Lc, ckeys, st));
+        PDX_TRY(launch_select_k(ckeys, nq, ep.mlp_Lc, 1, nearest, st));
+        PDX_TRY(launch_mlp_inputs(qd, nq, d, o.mlp_centroids, nearest, u, st));
+        PDX_TRY(mlp_scores(o.mlp, u, nq, zb, yb, st));
+        scores = yb;
+    }
     if (ep.op.rows)  // query preprocessing (Sec. 5): PDX-BOND visit orders
         PDX_TRY(launch_order(qd, ep.op.rows, d, ep.op.per_part ? ix->means : ix->cmean, ep.op.per_part, nullptr,
-                             ep.op.mode, std::max(1, (int)o.zone_dims), qorder, st));
+                             ep.op.mode, std::max(1, (int)o.zone_dims), scores, qorder, st));
     PDX_TRY(launch_fill_u32(reinterpret_cast<uint32_t *>(tau), 0xff800000u, nq, st));  // ordered +inf
     PDX_TRY(cudaMemsetAsync(counters, 0, C_COUNT * 8, st));
     PDX_TRY(cudaMemsetAsync(work, 0, 8, st));
@@ -665,6 +751,7 @@ void fill_stats(pdx_search_stats *so, const unsigned long long *c, const pdx_ind
     so->candidates = c[C_CANDIDATES];
     so->work_items = c[C_ITEMS];
     so->start_values = c[C_START];
+    so->dense_fallbacks = c[C_DENSE_FALLBACK];
     so->bytes_logical = c[C_VALUES] * elem_size(ix->storage) + c[C_START] * 4ull +
                         (ix->storage == PDX_F32 ? 0ull : c[C_CANDIDATES] * (uint64_t)ix->d * 4ull);
 }
@@ -995,6 +1082,10 @@ extern "C" pdx_status pdx_search_ivf(const pdx_index *ix, const float *q, int64_
         set_error("%s: index was not built by pdx_ivf_build", fn);
         return PDX_ERR_ARG;
     }
+    if (o.engine == PDX_ENGINE_TENSOR) {
+        set_error("%s: the tensor-core engine serves exact indexes only", fn);
+        return PDX_ERR_UNSUPPORTED;
+    }
     if (nprobe < 1 || nprobe > ix->nparts || nprobe > 4096) {
         set_error("%s: nprobe=%d outside [1, min(nlist=%d, 4096)]", fn, nprobe, ix->nparts);
         return PDX_ERR_ARG;
@@ -1078,7 +1169,8 @@ extern "C" pdx_status pdx_search_ivf(const pdx_index *ix, const float *q, int64_
     if (nchk > 0) PDX_TRY(launch_bsa_qaux(qt, nq, d, ix->pca_var, ix->chk, nchk, qaux, st));
     if (op.rows)  // PDX-BOND visit orders against the probed buckets' (or the collection's) means
         PDX_TRY(launch_order(qt, op.rows, d, op.per_part ? ix->means : ix->cmean, op.per_part,
-                             op.per_part ? probes : nullptr, op.mode, std::max(1, (int)o.zone_dims), qorder, st));
+                             op.per_part ? probes : nullptr, op.mode, std::max(1, (int)o.zone_dims), nullptr, qorder,
+                             st));
     PDX_TRY(launch_fill_u32(reinterpret_cast<uint32_t *>(tau), 0xff800000u, nq, st));
     PDX_TRY(cudaMemsetAsync(counters, 0, C_COUNT * 8, st));
     PDX_TRY(cudaMemsetAsync(work, 0, 16, st));
@@ -1157,6 +1249,7 @@ extern "C" pdx_status pdx_search_ivf(const pdx_index *ix, const float *q, int64_
         so->candidates = c[C_CANDIDATES];
         so->work_items = c[C_ITEMS];
         so->start_values = c[C_START];
+    so->dense_fallbacks = c[C_DENSE_FALLBACK];
         so->bytes_logical = c[C_VALUES] * elem_size(ix->storage) + c[C_START] * 4ull +
                             (ix->storage == PDX_F32 ? 0ull : c[C_CANDIDATES] * (uint64_t)d * 4ull);
     }

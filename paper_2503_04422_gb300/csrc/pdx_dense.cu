@@ -1,0 +1,722 @@
+// Dense (unpruned) exact k-NN on the 5th-generation tensor cores.
+//
+// Without pruning every query meets every vector, and the L2 distance splits
+// into ||q||^2 + ||x||^2 - 2 q.x (Sec. 2.1): the only term that couples q and
+// x is one entry of the product Q X^T, a dense contraction over the D
+// dimensions. This file computes that product tile by tile on tcgen05 and
+// turns it into exact top-k results:
+//
+//   1. prep      copy the queries into an aligned buffer, ||q|| per query,
+//                reset the per-query state.
+//   2. gemm      persistent, warp-specialised: one thread issues TMA loads of
+//                128x32 query and 256x32 vector FP32 tiles (128-byte swizzle)
+//                into a 4-stage shared-memory ring, one thread issues
+//                tcgen05.mma kind::tf32 (M=128, N=256, K=8) into one of two
+//                TMEM accumulators, eight warps drain the other accumulator
+//                with tcgen05.ld. For every (query, vector) the epilogue forms
+//                est = ||x||^2 - 2 acc (L2) or -acc (IP) and a proven error
+//                margin m (TF32 operands, FP32 accumulation; see dense_bounds),
+//                so that est - m <= exact <= est + m. Each thread keeps the KL
+//                smallest upper bounds of its query within the tile, shares the
+//                k-th through a per-query atomic minimum, and emits every
+//                vector whose lower bound does not exceed the tighter of the
+//                two thresholds.
+//   3. finish    one CTA per query: T = k-th smallest upper bound among the
+//                emitted entries; every entry with lower bound <= T is a
+//                candidate; candidates get their exact FP32 distance (same
+//                lanes and reduction as the scan path's refine), and the k best
+//                (distance, id) keys are kept.
+//
+// Why this is exact: every threshold above is the k-th upper bound of k real
+// vectors, so it is >= T* = the k-th smallest upper bound over all vectors.
+// The true k nearest have lower <= exact <= k-th exact distance <= T*, so
+// they are emitted and survive the final filter; the FP32 rerank decides.
+// If a query emits more entries than its buffer holds, or the GEMM gave up on
+// a wait, the finish kernel computes that query's result by a plain FP32 scan
+// of all vectors instead (counted in the search statistics).
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+#include <algorithm>
+#include <cmath>
+#include <mutex>
+
+#include "pdx_internal.cuh"
+
+namespace pdx {
+namespace {
+
+constexpr int TM = 128;                 // queries per tile = TMEM lanes
+constexpr int TN = 256;                 // vectors per tile = accumulator columns
+constexpr int TKF = 32;                 // FP32 elements per K chunk = one 128-byte swizzle row
+constexpr int STAGES = 4;
+constexpr int A_BYTES = TM * TKF * 4;   // 16 KB
+constexpr int B_BYTES = TN * TKF * 4;   // 32 KB
+constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
+constexpr int EPI_WARPS = 8;            // two per TMEM lane quarter, one per column half
+constexpr int THREADS = (2 + EPI_WARPS) * 32;
+constexpr int TMEM_COLS = 2 * TN;       // two accumulators
+constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024;  // + alignment of the swizzled tiles
+constexpr uint64_t kWaitNs = 2000000000ull;              // give up on a barrier after 2 s
+
+// Instruction descriptor of tcgen05.mma kind::tf32: FP32 accumulator (bits
+// 4-5 = 1), A and B TF32 (bits 7-9, 10-12 = 2), both K-major (bits 15, 16 =
+// 0), N >> 3 at bit 17, M >> 4 at bit 24.
+constexpr uint32_t kIdesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(TN >> 3) << 17) |
+                            ((uint32_t)(TM >> 4) << 24);
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ uint64_t globaltimer() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+
+// Bounded wait for the phase of the given parity. Gives up after kWaitNs, or
+// as soon as another role of the CTA has given up, and reports it.
+__device__ __forceinline__ bool wait_bar(uint32_t bar, uint32_t parity, volatile int *abort_flag) {
+    if (mbar_try(bar, parity)) return true;
+    const uint64_t t0 = globaltimer();
+    for (;;) {
+        if (mbar_try(bar, parity)) return true;
+        if (*abort_flag) return false;
+        if (globaltimer() - t0 > kWaitNs) {
+            *abort_flag = 1;
+            return false;
+        }
+    }
+}
+
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap *map, uint32_t bar, int x, int y) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+            dst),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(bar)
+        : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// Shared-memory matrix descriptor of a K-major tile with 128-byte swizzle:
+// rows of 128 bytes, groups of 8 rows 1024 bytes apart (stride byte offset),
+// descriptor version 1 at bit 46, swizzle mode 2 (128 B) at bits 61-63. The
+// leading byte offset is not used by this layout.
+__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
+    uint64_t d = (uint64_t)((saddr >> 4) & 0x3FFFu);
+    d |= (uint64_t)1 << 16;
+    d |= (uint64_t)(1024 >> 4) << 32;
+    d |= (uint64_t)1 << 46;
+    d |= (uint64_t)2 << 61;
+    return d;
+}
+
+__device__ __forceinline__ void mma_tf32(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t accum) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "l"(adesc), "l"(bdesc), "r"(kIdesc), "r"(accum)
+        : "memory");
+}
+__device__ __forceinline__ void mma_commit(uint32_t bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
+}
+
+// 32 consecutive accumulator columns of this thread's TMEM lane.
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
+    uint32_t r[32];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+        "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
+        "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+struct DenseParams {
+    int64_t nq, n;
+    int32_t d, k;
+    int32_t nqt;                 // query tiles
+    int64_t ntiles;              // query tiles x vector tiles
+    const float *qnorm;          // [nq] ||q||
+    const float2 *xnorm;         // [n] (||x||^2, ||x||)
+    uint32_t *tau_up;            // [nq] ordered bits of the best shared upper bound
+    int32_t *cnt;                // [nq] entries emitted
+    int32_t cap;                 // entries per query
+    float2 *ent;                 // [nq][cap] (lower, upper)
+    int32_t *ent_id;             // [nq][cap]
+    float c_qx, c_xx, c_rel;     // margin coefficients
+    int32_t *err;                // set when a wait gave up
+};
+
+// Error margin of est for one (query, vector) pair. With TF32 operands
+// (at most 2^-10 relative truncation each) and FP32 accumulation of D
+// products, |acc - q.x| <= (2^-9 + (D+16) 2^-22) sum_j |q_j x_j|
+// <= that * ||q|| ||x|| (Cauchy-Schwarz). The FP32 ||x||^2 is within
+// D 2^-23 ||x||^2 and forming est rounds once more; c_qx, c_xx, c_rel hold
+// these terms with extra slack for the FP32 arithmetic of the margin itself.
+template <int MET>
+__device__ __forceinline__ void dense_bounds(float acc, float2 xn, float aq, const DenseParams &p, float &lo,
+                                             float &up) {
+    float est, m;
+    if (MET == MT_L2) {
+        est = fmaf(-2.f, acc, xn.x);
+        m = fmaf(aq, xn.y, fmaf(p.c_xx, xn.x, p.c_rel * fabsf(est)));
+    } else {
+        est = -acc;
+        m = fmaf(aq, xn.y, p.c_rel * fabsf(est));
+    }
+    lo = est - m;
+    up = est + m;
+}
+
+template <int KL, int MET>
+__global__ void __launch_bounds__(THREADS, 1)
+    dense_tc_kernel(const __grid_constant__ CUtensorMap tmQ, const __grid_constant__ CUtensorMap tmX, DenseParams p) {
+    extern __shared__ unsigned char smem_raw[];
+    __shared__ __align__(8) uint64_t bars[2 * STAGES + 5];
+    __shared__ uint32_t tmem_holder;
+    __shared__ int abort_flag;
+    unsigned char *smem =
+        reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+    const uint32_t sbase = smem_u32(smem);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    // barriers: full[s], empty[s], tfull[b], tempty[b], done
+    auto full = [&](int s) { return smem_u32(&bars[s]); };
+    auto empty = [&](int s) { return smem_u32(&bars[STAGES + s]); };
+    auto tfull = [&](int b) { return smem_u32(&bars[2 * STAGES + b]); };
+    auto tempty = [&](int b) { return smem_u32(&bars[2 * STAGES + 2 + b]); };
+    const uint32_t done = smem_u32(&bars[2 * STAGES + 4]);
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < STAGES; ++s) {
+            mbar_init(full(s), 1);
+            mbar_init(empty(s), 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(tfull(b), 1);
+            mbar_init(tempty(b), EPI_WARPS);
+        }
+        mbar_init(done, 1);
+        abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_holder)),
+                     "r"(TMEM_COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tbase = tmem_holder;
+    const int nk = (p.d + TKF - 1) / TKF;
+    volatile int *ab = &abort_flag;
+
+    if (warp == 0) {
+        // ---- TMA producer ----
+        if (lane == 0) {
+            int s = 0;
+            uint32_t ph = 0;
+            uint32_t issued = 0, last_par = 0;  // per stage: loads issued, parity of the last one
+            for (int64_t t = blockIdx.x; t < p.ntiles && !*ab; t += gridDim.x) {
+                const int qt = (int)(t % p.nqt);
+                const int nt = (int)(t / p.nqt);
+                for (int kc = 0; kc < nk; ++kc) {
+                    if (!wait_bar(empty(s), ph ^ 1u, ab)) break;
+                    const uint32_t a = sbase + s * STAGE_BYTES, b = a + A_BYTES;
+                    mbar_expect_tx(full(s), STAGE_BYTES);
+                    tma_load_2d(a, &tmQ, full(s), kc * TKF, qt * TM);
+                    tma_load_2d(b, &tmX, full(s), kc * TKF, nt * TN);
+                    issued |= 1u << s;
+                    last_par = (last_par & ~(1u << s)) | (ph << s);
+                    if (++s == STAGES) {
+                        s = 0;
+                        ph ^= 1u;
+                    }
+                }
+            }
+            if (*ab) {
+                // copies in flight must land before the CTA's shared memory goes away
+                int dummy = 0;
+                for (int st = 0; st < STAGES; ++st)
+                    if (issued & (1u << st)) wait_bar(full(st), (last_par >> st) & 1u, &dummy);
+            }
+        }
+    } else if (warp == 1) {
+        // ---- MMA issuer ----
+        if (lane == 0) {
+            int s = 0;
+            uint32_t ph = 0;
+            int it = 0;
+            bool ok = true;
+            for (int64_t t = blockIdx.x; t < p.ntiles && ok; t += gridDim.x, ++it) {
+                const int b = it & 1;
+                const uint32_t use = (uint32_t)(it >> 1);
+                if (!wait_bar(tempty(b), (use & 1u) ^ 1u, ab)) break;
+                tc_fence_after();
+                const uint32_t dt = tbase + (uint32_t)(b * TN);
+                for (int kc = 0; kc < nk; ++kc) {
+                    if (!wait_bar(full(s), ph, ab)) {
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+                    const uint32_t a = sbase + s * STAGE_BYTES;
+                    const uint64_t ad = sw128_desc(a), bd = sw128_desc(a + A_BYTES);
+#pragma unroll
+                    for (int kk = 0; kk < TKF / 8; ++kk)  // K = 8 TF32 = 32 bytes per instruction
+                        mma_tf32(dt, ad + (uint64_t)(2 * kk), bd + (uint64_t)(2 * kk), (kc | kk) != 0);
+                    mma_commit(empty(s));  // the stage is free once these MMAs have read it
+                    if (++s == STAGES) {
+                        s = 0;
+                        ph ^= 1u;
+                    }
+                }
+                if (ok) mma_commit(tfull(b));
+            }
+            // no MMA may be in flight when TMEM is released
+            mma_commit(done);
+            int dummy = 0;
+            wait_bar(done, 0, &dummy);
+        }
+    } else {
+        // ---- epilogue: 8 warps; warp w reads TMEM lanes 32*(w%4).. (its quarter), columns of half (w-2)/4 ----
+        const int quarter = warp & 3;
+        const int half = (warp - 2) >> 2;
+        const int row_in_tile = quarter * 32 + lane;
+        int it = 0;
+        for (int64_t t = blockIdx.x; t < p.ntiles; t += gridDim.x, ++it) {
+            const int b = it & 1;
+            const uint32_t use = (uint32_t)(it >> 1);
+            const int qt = (int)(t % p.nqt);
+            const int64_t nt = t / p.nqt;
+            // one lane waits and the warp follows its verdict, so that the
+            // warp-collective TMEM loads below never run with lanes missing
+            int ok = 1;
+            if (lane == 0) ok = wait_bar(tfull(b), use & 1u, ab) ? 1 : 0;
+            if (!__shfl_sync(kFull, ok, 0)) break;
+            tc_fence_after();
+            const int64_t r = (int64_t)qt * TM + row_in_tile;
+            const bool rv = r < p.nq;
+            const float aq = rv ? p.c_qx * __ldg(p.qnorm + r) : 0.f;
+            const float tau_u = rv ? o2f(*reinterpret_cast<volatile uint32_t *>(p.tau_up + r))
+                                   : __int_as_float(0xff800000);
+            const int64_t col0 = nt * TN + half * (TN / 2);
+            const uint32_t taddr = tbase + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(b * TN + half * (TN / 2));
+            float L[KL];
+#pragma unroll
+            for (int i = 0; i < KL; ++i) L[i] = __int_as_float(0x7f800000);
+            // pass 1: the KL smallest upper bounds of this row below the shared bound
+#pragma unroll 1
+            for (int cb = 0; cb < TN / 2; cb += 32) {
+                float v[32];
+                tmem_ld32(taddr + cb, v);
+                if (rv) {
+#pragma unroll
+                    for (int i = 0; i < 32; ++i) {
+                        const int64_t c = col0 + cb + i;
+                        if (c < p.n) {
+                            float lo, up;
+                            dense_bounds<MET>(v[i], __ldg(p.xnorm + c), aq, p, lo, up);
+                            if (up < fminf(tau_u, L[KL - 1])) {
+                                float x = up;
+#pragma unroll
+                                for (int j = 0; j < KL; ++j) {
+                                    const float a = fminf(L[j], x);
+                                    x = fmaxf(L[j], x);
+                                    L[j] = a;
+                                }
+                            }
+                        }
+                    }
+                }
+            }
+            float kth = __int_as_float(0x7f800000);
+#pragma unroll
+            for (int i = 0; i < KL; ++i)
+                if (i == p.k - 1) kth = L[i];
+            const float T = fminf(tau_u, kth);
+            // pass 2: emit every vector whose lower bound is within T
+#pragma unroll 1
+            for (int cb = 0; cb < TN / 2; cb += 32) {
+                float v[32];
+                tmem_ld32(taddr + cb, v);
+                if (rv) {
+#pragma unroll
+                    for (int i = 0; i < 32; ++i) {
+                        const int64_t c = col0 + cb + i;
+                        if (c < p.n) {
+                            float lo, up;
+                            dense_bounds<MET>(v[i], __ldg(p.xnorm + c), aq, p, lo, up);
+                            if (lo <= T) {
+                                const int pos = atomicAdd(p.cnt + r, 1);
+                                if (pos < p.cap) {
+                                    p.ent[r * p.cap + pos] = make_float2(lo, up);
+                                    p.ent_id[r * p.cap + pos] = (int32_t)c;
+                                }
+                            }
+                        }
+                    }
+                }
+            }
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(tempty(b));
+            if (rv && kth < __int_as_float(0x7f800000)) atomicMin(p.tau_up + r, f2o(kth));
+        }
+    }
+    // ---- teardown ----
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        __syncwarp();
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tbase), "r"(TMEM_COLS) : "memory");
+    }
+    if (threadIdx.x == 0 && abort_flag) atomicExch(p.err, 1);
+}
+
+// ---------------------------------------------------------------------------
+__global__ void dense_prep_kernel(const float *__restrict__ q, int64_t nq, int32_t d, float *__restrict__ qs,
+                                  float *__restrict__ qnorm, uint32_t *__restrict__ tau_up, int32_t *__restrict__ cnt,
+                                  int32_t *__restrict__ err, unsigned long long *counters, int64_t n) {
+    const int64_t row = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        *err = 0;
+        atomicAdd(counters + C_VALUES, (unsigned long long)nq * (unsigned long long)n * (unsigned long long)d);
+        atomicAdd(counters + C_SCANNED, (unsigned long long)nq * (unsigned long long)n);
+    }
+    if (row >= nq) return;
+    float s = 0.f;
+    for (int j = lane; j < d; j += 32) {
+        const float v = q[row * d + j];
+        qs[row * d + j] = v;
+        s = fmaf(v, v, s);
+    }
+    s = warp_sum(s);
+    if (lane == 0) {
+        qnorm[row] = sqrtf(s);
+        tau_up[row] = f2o(__int_as_float(0x7f800000));
+        cnt[row] = 0;
+    }
+}
+
+__global__ void row_norms_kernel(const float *__restrict__ x, int64_t n, int32_t d, float2 *__restrict__ out) {
+    const int64_t row = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (row >= n) return;
+    float s = 0.f;
+    for (int j = lane; j < d; j += 32) {
+        const float v = x[row * d + j];
+        s = fmaf(v, v, s);
+    }
+    s = warp_sum(s);
+    if (lane == 0) out[row] = make_float2(s, sqrtf(s));
+}
+
+// Block-wide ascending bitonic sort of buf[0..len), len a power of two.
+__device__ void cta_bitonic(uint64_t *buf, int len) {
+    for (int size = 2; size <= len; size <<= 1) {
+        for (int stride = size >> 1; stride > 0; stride >>= 1) {
+            for (int i = threadIdx.x; i < (len >> 1); i += blockDim.x) {
+                const int lo = 2 * i - (i & (stride - 1));
+                const int hi = lo + stride;
+                const bool asc = (lo & size) == 0;
+                const uint64_t x = buf[lo], y = buf[hi];
+                if ((x > y) == asc) {
+                    buf[lo] = y;
+                    buf[hi] = x;
+                }
+            }
+            __syncthreads();
+        }
+    }
+}
+
+__device__ __forceinline__ int pow2_at_least(int v) {
+    int p = 1;
+    while (p < v) p <<= 1;
+    return p;
+}
+
+// Exact FP32 distance of query row qr to vector row xr: lane-strided
+// dimensions and a fixed butterfly (the scan path's refine arithmetic).
+template <int MET>
+__device__ __forceinline__ float exact_dist(const float *qr, const float *xr, int d, int lane) {
+    float acc = 0.f;
+    for (int j = lane; j < d; j += 32) acc = term<MET>(qr[j], xr[j], acc);
+    return rank_dist<MET>(warp_sum(acc));
+}
+
+struct FinishParams {
+    int64_t nq, n;
+    int32_t d, k, cap;
+    const float *q;               // [nq][d]
+    const float *x;               // [n][d]
+    const int32_t *cnt;
+    const float2 *ent;
+    const int32_t *ent_id;
+    const int32_t *err;
+    uint64_t *out;                // [nq][k] keys
+    unsigned long long *counters;
+};
+
+template <int MET>
+__global__ void __launch_bounds__(512) dense_finish_kernel(FinishParams f) {
+    extern __shared__ __align__(16) uint64_t fbuf[];  // cap keys, then cap int32 candidate slots
+    int32_t *cidx = reinterpret_cast<int32_t *>(fbuf + f.cap);
+    __shared__ int ncand;
+    const int64_t row = blockIdx.x;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+    const float *qr = f.q + row * f.d;
+    const int total = f.cnt[row];
+    if (total > f.cap || *f.err) {
+        // fallback: plain FP32 scan of all vectors, chunks merged into the best kpad
+        const int kpad = pow2_at_least(f.k);
+        const int chunk = f.cap - kpad;
+        for (int i = tid; i < kpad; i += blockDim.x) fbuf[i] = kEmptyKey;
+        for (int64_t off = 0; off < f.n; off += chunk) {
+            for (int i = warp; i < chunk; i += nw) {
+                const int64_t v = off + i;
+                uint64_t key = kEmptyKey;
+                if (v < f.n) key = make_key(exact_dist<MET>(qr, f.x + v * f.d, f.d, lane), (int32_t)v);
+                if (lane == 0) fbuf[kpad + i] = key;
+            }
+            __syncthreads();
+            cta_bitonic(fbuf, f.cap);
+        }
+        for (int i = tid; i < f.k; i += blockDim.x) f.out[row * f.k + i] = fbuf[i];
+        if (tid == 0) atomicAdd(f.counters + C_DENSE_FALLBACK, 1ull);
+        return;
+    }
+    const float2 *ent = f.ent + row * f.cap;
+    const int32_t *eid = f.ent_id + row * f.cap;
+    // T = k-th smallest upper bound among the emitted entries
+    const int len = pow2_at_least(total > 1 ? total : 1);
+    for (int i = tid; i < len; i += blockDim.x) fbuf[i] = i < total ? make_key(ent[i].y, i) : kEmptyKey;
+    if (tid == 0) ncand = 0;
+    __syncthreads();
+    cta_bitonic(fbuf, len);
+    const float T = total >= f.k ? key_dist(fbuf[f.k - 1]) : __int_as_float(0x7f800000);
+    __syncthreads();
+    for (int i = tid; i < total; i += blockDim.x)
+        if (ent[i].x <= T) cidx[atomicAdd(&ncand, 1)] = i;
+    __syncthreads();
+    const int nc = ncand;
+    for (int c = warp; c < nc; c += nw) {
+        const int32_t id = eid[cidx[c]];
+        const float dist = exact_dist<MET>(qr, f.x + (int64_t)id * f.d, f.d, lane);
+        if (lane == 0) fbuf[c] = make_key(dist, id);
+    }
+    const int len2 = pow2_at_least(nc > f.k ? nc : f.k);
+    for (int i = nc + tid; i < len2; i += blockDim.x) fbuf[i] = kEmptyKey;
+    __syncthreads();
+    cta_bitonic(fbuf, len2);
+    for (int i = tid; i < f.k; i += blockDim.x) f.out[row * f.k + i] = fbuf[i];
+    if (tid == 0) atomicAdd(f.counters + C_CANDIDATES, (unsigned long long)nc);
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult qr;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &qr) ==
+                cudaSuccess &&
+            qr == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    });
+    return fn;
+}
+
+// 2-D map over a row-major [rows][d] FP32 matrix, box of box_rows x 32
+// elements, 128-byte swizzle, zero fill outside.
+bool encode_rows(CUtensorMap *m, const float *base, int64_t rows, int32_t d, int box_rows) {
+    auto fn = encode_fn();
+    if (!fn) return false;
+    cuuint64_t dims[2] = {(cuuint64_t)d, (cuuint64_t)rows};
+    cuuint64_t strides[1] = {(cuuint64_t)d * 4};
+    cuuint32_t box[2] = {(cuuint32_t)TKF, (cuuint32_t)box_rows};
+    cuuint32_t estr[2] = {1, 1};
+    return fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float *>(base), dims, strides, box, estr,
+              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+template <int KL, int MET>
+cudaError_t launch_tc(const CUtensorMap &mq, const CUtensorMap &mx, const DenseParams &p, int grid, cudaStream_t st) {
+    cudaError_t e = cudaFuncSetAttribute(dense_tc_kernel<KL, MET>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         SMEM_BYTES);
+    if (e != cudaSuccess) return e;
+    dense_tc_kernel<KL, MET><<<grid, THREADS, SMEM_BYTES, st>>>(mq, mx, p);
+    return counted(cudaGetLastError());
+}
+
+template <int MET>
+cudaError_t launch_finish(const FinishParams &f, cudaStream_t st) {
+    const size_t smem = (size_t)f.cap * 12;
+    cudaError_t e =
+        cudaFuncSetAttribute(dense_finish_kernel<MET>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    dense_finish_kernel<MET><<<(unsigned)f.nq, 256, smem, st>>>(f);
+    return counted(cudaGetLastError());
+}
+
+}  // namespace
+
+int dense_cap(int64_t n, int32_t k) {
+    // entries per query: the k best of the first tiles plus the margin band;
+    // never more than the collection itself
+    int64_t c = 4096;
+    if (n < c) c = n;
+    int p = 64;
+    while (p < c) p <<= 1;
+    while (p < 4 * k) p <<= 1;
+    return p;
+}
+
+size_t dense_scratch_bytes(int64_t nq, int32_t d, int32_t k, int32_t cap) {
+    auto rup = [](size_t b) { return (b + 255) & ~size_t(255); };
+    return rup((size_t)nq * d * 4) + 3 * rup((size_t)nq * 4) + rup((size_t)nq * cap * 8) + rup((size_t)nq * cap * 4) +
+           rup((size_t)nq * k * 8) + rup(8);
+}
+
+bool dense_supported(const pdx_index *ix, int32_t k, const char **why) {
+    const char *w = nullptr;
+    if (ix->is_ivf) w = "the tensor-core engine serves exact indexes only";
+    else if (!ix->xnary || !ix->xnorm) w = "the index keeps no row-major FP32 vectors (build with dense_rows=1)";
+    else if (ix->metric != PDX_L2 && ix->metric != PDX_IP) w = "the tensor-core engine supports L2 and IP";
+    else if (ix->d % 4 != 0) w = "the tensor-core engine needs d to be a multiple of 4 (16-byte rows for TMA)";
+    else if (k > 64) w = "the tensor-core engine supports k <= 64";
+    if (why) *why = w;
+    return w == nullptr;
+}
+
+pdx_status dense_run(const pdx_index *ix, const float *qd, int64_t nq, int32_t k, int metric, int out_mode,
+                     unsigned char *scratch, size_t bytes, int cap, float *od, int64_t *oi, unsigned long long *counters,
+                     int sms, void *ev_start, void *ev_stop, cudaStream_t st) {
+    const int d = ix->d;
+    auto rup = [](size_t b) { return (b + 255) & ~size_t(255); };
+    size_t off = 0;
+    auto take = [&](size_t b) {
+        unsigned char *p = scratch + off;
+        off += rup(b);
+        return p;
+    };
+    float *qs = reinterpret_cast<float *>(take((size_t)nq * d * 4));
+    float *qnorm = reinterpret_cast<float *>(take((size_t)nq * 4));
+    uint32_t *tau_up = reinterpret_cast<uint32_t *>(take((size_t)nq * 4));
+    int32_t *cnt = reinterpret_cast<int32_t *>(take((size_t)nq * 4));
+    float2 *ent = reinterpret_cast<float2 *>(take((size_t)nq * cap * 8));
+    int32_t *ent_id = reinterpret_cast<int32_t *>(take((size_t)nq * cap * 4));
+    uint64_t *keys = reinterpret_cast<uint64_t *>(take((size_t)nq * k * 8));
+    int32_t *err = reinterpret_cast<int32_t *>(take(8));
+    if (off > bytes) {
+        set_error("internal error: dense-search scratch layout exceeds its plan");
+        return PDX_ERR_CUDA;
+    }
+    if (nq == 0) return PDX_OK;
+    {
+        const unsigned grid = (unsigned)((nq * 32 + 255) / 256);
+        dense_prep_kernel<<<grid, 256, 0, st>>>(qd, nq, d, qs, qnorm, tau_up, cnt, err, counters, ix->n);
+        cudaError_t e = counted(cudaGetLastError());
+        if (e != cudaSuccess) return cuda_status_ext(e, "dense_prep_kernel");
+    }
+    CUtensorMap mq, mx;
+    if (!encode_rows(&mq, qs, nq, d, TM) || !encode_rows(&mx, ix->xnary, ix->n, d, TN)) {
+        set_error("cuTensorMapEncodeTiled failed (d=%d)", d);
+        return PDX_ERR_CUDA;
+    }
+    DenseParams p;
+    p.nq = nq;
+    p.n = ix->n;
+    p.d = d;
+    p.k = k;
+    p.nqt = (int32_t)((nq + TM - 1) / TM);
+    p.ntiles = (int64_t)p.nqt * ((ix->n + TN - 1) / TN);
+    p.qnorm = qnorm;
+    p.xnorm = reinterpret_cast<const float2 *>(ix->xnorm);
+    p.tau_up = tau_up;
+    p.cnt = cnt;
+    p.cap = cap;
+    p.ent = ent;
+    p.ent_id = ent_id;
+    // margin coefficients (see dense_bounds), each with a 2^-10 relative cushion
+    const double u = std::ldexp(1.0, -22);
+    const double cdot = std::ldexp(1.0, -9) + (d + 16) * u;
+    const double cushion = 1.0 + std::ldexp(1.0, -10);
+    p.c_qx = (float)((metric == MT_L2 ? 2.0 : 1.0) * cdot * cushion);
+    p.c_xx = (float)((d + 8) * u * cushion);
+    p.c_rel = (float)(4.0 * u);
+    p.err = err;
+    const int grid = (int)std::min<int64_t>(p.ntiles, (int64_t)sms);
+    cudaError_t e;
+    if (ev_start && (e = cudaEventRecord(static_cast<cudaEvent_t>(ev_start), st)) != cudaSuccess)
+        return cuda_status_ext(e, "cudaEventRecord");
+    if (metric == MT_IP)
+        e = k <= 16 ? launch_tc<16, MT_IP>(mq, mx, p, grid, st) : launch_tc<64, MT_IP>(mq, mx, p, grid, st);
+    else
+        e = k <= 16 ? launch_tc<16, MT_L2>(mq, mx, p, grid, st) : launch_tc<64, MT_L2>(mq, mx, p, grid, st);
+    if (e != cudaSuccess) return cuda_status_ext(e, "dense_tc_kernel");
+    if (ev_stop && (e = cudaEventRecord(static_cast<cudaEvent_t>(ev_stop), st)) != cudaSuccess)
+        return cuda_status_ext(e, "cudaEventRecord");
+    FinishParams f;
+    f.nq = nq;
+    f.n = ix->n;
+    f.d = d;
+    f.k = k;
+    f.cap = cap;
+    f.q = qs;
+    f.x = ix->xnary;
+    f.cnt = cnt;
+    f.ent = ent;
+    f.ent_id = ent_id;
+    f.err = err;
+    f.out = keys;
+    f.counters = counters;
+    e = metric == MT_IP ? launch_finish<MT_IP>(f, st) : launch_finish<MT_L2>(f, st);
+    if (e != cudaSuccess) return cuda_status_ext(e, "dense_finish_kernel");
+    e = launch_write_out(keys, nq, k, out_mode, qd, d, od, oi, st);
+    if (e != cudaSuccess) return cuda_status_ext(e, "write_out_kernel");
+    return PDX_OK;
+}
+
+cudaError_t launch_row_norms(const float *x, int64_t n, int32_t d, float *out, cudaStream_t st) {
+    if (n == 0) return cudaSuccess;
+    row_norms_kernel<<<(unsigned)((n * 32 + 255) / 256), 256, 0, st>>>(x, n, d, reinterpret_cast<float2 *>(out));
+    return counted(cudaGetLastError());
+}
+
+}  // namespace pdx

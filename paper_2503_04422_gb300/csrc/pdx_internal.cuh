@@ -18,9 +18,11 @@ constexpr int kMaxK = 1024;
 constexpr int kMaxD = 4096;
 constexpr int kMaxSortUnits = 256;  // zone keys a scan warp sorts in-kernel (8 per lane)
 
-// Device counters, in the order of the first fields of pdx_search_stats.
+// Device counters, in the order of the first fields of pdx_search_stats
+// (slot 7 is bytes_logical, which the host derives and no kernel writes).
 enum Counter {
-    C_VALUES = 0, C_SCANNED, C_PRUNED, C_PRUNE_BLOCKS, C_CANDIDATES, C_ITEMS, C_START, C_COUNT
+    C_VALUES = 0, C_SCANNED, C_PRUNED, C_PRUNE_BLOCKS, C_CANDIDATES, C_ITEMS, C_START, C_BYTES_HOST,
+    C_DENSE_FALLBACK, C_COUNT
 };
 
 // Kernels launched through the library (host-side count).
@@ -48,7 +50,9 @@ struct pdx_index {
     float *data = nullptr;          // [nblocks][d][64] FP32 (absent for low-precision storage)
     void *data_lp = nullptr;        // [nblocks][d][64] BF16 / FP8-E4M3 blocks
     float *scale = nullptr;         // [d] FP8: per-dimension scale
-    float *xnary = nullptr;         // [n][d] FP32 vectors by id (low precision: START, rerank)
+    float *xnary = nullptr;         // [n][d] FP32 vectors by id (low precision: START, rerank;
+                                    // tensor-core dense engine)
+    float *xnorm = nullptr;         // [n][2] (||x||^2, ||x||) of the rows above (dense engine)
     int32_t *ids = nullptr;         // [nblocks*64]
     int32_t *slot_of = nullptr;     // [n] storage slot (block*64 + lane) of each vector id
     int32_t *blk_cnt = nullptr;     // [nblocks] valid lanes per block
@@ -71,6 +75,23 @@ struct pdx_index {
     // host mirrors
     int32_t *h_part_blk = nullptr;  // [nparts+1]
     uint64_t bytes = 0;
+};
+
+// Order-proposal network (pdx_mlp.cu).
+struct pdx_mlp {
+    int d = 0, hidden = 0;
+    // FP32 master parameters, one buffer: W1 [H][2D] | b1 [H] | W2 [D][H] | b2 [D]
+    float *p = nullptr;
+    float *g = nullptr;            // gradients, same layout
+    float *m = nullptr, *v = nullptr;  // Adam moments
+    uint16_t *w1h = nullptr, *w2h = nullptr;  // BF16 copies of W1, W2 for inference
+    bool bf16_stale = true;
+    int64_t adam_t = 0;
+    size_t count = 0;
+    float *w1() const { return p; }
+    float *b1() const { return p + (size_t)hidden * 2 * d; }
+    float *w2() const { return b1() + hidden; }
+    float *b2() const { return w2() + (size_t)d * hidden; }
 };
 
 namespace pdx {
@@ -105,6 +126,34 @@ __device__ __forceinline__ uint64_t make_key(float dist, int32_t id) {
 }
 __device__ __forceinline__ float key_dist(uint64_t key) { return o2f((uint32_t)(key >> 32)); }
 __device__ __forceinline__ int32_t key_id(uint64_t key) { return (int32_t)(uint32_t)(key & 0xffffffffu); }
+
+enum { MT_L2 = 0, MT_IP = 1, MT_L1 = 2 };
+constexpr unsigned kFull = 0xffffffffu;
+
+// One dimension's contribution to the distance (Sec. 2.1): squared
+// difference, product, or absolute difference.
+template <int MET>
+__device__ __forceinline__ float term(float qv, float x, float acc) {
+    if (MET == MT_L2) {
+        float t = qv - x;
+        return fmaf(t, t, acc);
+    } else if (MET == MT_IP) {
+        return fmaf(qv, x, acc);
+    } else {
+        return acc + fabsf(qv - x);
+    }
+}
+
+// distance used for ranking (smaller is better)
+template <int MET>
+__device__ __forceinline__ float rank_dist(float acc) { return MET == MT_IP ? -acc : acc; }
+
+// Fixed butterfly: every lane ends with the same sum, in the same order.
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+    for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+    return v;
+}
 #endif
 
 constexpr uint64_t kEmptyKey = ~0ull;
@@ -164,11 +213,17 @@ cudaError_t launch_scan(int pruner, int metric, const ScanParams &p, int num_sms
 // decreasing query value); per_part > 0: one row per (query, part) with
 // means[part], else one row per query with means[0..d).
 cudaError_t launch_order(const float *q, int64_t rows, int32_t d, const float *means, int32_t per_part,
-                         const int32_t *row_part, int mode, int32_t Z, uint16_t *out, cudaStream_t st);
+                         const int32_t *row_part, int mode, int32_t Z, const float *scores, uint16_t *out,
+                         cudaStream_t st);
+// learned order: network inputs [q; nearest centroid] and BF16 inference
+cudaError_t launch_mlp_inputs(const float *q, int64_t nq, int d, const float *cent, const uint64_t *nearest, float *u,
+                              cudaStream_t st);
+cudaError_t mlp_scores(pdx_mlp *net, const float *U, int64_t B, float *Z, float *Y, cudaStream_t st);
 
 // How a search gets its PDX-BOND visit orders (see plan_orders).
 struct OrderPlan {
-    int mode = -1;        // -1: none precomputed (in-kernel zones or storage order); 0: to means; 1: decreasing
+    int mode = -1;        // -1: none precomputed (in-kernel zones or storage order); 0: to means; 1: decreasing;
+                          // 2: learned (network scores)
     int per_part = 0;     // >0: rows per query (one per part rank); 0: one row per query
     int64_t rows = 0;
     size_t bytes = 0;
@@ -183,6 +238,10 @@ struct ExactPlan {
     int start_blk = 0;
     int64_t Lstart = 0;
     OrderPlan op;
+    size_t mlp_bytes = 0;      // learned order: centroid keys, nearest, inputs, hidden, scores
+    int64_t mlp_Lc = 0;
+    bool dense = false;        // tensor-core engine (pdx_dense.cu) instead of the scan
+    int dense_cap = 0;         // its candidate entries per query
     size_t bytes = 0;
 };
 pdx_status exact_check(const pdx_index *ix, const float *q, int64_t nq, int32_t k, const pdx_search_opts *opts,
@@ -193,6 +252,16 @@ pdx_status exact_run(const pdx_index *ix, const float *qd, int64_t nq, int32_t k
                      const SearchPlan &pl, const ExactPlan &ep, unsigned char *scratch, float *od, int64_t *oi,
                      unsigned long long **counters_out, int sms, cudaStream_t st);
 void fill_stats(pdx_search_stats *so, const unsigned long long *c, const pdx_index *ix);
+
+// Tensor-core dense engine (pdx_dense.cu).
+bool dense_supported(const pdx_index *ix, int32_t k, const char **why);
+int dense_cap(int64_t n, int32_t k);
+size_t dense_scratch_bytes(int64_t nq, int32_t d, int32_t k, int32_t cap);
+pdx_status dense_run(const pdx_index *ix, const float *qd, int64_t nq, int32_t k, int metric, int out_mode,
+                     unsigned char *scratch, size_t bytes, int cap, float *od, int64_t *oi, unsigned long long *counters,
+                     int sms, void *ev_start, void *ev_stop, cudaStream_t st);
+// (||x||^2, ||x||) of each row of x[n][d], FP32, as out[n][2]
+cudaError_t launch_row_norms(const float *x, int64_t n, int32_t d, float *out, cudaStream_t st);
 size_t scan_warp_smem(int d, int k, int zone_dims, int order);
 
 // START: exact distances of every query to the first `nvec` stored vectors,

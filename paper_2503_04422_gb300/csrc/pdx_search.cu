@@ -33,20 +33,6 @@
 namespace pdx {
 
 enum { PR_NONE = 0, PR_BOND = 1, PR_ADS = 2, PR_BSA = 3 };
-enum { MT_L2 = 0, MT_IP = 1, MT_L1 = 2 };
-constexpr unsigned kFull = 0xffffffffu;
-
-template <int MET>
-__device__ __forceinline__ float term(float qv, float x, float acc) {
-    if (MET == MT_L2) {
-        float t = qv - x;
-        return fmaf(t, t, acc);
-    } else if (MET == MT_IP) {
-        return fmaf(qv, x, acc);
-    } else {
-        return acc + fabsf(qv - x);
-    }
-}
 
 // ---- storage types of the PDX blocks ----
 enum { ST_F32 = 0, ST_BF16 = 1, ST_FP8 = 2 };
@@ -107,21 +93,11 @@ __device__ __forceinline__ float lp_term(float qv, float xh, float acc, float s2
     }
 }
 
-// distance used for ranking (smaller is better)
-template <int MET>
-__device__ __forceinline__ float rank_dist(float acc) { return MET == MT_IP ? -acc : acc; }
-
 __device__ __forceinline__ float sel4(const float4 &v, int c) {
     return c == 0 ? v.x : (c == 1 ? v.y : (c == 2 ? v.z : v.w));
 }
 
 __device__ __forceinline__ float slack(float tau, float gamma) { return tau + fabsf(tau) * gamma; }
-
-__device__ __forceinline__ float warp_sum(float v) {
-#pragma unroll
-    for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
-    return v;
-}
 
 __device__ __forceinline__ int next_pow2(int v) {
     int p = 1;
@@ -1043,13 +1019,15 @@ cudaError_t launch_write_out(const uint64_t *topk, int64_t nq, int32_t k, int mo
 // Query preprocessing for PDX-BOND (Sec. 5): the dimension visit order of each
 // row (a query, or a (query, part) pair when per_part > 0), computed once and
 // stored as uint16 dimension indices. mode 0: distance to the means (zones of
-// Z dimensions, score = sum (q_j - mu_j)^2); mode 1: decreasing query value.
+// Z dimensions, score = sum (q_j - mu_j)^2); mode 1: decreasing query value;
+// mode 2: decreasing (q_j - mu_j)^2 + s_q scores[row][j] (the network's
+// correction in units of s_q = mean_j (q_j - mu_j)^2).
 // One CTA per row sorts its keys (score descending, index ascending) with a
 // block-wide bitonic sort in shared memory.
 __global__ void __launch_bounds__(256) order_kernel(const float *__restrict__ q, int64_t rows, int32_t d,
                                                     const float *__restrict__ means, int32_t per_part,
                                                     const int32_t *__restrict__ row_part, int mode, int32_t Z,
-                                                    uint16_t *__restrict__ out) {
+                                                    const float *__restrict__ scores, uint16_t *__restrict__ out) {
     extern __shared__ __align__(16) uint64_t keys[];
     const int64_t row = blockIdx.x;
     if (row >= rows) return;
@@ -1059,14 +1037,36 @@ __global__ void __launch_bounds__(256) order_kernel(const float *__restrict__ q,
     if (per_part > 0) part = row_part ? row_part[row] : (int)(row % per_part);
     if (part < 0) part = 0;   // unused probe slot: any valid row of means
     const float *mu = means + (int64_t)part * d;
-    const int nunits = (mode == 1) ? d : (d + Z - 1) / Z;
-    const int zz = (mode == 1) ? 1 : Z;
+    const int nunits = (mode >= 1) ? d : (d + Z - 1) / Z;
+    const int zz = (mode >= 1) ? 1 : Z;
     const int npad = pow2_ceil(nunits);
+    // learned order: the network's outputs are in units of this query's mean
+    // heuristic term s_q = mean_j (q_j - mu_j)^2
+    __shared__ float sq_part[256];
+    float sq = 0.f;
+    if (mode == 2) {
+        float part = 0.f;
+        for (int j = threadIdx.x; j < d; j += blockDim.x) {
+            float t = qrow[j] - mu[j];
+            part = fmaf(t, t, part);
+        }
+        sq_part[threadIdx.x] = part;
+        __syncthreads();
+        for (int o = blockDim.x >> 1; o; o >>= 1) {
+            if ((int)threadIdx.x < o) sq_part[threadIdx.x] += sq_part[threadIdx.x + o];
+            __syncthreads();
+        }
+        sq = sq_part[0] / (float)d;
+    }
     for (int u = threadIdx.x; u < npad; u += blockDim.x) {
         uint64_t key = kEmptyKey;
         if (u < nunits) {
             float sc = 0.f;
-            if (mode == 1) {
+            if (mode == 2) {
+                // learned: heuristic (q_j - mu_j)^2 plus the network's correction
+                float t = qrow[u] - mu[u];
+                sc = fmaf(t, t, sq * scores[row * (int64_t)d + u]);
+            } else if (mode == 1) {
                 sc = qrow[u];
             } else {
                 int j1 = min(d, u * zz + zz);
@@ -1114,13 +1114,14 @@ __global__ void __launch_bounds__(256) order_kernel(const float *__restrict__ q,
 }
 
 cudaError_t launch_order(const float *q, int64_t rows, int32_t d, const float *means, int32_t per_part,
-                         const int32_t *row_part, int mode, int32_t Z, uint16_t *out, cudaStream_t st) {
+                         const int32_t *row_part, int mode, int32_t Z, const float *scores, uint16_t *out,
+                         cudaStream_t st) {
     if (rows == 0) return cudaSuccess;
-    const int nunits = (mode == 1) ? d : (d + Z - 1) / Z;
+    const int nunits = (mode >= 1) ? d : (d + Z - 1) / Z;
     size_t smem = (size_t)pow2_ceil(nunits) * 8;
     cudaError_t e = cudaFuncSetAttribute(order_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    order_kernel<<<(unsigned)rows, 256, smem, st>>>(q, rows, d, means, per_part, row_part, mode, Z, out);
+    order_kernel<<<(unsigned)rows, 256, smem, st>>>(q, rows, d, means, per_part, row_part, mode, Z, scores, out);
     return counted(cudaGetLastError());
 }
 

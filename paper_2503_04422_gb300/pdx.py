@@ -22,8 +22,9 @@ PDX_OK, PDX_ERR_ARG, PDX_ERR_OOM, PDX_ERR_CUDA, PDX_ERR_TIMEOUT, PDX_ERR_UNSUPPO
 METRIC = {"l2": 0, "ip": 1, "l1": 2}
 DTYPE = {"f32": 0, "bf16": 1, "fp8": 2}
 PRUNER = {"none": 0, "bond": 1, "ads": 2, "adsampling": 2, "bsa": 3}
-ORDER = {"dist_to_means": 0, "decreasing": 1, "sequential": 2}
+ORDER = {"dist_to_means": 0, "decreasing": 1, "sequential": 2, "learned": 3}
 MEANS = {"block": 0, "collection": 1, "auto": 2}
+ENGINE = {"auto": 0, "scan": 1, "tensor": 2}
 ARRAY = {"blocks": 0, "ids": 1, "part_blocks": 2, "means": 3, "centroids": 4, "assign": 5, "rotation": 6,
          "variances": 7, "blocks_lp": 8, "scales": 9}
 STATUS_NAMES = {0: "PDX_OK", 1: "PDX_ERR_ARG", 2: "PDX_ERR_OOM", 3: "PDX_ERR_CUDA", 4: "PDX_ERR_TIMEOUT",
@@ -32,7 +33,8 @@ STATUS_NAMES = {0: "PDX_OK", 1: "PDX_ERR_ARG", 2: "PDX_ERR_OOM", 3: "PDX_ERR_CUD
 
 class pdx_build_opts(ctypes.Structure):
     _fields_ = [("struct_size", ctypes.c_uint32), ("metric", ctypes.c_int), ("storage", ctypes.c_int),
-                ("partition_size", ctypes.c_uint32), ("keep_fp32_rerank", ctypes.c_int32)]
+                ("partition_size", ctypes.c_uint32), ("keep_fp32_rerank", ctypes.c_int32),
+                ("dense_rows", ctypes.c_int32)]
 
 
 class pdx_ivf_opts(ctypes.Structure):
@@ -46,9 +48,9 @@ class pdx_search_stats(ctypes.Structure):
                 ("vectors_pruned", ctypes.c_uint64), ("prune_phase_blocks", ctypes.c_uint64),
                 ("candidates", ctypes.c_uint64), ("work_items", ctypes.c_uint64),
                 ("start_values", ctypes.c_uint64), ("bytes_logical", ctypes.c_uint64),
-                ("reserved", ctypes.c_uint64 * 8)]
+                ("dense_fallbacks", ctypes.c_uint64), ("reserved", ctypes.c_uint64 * 7)]
     FIELDS = ("values_visited", "vectors_scanned", "vectors_pruned", "prune_phase_blocks", "candidates",
-              "work_items", "start_values", "bytes_logical")
+              "work_items", "start_values", "bytes_logical", "dense_fallbacks")
 
     def as_dict(self):
         return {f: int(getattr(self, f)) for f, _ in self._fields_ if f != "reserved"}
@@ -61,7 +63,8 @@ class pdx_search_opts(ctypes.Structure):
                 ("blocks_per_item", ctypes.c_uint32), ("stats_out", ctypes.POINTER(pdx_search_stats)),
                 ("stats_device", ctypes.c_void_p), ("scan_event_start", ctypes.c_void_p),
                 ("scan_event_stop", ctypes.c_void_p), ("means_scope", ctypes.c_int),
-                ("ctas_per_sm", ctypes.c_uint32)]
+                ("ctas_per_sm", ctypes.c_uint32), ("mlp", ctypes.c_void_p), ("mlp_centroids", ctypes.c_void_p),
+                ("mlp_ncentroids", ctypes.c_int32), ("engine", ctypes.c_int)]
 
 
 class pdx_index_info(ctypes.Structure):
@@ -196,23 +199,31 @@ class Index:
             pass
 
 
-def build_opts(metric="l2", storage="f32", partition_size=10000, keep_fp32_rerank=True) -> pdx_build_opts:
+def build_opts(metric="l2", storage="f32", partition_size=10000, keep_fp32_rerank=True,
+               dense_rows=False) -> pdx_build_opts:
     o = pdx_build_opts()
     lib().pdx_default_build_opts(ctypes.byref(o))
     o.metric = METRIC[metric]
     o.storage = DTYPE[storage]
     o.partition_size = partition_size
     o.keep_fp32_rerank = int(bool(keep_fp32_rerank))
+    o.dense_rows = int(bool(dense_rows))
     return o
 
 
 def search_opts(pruner="bond", order="dist_to_means", zone_dims=None, selection_threshold=None, eps0=None,
                 bsa_m=None, first_step=None, start_vectors=None, blocks_per_item=None,
-                means_scope=None, ctas_per_sm=None) -> pdx_search_opts:
+                means_scope=None, ctas_per_sm=None, mlp=None, mlp_centroids=None,
+                engine="auto") -> pdx_search_opts:
     o = pdx_search_opts()
     lib().pdx_default_search_opts(ctypes.byref(o))
     o.pruner = PRUNER[pruner]
     o.order = ORDER[order]
+    o.engine = ENGINE[engine]
+    if mlp is not None:
+        o.mlp = mlp.handle.value if hasattr(mlp.handle, "value") else mlp.handle
+        o.mlp_centroids = mlp_centroids.data_ptr()
+        o.mlp_ncentroids = mlp_centroids.shape[0]
     if means_scope is not None:
         o.means_scope = MEANS[means_scope]
     for name, v in (("zone_dims", zone_dims), ("selection_threshold", selection_threshold), ("eps0", eps0),
@@ -223,13 +234,15 @@ def search_opts(pruner="bond", order="dist_to_means", zone_dims=None, selection_
     return o
 
 
-def pdx_build_layout(x, metric="l2", partition_size=10000, storage="f32", stream=None) -> Index:
-    """Exact-search index over x [n][d] (Sec. 3, Sec. 6.6)."""
+def pdx_build_layout(x, metric="l2", partition_size=10000, storage="f32", stream=None,
+                     dense_rows=False) -> Index:
+    """Exact-search index over x [n][d] (Sec. 3, Sec. 6.6); dense_rows also
+    keeps the row-major FP32 vectors the tensor-core engine reads."""
     p, keep, cuda, shape = _ptr_f32(x, "x")
     if len(shape) != 2:
         raise ValueError("x must be [n][d]")
     h = ctypes.c_void_p()
-    o = build_opts(metric, storage, partition_size)
+    o = build_opts(metric, storage, partition_size, dense_rows=dense_rows)
     _check(lib().pdx_build_layout(p, shape[0], shape[1], ctypes.byref(o), _stream(cuda, stream), ctypes.byref(h)),
            "pdx_build_layout")
     del keep
@@ -417,3 +430,102 @@ class Server:
             self.free()
         except Exception:
             pass
+
+
+# ---------------------------------------------------------------- order network
+def _mlp_lib():
+    L = lib()
+    if not getattr(L, "_mlp_ready", False):
+        vp, i64, i32 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32
+        L.pdx_mlp_create.argtypes = [i32, i32, ctypes.c_uint64, ctypes.POINTER(vp)]
+        L.pdx_mlp_free.argtypes = [vp]
+        L.pdx_mlp_free.restype = None
+        L.pdx_mlp_param_count.argtypes = [vp]
+        L.pdx_mlp_param_count.restype = ctypes.c_size_t
+        L.pdx_mlp_set_params.argtypes = [vp, vp, ctypes.c_size_t]
+        L.pdx_mlp_get_params.argtypes = [vp, vp, ctypes.c_size_t]
+        L.pdx_mlp_forward.argtypes = [vp, vp, i64, i32, vp, vp]
+        L.pdx_mlp_backward.argtypes = [vp, vp, vp, i64, vp, ctypes.POINTER(ctypes.c_float), vp]
+        L.pdx_mlp_train.argtypes = [vp, vp, vp, i64, i32, i32, ctypes.c_float, ctypes.c_uint64,
+                                    ctypes.POINTER(ctypes.c_float), vp]
+        L.pdx_order_targets.argtypes = [vp, vp, i64, vp, i32, vp, vp]
+        L.pdx_mlp_inputs.argtypes = [vp, i64, i32, vp, i32, vp, vp]
+        L.pdx_mlp_inputs.restype = ctypes.c_int
+        for f in ("pdx_mlp_create", "pdx_mlp_set_params", "pdx_mlp_get_params", "pdx_mlp_forward",
+                  "pdx_mlp_backward", "pdx_mlp_train", "pdx_order_targets"):
+            getattr(L, f).restype = ctypes.c_int
+        L._mlp_ready = True
+    return L
+
+
+class Mlp:
+    """Order-proposal network (pdx_mlp_*). Device tensors in, device tensors out."""
+
+    def __init__(self, d, hidden=256, seed=2503):
+        L = _mlp_lib()
+        h = ctypes.c_void_p()
+        _check(L.pdx_mlp_create(d, hidden, seed, ctypes.byref(h)), "pdx_mlp_create")
+        self.handle, self.d, self.hidden = h, d, hidden
+        self.count = int(L.pdx_mlp_param_count(h))
+
+    def get_params(self):
+        out = np.empty(self.count, np.float32)
+        _check(_mlp_lib().pdx_mlp_get_params(self.handle, out.ctypes.data, self.count), "pdx_mlp_get_params")
+        return out
+
+    def set_params(self, p):
+        p = np.ascontiguousarray(p, np.float32)
+        _check(_mlp_lib().pdx_mlp_set_params(self.handle, p.ctypes.data, p.size), "pdx_mlp_set_params")
+
+    def forward(self, u, bf16=False):
+        import torch
+        y = torch.empty((u.shape[0], self.d), dtype=torch.float32, device=u.device)
+        _check(_mlp_lib().pdx_mlp_forward(self.handle, u.data_ptr(), u.shape[0], int(bf16), y.data_ptr(),
+                                          torch.cuda.current_stream().cuda_stream), "pdx_mlp_forward")
+        return y
+
+    def backward(self, u, t):
+        import torch
+        g = np.empty(self.count, np.float32)
+        loss = ctypes.c_float()
+        _check(_mlp_lib().pdx_mlp_backward(self.handle, u.data_ptr(), t.data_ptr(), u.shape[0], g.ctypes.data,
+                                           ctypes.byref(loss), torch.cuda.current_stream().cuda_stream),
+               "pdx_mlp_backward")
+        return g, loss.value
+
+    def train(self, u, t, epochs=10, batch=256, lr=1e-3, seed=1):
+        import torch
+        loss = ctypes.c_float()
+        _check(_mlp_lib().pdx_mlp_train(self.handle, u.data_ptr(), t.data_ptr(), u.shape[0], epochs, batch, lr, seed,
+                                        ctypes.byref(loss), torch.cuda.current_stream().cuda_stream), "pdx_mlp_train")
+        return loss.value
+
+    def free(self):
+        if self.handle:
+            _mlp_lib().pdx_mlp_free(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def pdx_order_targets(index: Index, q, ids, m=None):
+    """Trace targets for the network (see pdx.h), q and ids CUDA tensors."""
+    import torch
+    m = ids.shape[1] if m is None else m
+    t = torch.empty((q.shape[0], index.info.d), dtype=torch.float32, device=q.device)
+    _check(_mlp_lib().pdx_order_targets(index.handle, q.data_ptr(), q.shape[0], ids.data_ptr(), m, t.data_ptr(),
+                                        torch.cuda.current_stream().cuda_stream), "pdx_order_targets")
+    return t
+
+
+def pdx_mlp_inputs(q, centroids):
+    """[q; nearest centroid] rows for the network (CUDA tensors)."""
+    import torch
+    u = torch.empty((q.shape[0], 2 * q.shape[1]), dtype=torch.float32, device=q.device)
+    _check(_mlp_lib().pdx_mlp_inputs(q.data_ptr(), q.shape[0], q.shape[1], centroids.data_ptr(), centroids.shape[0],
+                                     u.data_ptr(), torch.cuda.current_stream().cuda_stream), "pdx_mlp_inputs")
+    return u

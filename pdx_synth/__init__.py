@@ -137,6 +137,23 @@ def embedding_like(n: int, d: int, nq: int, n_clusters: int = 4096, rank: int = 
     return rows(n, 1), rows(nq, 2)
 
 
+def hetero_mixture(n: int, d: int, nq: int, n_centres: int = 64, seed: int = BASE_SEED + 6):
+    """Gaussian mixture whose per-dimension spread varies strongly across
+    dimensions (log-uniform in [0.05, 2]) around centres ~ N(0, 0.25 I): the
+    distance-to-means order alone does not see the spread, so a learned
+    correction has something to learn."""
+    rng = _rng(seed, 600)
+    sig = np.exp(rng.uniform(math.log(0.05), math.log(2.0), d)).astype(np.float32)
+    cen = (rng.standard_normal((n_centres, d)) * 0.5).astype(np.float32)
+
+    def rows(count, stream):
+        r = _rng(seed, stream)
+        lab = r.integers(0, n_centres, count)
+        return (cen[lab] + sig * r.standard_normal((count, d), dtype=np.float32)).astype(np.float32)
+
+    return rows(n, 1), rows(nq, 2)
+
+
 @dataclass
 class Collection:
     n: int

@@ -47,15 +47,19 @@ def test_struct_layouts_match_c(tmp_path):
         '#include <stdio.h>\n#include <stddef.h>\n#include "pdx.h"\n'
         "int main(void){printf(\"%zu %zu %zu %zu %zu %zu %zu\\n\", sizeof(pdx_build_opts), sizeof(pdx_ivf_opts),"
         " sizeof(pdx_search_opts), sizeof(pdx_search_stats), sizeof(pdx_index_info),"
-        " offsetof(pdx_search_opts, ctas_per_sm), offsetof(pdx_ivf_opts, init_centroids));"
-        "printf(\"%zu %zu\\n\", sizeof(pdx_server_opts), sizeof(pdx_server_info_t));return 0;}\n")
+        " offsetof(pdx_search_opts, mlp_ncentroids), offsetof(pdx_ivf_opts, init_centroids));"
+        "printf(\"%zu %zu\\n\", sizeof(pdx_server_opts), sizeof(pdx_server_info_t));"
+        "printf(\"%zu %zu %zu\\n\", offsetof(pdx_search_opts, engine), offsetof(pdx_build_opts, dense_rows),"
+        " offsetof(pdx_search_stats, dense_fallbacks));return 0;}\n")
     exe = tmp_path / "sizes"
     subprocess.check_call(["gcc", "-I", os.path.join(ROOT, "include"), str(prog), "-o", str(exe)])
     got = [int(v) for v in subprocess.check_output([str(exe)]).split()]
     want = [ctypes.sizeof(P.pdx_build_opts), ctypes.sizeof(P.pdx_ivf_opts), ctypes.sizeof(P.pdx_search_opts),
             ctypes.sizeof(P.pdx_search_stats), ctypes.sizeof(P.pdx_index_info),
-            P.pdx_search_opts.ctas_per_sm.offset, P.pdx_ivf_opts.init_centroids.offset,
-            ctypes.sizeof(P.pdx_server_opts), ctypes.sizeof(P.pdx_server_info_t)]
+            P.pdx_search_opts.mlp_ncentroids.offset, P.pdx_ivf_opts.init_centroids.offset,
+            ctypes.sizeof(P.pdx_server_opts), ctypes.sizeof(P.pdx_server_info_t),
+            P.pdx_search_opts.engine.offset, P.pdx_build_opts.dense_rows.offset,
+            P.pdx_search_stats.dense_fallbacks.offset]
     assert got == want
 
 
@@ -67,7 +71,8 @@ def test_defaults(L):
     assert abs(o.selection_threshold - 0.20) < 1e-7 and abs(o.eps0 - 2.1) < 1e-6
     b = P.pdx_build_opts()
     L.pdx_default_build_opts(ctypes.byref(b))
-    assert b.partition_size == 10000 and b.metric == 0
+    assert b.partition_size == 10000 and b.metric == 0 and b.dense_rows == 0
+    assert o.engine == P.ENGINE["auto"]
 
 
 def test_argument_errors_without_gpu(L):
