@@ -399,6 +399,23 @@ pdx_status pdx_order_targets(const pdx_index *index, const float *q, int64_t nq,
 /* Release an index and all of its device memory. NULL-safe. */
 void pdx_free(pdx_index *index);
 
+/*
+ * pdx_merge_topk -- the exchange step of a sharded collection (not in the
+ * paper, whose search runs on one machine). Each shard answered the same
+ * queries over its own vectors with global ids, best-first as the searches
+ * return them; this keeps the k best per query over all shards.
+ *   dist, idx  [nshards][nq][k] row-major (padding: idx -1)
+ *   metric     order of the lists: L2/L1 ascending, IP descending; ties go
+ *              to the lower id and padding comes last
+ *   out_*      [nq][k], the same order and padding
+ * All four arrays are host pointers (merged on the calling thread; no GPU
+ * needed) or all device pointers (one kernel on `stream`, asynchronous).
+ * Returns PDX_ERR_ARG for nshards outside [1, 64], k outside [1, 1024], a bad
+ * metric, NULL arrays, or a mix of host and device arrays.
+ */
+pdx_status pdx_merge_topk(const float *dist, const int64_t *idx, int32_t nshards, int64_t nq, int32_t k,
+                          pdx_metric metric, float *out_dist, int64_t *out_idx, void *stream);
+
 /* Number of CUDA kernels this process has launched through the library. */
 uint64_t pdx_kernel_launches(void);
 

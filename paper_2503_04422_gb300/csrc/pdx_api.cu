@@ -580,7 +580,7 @@ pdx_status exact_plan(const pdx_index *ix, int64_t nq, int32_t k, const pdx_sear
     if (ep->dense) {
         ep->dense_cap = dense_cap(ix->n, k);
         ep->nslots = 0;
-        ep->bytes = dense_scratch_bytes(nq, ix->d, k, ep->dense_cap) + rup(C_COUNT * 8);
+        ep->bytes = dense_scratch_bytes(nq, ix->d, k, ep->dense_cap, ix->n) + rup(C_COUNT * 8);
         return PDX_OK;
     }
     ep->nslots = ix->nparts * ep->chunks;
@@ -596,7 +596,8 @@ pdx_status exact_plan(const pdx_index *ix, int64_t nq, int32_t k, const pdx_sear
                + rup((size_t)nq * ep->nslots * k * 8)           // per-item lists
                + 3 * rup((size_t)nq * k * 8)                    // merged, refined, final top-k
                + rup(C_COUNT * 8) + rup(8)                      // counters, work counter
-               + rup(ep->op.bytes);                             // visit orders
+               + rup(ep->op.bytes)                              // visit orders
+               + rup((size_t)nq * kPoolCap * 4) + rup((size_t)nq * 4);  // shared candidate pools
     if (ep->start) b += rup((size_t)nq * ep->Lstart * 8) + rup((size_t)nq * k * 8);
     ep->mlp_bytes = 0;
     if (ep->op.mode == 2) {
@@ -618,7 +619,7 @@ pdx_status exact_run(const pdx_index *ix, const float *qd, int64_t nq, int32_t k
                      unsigned long long **counters_out, int sms, cudaStream_t st) {
     const int d = ix->d;
     if (ep.dense) {
-        const size_t db = dense_scratch_bytes(nq, d, k, ep.dense_cap);
+        const size_t db = dense_scratch_bytes(nq, d, k, ep.dense_cap, ix->n);
         unsigned long long *counters = reinterpret_cast<unsigned long long *>(scratch + db);
         PDX_TRY(cudaMemsetAsync(counters, 0, C_COUNT * 8, st));
         unsigned long long *kc = o.stats_device ? reinterpret_cast<unsigned long long *>(o.stats_device) : counters;
@@ -641,6 +642,8 @@ pdx_status exact_run(const pdx_index *ix, const float *qd, int64_t nq, int32_t k
     unsigned long long *counters = reinterpret_cast<unsigned long long *>(take(C_COUNT * 8));
     int *work = reinterpret_cast<int *>(take(8));
     uint16_t *qorder = ep.op.rows ? reinterpret_cast<uint16_t *>(take(ep.op.bytes)) : nullptr;
+    float *pool = reinterpret_cast<float *>(take((size_t)nq * kPoolCap * 4));
+    int32_t *pool_cnt = reinterpret_cast<int32_t *>(take((size_t)nq * 4));
     uint64_t *skeys = ep.start ? reinterpret_cast<uint64_t *>(take((size_t)nq * ep.Lstart * 8)) : nullptr;
     uint64_t *stopk = ep.start ? reinterpret_cast<uint64_t *>(take((size_t)nq * k * 8)) : nullptr;
     unsigned char *mlp_ws = ep.mlp_bytes ? take(ep.mlp_bytes) : nullptr;
@@ -676,6 +679,11 @@ pdx_status exact_run(const pdx_index *ix, const float *qd, int64_t nq, int32_t k
     PDX_TRY(launch_fill_u32(reinterpret_cast<uint32_t *>(tau), 0xff800000u, nq, st));  // ordered +inf
     PDX_TRY(cudaMemsetAsync(counters, 0, C_COUNT * 8, st));
     PDX_TRY(cudaMemsetAsync(work, 0, 8, st));
+    const bool use_pool = pl.pruner != PDX_PRUNE_NONE;
+    if (use_pool) {
+        PDX_TRY(launch_fill_u32(reinterpret_cast<uint32_t *>(pool), 0x7f800000u, nq * kPoolCap, st));  // +inf
+        PDX_TRY(cudaMemsetAsync(pool_cnt, 0, (size_t)nq * 4, st));
+    }
     // kernels accumulate into the caller's device stats when given, else into scratch
     unsigned long long *kc = o.stats_device ? reinterpret_cast<unsigned long long *>(o.stats_device) : counters;
     if (counters_out) *counters_out = kc;
@@ -729,6 +737,8 @@ pdx_status exact_run(const pdx_index *ix, const float *qd, int64_t nq, int32_t k
     p.bsa_m = o.bsa_m;
     p.qorder = qorder;
     p.qorder_per_part = ep.op.per_part;
+    p.pool = use_pool ? pool : nullptr;
+    p.pool_cnt = pool_cnt;
     if (o.scan_event_start) PDX_TRY(cudaEventRecord(static_cast<cudaEvent_t>(o.scan_event_start), st));
     PDX_TRY(launch_scan(pl.pruner, pl.metric, p, sms, st));
     if (o.scan_event_stop) PDX_TRY(cudaEventRecord(static_cast<cudaEvent_t>(o.scan_event_stop), st));
@@ -1127,6 +1137,7 @@ extern "C" pdx_status pdx_search_ivf(const pdx_index *ix, const float *q, int64_
                   rup((size_t)nq * Lc * 8) + rup((size_t)nq * nprobe * 8) + rup((size_t)nq * nprobe * 4) +
                   rup((size_t)nq * 4) + rup((size_t)nq * nprobe * k * 8) + 3 * rup((size_t)nq * k * 8) +
                   rup(C_COUNT * 8) + rup(16) + rup((size_t)nq * (nchk + 1) * 8) +
+                  rup((size_t)nq * kPoolCap * 4) + rup((size_t)nq * 4) +
                   (o_dev ? 0 : rup((size_t)nq * k * 4) + rup((size_t)nq * k * 8));
     PDX_TRY(scr.reserve(need));
     const float *qd = q;
@@ -1155,6 +1166,8 @@ extern "C" pdx_status pdx_search_ivf(const pdx_index *ix, const float *q, int64_
     int *work = scr.take<int>(4);
     float *qaux = scr.take<float>((size_t)nq * (nchk + 1) * 2);
     uint16_t *qorder = op.rows ? scr.take<uint16_t>((size_t)op.rows * d) : nullptr;
+    float *pool = scr.take<float>((size_t)nq * kPoolCap);
+    int32_t *pool_cnt = scr.take<int32_t>((size_t)nq);
     float *od = out_dist;
     int64_t *oi = out_idx;
     if (!o_dev) {
@@ -1174,6 +1187,11 @@ extern "C" pdx_status pdx_search_ivf(const pdx_index *ix, const float *q, int64_
     PDX_TRY(launch_fill_u32(reinterpret_cast<uint32_t *>(tau), 0xff800000u, nq, st));
     PDX_TRY(cudaMemsetAsync(counters, 0, C_COUNT * 8, st));
     PDX_TRY(cudaMemsetAsync(work, 0, 16, st));
+    const bool use_pool = pl.pruner != PDX_PRUNE_NONE;
+    if (use_pool) {
+        PDX_TRY(launch_fill_u32(reinterpret_cast<uint32_t *>(pool), 0x7f800000u, nq * kPoolCap, st));  // +inf
+        PDX_TRY(cudaMemsetAsync(pool_cnt, 0, (size_t)nq * 4, st));
+    }
     unsigned long long *kc = o.stats_device ? reinterpret_cast<unsigned long long *>(o.stats_device) : counters;
     ScanParams p;
     std::memset(&p, 0, sizeof p);
@@ -1209,6 +1227,8 @@ extern "C" pdx_status pdx_search_ivf(const pdx_index *ix, const float *q, int64_
     p.qaux = qaux;
     p.resid = ix->resid;
     p.nchk = nchk;
+    p.pool = use_pool ? pool : nullptr;
+    p.pool_cnt = pool_cnt;
     p.qorder = qorder;
     p.qorder_per_part = op.per_part;
     if (o.scan_event_start) PDX_TRY(cudaEventRecord(static_cast<cudaEvent_t>(o.scan_event_start), st));

@@ -16,22 +16,25 @@
 //                with tcgen05.ld. For every (query, vector) the epilogue forms
 //                est = ||x||^2 - 2 acc (L2) or -acc (IP) and a proven error
 //                margin m (TF32 operands, FP32 accumulation; see dense_bounds),
-//                so that est - m <= exact <= est + m. Each thread keeps the KL
-//                smallest upper bounds of its query within the tile, shares the
-//                k-th through a per-query atomic minimum, and emits every
-//                vector whose lower bound does not exceed the tighter of the
-//                two thresholds.
-//   3. finish    one CTA per query: T = k-th smallest upper bound among the
-//                emitted entries; every entry with lower bound <= T is a
-//                candidate; candidates get their exact FP32 distance (same
-//                lanes and reduction as the scan path's refine), and the k best
-//                (distance, id) keys are kept.
+//                so that est - m <= exact <= est + m. The kernel runs twice:
+//                the bound pass writes the k smallest upper bounds of every
+//                (query, 128-vector half tile); the emit pass lists the vectors
+//                whose lower bound is within T*.
+//   3. select    one CTA per query: T* = k-th smallest of those upper bounds,
+//                which is the k-th smallest upper bound over all vectors.
+//   4. finish    one CTA per query: every listed vector gets its exact FP32
+//                distance (same lanes and reduction as the scan path's
+//                refine), and the k best (distance, id) keys are kept.
 //
-// Why this is exact: every threshold above is the k-th upper bound of k real
-// vectors, so it is >= T* = the k-th smallest upper bound over all vectors.
-// The true k nearest have lower <= exact <= k-th exact distance <= T*, so
-// they are emitted and survive the final filter; the FP32 rerank decides.
-// If a query emits more entries than its buffer holds, or the GEMM gave up on
+// Why this is exact: the true k nearest have lower <= exact <= k-th exact
+// distance <= T* (T* is the k-th of upper bounds, each above its own exact
+// distance), so they are listed; the FP32 rerank decides among the listed.
+// A threshold shared between tiles while the GEMM runs cannot work here: a
+// tile of random vectors rarely holds k near neighbours of a query, so its
+// local k-th stays at the far distances (clustered data), and the list would
+// hold a large part of the collection. Two passes cost a second GEMM and give
+// the smallest candidate list the margin allows.
+// If a query lists more vectors than its buffer holds, or the GEMM gave up on
 // a wait, the finish kernel computes that query's result by a plain FP32 scan
 // of all vectors instead (counted in the search statistics).
 #include <cuda.h>
@@ -167,13 +170,14 @@ struct DenseParams {
     int32_t d, k;
     int32_t nqt;                 // query tiles
     int64_t ntiles;              // query tiles x vector tiles
+    int64_t nhalf;               // half tiles (128 vectors) of the collection
     const float *qnorm;          // [nq] ||q||
     const float2 *xnorm;         // [n] (||x||^2, ||x||)
-    uint32_t *tau_up;            // [nq] ordered bits of the best shared upper bound
+    float *ubuf;                 // bound pass: [nq][nhalf][k] smallest upper bounds per half tile
+    const float *tstar;          // emit pass: [nq] k-th smallest upper bound over all vectors
     int32_t *cnt;                // [nq] entries emitted
     int32_t cap;                 // entries per query
-    float2 *ent;                 // [nq][cap] (lower, upper)
-    int32_t *ent_id;             // [nq][cap]
+    int32_t *ent_id;             // [nq][cap] emitted vector ids
     float c_qx, c_xx, c_rel;     // margin coefficients
     int32_t *err;                // set when a wait gave up
 };
@@ -199,7 +203,7 @@ __device__ __forceinline__ void dense_bounds(float acc, float2 xn, float aq, con
     up = est + m;
 }
 
-template <int KL, int MET>
+template <int KL, int MET, int MODE>
 __global__ void __launch_bounds__(THREADS, 1)
     dense_tc_kernel(const __grid_constant__ CUtensorMap tmQ, const __grid_constant__ CUtensorMap tmX, DenseParams p) {
     extern __shared__ unsigned char smem_raw[];
@@ -329,60 +333,61 @@ __global__ void __launch_bounds__(THREADS, 1)
             const int64_t r = (int64_t)qt * TM + row_in_tile;
             const bool rv = r < p.nq;
             const float aq = rv ? p.c_qx * __ldg(p.qnorm + r) : 0.f;
-            const float tau_u = rv ? o2f(*reinterpret_cast<volatile uint32_t *>(p.tau_up + r))
-                                   : __int_as_float(0xff800000);
             const int64_t col0 = nt * TN + half * (TN / 2);
             const uint32_t taddr = tbase + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(b * TN + half * (TN / 2));
-            float L[KL];
+            if (MODE == 0) {
+                // bound pass: the k smallest upper bounds of this row within the half tile
+                float L[KL];
 #pragma unroll
-            for (int i = 0; i < KL; ++i) L[i] = __int_as_float(0x7f800000);
-            // pass 1: the KL smallest upper bounds of this row below the shared bound
+                for (int i = 0; i < KL; ++i) L[i] = __int_as_float(0x7f800000);
 #pragma unroll 1
-            for (int cb = 0; cb < TN / 2; cb += 32) {
-                float v[32];
-                tmem_ld32(taddr + cb, v);
-                if (rv) {
+                for (int cb = 0; cb < TN / 2; cb += 32) {
+                    float v[32];
+                    tmem_ld32(taddr + cb, v);
+                    if (rv) {
 #pragma unroll
-                    for (int i = 0; i < 32; ++i) {
-                        const int64_t c = col0 + cb + i;
-                        if (c < p.n) {
-                            float lo, up;
-                            dense_bounds<MET>(v[i], __ldg(p.xnorm + c), aq, p, lo, up);
-                            if (up < fminf(tau_u, L[KL - 1])) {
-                                float x = up;
+                        for (int i = 0; i < 32; ++i) {
+                            const int64_t c = col0 + cb + i;
+                            if (c < p.n) {
+                                float lo, up;
+                                dense_bounds<MET>(v[i], __ldg(p.xnorm + c), aq, p, lo, up);
+                                if (up < L[KL - 1]) {
+                                    float x = up;
 #pragma unroll
-                                for (int j = 0; j < KL; ++j) {
-                                    const float a = fminf(L[j], x);
-                                    x = fmaxf(L[j], x);
-                                    L[j] = a;
+                                    for (int j = 0; j < KL; ++j) {
+                                        const float a = fminf(L[j], x);
+                                        x = fmaxf(L[j], x);
+                                        L[j] = a;
+                                    }
                                 }
                             }
                         }
                     }
                 }
-            }
-            float kth = __int_as_float(0x7f800000);
-#pragma unroll
-            for (int i = 0; i < KL; ++i)
-                if (i == p.k - 1) kth = L[i];
-            const float T = fminf(tau_u, kth);
-            // pass 2: emit every vector whose lower bound is within T
-#pragma unroll 1
-            for (int cb = 0; cb < TN / 2; cb += 32) {
-                float v[32];
-                tmem_ld32(taddr + cb, v);
                 if (rv) {
+                    float *u = p.ubuf + (r * p.nhalf + (2 * nt + half)) * p.k;
 #pragma unroll
-                    for (int i = 0; i < 32; ++i) {
-                        const int64_t c = col0 + cb + i;
-                        if (c < p.n) {
-                            float lo, up;
-                            dense_bounds<MET>(v[i], __ldg(p.xnorm + c), aq, p, lo, up);
-                            if (lo <= T) {
-                                const int pos = atomicAdd(p.cnt + r, 1);
-                                if (pos < p.cap) {
-                                    p.ent[r * p.cap + pos] = make_float2(lo, up);
-                                    p.ent_id[r * p.cap + pos] = (int32_t)c;
+                    for (int i = 0; i < KL; ++i)
+                        if (i < p.k) u[i] = L[i];
+                }
+            } else {
+                // emit pass: every vector whose lower bound is within the
+                // query's k-th smallest upper bound
+                const float T = rv ? __ldg(p.tstar + r) : __int_as_float(0xff800000);
+#pragma unroll 1
+                for (int cb = 0; cb < TN / 2; cb += 32) {
+                    float v[32];
+                    tmem_ld32(taddr + cb, v);
+                    if (rv) {
+#pragma unroll
+                        for (int i = 0; i < 32; ++i) {
+                            const int64_t c = col0 + cb + i;
+                            if (c < p.n) {
+                                float lo, up;
+                                dense_bounds<MET>(v[i], __ldg(p.xnorm + c), aq, p, lo, up);
+                                if (lo <= T) {
+                                    const int pos = atomicAdd(p.cnt + r, 1);
+                                    if (pos < p.cap) p.ent_id[r * p.cap + pos] = (int32_t)c;
                                 }
                             }
                         }
@@ -392,7 +397,6 @@ __global__ void __launch_bounds__(THREADS, 1)
             tc_fence_before();
             __syncwarp();
             if (lane == 0) mbar_arrive(tempty(b));
-            if (rv && kth < __int_as_float(0x7f800000)) atomicMin(p.tau_up + r, f2o(kth));
         }
     }
     // ---- teardown ----
@@ -408,8 +412,8 @@ __global__ void __launch_bounds__(THREADS, 1)
 
 // ---------------------------------------------------------------------------
 __global__ void dense_prep_kernel(const float *__restrict__ q, int64_t nq, int32_t d, float *__restrict__ qs,
-                                  float *__restrict__ qnorm, uint32_t *__restrict__ tau_up, int32_t *__restrict__ cnt,
-                                  int32_t *__restrict__ err, unsigned long long *counters, int64_t n) {
+                                  float *__restrict__ qnorm, int32_t *__restrict__ cnt, int32_t *__restrict__ err,
+                                  unsigned long long *counters, int64_t n) {
     const int64_t row = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     if (blockIdx.x == 0 && threadIdx.x == 0) {
@@ -427,7 +431,6 @@ __global__ void dense_prep_kernel(const float *__restrict__ q, int64_t nq, int32
     s = warp_sum(s);
     if (lane == 0) {
         qnorm[row] = sqrtf(s);
-        tau_up[row] = f2o(__int_as_float(0x7f800000));
         cnt[row] = 0;
     }
 }
@@ -443,6 +446,51 @@ __global__ void row_norms_kernel(const float *__restrict__ x, int64_t n, int32_t
     }
     s = warp_sum(s);
     if (lane == 0) out[row] = make_float2(s, sqrtf(s));
+}
+
+// T*[q] = k-th smallest value of ubuf[q][0..L): a radix select over the
+// order-preserving uint32 keys, 11 + 11 + 10 bits, one CTA per query. Every
+// vector among the k smallest upper bounds of the whole collection is among
+// the k smallest of its own half tile, so this is the k-th smallest upper
+// bound over all vectors (+inf when fewer than k are finite).
+__global__ void __launch_bounds__(256) dense_select_kernel(const float *__restrict__ ubuf, int64_t L, int32_t k,
+                                                           float *__restrict__ tstar) {
+    __shared__ int hist[2048];
+    __shared__ uint32_t s_prefix, s_want;
+    const int64_t row = blockIdx.x;
+    const float *u = ubuf + row * L;
+    uint32_t prefix = 0, mask = 0;
+    if (threadIdx.x == 0) s_want = (uint32_t)k;
+    const int shifts[3] = {21, 10, 0};
+    const int widths[3] = {11, 11, 10};
+    for (int pass = 0; pass < 3; ++pass) {
+        const int sh = shifts[pass], nb = 1 << widths[pass];
+        for (int i = threadIdx.x; i < nb; i += blockDim.x) hist[i] = 0;
+        __syncthreads();
+        for (int64_t i = threadIdx.x; i < L; i += blockDim.x) {
+            const uint32_t key = f2o(u[i]);
+            if ((key & mask) == prefix) atomicAdd(&hist[(key >> sh) & (nb - 1)], 1);
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            uint32_t want = s_want, cum = 0;
+            int bsel = nb - 1;
+            for (int bi = 0; bi < nb; ++bi) {
+                if (cum + (uint32_t)hist[bi] >= want) {
+                    bsel = bi;
+                    break;
+                }
+                cum += (uint32_t)hist[bi];
+            }
+            s_want = want - cum;
+            s_prefix = prefix | ((uint32_t)bsel << sh);
+        }
+        __syncthreads();
+        prefix = s_prefix;
+        mask |= (uint32_t)(nb - 1) << sh;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) tstar[row] = o2f(prefix);
 }
 
 // Block-wide ascending bitonic sort of buf[0..len), len a power of two.
@@ -485,18 +533,18 @@ struct FinishParams {
     const float *q;               // [nq][d]
     const float *x;               // [n][d]
     const int32_t *cnt;
-    const float2 *ent;
     const int32_t *ent_id;
     const int32_t *err;
     uint64_t *out;                // [nq][k] keys
     unsigned long long *counters;
 };
 
+// One CTA per query: every emitted vector is a candidate (its lower bound is
+// within T*); each gets its exact FP32 distance and the k best (distance, id)
+// keys are kept.
 template <int MET>
-__global__ void __launch_bounds__(512) dense_finish_kernel(FinishParams f) {
-    extern __shared__ __align__(16) uint64_t fbuf[];  // cap keys, then cap int32 candidate slots
-    int32_t *cidx = reinterpret_cast<int32_t *>(fbuf + f.cap);
-    __shared__ int ncand;
+__global__ void __launch_bounds__(256) dense_finish_kernel(FinishParams f) {
+    extern __shared__ __align__(16) uint64_t fbuf[];  // cap keys
     const int64_t row = blockIdx.x;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
     const float *qr = f.q + row * f.d;
@@ -520,31 +568,18 @@ __global__ void __launch_bounds__(512) dense_finish_kernel(FinishParams f) {
         if (tid == 0) atomicAdd(f.counters + C_DENSE_FALLBACK, 1ull);
         return;
     }
-    const float2 *ent = f.ent + row * f.cap;
     const int32_t *eid = f.ent_id + row * f.cap;
-    // T = k-th smallest upper bound among the emitted entries
-    const int len = pow2_at_least(total > 1 ? total : 1);
-    for (int i = tid; i < len; i += blockDim.x) fbuf[i] = i < total ? make_key(ent[i].y, i) : kEmptyKey;
-    if (tid == 0) ncand = 0;
-    __syncthreads();
-    cta_bitonic(fbuf, len);
-    const float T = total >= f.k ? key_dist(fbuf[f.k - 1]) : __int_as_float(0x7f800000);
-    __syncthreads();
-    for (int i = tid; i < total; i += blockDim.x)
-        if (ent[i].x <= T) cidx[atomicAdd(&ncand, 1)] = i;
-    __syncthreads();
-    const int nc = ncand;
-    for (int c = warp; c < nc; c += nw) {
-        const int32_t id = eid[cidx[c]];
+    for (int c = warp; c < total; c += nw) {
+        const int32_t id = eid[c];
         const float dist = exact_dist<MET>(qr, f.x + (int64_t)id * f.d, f.d, lane);
         if (lane == 0) fbuf[c] = make_key(dist, id);
     }
-    const int len2 = pow2_at_least(nc > f.k ? nc : f.k);
-    for (int i = nc + tid; i < len2; i += blockDim.x) fbuf[i] = kEmptyKey;
+    const int len = pow2_at_least(total > f.k ? total : f.k);
+    for (int i = total + tid; i < len; i += blockDim.x) fbuf[i] = kEmptyKey;
     __syncthreads();
-    cta_bitonic(fbuf, len2);
+    cta_bitonic(fbuf, len);
     for (int i = tid; i < f.k; i += blockDim.x) f.out[row * f.k + i] = fbuf[i];
-    if (tid == 0) atomicAdd(f.counters + C_CANDIDATES, (unsigned long long)nc);
+    if (tid == 0) atomicAdd(f.counters + C_CANDIDATES, (unsigned long long)total);
 }
 
 PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
@@ -575,18 +610,26 @@ bool encode_rows(CUtensorMap *m, const float *base, int64_t rows, int32_t d, int
               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-template <int KL, int MET>
+template <int KL, int MET, int MODE>
 cudaError_t launch_tc(const CUtensorMap &mq, const CUtensorMap &mx, const DenseParams &p, int grid, cudaStream_t st) {
-    cudaError_t e = cudaFuncSetAttribute(dense_tc_kernel<KL, MET>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaError_t e = cudaFuncSetAttribute(dense_tc_kernel<KL, MET, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          SMEM_BYTES);
     if (e != cudaSuccess) return e;
-    dense_tc_kernel<KL, MET><<<grid, THREADS, SMEM_BYTES, st>>>(mq, mx, p);
+    dense_tc_kernel<KL, MET, MODE><<<grid, THREADS, SMEM_BYTES, st>>>(mq, mx, p);
     return counted(cudaGetLastError());
+}
+
+template <int MODE>
+cudaError_t launch_tc_any(const CUtensorMap &mq, const CUtensorMap &mx, const DenseParams &p, int grid, int metric,
+                          cudaStream_t st) {
+    if (metric == MT_IP)
+        return p.k <= 16 ? launch_tc<16, MT_IP, MODE>(mq, mx, p, grid, st) : launch_tc<64, MT_IP, MODE>(mq, mx, p, grid, st);
+    return p.k <= 16 ? launch_tc<16, MT_L2, MODE>(mq, mx, p, grid, st) : launch_tc<64, MT_L2, MODE>(mq, mx, p, grid, st);
 }
 
 template <int MET>
 cudaError_t launch_finish(const FinishParams &f, cudaStream_t st) {
-    const size_t smem = (size_t)f.cap * 12;
+    const size_t smem = (size_t)f.cap * 8;
     cudaError_t e =
         cudaFuncSetAttribute(dense_finish_kernel<MET>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
@@ -594,24 +637,9 @@ cudaError_t launch_finish(const FinishParams &f, cudaStream_t st) {
     return counted(cudaGetLastError());
 }
 
+int64_t half_tiles(int64_t n) { return 2 * ((n + TN - 1) / TN); }
+
 }  // namespace
-
-int dense_cap(int64_t n, int32_t k) {
-    // entries per query: the k best of the first tiles plus the margin band;
-    // never more than the collection itself
-    int64_t c = 4096;
-    if (n < c) c = n;
-    int p = 64;
-    while (p < c) p <<= 1;
-    while (p < 4 * k) p <<= 1;
-    return p;
-}
-
-size_t dense_scratch_bytes(int64_t nq, int32_t d, int32_t k, int32_t cap) {
-    auto rup = [](size_t b) { return (b + 255) & ~size_t(255); };
-    return rup((size_t)nq * d * 4) + 3 * rup((size_t)nq * 4) + rup((size_t)nq * cap * 8) + rup((size_t)nq * cap * 4) +
-           rup((size_t)nq * k * 8) + rup(8);
-}
 
 bool dense_supported(const pdx_index *ix, int32_t k, const char **why) {
     const char *w = nullptr;
@@ -624,10 +652,28 @@ bool dense_supported(const pdx_index *ix, int32_t k, const char **why) {
     return w == nullptr;
 }
 
+int dense_cap(int64_t n, int32_t k) {
+    // candidates per query: the vectors whose lower bound is within the k-th
+    // smallest upper bound; never more than the collection itself
+    int64_t c = 4096;
+    if (n < c) c = n;
+    int p = 64;
+    while (p < c) p <<= 1;
+    while (p < 4 * k) p <<= 1;
+    return p;
+}
+
+size_t dense_scratch_bytes(int64_t nq, int32_t d, int32_t k, int32_t cap, int64_t n) {
+    auto rup = [](size_t b) { return (b + 255) & ~size_t(255); };
+    return rup((size_t)nq * d * 4) + 3 * rup((size_t)nq * 4) + rup((size_t)nq * half_tiles(n) * k * 4) +
+           rup((size_t)nq * cap * 4) + rup((size_t)nq * k * 8) + rup(8);
+}
+
 pdx_status dense_run(const pdx_index *ix, const float *qd, int64_t nq, int32_t k, int metric, int out_mode,
                      unsigned char *scratch, size_t bytes, int cap, float *od, int64_t *oi, unsigned long long *counters,
                      int sms, void *ev_start, void *ev_stop, cudaStream_t st) {
     const int d = ix->d;
+    const int64_t nhalf = half_tiles(ix->n);
     auto rup = [](size_t b) { return (b + 255) & ~size_t(255); };
     size_t off = 0;
     auto take = [&](size_t b) {
@@ -637,9 +683,9 @@ pdx_status dense_run(const pdx_index *ix, const float *qd, int64_t nq, int32_t k
     };
     float *qs = reinterpret_cast<float *>(take((size_t)nq * d * 4));
     float *qnorm = reinterpret_cast<float *>(take((size_t)nq * 4));
-    uint32_t *tau_up = reinterpret_cast<uint32_t *>(take((size_t)nq * 4));
+    float *tstar = reinterpret_cast<float *>(take((size_t)nq * 4));
     int32_t *cnt = reinterpret_cast<int32_t *>(take((size_t)nq * 4));
-    float2 *ent = reinterpret_cast<float2 *>(take((size_t)nq * cap * 8));
+    float *ubuf = reinterpret_cast<float *>(take((size_t)nq * nhalf * k * 4));
     int32_t *ent_id = reinterpret_cast<int32_t *>(take((size_t)nq * cap * 4));
     uint64_t *keys = reinterpret_cast<uint64_t *>(take((size_t)nq * k * 8));
     int32_t *err = reinterpret_cast<int32_t *>(take(8));
@@ -650,7 +696,7 @@ pdx_status dense_run(const pdx_index *ix, const float *qd, int64_t nq, int32_t k
     if (nq == 0) return PDX_OK;
     {
         const unsigned grid = (unsigned)((nq * 32 + 255) / 256);
-        dense_prep_kernel<<<grid, 256, 0, st>>>(qd, nq, d, qs, qnorm, tau_up, cnt, err, counters, ix->n);
+        dense_prep_kernel<<<grid, 256, 0, st>>>(qd, nq, d, qs, qnorm, cnt, err, counters, ix->n);
         cudaError_t e = counted(cudaGetLastError());
         if (e != cudaSuccess) return cuda_status_ext(e, "dense_prep_kernel");
     }
@@ -666,12 +712,13 @@ pdx_status dense_run(const pdx_index *ix, const float *qd, int64_t nq, int32_t k
     p.k = k;
     p.nqt = (int32_t)((nq + TM - 1) / TM);
     p.ntiles = (int64_t)p.nqt * ((ix->n + TN - 1) / TN);
+    p.nhalf = nhalf;
     p.qnorm = qnorm;
     p.xnorm = reinterpret_cast<const float2 *>(ix->xnorm);
-    p.tau_up = tau_up;
+    p.ubuf = ubuf;
+    p.tstar = tstar;
     p.cnt = cnt;
     p.cap = cap;
-    p.ent = ent;
     p.ent_id = ent_id;
     // margin coefficients (see dense_bounds), each with a 2^-10 relative cushion
     const double u = std::ldexp(1.0, -22);
@@ -685,11 +732,14 @@ pdx_status dense_run(const pdx_index *ix, const float *qd, int64_t nq, int32_t k
     cudaError_t e;
     if (ev_start && (e = cudaEventRecord(static_cast<cudaEvent_t>(ev_start), st)) != cudaSuccess)
         return cuda_status_ext(e, "cudaEventRecord");
-    if (metric == MT_IP)
-        e = k <= 16 ? launch_tc<16, MT_IP>(mq, mx, p, grid, st) : launch_tc<64, MT_IP>(mq, mx, p, grid, st);
-    else
-        e = k <= 16 ? launch_tc<16, MT_L2>(mq, mx, p, grid, st) : launch_tc<64, MT_L2>(mq, mx, p, grid, st);
-    if (e != cudaSuccess) return cuda_status_ext(e, "dense_tc_kernel");
+    // pass 1: per half tile, the k smallest upper bounds; then T* per query
+    if ((e = launch_tc_any<0>(mq, mx, p, grid, metric, st)) != cudaSuccess)
+        return cuda_status_ext(e, "dense_tc_kernel (bound pass)");
+    dense_select_kernel<<<(unsigned)nq, 256, 0, st>>>(ubuf, nhalf * k, k, tstar);
+    if ((e = counted(cudaGetLastError())) != cudaSuccess) return cuda_status_ext(e, "dense_select_kernel");
+    // pass 2: emit the vectors whose lower bound is within T*
+    if ((e = launch_tc_any<1>(mq, mx, p, grid, metric, st)) != cudaSuccess)
+        return cuda_status_ext(e, "dense_tc_kernel (emit pass)");
     if (ev_stop && (e = cudaEventRecord(static_cast<cudaEvent_t>(ev_stop), st)) != cudaSuccess)
         return cuda_status_ext(e, "cudaEventRecord");
     FinishParams f;
@@ -701,7 +751,6 @@ pdx_status dense_run(const pdx_index *ix, const float *qd, int64_t nq, int32_t k
     f.q = qs;
     f.x = ix->xnary;
     f.cnt = cnt;
-    f.ent = ent;
     f.ent_id = ent_id;
     f.err = err;
     f.out = keys;

@@ -17,6 +17,7 @@ constexpr int kMaxSurv = 16;   // PRUNE-phase survivors held in registers (selec
 constexpr int kMaxK = 1024;
 constexpr int kMaxD = 4096;
 constexpr int kMaxSortUnits = 256;  // zone keys a scan warp sorts in-kernel (8 per lane)
+constexpr int kPoolCap = 256;       // shared candidate distances per query (8 per lane)
 
 // Device counters, in the order of the first fields of pdx_search_stats
 // (slot 7 is bytes_logical, which the host derives and no kernel writes).
@@ -207,6 +208,11 @@ struct ScanParams {
     const float *qaux;         // BSA: [nq][nchk][2] (||q_r||^2, s_d(q)^2) per check point
     const float *resid;        // BSA: [nblocks][nchk][64]
     int32_t nchk;
+    // Per-query pool of full distances found by any warp (kPoolCap slots,
+    // +inf until written): its k-th smallest is the query's running k-th
+    // best over everything scanned so far, as one heap per query would give.
+    float *pool;               // [nq][kPoolCap] or null
+    int32_t *pool_cnt;         // [nq]
 };
 cudaError_t launch_scan(int pruner, int metric, const ScanParams &p, int num_sms, cudaStream_t st);
 // Visit orders for PDX-BOND (mode 0 distance to means with zones of Z, mode 1
@@ -256,7 +262,7 @@ void fill_stats(pdx_search_stats *so, const unsigned long long *c, const pdx_ind
 // Tensor-core dense engine (pdx_dense.cu).
 bool dense_supported(const pdx_index *ix, int32_t k, const char **why);
 int dense_cap(int64_t n, int32_t k);
-size_t dense_scratch_bytes(int64_t nq, int32_t d, int32_t k, int32_t cap);
+size_t dense_scratch_bytes(int64_t nq, int32_t d, int32_t k, int32_t cap, int64_t n);
 pdx_status dense_run(const pdx_index *ix, const float *qd, int64_t nq, int32_t k, int metric, int out_mode,
                      unsigned char *scratch, size_t bytes, int cap, float *od, int64_t *oi, unsigned long long *counters,
                      int sms, void *ev_start, void *ev_stop, cudaStream_t st);

@@ -346,6 +346,45 @@ __device__ __forceinline__ float rerank_l2(const float *__restrict__ xrow, const
     return warp_sum(acc);
 }
 
+// Offer a full distance to the query's shared pool (lane 0 writes). The pool
+// is a ring: once full, new distances (only those below the current
+// threshold are offered) replace the oldest. Each (query, vector) pair is
+// scanned once, so the pool never holds a vector twice, and the k-th smallest
+// of any set of distinct scanned vectors bounds the final k-th from above.
+__device__ __forceinline__ void pool_push(const ScanParams &a, int64_t qi, float dist, int lane) {
+    if (lane == 0) {
+        const unsigned pos = (unsigned)atomicAdd(a.pool_cnt + qi, 1);
+        a.pool[qi * kPoolCap + (pos % kPoolCap)] = dist;
+    }
+}
+
+// k-th smallest distance in the query's pool as an ordered uint32 (+inf when
+// fewer than k slots are filled): a bitwise search for the largest key v with
+// fewer than k pool keys below it. Slots claimed but not yet written still
+// read +inf, which can only raise the result.
+__device__ __forceinline__ uint32_t pool_kth(const ScanParams &a, int64_t qi, int k, int lane) {
+    const unsigned pushed = (unsigned)*reinterpret_cast<volatile int32_t *>(a.pool_cnt + qi);
+    const int n = (int)min(pushed, (unsigned)kPoolCap);
+    if (n < k) return 0xff800000u;  // f2o(+inf)
+    const volatile float *pl = a.pool + qi * kPoolCap;
+    uint32_t v[kPoolCap / 32];
+#pragma unroll
+    for (int i = 0; i < kPoolCap / 32; ++i) {
+        const int idx = lane + 32 * i;
+        v[i] = idx < n ? f2o(pl[idx]) : 0xffffffffu;
+    }
+    uint32_t prefix = 0;
+#pragma unroll 1
+    for (int bit = 31; bit >= 0; --bit) {
+        const uint32_t trial = prefix | (1u << bit);
+        int c = 0;
+#pragma unroll
+        for (int i = 0; i < kPoolCap / 32; ++i) c += v[i] < trial;
+        if (__reduce_add_sync(kFull, c) < k) prefix = trial;
+    }
+    return prefix;
+}
+
 template <int PR, int MET, int ST>
 __global__ void __launch_bounds__(256, PDX_SCAN_MIN_CTAS) pdxsearch_kernel(ScanParams a) {
     using ET = typename Elem<ST>::T;
@@ -579,6 +618,7 @@ __global__ void __launch_bounds__(256, PDX_SCAN_MIN_CTAS) pdxsearch_kernel(ScanP
             }
             // ---------------- merge ----------------
             int nfinal = 0;
+            bool pushed = false;
             if (nsurv < 0) {
                 // finished in WARMUP: every alive vector has its full distance
                 const float4 fm = make_float4(acc.x + __shfl_xor_sync(kFull, acc.x, 16),
@@ -599,6 +639,11 @@ __global__ void __launch_bounds__(256, PDX_SCAN_MIN_CTAS) pdxsearch_kernel(ScanP
                         uint64_t key = make_key(dd, id);
                         topk_insert(w.topk, cnt, k, key, lane);
                         ++c_cand;
+                        // lane 0 reads the shared threshold and the warp follows it
+                        if (a.pool && __shfl_sync(kFull, (int)(f2o(dd) < *tau_g_ptr), 0)) {
+                            pool_push(a, qi, dd, lane);
+                            pushed = true;
+                        }
                     }
                 }
                 unsigned m0 = __ballot_sync(kFull, alive & 1u) & 0xffffu;
@@ -620,6 +665,10 @@ __global__ void __launch_bounds__(256, PDX_SCAN_MIN_CTAS) pdxsearch_kernel(ScanP
                     uint64_t key = make_key(dd, id);
                     topk_insert(w.topk, cnt, k, key, lane);
                     ++c_cand;
+                    if (a.pool && __shfl_sync(kFull, (int)(f2o(dd) < *tau_g_ptr), 0)) {
+                        pool_push(a, qi, dd, lane);
+                        pushed = true;
+                    }
                 }
                 nfinal = nsurv;
             }
@@ -630,6 +679,11 @@ __global__ void __launch_bounds__(256, PDX_SCAN_MIN_CTAS) pdxsearch_kernel(ScanP
                     tau_loc = t;
                     if (lane == 0 && f2o(t) < *tau_g_ptr) atomicMin(reinterpret_cast<unsigned *>(a.tau) + qi, f2o(t));
                 }
+            }
+            if (pushed) {
+                // the k-th best over all warps' finds so far
+                const uint32_t kt = pool_kth(a, qi, k, lane);
+                if (lane == 0 && kt < *tau_g_ptr) atomicMin(reinterpret_cast<unsigned *>(a.tau) + qi, kt);
             }
         }
         for (int i = lane; i < k; i += 32) out[i] = (i < cnt) ? w.topk[i] : kEmptyKey;

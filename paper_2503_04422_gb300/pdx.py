@@ -330,6 +330,32 @@ def pdx_search_ivf(index: Index, q, k: int, nprobe: int, opts: pdx_search_opts |
     return (od, oi, st.as_dict()) if stats else (od, oi)
 
 
+def pdx_merge_topk(dist, idx, metric="l2", out=None, stream=None):
+    """Merge per-shard top-k lists dist/idx [nshards][nq][k] (global ids) into
+    [nq][k] (pdx_merge_topk). Host arrays merge on the CPU, CUDA tensors on
+    the GPU."""
+    L = lib()
+    f = L.pdx_merge_topk
+    f.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_int32, ctypes.c_int,
+                  ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
+    f.restype = ctypes.c_int
+    p, keep, cuda, shape = _ptr_f32(dist, "dist")
+    if len(shape) != 3:
+        raise ValueError("dist must be [nshards][nq][k]")
+    ns, nq, k = shape
+    if _is_torch(idx):
+        import torch
+        idx = idx.to(torch.int64).contiguous()
+        pi = idx.data_ptr()
+    else:
+        idx = np.ascontiguousarray(idx, dtype=np.int64)
+        pi = idx.ctypes.data
+    od, oi = _outputs(nq, k, cuda, out)
+    _check(f(p, pi, ns, nq, k, METRIC[metric], _out_ptr(od), _out_ptr(oi), _stream(cuda, stream)), "pdx_merge_topk")
+    del keep
+    return od, oi
+
+
 def pdx_free(index: Index):
     index.free()
 

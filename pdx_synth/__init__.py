@@ -25,7 +25,8 @@ of the collection it replaces. Recipes:
                            anisotropic term of norm ~0.3 plus isotropic noise of norm
                            0.05 (stand-in for OpenAI/1536 text embeddings).
 * ``serving_collections``  64 collections with log-uniform sizes and D drawn from
-                           {96, 384, 1024}, each a Gaussian mixture.
+                           {96, 384, 1024}, each a Gaussian mixture (drawn on the
+                           device by ``mixture_device`` at full size).
 
 Seeds: base seed 2503 plus the workload index, PCG64 streams keyed by
 ``[seed, stream, chunk]`` so that any chunk can be regenerated on its own.
@@ -173,6 +174,26 @@ def serving_collections(n_coll: int = 64, n_min: int = 10_000, n_max: int = 2_00
 
 def collection_data(c: Collection, nq: int = 0):
     return gaussian_mixture(MixtureSpec(n=c.n, d=c.d, nq=nq, seed=c.seed))
+
+
+def mixture_device(n: int, d: int, nq: int, seed: int, n_centres: int = 256, device="cuda"):
+    """The ``gaussian_mixture`` recipe (centres ~ N(0, I), spread
+    sigma_j = pi(j)^-1/2 under a seeded permutation) drawn with torch's
+    generator on ``device``, for collections too large to draw on the host.
+    Deterministic for a given seed and device type; returns (x, q) tensors."""
+    import torch
+    g = torch.Generator(device=device).manual_seed(int(seed))
+    centres = torch.randn(n_centres, d, generator=g, device=device)
+    perm = torch.randperm(d, generator=g, device=device)
+    sigma = (torch.arange(1, d + 1, device=device, dtype=torch.float64) ** -0.5)[perm].float()
+
+    def rows(count):
+        lab = torch.randint(0, n_centres, (count,), generator=g, device=device)
+        out = torch.randn(count, d, generator=g, device=device)
+        out.mul_(sigma).add_(centres[lab])
+        return out
+
+    return rows(n), rows(nq)
 
 
 def serving_stream(n_batches: int, n_coll: int, max_batch: int = 4096, seed: int = BASE_SEED + 5):

@@ -171,6 +171,21 @@ def test_bond_prunes_and_counts(P, torch):
     assert 0 < sb["vectors_pruned"] < 20000 * 16
 
 
+def test_bond_threshold_shared_across_partitions(P, torch):
+    # 2048 small clusters over 100k vectors: a 10k-vector partition holds only
+    # ~5 of a query's ~49 cluster-mates, so no single work item ever sees k
+    # near neighbours. The query's threshold must come from everything scanned
+    # so far (the paper's one heap per query), or almost nothing gets pruned.
+    # The sequential oracle visits 17% of the values with one heap per query
+    # and 97.6% with one heap per partition.
+    x, q = pdx_synth.embedding_like(100_000, 256, 64, n_clusters=2048, rank=16, seed=91)
+    ix = P.pdx_build_layout(_dev(torch, x), metric="ip")
+    d, i, sb = P.pdx_search_exact(ix, _dev(torch, q), 10, pruner="bond", stats=True)
+    torch.cuda.synchronize()
+    check_topk(x, q, 10, d, i, metric="ip")
+    assert sb["values_visited"] < 0.4 * 100_000 * 256 * 64, sb
+
+
 def test_mixture_768_medium(P, torch):
     # the 768-d Gaussian-mixture workload at 100k vectors (oracle on all queries)
     x, q = pdx_synth.make("bond_exact_1m_d768", n=100_000, nq=48)
@@ -202,3 +217,24 @@ def test_bond_precomputed_orders(P, torch, scope, zone, d):
         dist, idx = P.pdx_search_exact(ix, _dev(torch, q), 10, order=order, zone_dims=zone, means_scope=scope)
         torch.cuda.synchronize()
         check_topk(x, q, 10, dist, idx)
+
+
+def test_sharded_search_merged_on_device(P, torch):
+    # two shards of one collection searched separately, ids made global, lists
+    # merged by pdx_merge_topk on the device: the same answer as one index
+    x, q = pdx_synth.gaussian_mixture(pdx_synth.MixtureSpec(n=30000, d=96, nq=40, n_centres=16, seed=21))
+    half = 13001
+    full = P.pdx_build_layout(_dev(torch, x))
+    d_full, i_full = P.pdx_search_exact(full, _dev(torch, q), 10)
+    parts = []
+    for lo, hi in ((0, half), (half, x.shape[0])):
+        ix = P.pdx_build_layout(_dev(torch, x[lo:hi]))
+        d, i = P.pdx_search_exact(ix, _dev(torch, q), 10)
+        parts.append((d, torch.where(i >= 0, i + lo, i)))
+    md, mi = P.pdx_merge_topk(torch.stack([p[0] for p in parts]), torch.stack([p[1] for p in parts]))
+    torch.cuda.synchronize()
+    assert torch.equal(mi, i_full) and torch.equal(md, d_full)
+    hd, hi_ = P.pdx_merge_topk(torch.stack([p[0] for p in parts]).cpu().numpy(),
+                               torch.stack([p[1] for p in parts]).cpu().numpy())
+    assert np.array_equal(hi_, mi.cpu().numpy()) and np.array_equal(hd, md.cpu().numpy())
+    check_topk(x, q, 10, md, mi)
