@@ -251,7 +251,8 @@ def run_ours(args, rank, world, local_rank):
     oi = torch.empty((nq, k), dtype=torch.int64, device="cuda")
     stats_dev = torch.zeros(16, dtype=torch.int64, device="cuda")
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")   # > 129 MB L2
-    opts = pdx.search_opts(pruner=pruner, engine=engine if pruner == "none" else "auto")
+    opts = pdx.search_opts(pruner=pruner, engine=engine if pruner == "none" else "auto",
+                           first_step=args.first_step, ctas_per_sm=args.ctas_per_sm)
     stream = torch.cuda.current_stream()
 
     def step(ev_scan=None):
@@ -355,7 +356,7 @@ def run_ours(args, rank, world, local_rank):
                        "order": "dist_to_means",
                        "means": "collection (automatic for exact search)", "zone_dims": "1 (automatic)",
                        "first_step": int(opts.first_step), "selection_threshold": round(float(opts.selection_threshold), 3),
-                       "start_vectors": int(opts.start_vectors), "ctas_per_sm": "3 (automatic)",
+                       "start_vectors": int(opts.start_vectors), "ctas_per_sm": int(opts.ctas_per_sm) or "3 (automatic)",
                        "l2": (f"collection {n * d * 4 / 1e9:.3g} GB; 256 MB L2 flush between timed steps "
                               "(untimed)")},
             "roofline": roofline,
@@ -743,6 +744,8 @@ def main():
     ap.add_argument("--traces", type=int, default=None, help="learned-order workload: training queries")
     ap.add_argument("--epochs", type=int, default=30, help="learned-order workload: training epochs")
     ap.add_argument("--no-f32-compare", action="store_true", help="serving workload: skip the FP32-storage stream")
+    ap.add_argument("--first-step", type=int, default=None, help="exact workloads: first fetch step (default 4)")
+    ap.add_argument("--ctas-per-sm", type=int, default=None, help="exact workloads: resident scan CTAs per SM")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3

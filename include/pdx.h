@@ -99,9 +99,10 @@ typedef enum pdx_means_scope {
  *           proven error bound; vectors whose lower bound is within the k-th
  *           smallest upper bound are reranked in FP32 from the row-major
  *           copy, so results equal the SCAN engine's (up to ties within
- *           FP32 rounding). Needs an exact index built with dense_rows (or
- *           low-precision storage), L2 or IP, d a multiple of 4, k <= 64.
- * AUTO   -- TENSOR when those conditions hold, else SCAN.
+ *           FP32 rounding). Needs an exact index built with dense_rows, L2
+ *           or IP, d a multiple of 4, k <= 64.
+ * AUTO   -- TENSOR when those conditions hold and the product is large
+ *           enough to pay for its fixed cost (nq * n * d >= 2^32), else SCAN.
  */
 typedef enum pdx_engine {
     PDX_ENGINE_AUTO = 0,
@@ -119,10 +120,11 @@ typedef struct pdx_build_opts {
     uint32_t partition_size;   /* exact search: at most this many vectors per PDXearch
                                   block, equal horizontal partitions (Sec. 6.6; 10000)    */
     int32_t keep_fp32_rerank;  /* low-precision storage: keep an FP32 copy (default 1)     */
-    int32_t dense_rows;        /* keep the vectors row-major in FP32 with their norms
-                                  (n*(d+2)*4 bytes) for the tensor-core dense engine;
-                                  low-precision storage keeps the FP32 rows anyway and then
-                                  only adds the norms (default 0)                           */
+    int32_t dense_rows;        /* keep, for the tensor-core dense engine, the vectors
+                                  row-major in FP32 (the rerank source), a copy rounded to
+                                  TF32 (the GEMM operand) and per-row norms: n*(2d+4)*4
+                                  bytes. Low-precision storage keeps the FP32 rows anyway
+                                  and adds n*(d+4)*4 bytes (default 0)                     */
 } pdx_build_opts;
 
 typedef struct pdx_ivf_opts {

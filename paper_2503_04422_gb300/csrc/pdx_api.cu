@@ -107,7 +107,7 @@ static size_t rup(size_t b) { return (b + 255) & ~size_t(255); }
 
 static void free_index(pdx_index *ix) {
     if (!ix) return;
-    void *ptrs[] = {ix->data, ix->data_lp, ix->scale, ix->xnary, ix->xnorm, ix->ids, ix->slot_of, ix->blk_cnt, ix->part_blk, ix->means, ix->cmean, ix->centroids, ix->centroid_norms,
+    void *ptrs[] = {ix->data, ix->data_lp, ix->scale, ix->xnary, ix->xtc, ix->xnorm, ix->ids, ix->slot_of, ix->blk_cnt, ix->part_blk, ix->means, ix->cmean, ix->centroids, ix->centroid_norms,
                     ix->assign, ix->rot, ix->shift, ix->pca_var, ix->resid, ix->chk, ix->cdata, ix->cids};
     for (void *p : ptrs)
         if (p) cudaFree(p);
@@ -224,16 +224,18 @@ static pdx_status finish_low_precision(pdx_index *ix, const float *xrows, cudaSt
     return PDX_OK;
 }
 
-// Row-major FP32 vectors and their (||x||^2, ||x||) for the tensor-core
-// dense engine (the rows are already there for low-precision storage).
+// Tensor-core dense engine: the exact row-major FP32 vectors (rerank; already
+// there for low-precision storage), their TF32-rounded copy (the GEMM
+// operand) and per-row norms.
 static pdx_status keep_dense_rows(pdx_index *ix, const float *xrows, cudaStream_t st) {
     const int d = ix->d;
     if (!ix->xnary) {
         PDX_TRY(dalloc(ix, &ix->xnary, (size_t)ix->n * d));
         PDX_TRY(cudaMemcpyAsync(ix->xnary, xrows, (size_t)ix->n * d * 4, cudaMemcpyDeviceToDevice, st));
     }
-    PDX_TRY(dalloc(ix, &ix->xnorm, (size_t)ix->n * 2));
-    PDX_TRY(launch_row_norms(ix->xnary, ix->n, d, ix->xnorm, st));
+    PDX_TRY(dalloc(ix, &ix->xtc, (size_t)ix->n * d));
+    PDX_TRY(dalloc(ix, &ix->xnorm, (size_t)ix->n * 4));
+    PDX_TRY(launch_dense_operand(ix->xnary, ix->n, d, ix->xtc, ix->xnorm, st));
     PDX_TRY(cudaStreamSynchronize(st));
     return PDX_OK;
 }
@@ -576,7 +578,11 @@ pdx_status exact_plan(const pdx_index *ix, int64_t nq, int32_t k, const pdx_sear
                   pl.pruner != PDX_PRUNE_NONE ? "it runs unpruned searches only (pruner PDX_PRUNE_NONE)" : why);
         return PDX_ERR_UNSUPPORTED;
     }
-    ep->dense = can_dense && o.engine != PDX_ENGINE_SCAN;
+    // AUTO: the GEMM's fixed cost (two passes, select, finish) pays off once
+    // the product is large; small searches (e.g. 100 x 10k x 128) run faster
+    // on the scan
+    const bool big = (double)nq * (double)ix->n * (double)ix->d >= 4294967296.0;
+    ep->dense = can_dense && (o.engine == PDX_ENGINE_TENSOR || (o.engine == PDX_ENGINE_AUTO && big));
     if (ep->dense) {
         ep->dense_cap = dense_cap(ix->n, k);
         ep->nslots = 0;
@@ -592,12 +598,17 @@ pdx_status exact_plan(const pdx_index *ix, int64_t nq, int32_t k, const pdx_sear
     }
     ep->Lstart = (int64_t)ep->start_blk * kBlock;
     ep->op = plan_orders(ix, o, pl.pruner, nq, ix->nparts);
+    // first-step filter: PDX-BOND over FP32 blocks with one visit order per query
+    ep->filter = pl.pruner == PDX_PRUNE_BOND && ix->storage == PDX_F32 && pl.metric == PDX_L2 &&
+                 ep->op.rows > 0 && ep->op.per_part == 0 && (o.first_step == 4 || o.first_step == 8) && ep->start;
+    ep->filter_words = ep->filter ? (int)((ix->nblocks + 31) / 32) : 0;
     size_t b = rup((size_t)nq * 4)                              // tau
                + rup((size_t)nq * ep->nslots * k * 8)           // per-item lists
                + 3 * rup((size_t)nq * k * 8)                    // merged, refined, final top-k
                + rup(C_COUNT * 8) + rup(8)                      // counters, work counter
                + rup(ep->op.bytes)                              // visit orders
-               + rup((size_t)nq * kPoolCap * 4) + rup((size_t)nq * 4);  // shared candidate pools
+               + rup((size_t)nq * kPoolCap * 4) + rup((size_t)nq * 4)   // shared candidate pools
+               + rup((size_t)nq * ep->filter_words * 4);                 // first-step filter bitmap
     if (ep->start) b += rup((size_t)nq * ep->Lstart * 8) + rup((size_t)nq * k * 8);
     ep->mlp_bytes = 0;
     if (ep->op.mode == 2) {
@@ -644,6 +655,7 @@ pdx_status exact_run(const pdx_index *ix, const float *qd, int64_t nq, int32_t k
     uint16_t *qorder = ep.op.rows ? reinterpret_cast<uint16_t *>(take(ep.op.bytes)) : nullptr;
     float *pool = reinterpret_cast<float *>(take((size_t)nq * kPoolCap * 4));
     int32_t *pool_cnt = reinterpret_cast<int32_t *>(take((size_t)nq * 4));
+    uint32_t *fbits = reinterpret_cast<uint32_t *>(take((size_t)nq * ep.filter_words * 4));
     uint64_t *skeys = ep.start ? reinterpret_cast<uint64_t *>(take((size_t)nq * ep.Lstart * 8)) : nullptr;
     uint64_t *stopk = ep.start ? reinterpret_cast<uint64_t *>(take((size_t)nq * k * 8)) : nullptr;
     unsigned char *mlp_ws = ep.mlp_bytes ? take(ep.mlp_bytes) : nullptr;
@@ -740,6 +752,24 @@ pdx_status exact_run(const pdx_index *ix, const float *qd, int64_t nq, int32_t k
     p.pool = use_pool ? pool : nullptr;
     p.pool_cnt = pool_cnt;
     if (o.scan_event_start) PDX_TRY(cudaEventRecord(static_cast<cudaEvent_t>(o.scan_event_start), st));
+    if (ep.filter) {
+        FilterParams f;
+        f.data = ix->data;
+        f.blk_cnt = ix->blk_cnt;
+        f.nblocks = ix->nblocks;
+        f.d = d;
+        f.q = qd;
+        f.nq = nq;
+        f.qorder = qorder;
+        f.tau = tau;
+        f.gamma = p.gamma;
+        f.bits = fbits;
+        f.words = ep.filter_words;
+        f.counters = kc;
+        PDX_TRY(launch_first_step_filter(f, (int)o.first_step, sms, st));
+        p.block_bits = fbits;
+        p.bit_words = ep.filter_words;
+    }
     PDX_TRY(launch_scan(pl.pruner, pl.metric, p, sms, st));
     if (o.scan_event_stop) PDX_TRY(cudaEventRecord(static_cast<cudaEvent_t>(o.scan_event_stop), st));
     PDX_TRY(launch_select_k(cand, nq, (int64_t)ep.nslots * k, k, topk, st));

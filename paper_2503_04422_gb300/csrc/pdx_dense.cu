@@ -18,7 +18,7 @@
 //                margin m (TF32 operands, FP32 accumulation; see dense_bounds),
 //                so that est - m <= exact <= est + m. The kernel runs twice:
 //                the bound pass writes the k smallest upper bounds of every
-//                (query, 128-vector half tile); the emit pass lists the vectors
+//                (query, sub-tile of 64 or 128 vectors); the emit pass lists the vectors
 //                whose lower bound is within T*.
 //   3. select    one CTA per query: T* = k-th smallest of those upper bounds,
 //                which is the k-th smallest upper bound over all vectors.
@@ -41,6 +41,7 @@
 #include <cudaTypedefs.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <mutex>
 
@@ -56,8 +57,14 @@ constexpr int STAGES = 4;
 constexpr int A_BYTES = TM * TKF * 4;   // 16 KB
 constexpr int B_BYTES = TN * TKF * 4;   // 32 KB
 constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
-constexpr int EPI_WARPS = 8;            // two per TMEM lane quarter, one per column half
-constexpr int THREADS = (2 + EPI_WARPS) * 32;
+// Epilogue warps: EW per TMEM lane quarter, each draining TN / EW columns
+// (EW = 4 for k <= 16, 2 for the larger register lists of k <= 64).
+template <int EW> struct Epi {
+    static constexpr int warps = 4 * EW;
+    static constexpr int threads = (2 + warps) * 32;
+    static constexpr int span = TN / EW;
+};
+constexpr int ew_for(int k) { return k <= 16 ? 4 : 2; }
 constexpr int TMEM_COLS = 2 * TN;       // two accumulators
 constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024;  // + alignment of the swizzled tiles
 constexpr uint64_t kWaitNs = 2000000000ull;              // give up on a barrier after 2 s
@@ -170,41 +177,46 @@ struct DenseParams {
     int32_t d, k;
     int32_t nqt;                 // query tiles
     int64_t ntiles;              // query tiles x vector tiles
-    int64_t nhalf;               // half tiles (128 vectors) of the collection
-    const float *qnorm;          // [nq] ||q||
-    const float2 *xnorm;         // [n] (||x||^2, ||x||)
-    float *ubuf;                 // bound pass: [nq][nhalf][k] smallest upper bounds per half tile
+    int64_t nsub;                // sub-tiles (TN / EW vectors) of the collection
+    const float2 *qnorm;         // [nq] (||tf32(q)||, ||q - tf32(q)||), rounded up
+    const float4 *xnorm;         // [n] (||x||^2, ||x||, ||x - tf32(x)||, 0), norms rounded up
+    float *ubuf;                 // bound pass: [nq][nsub][k] smallest upper bounds per sub-tile
     const float *tstar;          // emit pass: [nq] k-th smallest upper bound over all vectors
     int32_t *cnt;                // [nq] entries emitted
     int32_t cap;                 // entries per query
     int32_t *ent_id;             // [nq][cap] emitted vector ids
-    float c_qx, c_xx, c_rel;     // margin coefficients
+    float k2, c_acc, c_xx, c_rel;  // margin coefficients (see dense_bounds)
     int32_t *err;                // set when a wait gave up
 };
 
-// Error margin of est for one (query, vector) pair. With TF32 operands
-// (at most 2^-10 relative truncation each) and FP32 accumulation of D
-// products, |acc - q.x| <= (2^-9 + (D+16) 2^-22) sum_j |q_j x_j|
-// <= that * ||q|| ||x|| (Cauchy-Schwarz). The FP32 ||x||^2 is within
-// D 2^-23 ||x||^2 and forming est rounds once more; c_qx, c_xx, c_rel hold
-// these terms with extra slack for the FP32 arithmetic of the margin itself.
+// Error margin of est for one (query, vector) pair. Both operands are
+// rounded to TF32 before the GEMM (q~, x~), so the tensor core's own
+// conversion is exact, and TF32 x TF32 products are exact in FP32. Then
+//   q.x - q~.x~ = (q - q~).x + q~.(x - x~),
+// so |q.x - q~.x~| <= ||q - q~|| ||x|| + ||q~|| ||x - x~|| (Cauchy-Schwarz, with
+// the residual norms measured per row), and FP32 accumulation of the D exact
+// products adds at most c_acc sum_j |q~_j x~_j| <= c_acc ||q~|| ||x~||, with
+// ||x~|| <= ||x|| + ||x - x~||. For L2 the dot enters twice (k2 = 2); ||x||^2
+// carries its FP32 rounding (c_xx) and forming est rounds once more (c_rel).
+// Per row: P = k2 ||q~|| (1 + c_acc), Q = k2 (||q - q~|| + c_acc ||q~||), and
+//   m = P ||x - x~|| + Q ||x|| + c_xx ||x||^2 + c_rel |est|.
 template <int MET>
-__device__ __forceinline__ void dense_bounds(float acc, float2 xn, float aq, const DenseParams &p, float &lo,
+__device__ __forceinline__ void dense_bounds(float acc, float4 xn, float P, float Q, const DenseParams &p, float &lo,
                                              float &up) {
     float est, m;
     if (MET == MT_L2) {
         est = fmaf(-2.f, acc, xn.x);
-        m = fmaf(aq, xn.y, fmaf(p.c_xx, xn.x, p.c_rel * fabsf(est)));
+        m = fmaf(P, xn.z, fmaf(Q, xn.y, fmaf(p.c_xx, xn.x, p.c_rel * fabsf(est))));
     } else {
         est = -acc;
-        m = fmaf(aq, xn.y, p.c_rel * fabsf(est));
+        m = fmaf(P, xn.z, fmaf(Q, xn.y, p.c_rel * fabsf(est)));
     }
     lo = est - m;
     up = est + m;
 }
 
-template <int KL, int MET, int MODE>
-__global__ void __launch_bounds__(THREADS, 1)
+template <int KL, int MET, int MODE, int EW>
+__global__ void __launch_bounds__(Epi<EW>::threads, 1)
     dense_tc_kernel(const __grid_constant__ CUtensorMap tmQ, const __grid_constant__ CUtensorMap tmX, DenseParams p) {
     extern __shared__ unsigned char smem_raw[];
     __shared__ __align__(8) uint64_t bars[2 * STAGES + 5];
@@ -227,7 +239,7 @@ __global__ void __launch_bounds__(THREADS, 1)
         }
         for (int b = 0; b < 2; ++b) {
             mbar_init(tfull(b), 1);
-            mbar_init(tempty(b), EPI_WARPS);
+            mbar_init(tempty(b), Epi<EW>::warps);
         }
         mbar_init(done, 1);
         abort_flag = 0;
@@ -314,9 +326,11 @@ __global__ void __launch_bounds__(THREADS, 1)
             wait_bar(done, 0, &dummy);
         }
     } else {
-        // ---- epilogue: 8 warps; warp w reads TMEM lanes 32*(w%4).. (its quarter), columns of half (w-2)/4 ----
+        // ---- epilogue: warp w reads TMEM lanes 32*(w%4).. (its quarter) and
+        // columns [part*span, (part+1)*span) with part = (w-2)/4 ----
+        constexpr int SPAN = Epi<EW>::span;
         const int quarter = warp & 3;
-        const int half = (warp - 2) >> 2;
+        const int part = (warp - 2) >> 2;
         const int row_in_tile = quarter * 32 + lane;
         int it = 0;
         for (int64_t t = blockIdx.x; t < p.ntiles; t += gridDim.x, ++it) {
@@ -332,67 +346,59 @@ __global__ void __launch_bounds__(THREADS, 1)
             tc_fence_after();
             const int64_t r = (int64_t)qt * TM + row_in_tile;
             const bool rv = r < p.nq;
-            const float aq = rv ? p.c_qx * __ldg(p.qnorm + r) : 0.f;
-            const int64_t col0 = nt * TN + half * (TN / 2);
-            const uint32_t taddr = tbase + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(b * TN + half * (TN / 2));
-            if (MODE == 0) {
-                // bound pass: the k smallest upper bounds of this row within the half tile
-                float L[KL];
+            float P = 0.f, Q = 0.f;
+            if (rv) {
+                const float2 qn = __ldg(p.qnorm + r);
+                P = p.k2 * qn.x * (1.f + p.c_acc);
+                Q = p.k2 * (qn.y + p.c_acc * qn.x);
+            }
+            const int64_t col0 = nt * TN + part * SPAN;
+            const uint32_t taddr = tbase + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(b * TN + part * SPAN);
+            float L[KL];
 #pragma unroll
-                for (int i = 0; i < KL; ++i) L[i] = __int_as_float(0x7f800000);
+            for (int i = 0; i < KL; ++i) L[i] = __int_as_float(0x7f800000);
+            const float T = (MODE == 1 && rv) ? __ldg(p.tstar + r) : __int_as_float(0xff800000);
 #pragma unroll 1
-                for (int cb = 0; cb < TN / 2; cb += 32) {
-                    float v[32];
-                    tmem_ld32(taddr + cb, v);
-                    if (rv) {
+            for (int cb = 0; cb < SPAN; cb += 32) {
+                // the chunk's per-vector norms: one coalesced load, then each
+                // column's values are broadcast to the warp by shuffles
+                const int64_t cbase = col0 + cb;
+                const int64_t left = p.n - cbase;
+                const int nvalid = left <= 0 ? 0 : (left >= 32 ? 32 : (int)left);
+                const float4 mine = lane < nvalid ? __ldg(p.xnorm + cbase + lane) : make_float4(0.f, 0.f, 0.f, 0.f);
+                float v[32];
+                tmem_ld32(taddr + cb, v);
 #pragma unroll
-                        for (int i = 0; i < 32; ++i) {
-                            const int64_t c = col0 + cb + i;
-                            if (c < p.n) {
-                                float lo, up;
-                                dense_bounds<MET>(v[i], __ldg(p.xnorm + c), aq, p, lo, up);
-                                if (up < L[KL - 1]) {
-                                    float x = up;
+                for (int i = 0; i < 32; ++i) {
+                    const float4 xn = make_float4(__shfl_sync(kFull, mine.x, i), __shfl_sync(kFull, mine.y, i),
+                                                  __shfl_sync(kFull, mine.z, i), 0.f);
+                    if (rv && i < nvalid) {
+                        float lo, up;
+                        dense_bounds<MET>(v[i], xn, P, Q, p, lo, up);
+                        if (MODE == 0) {
+                            // bound pass: the k smallest upper bounds of this row in the sub-tile
+                            if (up < L[KL - 1]) {
+                                float x = up;
 #pragma unroll
-                                    for (int j = 0; j < KL; ++j) {
-                                        const float a = fminf(L[j], x);
-                                        x = fmaxf(L[j], x);
-                                        L[j] = a;
-                                    }
+                                for (int j = 0; j < KL; ++j) {
+                                    const float a = fminf(L[j], x);
+                                    x = fmaxf(L[j], x);
+                                    L[j] = a;
                                 }
                             }
+                        } else if (lo <= T) {
+                            // emit pass: the vector's lower bound is within T*
+                            const int pos = atomicAdd(p.cnt + r, 1);
+                            if (pos < p.cap) p.ent_id[r * p.cap + pos] = (int32_t)(cbase + i);
                         }
                     }
                 }
-                if (rv) {
-                    float *u = p.ubuf + (r * p.nhalf + (2 * nt + half)) * p.k;
+            }
+            if (MODE == 0 && rv) {
+                float *u = p.ubuf + (r * p.nsub + (nt * EW + part)) * p.k;
 #pragma unroll
-                    for (int i = 0; i < KL; ++i)
-                        if (i < p.k) u[i] = L[i];
-                }
-            } else {
-                // emit pass: every vector whose lower bound is within the
-                // query's k-th smallest upper bound
-                const float T = rv ? __ldg(p.tstar + r) : __int_as_float(0xff800000);
-#pragma unroll 1
-                for (int cb = 0; cb < TN / 2; cb += 32) {
-                    float v[32];
-                    tmem_ld32(taddr + cb, v);
-                    if (rv) {
-#pragma unroll
-                        for (int i = 0; i < 32; ++i) {
-                            const int64_t c = col0 + cb + i;
-                            if (c < p.n) {
-                                float lo, up;
-                                dense_bounds<MET>(v[i], __ldg(p.xnorm + c), aq, p, lo, up);
-                                if (lo <= T) {
-                                    const int pos = atomicAdd(p.cnt + r, 1);
-                                    if (pos < p.cap) p.ent_id[r * p.cap + pos] = (int32_t)c;
-                                }
-                            }
-                        }
-                    }
-                }
+                for (int i = 0; i < KL; ++i)
+                    if (i < p.k) u[i] = L[i];
             }
             tc_fence_before();
             __syncwarp();
@@ -411,8 +417,25 @@ __global__ void __launch_bounds__(THREADS, 1)
 }
 
 // ---------------------------------------------------------------------------
+__device__ __forceinline__ float tf32_rna(float v) {
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(v));
+    return __uint_as_float(r);
+}
+
+__device__ __forceinline__ double warp_sum_f64(double v) {
+#pragma unroll
+    for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+    return v;
+}
+
+// FP64 norm rounded up to FP32 (a bound used only inside margins)
+__device__ __forceinline__ float norm_up(double sq) { return (float)sqrt(sq) * (1.f + 1.0f / 1048576.f); }
+
+// Queries rounded to TF32 into the aligned operand buffer, with
+// (||tf32(q)||, ||q - tf32(q)||); per-query state reset.
 __global__ void dense_prep_kernel(const float *__restrict__ q, int64_t nq, int32_t d, float *__restrict__ qs,
-                                  float *__restrict__ qnorm, int32_t *__restrict__ cnt, int32_t *__restrict__ err,
+                                  float2 *__restrict__ qnorm, int32_t *__restrict__ cnt, int32_t *__restrict__ err,
                                   unsigned long long *counters, int64_t n) {
     const int64_t row = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
@@ -422,36 +445,46 @@ __global__ void dense_prep_kernel(const float *__restrict__ q, int64_t nq, int32
         atomicAdd(counters + C_SCANNED, (unsigned long long)nq * (unsigned long long)n);
     }
     if (row >= nq) return;
-    float s = 0.f;
+    double st = 0.0, se = 0.0;
     for (int j = lane; j < d; j += 32) {
         const float v = q[row * d + j];
-        qs[row * d + j] = v;
-        s = fmaf(v, v, s);
+        const float t = tf32_rna(v);
+        qs[row * d + j] = t;
+        st += (double)t * t;
+        se += ((double)v - t) * ((double)v - t);
     }
-    s = warp_sum(s);
+    st = warp_sum_f64(st);
+    se = warp_sum_f64(se);
     if (lane == 0) {
-        qnorm[row] = sqrtf(s);
+        qnorm[row] = make_float2(norm_up(st), norm_up(se));
         cnt[row] = 0;
     }
 }
 
-__global__ void row_norms_kernel(const float *__restrict__ x, int64_t n, int32_t d, float2 *__restrict__ out) {
+// Tensor-engine operand of the collection: rows rounded to TF32 and
+// (||x||^2, ||x||, ||x - tf32(x)||, 0) from FP64 sums.
+__global__ void dense_operand_kernel(const float *__restrict__ x, int64_t n, int32_t d, float *__restrict__ xtc,
+                                     float4 *__restrict__ out) {
     const int64_t row = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     if (row >= n) return;
-    float s = 0.f;
+    double sx = 0.0, se = 0.0;
     for (int j = lane; j < d; j += 32) {
         const float v = x[row * d + j];
-        s = fmaf(v, v, s);
+        const float t = tf32_rna(v);
+        xtc[row * d + j] = t;
+        sx += (double)v * v;
+        se += ((double)v - t) * ((double)v - t);
     }
-    s = warp_sum(s);
-    if (lane == 0) out[row] = make_float2(s, sqrtf(s));
+    sx = warp_sum_f64(sx);
+    se = warp_sum_f64(se);
+    if (lane == 0) out[row] = make_float4((float)sx, norm_up(sx), norm_up(se), 0.f);
 }
 
 // T*[q] = k-th smallest value of ubuf[q][0..L): a radix select over the
 // order-preserving uint32 keys, 11 + 11 + 10 bits, one CTA per query. Every
 // vector among the k smallest upper bounds of the whole collection is among
-// the k smallest of its own half tile, so this is the k-th smallest upper
+// the k smallest of its own sub-tile, so this is the k-th smallest upper
 // bound over all vectors (+inf when fewer than k are finite).
 __global__ void __launch_bounds__(256) dense_select_kernel(const float *__restrict__ ubuf, int64_t L, int32_t k,
                                                            float *__restrict__ tstar) {
@@ -610,12 +643,30 @@ bool encode_rows(CUtensorMap *m, const float *base, int64_t rows, int32_t d, int
               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
+// Raises a kernel's dynamic shared-memory limit to at least `bytes` on the
+// current device, once per (kernel, device) and size (host-side cost only).
+template <class K>
+cudaError_t ensure_smem(K kernel, std::atomic<int> (&done)[64], int bytes) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    std::atomic<int> &have = done[dev & 63];
+    if (have.load(std::memory_order_acquire) >= bytes) return cudaSuccess;
+    cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e == cudaSuccess) {
+        int cur = have.load();
+        while (cur < bytes && !have.compare_exchange_weak(cur, bytes)) {
+        }
+    }
+    return e;
+}
+
 template <int KL, int MET, int MODE>
 cudaError_t launch_tc(const CUtensorMap &mq, const CUtensorMap &mx, const DenseParams &p, int grid, cudaStream_t st) {
-    cudaError_t e = cudaFuncSetAttribute(dense_tc_kernel<KL, MET, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         SMEM_BYTES);
+    constexpr int EW = ew_for(KL);
+    static std::atomic<int> done[64];
+    cudaError_t e = ensure_smem(dense_tc_kernel<KL, MET, MODE, EW>, done, SMEM_BYTES);
     if (e != cudaSuccess) return e;
-    dense_tc_kernel<KL, MET, MODE><<<grid, THREADS, SMEM_BYTES, st>>>(mq, mx, p);
+    dense_tc_kernel<KL, MET, MODE, EW><<<grid, Epi<EW>::threads, SMEM_BYTES, st>>>(mq, mx, p);
     return counted(cudaGetLastError());
 }
 
@@ -629,22 +680,23 @@ cudaError_t launch_tc_any(const CUtensorMap &mq, const CUtensorMap &mx, const De
 
 template <int MET>
 cudaError_t launch_finish(const FinishParams &f, cudaStream_t st) {
+    static std::atomic<int> done[64];
     const size_t smem = (size_t)f.cap * 8;
-    cudaError_t e =
-        cudaFuncSetAttribute(dense_finish_kernel<MET>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = ensure_smem(dense_finish_kernel<MET>, done, (int)smem);
     if (e != cudaSuccess) return e;
     dense_finish_kernel<MET><<<(unsigned)f.nq, 256, smem, st>>>(f);
     return counted(cudaGetLastError());
 }
 
-int64_t half_tiles(int64_t n) { return 2 * ((n + TN - 1) / TN); }
+// sub-tiles of the bound pass: EW per TN-vector tile
+int64_t sub_tiles(int64_t n, int32_t k) { return (int64_t)ew_for(k <= 16 ? 16 : 64) * ((n + TN - 1) / TN); }
 
 }  // namespace
 
 bool dense_supported(const pdx_index *ix, int32_t k, const char **why) {
     const char *w = nullptr;
     if (ix->is_ivf) w = "the tensor-core engine serves exact indexes only";
-    else if (!ix->xnary || !ix->xnorm) w = "the index keeps no row-major FP32 vectors (build with dense_rows=1)";
+    else if (!ix->xnary || !ix->xtc || !ix->xnorm) w = "the index keeps no tensor-engine operand (build with dense_rows=1)";
     else if (ix->metric != PDX_L2 && ix->metric != PDX_IP) w = "the tensor-core engine supports L2 and IP";
     else if (ix->d % 4 != 0) w = "the tensor-core engine needs d to be a multiple of 4 (16-byte rows for TMA)";
     else if (k > 64) w = "the tensor-core engine supports k <= 64";
@@ -665,7 +717,8 @@ int dense_cap(int64_t n, int32_t k) {
 
 size_t dense_scratch_bytes(int64_t nq, int32_t d, int32_t k, int32_t cap, int64_t n) {
     auto rup = [](size_t b) { return (b + 255) & ~size_t(255); };
-    return rup((size_t)nq * d * 4) + 3 * rup((size_t)nq * 4) + rup((size_t)nq * half_tiles(n) * k * 4) +
+    return rup((size_t)nq * d * 4) + rup((size_t)nq * 8) + 2 * rup((size_t)nq * 4) +
+           rup((size_t)nq * sub_tiles(n, k) * k * 4) +
            rup((size_t)nq * cap * 4) + rup((size_t)nq * k * 8) + rup(8);
 }
 
@@ -673,7 +726,7 @@ pdx_status dense_run(const pdx_index *ix, const float *qd, int64_t nq, int32_t k
                      unsigned char *scratch, size_t bytes, int cap, float *od, int64_t *oi, unsigned long long *counters,
                      int sms, void *ev_start, void *ev_stop, cudaStream_t st) {
     const int d = ix->d;
-    const int64_t nhalf = half_tiles(ix->n);
+    const int64_t nsub = sub_tiles(ix->n, k);
     auto rup = [](size_t b) { return (b + 255) & ~size_t(255); };
     size_t off = 0;
     auto take = [&](size_t b) {
@@ -682,10 +735,10 @@ pdx_status dense_run(const pdx_index *ix, const float *qd, int64_t nq, int32_t k
         return p;
     };
     float *qs = reinterpret_cast<float *>(take((size_t)nq * d * 4));
-    float *qnorm = reinterpret_cast<float *>(take((size_t)nq * 4));
+    float2 *qnorm = reinterpret_cast<float2 *>(take((size_t)nq * 8));
     float *tstar = reinterpret_cast<float *>(take((size_t)nq * 4));
     int32_t *cnt = reinterpret_cast<int32_t *>(take((size_t)nq * 4));
-    float *ubuf = reinterpret_cast<float *>(take((size_t)nq * nhalf * k * 4));
+    float *ubuf = reinterpret_cast<float *>(take((size_t)nq * nsub * k * 4));
     int32_t *ent_id = reinterpret_cast<int32_t *>(take((size_t)nq * cap * 4));
     uint64_t *keys = reinterpret_cast<uint64_t *>(take((size_t)nq * k * 8));
     int32_t *err = reinterpret_cast<int32_t *>(take(8));
@@ -701,7 +754,7 @@ pdx_status dense_run(const pdx_index *ix, const float *qd, int64_t nq, int32_t k
         if (e != cudaSuccess) return cuda_status_ext(e, "dense_prep_kernel");
     }
     CUtensorMap mq, mx;
-    if (!encode_rows(&mq, qs, nq, d, TM) || !encode_rows(&mx, ix->xnary, ix->n, d, TN)) {
+    if (!encode_rows(&mq, qs, nq, d, TM) || !encode_rows(&mx, ix->xtc, ix->n, d, TN)) {
         set_error("cuTensorMapEncodeTiled failed (d=%d)", d);
         return PDX_ERR_CUDA;
     }
@@ -712,30 +765,33 @@ pdx_status dense_run(const pdx_index *ix, const float *qd, int64_t nq, int32_t k
     p.k = k;
     p.nqt = (int32_t)((nq + TM - 1) / TM);
     p.ntiles = (int64_t)p.nqt * ((ix->n + TN - 1) / TN);
-    p.nhalf = nhalf;
+    p.nsub = nsub;
     p.qnorm = qnorm;
-    p.xnorm = reinterpret_cast<const float2 *>(ix->xnorm);
+    p.xnorm = reinterpret_cast<const float4 *>(ix->xnorm);
     p.ubuf = ubuf;
     p.tstar = tstar;
     p.cnt = cnt;
     p.cap = cap;
     p.ent_id = ent_id;
-    // margin coefficients (see dense_bounds), each with a 2^-10 relative cushion
+    // margin coefficients (see dense_bounds): FP32 accumulation of D exact
+    // products within (D+16) 2^-22 of sum |q~_j x~_j| (twice the sequential
+    // bound, for an accumulation order we cannot see), a 2^-10 relative
+    // cushion for the FP32 arithmetic of the margin itself
     const double u = std::ldexp(1.0, -22);
-    const double cdot = std::ldexp(1.0, -9) + (d + 16) * u;
     const double cushion = 1.0 + std::ldexp(1.0, -10);
-    p.c_qx = (float)((metric == MT_L2 ? 2.0 : 1.0) * cdot * cushion);
-    p.c_xx = (float)((d + 8) * u * cushion);
+    p.k2 = (float)((metric == MT_L2 ? 2.0 : 1.0) * cushion);
+    p.c_acc = (float)((d + 16) * u);
+    p.c_xx = (float)(u);
     p.c_rel = (float)(4.0 * u);
     p.err = err;
     const int grid = (int)std::min<int64_t>(p.ntiles, (int64_t)sms);
     cudaError_t e;
     if (ev_start && (e = cudaEventRecord(static_cast<cudaEvent_t>(ev_start), st)) != cudaSuccess)
         return cuda_status_ext(e, "cudaEventRecord");
-    // pass 1: per half tile, the k smallest upper bounds; then T* per query
+    // pass 1: per sub-tile, the k smallest upper bounds; then T* per query
     if ((e = launch_tc_any<0>(mq, mx, p, grid, metric, st)) != cudaSuccess)
         return cuda_status_ext(e, "dense_tc_kernel (bound pass)");
-    dense_select_kernel<<<(unsigned)nq, 256, 0, st>>>(ubuf, nhalf * k, k, tstar);
+    dense_select_kernel<<<(unsigned)nq, 256, 0, st>>>(ubuf, nsub * k, k, tstar);
     if ((e = counted(cudaGetLastError())) != cudaSuccess) return cuda_status_ext(e, "dense_select_kernel");
     // pass 2: emit the vectors whose lower bound is within T*
     if ((e = launch_tc_any<1>(mq, mx, p, grid, metric, st)) != cudaSuccess)
@@ -748,7 +804,7 @@ pdx_status dense_run(const pdx_index *ix, const float *qd, int64_t nq, int32_t k
     f.d = d;
     f.k = k;
     f.cap = cap;
-    f.q = qs;
+    f.q = qd;             // the rerank reads the exact FP32 queries and vectors
     f.x = ix->xnary;
     f.cnt = cnt;
     f.ent_id = ent_id;
@@ -762,9 +818,10 @@ pdx_status dense_run(const pdx_index *ix, const float *qd, int64_t nq, int32_t k
     return PDX_OK;
 }
 
-cudaError_t launch_row_norms(const float *x, int64_t n, int32_t d, float *out, cudaStream_t st) {
+cudaError_t launch_dense_operand(const float *x, int64_t n, int32_t d, float *xtc, float *out, cudaStream_t st) {
     if (n == 0) return cudaSuccess;
-    row_norms_kernel<<<(unsigned)((n * 32 + 255) / 256), 256, 0, st>>>(x, n, d, reinterpret_cast<float2 *>(out));
+    dense_operand_kernel<<<(unsigned)((n * 32 + 255) / 256), 256, 0, st>>>(x, n, d, xtc,
+                                                                           reinterpret_cast<float4 *>(out));
     return counted(cudaGetLastError());
 }
 

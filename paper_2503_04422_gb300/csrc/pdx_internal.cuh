@@ -53,7 +53,8 @@ struct pdx_index {
     float *scale = nullptr;         // [d] FP8: per-dimension scale
     float *xnary = nullptr;         // [n][d] FP32 vectors by id (low precision: START, rerank;
                                     // tensor-core dense engine)
-    float *xnorm = nullptr;         // [n][2] (||x||^2, ||x||) of the rows above (dense engine)
+    float *xtc = nullptr;           // [n][d] the rows rounded to TF32 (tensor-core operand)
+    float *xnorm = nullptr;         // [n][4] (||x||^2, ||x||, ||x - tf32(x)||, 0) (dense engine)
     int32_t *ids = nullptr;         // [nblocks*64]
     int32_t *slot_of = nullptr;     // [n] storage slot (block*64 + lane) of each vector id
     int32_t *blk_cnt = nullptr;     // [nblocks] valid lanes per block
@@ -213,7 +214,30 @@ struct ScanParams {
     // best over everything scanned so far, as one heap per query would give.
     float *pool;               // [nq][kPoolCap] or null
     int32_t *pool_cnt;         // [nq]
+    // First-step filter result (or null): bit b of row qi is 0 when every
+    // vector of storage block b was pruned by the first fetch step.
+    const uint32_t *block_bits;  // [nq][bit_words]
+    int32_t bit_words;
 };
+
+// First-step filter for exact PDX-BOND over FP32 blocks with per-query visit
+// orders: block_bits[qi][b / 32] bit b % 32 = some vector of block b survives
+// the first `s0` dimensions of the query's order against slack(tau[qi]).
+struct FilterParams {
+    const float *data;         // [nblocks][d][64]
+    const int32_t *blk_cnt;
+    int64_t nblocks;
+    int32_t d;
+    const float *q;            // [nq][d]
+    int64_t nq;
+    const uint16_t *qorder;    // [nq][d]
+    const float *tau;          // [nq] ordered-uint thresholds (START)
+    float gamma;
+    uint32_t *bits;            // [nq][words]
+    int32_t words;
+    unsigned long long *counters;
+};
+cudaError_t launch_first_step_filter(const FilterParams &f, int s0, int num_sms, cudaStream_t st);
 cudaError_t launch_scan(int pruner, int metric, const ScanParams &p, int num_sms, cudaStream_t st);
 // Visit orders for PDX-BOND (mode 0 distance to means with zones of Z, mode 1
 // decreasing query value); per_part > 0: one row per (query, part) with
@@ -246,6 +270,8 @@ struct ExactPlan {
     OrderPlan op;
     size_t mlp_bytes = 0;      // learned order: centroid keys, nearest, inputs, hidden, scores
     int64_t mlp_Lc = 0;
+    bool filter = false;       // first-step filter ahead of the scan
+    int filter_words = 0;      // 32-block words per query of its bitmap
     bool dense = false;        // tensor-core engine (pdx_dense.cu) instead of the scan
     int dense_cap = 0;         // its candidate entries per query
     size_t bytes = 0;
@@ -266,8 +292,9 @@ size_t dense_scratch_bytes(int64_t nq, int32_t d, int32_t k, int32_t cap, int64_
 pdx_status dense_run(const pdx_index *ix, const float *qd, int64_t nq, int32_t k, int metric, int out_mode,
                      unsigned char *scratch, size_t bytes, int cap, float *od, int64_t *oi, unsigned long long *counters,
                      int sms, void *ev_start, void *ev_stop, cudaStream_t st);
-// (||x||^2, ||x||) of each row of x[n][d], FP32, as out[n][2]
-cudaError_t launch_row_norms(const float *x, int64_t n, int32_t d, float *out, cudaStream_t st);
+// Tensor-engine operand of x[n][d]: xtc = x rounded to TF32 (to nearest) and
+// out[n][4] = (||x||^2, ||x||, ||x - xtc||, 0), sums in FP64, norms rounded up.
+cudaError_t launch_dense_operand(const float *x, int64_t n, int32_t d, float *xtc, float *out, cudaStream_t st);
 size_t scan_warp_smem(int d, int k, int zone_dims, int order);
 
 // START: exact distances of every query to the first `nvec` stored vectors,

@@ -25,6 +25,8 @@
 // A relative slack gamma = D * 2^-23 on every threshold covers the rounding of
 // FP32 partial sums, so an FP32 partial that exceeds tau*(1+gamma) has an
 // exact partial above the exact tau.
+#include <algorithm>
+
 #include <cuda_bf16.h>
 #include <cuda_fp8.h>
 
@@ -431,6 +433,8 @@ __global__ void __launch_bounds__(256, PDX_SCAN_MIN_CTAS) pdxsearch_kernel(ScanP
         const float *qaux = (PR == PR_BSA) ? a.qaux + qi * a.nchk * 2 : nullptr;
 
         for (int b = b0; b < b1; ++b) {
+            // blocks the first-step filter pruned whole (it counted them)
+            if (a.block_bits && !((__ldg(a.block_bits + qi * a.bit_words + (b >> 5)) >> (b & 31)) & 1u)) continue;
             const ET *xb = xbase + (int64_t)b * D * kBlock;
             const int nvalid = a.blk_cnt[b];
             const float tau_g = o2f(*tau_g_ptr);
@@ -742,6 +746,105 @@ static cudaError_t launch_scan_lp(int pruner, const ScanParams &p, int num_sms, 
     case PR_BSA: return launch_scan_t<PR_BSA, MT_L2, ST>(p, num_sms, st);
     default: return cudaErrorInvalidValue;
     }
+}
+
+// ---------------------------------------------------------------------------
+// First-step filter. In the exact search most (query, block) pairs end after
+// the first fetch step: every vector's partial over the first s0 dimensions of
+// the query's order already exceeds the threshold. Inside the scan each such
+// block costs one dependent round trip to L2 plus the block's setup. This
+// kernel evaluates only that step, for all blocks, with the query's s0
+// dimensions and values in registers and U blocks' loads in flight per warp,
+// against the START threshold (the k-th distance of k real vectors, widened by
+// the same FP32 slack as the scan). Blocks where some vector survives keep
+// their bit and are scanned in full; the others are skipped. Exactness is
+// that of the scan's own predicate.
+template <int S0, int U>
+__global__ void __launch_bounds__(256) first_step_filter_kernel(FilterParams f) {
+    const int lane = threadIdx.x & 31;
+    const int h = lane >> 4, sl = lane & 15;
+    const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const int64_t items = (int64_t)f.words * f.nq;  // word-major: all queries of a 32-block group together
+    const int D = f.d;
+    unsigned long long c_values = 0, c_scanned = 0, c_pruned = 0;
+    for (int64_t it = gw; it < items; it += nw) {
+        const int64_t word = it / f.nq, qi = it % f.nq;
+        const int64_t b_lo = word * 32;
+        // this lane's dimensions of the first step (even/odd by half-warp) and the query values
+        int jt[S0 / 2];
+        float qv[S0 / 2];
+#pragma unroll
+        for (int t = 0; t < S0 / 2; ++t) {
+            jt[t] = f.qorder[qi * D + 2 * t + h];
+            qv[t] = f.q[qi * D + jt[t]];
+        }
+        const float tau = o2f(reinterpret_cast<const uint32_t *>(f.tau)[qi]);
+        const float thr = tau + fabsf(tau) * f.gamma;
+        const int cnt32 = (b_lo + lane < f.nblocks) ? f.blk_cnt[b_lo + lane] : 0;
+        uint32_t bits = 0;
+#pragma unroll 1
+        for (int bb = 0; bb < 32; bb += U) {
+            float4 x[U][S0 / 2];
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int64_t b = b_lo + bb + u;
+                const bool in = b < f.nblocks;
+#pragma unroll
+                for (int t = 0; t < S0 / 2; ++t)
+                    x[u][t] = in ? __ldg(reinterpret_cast<const float4 *>(f.data + ((b * D + jt[t]) * kBlock + 4 * sl)))
+                                 : make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+                for (int t = 0; t < S0 / 2; ++t) {
+                    acc.x = term<MT_L2>(qv[t], x[u][t].x, acc.x);
+                    acc.y = term<MT_L2>(qv[t], x[u][t].y, acc.y);
+                    acc.z = term<MT_L2>(qv[t], x[u][t].z, acc.z);
+                    acc.w = term<MT_L2>(qv[t], x[u][t].w, acc.w);
+                }
+                acc.x += __shfl_xor_sync(kFull, acc.x, 16);
+                acc.y += __shfl_xor_sync(kFull, acc.y, 16);
+                acc.z += __shfl_xor_sync(kFull, acc.z, 16);
+                acc.w += __shfl_xor_sync(kFull, acc.w, 16);
+                const int nvalid = __shfl_sync(kFull, cnt32, bb + u);
+                bool alive = false;
+                alive |= (4 * sl + 0 < nvalid) && !(acc.x > thr);
+                alive |= (4 * sl + 1 < nvalid) && !(acc.y > thr);
+                alive |= (4 * sl + 2 < nvalid) && !(acc.z > thr);
+                alive |= (4 * sl + 3 < nvalid) && !(acc.w > thr);
+                const bool any = __ballot_sync(kFull, h == 0 && alive) != 0u;
+                bits |= (uint32_t)any << (bb + u);
+                c_values += (unsigned long long)S0 * nvalid;
+                if (!any) {
+                    c_scanned += nvalid;
+                    c_pruned += nvalid;
+                }
+            }
+        }
+        if (lane == 0) f.bits[qi * f.words + word] = bits;
+    }
+    if (lane == 0 && f.counters) {
+        atomicAdd(f.counters + C_VALUES, c_values);
+        atomicAdd(f.counters + C_SCANNED, c_scanned);
+        atomicAdd(f.counters + C_PRUNED, c_pruned);
+    }
+}
+
+cudaError_t launch_first_step_filter(const FilterParams &f, int s0, int num_sms, cudaStream_t st) {
+    if (f.nq == 0 || f.words == 0) return cudaSuccess;
+    const int64_t items = (int64_t)f.words * f.nq;
+    const int64_t want = (items + 7) / 8;  // 8 warps per CTA
+    const unsigned grid = (unsigned)std::min<int64_t>(want, (int64_t)num_sms * 8);
+    if (s0 == 4)
+        first_step_filter_kernel<4, 4><<<grid, 256, 0, st>>>(f);
+    else if (s0 == 8)
+        first_step_filter_kernel<8, 2><<<grid, 256, 0, st>>>(f);
+    else
+        return cudaErrorInvalidValue;
+    return counted(cudaGetLastError());
 }
 
 cudaError_t launch_scan(int pruner, int metric, const ScanParams &p, int num_sms, cudaStream_t st) {
