@@ -564,7 +564,11 @@ pdx_status exact_plan(const pdx_index *ix, int64_t nq, int32_t k, const pdx_sear
     if (bpi <= 0) {
         const int64_t target = (int64_t)sms * 64 * 3;
         int64_t pairs = std::max<int64_t>(1, nq * (int64_t)ix->nparts);
-        int chunks = (int)std::min<int64_t>(max_blk, std::max<int64_t>(1, (target + pairs - 1) / pairs));
+        int64_t want = std::max<int64_t>(1, (target + pairs - 1) / pairs);
+        // each item leaves a k-entry list per query for the merge: keep the
+        // lists of one query within 256k keys
+        want = std::min<int64_t>(want, std::max<int64_t>(1, ((int64_t)1 << 18) / ((int64_t)ix->nparts * k)));
+        int chunks = (int)std::min<int64_t>(max_blk, want);
         bpi = (max_blk + chunks - 1) / chunks;
     }
     if (bpi < 1) bpi = 1;
@@ -598,17 +602,13 @@ pdx_status exact_plan(const pdx_index *ix, int64_t nq, int32_t k, const pdx_sear
     }
     ep->Lstart = (int64_t)ep->start_blk * kBlock;
     ep->op = plan_orders(ix, o, pl.pruner, nq, ix->nparts);
-    // first-step filter: PDX-BOND over FP32 blocks with one visit order per query
-    ep->filter = pl.pruner == PDX_PRUNE_BOND && ix->storage == PDX_F32 && pl.metric == PDX_L2 &&
-                 ep->op.rows > 0 && ep->op.per_part == 0 && (o.first_step == 4 || o.first_step == 8) && ep->start;
-    ep->filter_words = ep->filter ? (int)((ix->nblocks + 31) / 32) : 0;
+
     size_t b = rup((size_t)nq * 4)                              // tau
                + rup((size_t)nq * ep->nslots * k * 8)           // per-item lists
                + 3 * rup((size_t)nq * k * 8)                    // merged, refined, final top-k
                + rup(C_COUNT * 8) + rup(8)                      // counters, work counter
                + rup(ep->op.bytes)                              // visit orders
-               + rup((size_t)nq * kPoolCap * 4) + rup((size_t)nq * 4)   // shared candidate pools
-               + rup((size_t)nq * ep->filter_words * 4);                 // first-step filter bitmap
+               + rup((size_t)nq * kPoolCap * 4) + rup((size_t)nq * 4);  // shared candidate pools
     if (ep->start) b += rup((size_t)nq * ep->Lstart * 8) + rup((size_t)nq * k * 8);
     ep->mlp_bytes = 0;
     if (ep->op.mode == 2) {
@@ -655,7 +655,6 @@ pdx_status exact_run(const pdx_index *ix, const float *qd, int64_t nq, int32_t k
     uint16_t *qorder = ep.op.rows ? reinterpret_cast<uint16_t *>(take(ep.op.bytes)) : nullptr;
     float *pool = reinterpret_cast<float *>(take((size_t)nq * kPoolCap * 4));
     int32_t *pool_cnt = reinterpret_cast<int32_t *>(take((size_t)nq * 4));
-    uint32_t *fbits = reinterpret_cast<uint32_t *>(take((size_t)nq * ep.filter_words * 4));
     uint64_t *skeys = ep.start ? reinterpret_cast<uint64_t *>(take((size_t)nq * ep.Lstart * 8)) : nullptr;
     uint64_t *stopk = ep.start ? reinterpret_cast<uint64_t *>(take((size_t)nq * k * 8)) : nullptr;
     unsigned char *mlp_ws = ep.mlp_bytes ? take(ep.mlp_bytes) : nullptr;
@@ -752,27 +751,9 @@ pdx_status exact_run(const pdx_index *ix, const float *qd, int64_t nq, int32_t k
     p.pool = use_pool ? pool : nullptr;
     p.pool_cnt = pool_cnt;
     if (o.scan_event_start) PDX_TRY(cudaEventRecord(static_cast<cudaEvent_t>(o.scan_event_start), st));
-    if (ep.filter) {
-        FilterParams f;
-        f.data = ix->data;
-        f.blk_cnt = ix->blk_cnt;
-        f.nblocks = ix->nblocks;
-        f.d = d;
-        f.q = qd;
-        f.nq = nq;
-        f.qorder = qorder;
-        f.tau = tau;
-        f.gamma = p.gamma;
-        f.bits = fbits;
-        f.words = ep.filter_words;
-        f.counters = kc;
-        PDX_TRY(launch_first_step_filter(f, (int)o.first_step, sms, st));
-        p.block_bits = fbits;
-        p.bit_words = ep.filter_words;
-    }
     PDX_TRY(launch_scan(pl.pruner, pl.metric, p, sms, st));
     if (o.scan_event_stop) PDX_TRY(cudaEventRecord(static_cast<cudaEvent_t>(o.scan_event_stop), st));
-    PDX_TRY(launch_select_k(cand, nq, (int64_t)ep.nslots * k, k, topk, st));
+    PDX_TRY(launch_select_k_tau(cand, nq, (int64_t)ep.nslots * k, k, tau, p.gamma, topk, st));
     if (ix->storage == PDX_F32)
         PDX_TRY(launch_refine(topk, nq, k, qd, d, ix->data, ix->slot_of, ix->metric, refined, st));
     else

@@ -181,6 +181,7 @@ struct DenseParams {
     const float2 *qnorm;         // [nq] (||tf32(q)||, ||q - tf32(q)||), rounded up
     const float4 *xnorm;         // [n] (||x||^2, ||x||, ||x - tf32(x)||, 0), norms rounded up
     float *ubuf;                 // bound pass: [nq][nsub][k] smallest upper bounds per sub-tile
+    uint32_t *ushare;            // bound pass: [nq] ordered bits of the smallest sub-tile k-th so far
     const float *tstar;          // emit pass: [nq] k-th smallest upper bound over all vectors
     int32_t *cnt;                // [nq] entries emitted
     int32_t cap;                 // entries per query
@@ -357,7 +358,11 @@ __global__ void __launch_bounds__(Epi<EW>::threads, 1)
             float L[KL];
 #pragma unroll
             for (int i = 0; i < KL; ++i) L[i] = __int_as_float(0x7f800000);
-            const float T = (MODE == 1 && rv) ? __ldg(p.tstar + r) : __int_as_float(0xff800000);
+            // emit pass: T*; bound pass: the smallest k-th upper bound any sub-tile
+            // has shared so far (no vector above it can change T*)
+            const float T = !rv ? __int_as_float(0xff800000)
+                                : (MODE == 1 ? __ldg(p.tstar + r)
+                                             : o2f(*reinterpret_cast<volatile uint32_t *>(p.ushare + r)));
 #pragma unroll 1
             for (int cb = 0; cb < SPAN; cb += 32) {
                 // the chunk's per-vector norms: one coalesced load, then each
@@ -377,7 +382,7 @@ __global__ void __launch_bounds__(Epi<EW>::threads, 1)
                         dense_bounds<MET>(v[i], xn, P, Q, p, lo, up);
                         if (MODE == 0) {
                             // bound pass: the k smallest upper bounds of this row in the sub-tile
-                            if (up < L[KL - 1]) {
+                            if (up <= T && up < L[KL - 1]) {
                                 float x = up;
 #pragma unroll
                                 for (int j = 0; j < KL; ++j) {
@@ -399,6 +404,10 @@ __global__ void __launch_bounds__(Epi<EW>::threads, 1)
 #pragma unroll
                 for (int i = 0; i < KL; ++i)
                     if (i < p.k) u[i] = L[i];
+                // the k-th of the row just written (read back rather than
+                // selected from registers by a runtime index)
+                const float kth = u[p.k - 1];
+                if (kth < T) atomicMin(p.ushare + r, f2o(kth));
             }
             tc_fence_before();
             __syncwarp();
@@ -435,8 +444,8 @@ __device__ __forceinline__ float norm_up(double sq) { return (float)sqrt(sq) * (
 // Queries rounded to TF32 into the aligned operand buffer, with
 // (||tf32(q)||, ||q - tf32(q)||); per-query state reset.
 __global__ void dense_prep_kernel(const float *__restrict__ q, int64_t nq, int32_t d, float *__restrict__ qs,
-                                  float2 *__restrict__ qnorm, int32_t *__restrict__ cnt, int32_t *__restrict__ err,
-                                  unsigned long long *counters, int64_t n) {
+                                  float2 *__restrict__ qnorm, int32_t *__restrict__ cnt, uint32_t *__restrict__ ushare,
+                                  int32_t *__restrict__ err, unsigned long long *counters, int64_t n) {
     const int64_t row = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     if (blockIdx.x == 0 && threadIdx.x == 0) {
@@ -458,6 +467,7 @@ __global__ void dense_prep_kernel(const float *__restrict__ q, int64_t nq, int32
     if (lane == 0) {
         qnorm[row] = make_float2(norm_up(st), norm_up(se));
         cnt[row] = 0;
+        ushare[row] = 0xff800000u;  // ordered +inf
     }
 }
 
@@ -717,7 +727,7 @@ int dense_cap(int64_t n, int32_t k) {
 
 size_t dense_scratch_bytes(int64_t nq, int32_t d, int32_t k, int32_t cap, int64_t n) {
     auto rup = [](size_t b) { return (b + 255) & ~size_t(255); };
-    return rup((size_t)nq * d * 4) + rup((size_t)nq * 8) + 2 * rup((size_t)nq * 4) +
+    return rup((size_t)nq * d * 4) + rup((size_t)nq * 8) + 3 * rup((size_t)nq * 4) +
            rup((size_t)nq * sub_tiles(n, k) * k * 4) +
            rup((size_t)nq * cap * 4) + rup((size_t)nq * k * 8) + rup(8);
 }
@@ -738,6 +748,7 @@ pdx_status dense_run(const pdx_index *ix, const float *qd, int64_t nq, int32_t k
     float2 *qnorm = reinterpret_cast<float2 *>(take((size_t)nq * 8));
     float *tstar = reinterpret_cast<float *>(take((size_t)nq * 4));
     int32_t *cnt = reinterpret_cast<int32_t *>(take((size_t)nq * 4));
+    uint32_t *ushare = reinterpret_cast<uint32_t *>(take((size_t)nq * 4));
     float *ubuf = reinterpret_cast<float *>(take((size_t)nq * nsub * k * 4));
     int32_t *ent_id = reinterpret_cast<int32_t *>(take((size_t)nq * cap * 4));
     uint64_t *keys = reinterpret_cast<uint64_t *>(take((size_t)nq * k * 8));
@@ -749,7 +760,7 @@ pdx_status dense_run(const pdx_index *ix, const float *qd, int64_t nq, int32_t k
     if (nq == 0) return PDX_OK;
     {
         const unsigned grid = (unsigned)((nq * 32 + 255) / 256);
-        dense_prep_kernel<<<grid, 256, 0, st>>>(qd, nq, d, qs, qnorm, cnt, err, counters, ix->n);
+        dense_prep_kernel<<<grid, 256, 0, st>>>(qd, nq, d, qs, qnorm, cnt, ushare, err, counters, ix->n);
         cudaError_t e = counted(cudaGetLastError());
         if (e != cudaSuccess) return cuda_status_ext(e, "dense_prep_kernel");
     }
@@ -769,6 +780,7 @@ pdx_status dense_run(const pdx_index *ix, const float *qd, int64_t nq, int32_t k
     p.qnorm = qnorm;
     p.xnorm = reinterpret_cast<const float4 *>(ix->xnorm);
     p.ubuf = ubuf;
+    p.ushare = ushare;
     p.tstar = tstar;
     p.cnt = cnt;
     p.cap = cap;

@@ -214,30 +214,9 @@ struct ScanParams {
     // best over everything scanned so far, as one heap per query would give.
     float *pool;               // [nq][kPoolCap] or null
     int32_t *pool_cnt;         // [nq]
-    // First-step filter result (or null): bit b of row qi is 0 when every
-    // vector of storage block b was pruned by the first fetch step.
-    const uint32_t *block_bits;  // [nq][bit_words]
-    int32_t bit_words;
 };
 
-// First-step filter for exact PDX-BOND over FP32 blocks with per-query visit
-// orders: block_bits[qi][b / 32] bit b % 32 = some vector of block b survives
-// the first `s0` dimensions of the query's order against slack(tau[qi]).
-struct FilterParams {
-    const float *data;         // [nblocks][d][64]
-    const int32_t *blk_cnt;
-    int64_t nblocks;
-    int32_t d;
-    const float *q;            // [nq][d]
-    int64_t nq;
-    const uint16_t *qorder;    // [nq][d]
-    const float *tau;          // [nq] ordered-uint thresholds (START)
-    float gamma;
-    uint32_t *bits;            // [nq][words]
-    int32_t words;
-    unsigned long long *counters;
-};
-cudaError_t launch_first_step_filter(const FilterParams &f, int s0, int num_sms, cudaStream_t st);
+
 cudaError_t launch_scan(int pruner, int metric, const ScanParams &p, int num_sms, cudaStream_t st);
 // Visit orders for PDX-BOND (mode 0 distance to means with zones of Z, mode 1
 // decreasing query value); per_part > 0: one row per (query, part) with
@@ -270,8 +249,6 @@ struct ExactPlan {
     OrderPlan op;
     size_t mlp_bytes = 0;      // learned order: centroid keys, nearest, inputs, hidden, scores
     int64_t mlp_Lc = 0;
-    bool filter = false;       // first-step filter ahead of the scan
-    int filter_words = 0;      // 32-block words per query of its bitmap
     bool dense = false;        // tensor-core engine (pdx_dense.cu) instead of the scan
     int dense_cap = 0;         // its candidate entries per query
     size_t bytes = 0;
@@ -312,6 +289,10 @@ cudaError_t launch_quantize(const float *data, int64_t nblocks, int32_t d, int s
 // Per-row k smallest keys of a [rows][L] array (sorted ascending) -> out [rows][k].
 cudaError_t launch_select_k(const uint64_t *keys, int64_t rows, int64_t L, int32_t k, uint64_t *out,
                             cudaStream_t st);
+// The same over keys whose distance is within slack(tau[row], gamma), where
+// tau[row] is the row's final threshold (the k-th distance of k real vectors).
+cudaError_t launch_select_k_tau(const uint64_t *keys, int64_t rows, int64_t L, int32_t k, const float *tau,
+                                float gamma, uint64_t *out, cudaStream_t st);
 // tau[row] = distance of the k-th key of each row (or +inf).
 cudaError_t launch_tau_from_keys(const uint64_t *topk, int64_t rows, int32_t k, float *tau, cudaStream_t st);
 // Canonical distances of the selected results: recomputed in the natural

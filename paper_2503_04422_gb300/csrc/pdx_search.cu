@@ -433,8 +433,6 @@ __global__ void __launch_bounds__(256, PDX_SCAN_MIN_CTAS) pdxsearch_kernel(ScanP
         const float *qaux = (PR == PR_BSA) ? a.qaux + qi * a.nchk * 2 : nullptr;
 
         for (int b = b0; b < b1; ++b) {
-            // blocks the first-step filter pruned whole (it counted them)
-            if (a.block_bits && !((__ldg(a.block_bits + qi * a.bit_words + (b >> 5)) >> (b & 31)) & 1u)) continue;
             const ET *xb = xbase + (int64_t)b * D * kBlock;
             const int nvalid = a.blk_cnt[b];
             const float tau_g = o2f(*tau_g_ptr);
@@ -480,23 +478,38 @@ __global__ void __launch_bounds__(256, PDX_SCAN_MIN_CTAS) pdxsearch_kernel(ScanP
                         }
                     }
                 }
-                for (; i < e; i += 2) {
-                    int ii = i + h;
-                    if (ii < e) {
-                        const int j = w.ord[ii];
-                        const float qv = w.qo[ii];
-                        const float4 x = Elem<ST>::load4(xb + j * kBlock + 4 * sl);
-                        if (ST == ST_F32) {
-                            acc.x = term<MET>(qv, x.x, acc.x);
-                            acc.y = term<MET>(qv, x.y, acc.y);
-                            acc.z = term<MET>(qv, x.z, acc.z);
-                            acc.w = term<MET>(qv, x.w, acc.w);
-                        } else {
-                            const float s2 = (ST == ST_FP8) ? w.s2o[ii] : 1.f;
-                            acc.x = lp_term<ST, kLB>(qv, x.x, acc.x, s2);
-                            acc.y = lp_term<ST, kLB>(qv, x.y, acc.y, s2);
-                            acc.z = lp_term<ST, kLB>(qv, x.z, acc.z, s2);
-                            acc.w = lp_term<ST, kLB>(qv, x.w, acc.w, s2);
+                // the remaining (< 8) dimensions: up to 4 pairs, every load
+                // issued before the first is consumed (one round trip)
+                if (i < e) {
+                    float4 x[4];
+                    float qv[4], s2[4];
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        const int ii = i + 2 * u + h;
+                        qv[u] = 0.f;
+                        s2[u] = 1.f;
+                        x[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+                        if (ii < e) {
+                            const int j = w.ord[ii];
+                            qv[u] = w.qo[ii];
+                            if (ST == ST_FP8) s2[u] = w.s2o[ii];
+                            x[u] = Elem<ST>::load4(xb + j * kBlock + 4 * sl);
+                        }
+                    }
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        if (i + 2 * u + h < e) {
+                            if (ST == ST_F32) {
+                                acc.x = term<MET>(qv[u], x[u].x, acc.x);
+                                acc.y = term<MET>(qv[u], x[u].y, acc.y);
+                                acc.z = term<MET>(qv[u], x[u].z, acc.z);
+                                acc.w = term<MET>(qv[u], x[u].w, acc.w);
+                            } else {
+                                acc.x = lp_term<ST, kLB>(qv[u], x[u].x, acc.x, s2[u]);
+                                acc.y = lp_term<ST, kLB>(qv[u], x[u].y, acc.y, s2[u]);
+                                acc.z = lp_term<ST, kLB>(qv[u], x[u].z, acc.z, s2[u]);
+                                acc.w = lp_term<ST, kLB>(qv[u], x[u].w, acc.w, s2[u]);
+                            }
                         }
                     }
                 }
@@ -567,12 +580,31 @@ __global__ void __launch_bounds__(256, PDX_SCAN_MIN_CTAS) pdxsearch_kernel(ScanP
                     const int e = min(D, pos + step);
                     float acc1 = 0.f;
                     if (m < nsurv) {
-                        for (int i = pos + g; i < e; i += G) {
-                            const float xv = Elem<ST>::load1(xb + (int)w.ord[i] * kBlock + my_v);
-                            if (ST == ST_F32)
-                                acc1 = term<MET>(w.qo[i], xv, acc1);
-                            else
-                                acc1 = lp_term<ST, kLB>(w.qo[i], xv, acc1, (ST == ST_FP8) ? w.s2o[i] : 1.f);
+                        // 4 of this lane's dimensions per round: all loads
+                        // issued before the first is consumed
+                        for (int i = pos + g; i < e; i += 4 * G) {
+                            float xv[4], qv[4], s2[4];
+#pragma unroll
+                            for (int u = 0; u < 4; ++u) {
+                                const int ii = i + u * G;
+                                xv[u] = 0.f;
+                                qv[u] = 0.f;
+                                s2[u] = 1.f;
+                                if (ii < e) {
+                                    xv[u] = Elem<ST>::load1(xb + (int)w.ord[ii] * kBlock + my_v);
+                                    qv[u] = w.qo[ii];
+                                    if (ST == ST_FP8) s2[u] = w.s2o[ii];
+                                }
+                            }
+#pragma unroll
+                            for (int u = 0; u < 4; ++u) {
+                                if (i + u * G < e) {
+                                    if (ST == ST_F32)
+                                        acc1 = term<MET>(qv[u], xv[u], acc1);
+                                    else
+                                        acc1 = lp_term<ST, kLB>(qv[u], xv[u], acc1, s2[u]);
+                                }
+                            }
                         }
                     }
                     for (int o = G >> 1; o; o >>= 1) acc1 += __shfl_xor_sync(kFull, acc1, o);
@@ -746,105 +778,6 @@ static cudaError_t launch_scan_lp(int pruner, const ScanParams &p, int num_sms, 
     case PR_BSA: return launch_scan_t<PR_BSA, MT_L2, ST>(p, num_sms, st);
     default: return cudaErrorInvalidValue;
     }
-}
-
-// ---------------------------------------------------------------------------
-// First-step filter. In the exact search most (query, block) pairs end after
-// the first fetch step: every vector's partial over the first s0 dimensions of
-// the query's order already exceeds the threshold. Inside the scan each such
-// block costs one dependent round trip to L2 plus the block's setup. This
-// kernel evaluates only that step, for all blocks, with the query's s0
-// dimensions and values in registers and U blocks' loads in flight per warp,
-// against the START threshold (the k-th distance of k real vectors, widened by
-// the same FP32 slack as the scan). Blocks where some vector survives keep
-// their bit and are scanned in full; the others are skipped. Exactness is
-// that of the scan's own predicate.
-template <int S0, int U>
-__global__ void __launch_bounds__(256) first_step_filter_kernel(FilterParams f) {
-    const int lane = threadIdx.x & 31;
-    const int h = lane >> 4, sl = lane & 15;
-    const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    const int64_t items = (int64_t)f.words * f.nq;  // word-major: all queries of a 32-block group together
-    const int D = f.d;
-    unsigned long long c_values = 0, c_scanned = 0, c_pruned = 0;
-    for (int64_t it = gw; it < items; it += nw) {
-        const int64_t word = it / f.nq, qi = it % f.nq;
-        const int64_t b_lo = word * 32;
-        // this lane's dimensions of the first step (even/odd by half-warp) and the query values
-        int jt[S0 / 2];
-        float qv[S0 / 2];
-#pragma unroll
-        for (int t = 0; t < S0 / 2; ++t) {
-            jt[t] = f.qorder[qi * D + 2 * t + h];
-            qv[t] = f.q[qi * D + jt[t]];
-        }
-        const float tau = o2f(reinterpret_cast<const uint32_t *>(f.tau)[qi]);
-        const float thr = tau + fabsf(tau) * f.gamma;
-        const int cnt32 = (b_lo + lane < f.nblocks) ? f.blk_cnt[b_lo + lane] : 0;
-        uint32_t bits = 0;
-#pragma unroll 1
-        for (int bb = 0; bb < 32; bb += U) {
-            float4 x[U][S0 / 2];
-#pragma unroll
-            for (int u = 0; u < U; ++u) {
-                const int64_t b = b_lo + bb + u;
-                const bool in = b < f.nblocks;
-#pragma unroll
-                for (int t = 0; t < S0 / 2; ++t)
-                    x[u][t] = in ? __ldg(reinterpret_cast<const float4 *>(f.data + ((b * D + jt[t]) * kBlock + 4 * sl)))
-                                 : make_float4(0.f, 0.f, 0.f, 0.f);
-            }
-#pragma unroll
-            for (int u = 0; u < U; ++u) {
-                float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
-#pragma unroll
-                for (int t = 0; t < S0 / 2; ++t) {
-                    acc.x = term<MT_L2>(qv[t], x[u][t].x, acc.x);
-                    acc.y = term<MT_L2>(qv[t], x[u][t].y, acc.y);
-                    acc.z = term<MT_L2>(qv[t], x[u][t].z, acc.z);
-                    acc.w = term<MT_L2>(qv[t], x[u][t].w, acc.w);
-                }
-                acc.x += __shfl_xor_sync(kFull, acc.x, 16);
-                acc.y += __shfl_xor_sync(kFull, acc.y, 16);
-                acc.z += __shfl_xor_sync(kFull, acc.z, 16);
-                acc.w += __shfl_xor_sync(kFull, acc.w, 16);
-                const int nvalid = __shfl_sync(kFull, cnt32, bb + u);
-                bool alive = false;
-                alive |= (4 * sl + 0 < nvalid) && !(acc.x > thr);
-                alive |= (4 * sl + 1 < nvalid) && !(acc.y > thr);
-                alive |= (4 * sl + 2 < nvalid) && !(acc.z > thr);
-                alive |= (4 * sl + 3 < nvalid) && !(acc.w > thr);
-                const bool any = __ballot_sync(kFull, h == 0 && alive) != 0u;
-                bits |= (uint32_t)any << (bb + u);
-                c_values += (unsigned long long)S0 * nvalid;
-                if (!any) {
-                    c_scanned += nvalid;
-                    c_pruned += nvalid;
-                }
-            }
-        }
-        if (lane == 0) f.bits[qi * f.words + word] = bits;
-    }
-    if (lane == 0 && f.counters) {
-        atomicAdd(f.counters + C_VALUES, c_values);
-        atomicAdd(f.counters + C_SCANNED, c_scanned);
-        atomicAdd(f.counters + C_PRUNED, c_pruned);
-    }
-}
-
-cudaError_t launch_first_step_filter(const FilterParams &f, int s0, int num_sms, cudaStream_t st) {
-    if (f.nq == 0 || f.words == 0) return cudaSuccess;
-    const int64_t items = (int64_t)f.words * f.nq;
-    const int64_t want = (items + 7) / 8;  // 8 warps per CTA
-    const unsigned grid = (unsigned)std::min<int64_t>(want, (int64_t)num_sms * 8);
-    if (s0 == 4)
-        first_step_filter_kernel<4, 4><<<grid, 256, 0, st>>>(f);
-    else if (s0 == 8)
-        first_step_filter_kernel<8, 2><<<grid, 256, 0, st>>>(f);
-    else
-        return cudaErrorInvalidValue;
-    return counted(cudaGetLastError());
 }
 
 cudaError_t launch_scan(int pruner, int metric, const ScanParams &p, int num_sms, cudaStream_t st) {
@@ -1046,6 +979,103 @@ cudaError_t launch_select_k(const uint64_t *keys, int64_t rows, int64_t L, int32
     if (e != cudaSuccess) return e;
     int threads = sb >= 1024 ? 512 : (sb / 2 < 32 ? 32 : sb / 2);
     select_k_kernel<<<(unsigned)rows, threads, smem, st>>>(keys, L, k, kpad, sb, out);
+    return counted(cudaGetLastError());
+}
+
+// k smallest keys of each row whose distance is within the row's final
+// threshold: tau[row] is the k-th distance of k real vectors found by the
+// scan, so the k smallest keys are all within slack(tau, gamma) (the slack
+// covers FP32 sums taken in another order, e.g. by START). Keys within it are
+// compacted into shared memory and sorted; a row with more of them than the
+// buffer holds falls back to the chunked sort of select_k_kernel.
+__global__ void __launch_bounds__(512) select_k_tau_kernel(const uint64_t *__restrict__ keys, int64_t L, int32_t k,
+                                                           const float *__restrict__ tau, float gamma, int32_t sb,
+                                                           uint64_t *__restrict__ out) {
+    extern __shared__ __align__(16) uint64_t buf[];
+    __shared__ int count;
+    const int64_t row = blockIdx.x;
+    const uint64_t *src = keys + row * L;
+    const int tid = threadIdx.x, nt = blockDim.x;
+    const float t = o2f(reinterpret_cast<const uint32_t *>(tau)[row]);
+    const uint32_t lim = f2o(t + fabsf(t) * gamma);
+    if (tid == 0) count = 0;
+    __syncthreads();
+    for (int64_t i = tid; i < L; i += nt) {
+        const uint64_t key = src[i];
+        if (key != kEmptyKey && (uint32_t)(key >> 32) <= lim) {
+            const int pos = atomicAdd(&count, 1);
+            if (pos < sb) buf[pos] = key;
+        }
+    }
+    __syncthreads();
+    const int c = count;
+    if (c <= sb) {
+        int len = 1;
+        while (len < (c > k ? c : k)) len <<= 1;
+        for (int i = c + tid; i < len; i += nt) buf[i] = kEmptyKey;
+        __syncthreads();
+        for (int size = 2; size <= len; size <<= 1) {
+            for (int stride = size >> 1; stride > 0; stride >>= 1) {
+                for (int i = tid; i < (len >> 1); i += nt) {
+                    const int lo = 2 * i - (i & (stride - 1));
+                    const int hi = lo + stride;
+                    const bool asc = (lo & size) == 0;
+                    const uint64_t x = buf[lo], y = buf[hi];
+                    if ((x > y) == asc) {
+                        buf[lo] = y;
+                        buf[hi] = x;
+                    }
+                }
+                __syncthreads();
+            }
+        }
+        for (int i = tid; i < k; i += nt) out[row * k + i] = buf[i];
+        return;
+    }
+    // fallback: running best kpad of all keys, chunks appended and sorted
+    int kpad = 1;
+    while (kpad < k) kpad <<= 1;
+    for (int i = tid; i < kpad; i += nt) buf[i] = kEmptyKey;
+    const int chunk = sb - kpad;
+    for (int64_t off = 0; off < L; off += chunk) {
+        __syncthreads();
+        for (int i = tid; i < chunk; i += nt) buf[kpad + i] = (off + i < L) ? src[off + i] : kEmptyKey;
+        __syncthreads();
+        for (int size = 2; size <= sb; size <<= 1) {
+            for (int stride = size >> 1; stride > 0; stride >>= 1) {
+                for (int i = tid; i < (sb >> 1); i += nt) {
+                    const int lo = 2 * i - (i & (stride - 1));
+                    const int hi = lo + stride;
+                    const bool asc = (lo & size) == 0;
+                    const uint64_t x = buf[lo], y = buf[hi];
+                    if ((x > y) == asc) {
+                        buf[lo] = y;
+                        buf[hi] = x;
+                    }
+                }
+                __syncthreads();
+            }
+        }
+    }
+    for (int i = tid; i < k; i += nt) out[row * k + i] = buf[i];
+}
+
+cudaError_t launch_select_k_tau(const uint64_t *keys, int64_t rows, int64_t L, int32_t k, const float *tau,
+                                float gamma, uint64_t *out, cudaStream_t st) {
+    if (rows == 0) return cudaSuccess;
+    int kpad = pow2_ceil(k);
+    const int sb = std::max(8192, 2 * kpad);  // power of two (kpad <= 1024)
+    const size_t smem = (size_t)sb * 8;
+    static int have[64];
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (have[dev & 63] < (int)smem) {
+        cudaError_t e = cudaFuncSetAttribute(select_k_tau_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)smem);
+        if (e != cudaSuccess) return e;
+        have[dev & 63] = (int)smem;
+    }
+    select_k_tau_kernel<<<(unsigned)rows, 512, smem, st>>>(keys, L, k, tau, gamma, sb, out);
     return counted(cudaGetLastError());
 }
 
