@@ -340,6 +340,33 @@ def run_ours(args, rank, world, local_rank):
     if not args.no_e2e:
         e2e = _e2e(pdx, ix, q, k, opts, stream, flush, K, world, dist)
 
+    # the other exact engine on the same workload: no pruning, the L2
+    # decomposition's q.x on the tensor cores (same exact results)
+    alt = None
+    if pruner == "bond" and args.storage == "f32" and not args.no_alt:
+        ix_t = pdx.pdx_build_layout(torch.from_numpy(x).cuda(), dense_rows=True)
+        torch.cuda.synchronize()
+        opts_t = pdx.search_opts(pruner="none", engine="tensor")
+        od_t = torch.empty_like(od)
+        oi_t = torch.empty_like(oi)
+        for _ in range(args.warmup):
+            pdx.pdx_search_exact(ix_t, q_dev, k, opts=opts_t, out=(od_t, oi_t))
+        ev_t = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+        torch.cuda.synchronize()
+        for i in range(K):
+            flush.zero_()
+            ev_t[i][0].record(stream)
+            pdx.pdx_search_exact(ix_t, q_dev, k, opts=opts_t, out=(od_t, oi_t))
+            ev_t[i][1].record(stream)
+        torch.cuda.synchronize()
+        t_ms = sum(a_.elapsed_time(b_) for a_, b_ in ev_t)
+        same = bool(torch.equal(oi_t, oi))
+        alt = {"engine": "tensor (no pruning; TF32 tcgen05 GEMM, proven margins, FP32 rerank)",
+               "value": nq * world * K / (t_ms / 1e3), "unit": "queries/s", "ms_per_step": t_ms / K,
+               "same_ids_as_pdx_bond": same}
+        del ix_t
+        torch.cuda.empty_cache()
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         rate, thr, done = cpu_oracle_rate(x, q, k, budget_s=args.cpu_budget)
@@ -368,6 +395,7 @@ def run_ours(args, rank, world, local_rank):
             "gpu_launches_per_step": launches / K,
             "clocks": clk,
             "cpu_baseline": cpu,
+            "other_exact_engine": alt,
         }
         print(json.dumps(line), flush=True)
     if dist:
@@ -745,6 +773,7 @@ def main():
     ap.add_argument("--epochs", type=int, default=30, help="learned-order workload: training epochs")
     ap.add_argument("--no-f32-compare", action="store_true", help="serving workload: skip the FP32-storage stream")
     ap.add_argument("--first-step", type=int, default=None, help="exact workloads: first fetch step (default 4)")
+    ap.add_argument("--no-alt", action="store_true", help="exact workload: skip the tensor-engine companion line")
     ap.add_argument("--ctas-per-sm", type=int, default=None, help="exact workloads: resident scan CTAs per SM")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":

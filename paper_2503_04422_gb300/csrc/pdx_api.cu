@@ -590,7 +590,7 @@ pdx_status exact_plan(const pdx_index *ix, int64_t nq, int32_t k, const pdx_sear
     if (ep->dense) {
         ep->dense_cap = dense_cap(ix->n, k);
         ep->nslots = 0;
-        ep->bytes = dense_scratch_bytes(nq, ix->d, k, ep->dense_cap, ix->n) + rup(C_COUNT * 8);
+        ep->bytes = dense_scratch_bytes(nq, ix->d, k, ep->dense_cap, ix->n, sms) + rup(C_COUNT * 8);
         return PDX_OK;
     }
     ep->nslots = ix->nparts * ep->chunks;
@@ -630,7 +630,7 @@ pdx_status exact_run(const pdx_index *ix, const float *qd, int64_t nq, int32_t k
                      unsigned long long **counters_out, int sms, cudaStream_t st) {
     const int d = ix->d;
     if (ep.dense) {
-        const size_t db = dense_scratch_bytes(nq, d, k, ep.dense_cap, ix->n);
+        const size_t db = dense_scratch_bytes(nq, d, k, ep.dense_cap, ix->n, sms);
         unsigned long long *counters = reinterpret_cast<unsigned long long *>(scratch + db);
         PDX_TRY(cudaMemsetAsync(counters, 0, C_COUNT * 8, st));
         unsigned long long *kc = o.stats_device ? reinterpret_cast<unsigned long long *>(o.stats_device) : counters;

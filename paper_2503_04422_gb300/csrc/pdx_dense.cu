@@ -12,14 +12,17 @@
 //                128x32 query and 256x32 vector FP32 tiles (128-byte swizzle)
 //                into a 4-stage shared-memory ring, one thread issues
 //                tcgen05.mma kind::tf32 (M=128, N=256, K=8) into one of two
-//                TMEM accumulators, eight warps drain the other accumulator
-//                with tcgen05.ld. For every (query, vector) the epilogue forms
+//                TMEM accumulators, 8 or 16 epilogue warps drain the other
+//                accumulator with tcgen05.ld. For every (query, vector) the epilogue forms
 //                est = ||x||^2 - 2 acc (L2) or -acc (IP) and a proven error
 //                margin m (TF32 operands, FP32 accumulation; see dense_bounds),
-//                so that est - m <= exact <= est + m. The kernel runs twice:
-//                the bound pass writes the k smallest upper bounds of every
-//                (query, sub-tile of 64 or 128 vectors); the emit pass lists the vectors
-//                whose lower bound is within T*.
+//                so that est - m <= exact <= est + m. The kernel runs twice.
+//                In the bound pass each epilogue thread keeps the k smallest
+//                upper bounds of its query over all the tiles its CTA serves
+//                for that query tile (a run; the grid is a multiple of the
+//                query tiles, so one run per CTA) and appends them at the
+//                end. The emit pass lists the vectors whose lower bound is
+//                within T*.
 //   3. select    one CTA per query: T* = k-th smallest of those upper bounds,
 //                which is the k-th smallest upper bound over all vectors.
 //   4. finish    one CTA per query: every listed vector gets its exact FP32
@@ -177,11 +180,12 @@ struct DenseParams {
     int32_t d, k;
     int32_t nqt;                 // query tiles
     int64_t ntiles;              // query tiles x vector tiles
-    int64_t nsub;                // sub-tiles (TN / EW vectors) of the collection
     const float2 *qnorm;         // [nq] (||tf32(q)||, ||q - tf32(q)||), rounded up
     const float4 *xnorm;         // [n] (||x||^2, ||x||, ||x - tf32(x)||, 0), norms rounded up
-    float *ubuf;                 // bound pass: [nq][nsub][k] smallest upper bounds per sub-tile
-    uint32_t *ushare;            // bound pass: [nq] ordered bits of the smallest sub-tile k-th so far
+    float *ubuf;                 // bound pass: [nq][ucap] the k smallest upper bounds of each
+                                 // (CTA, row, column part) run, appended
+    int32_t *ucnt;               // [nq] values appended
+    int32_t ucap;
     const float *tstar;          // emit pass: [nq] k-th smallest upper bound over all vectors
     int32_t *cnt;                // [nq] entries emitted
     int32_t cap;                 // entries per query
@@ -333,6 +337,28 @@ __global__ void __launch_bounds__(Epi<EW>::threads, 1)
         const int quarter = warp & 3;
         const int part = (warp - 2) >> 2;
         const int row_in_tile = quarter * 32 + lane;
+        // bound pass: the k smallest upper bounds of this thread's row over all
+        // its tiles of one query tile (a run), appended when the run ends
+        float L[KL];
+#pragma unroll
+        for (int i = 0; i < KL; ++i) L[i] = __int_as_float(0x7f800000);
+        int64_t run_row = -1;
+        auto flush = [&]() {
+            if (MODE == 0 && run_row >= 0 && run_row < p.nq) {
+                int nf = 0;
+#pragma unroll
+                for (int i = 0; i < KL; ++i) nf += (i < p.k && L[i] < __int_as_float(0x7f800000)) ? 1 : 0;
+                if (nf > 0) {
+                    const int pos = atomicAdd(p.ucnt + run_row, nf);
+                    float *u = p.ubuf + run_row * p.ucap;
+#pragma unroll
+                    for (int i = 0; i < KL; ++i)
+                        if (i < nf && pos + i < p.ucap) u[pos + i] = L[i];
+                }
+            }
+#pragma unroll
+            for (int i = 0; i < KL; ++i) L[i] = __int_as_float(0x7f800000);
+        };
         int it = 0;
         for (int64_t t = blockIdx.x; t < p.ntiles; t += gridDim.x, ++it) {
             const int b = it & 1;
@@ -347,6 +373,10 @@ __global__ void __launch_bounds__(Epi<EW>::threads, 1)
             tc_fence_after();
             const int64_t r = (int64_t)qt * TM + row_in_tile;
             const bool rv = r < p.nq;
+            if (MODE == 0 && r != run_row) {
+                flush();
+                run_row = r;
+            }
             float P = 0.f, Q = 0.f;
             if (rv) {
                 const float2 qn = __ldg(p.qnorm + r);
@@ -355,14 +385,7 @@ __global__ void __launch_bounds__(Epi<EW>::threads, 1)
             }
             const int64_t col0 = nt * TN + part * SPAN;
             const uint32_t taddr = tbase + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(b * TN + part * SPAN);
-            float L[KL];
-#pragma unroll
-            for (int i = 0; i < KL; ++i) L[i] = __int_as_float(0x7f800000);
-            // emit pass: T*; bound pass: the smallest k-th upper bound any sub-tile
-            // has shared so far (no vector above it can change T*)
-            const float T = !rv ? __int_as_float(0xff800000)
-                                : (MODE == 1 ? __ldg(p.tstar + r)
-                                             : o2f(*reinterpret_cast<volatile uint32_t *>(p.ushare + r)));
+            const float T = (MODE == 1 && rv) ? __ldg(p.tstar + r) : __int_as_float(0xff800000);
 #pragma unroll 1
             for (int cb = 0; cb < SPAN; cb += 32) {
                 // the chunk's per-vector norms: one coalesced load, then each
@@ -381,8 +404,8 @@ __global__ void __launch_bounds__(Epi<EW>::threads, 1)
                         float lo, up;
                         dense_bounds<MET>(v[i], xn, P, Q, p, lo, up);
                         if (MODE == 0) {
-                            // bound pass: the k smallest upper bounds of this row in the sub-tile
-                            if (up <= T && up < L[KL - 1]) {
+                            // bound pass: the k smallest upper bounds of this row's run
+                            if (up < L[KL - 1]) {
                                 float x = up;
 #pragma unroll
                                 for (int j = 0; j < KL; ++j) {
@@ -399,20 +422,11 @@ __global__ void __launch_bounds__(Epi<EW>::threads, 1)
                     }
                 }
             }
-            if (MODE == 0 && rv) {
-                float *u = p.ubuf + (r * p.nsub + (nt * EW + part)) * p.k;
-#pragma unroll
-                for (int i = 0; i < KL; ++i)
-                    if (i < p.k) u[i] = L[i];
-                // the k-th of the row just written (read back rather than
-                // selected from registers by a runtime index)
-                const float kth = u[p.k - 1];
-                if (kth < T) atomicMin(p.ushare + r, f2o(kth));
-            }
             tc_fence_before();
             __syncwarp();
             if (lane == 0) mbar_arrive(tempty(b));
         }
+        flush();
     }
     // ---- teardown ----
     tc_fence_before();
@@ -444,7 +458,7 @@ __device__ __forceinline__ float norm_up(double sq) { return (float)sqrt(sq) * (
 // Queries rounded to TF32 into the aligned operand buffer, with
 // (||tf32(q)||, ||q - tf32(q)||); per-query state reset.
 __global__ void dense_prep_kernel(const float *__restrict__ q, int64_t nq, int32_t d, float *__restrict__ qs,
-                                  float2 *__restrict__ qnorm, int32_t *__restrict__ cnt, uint32_t *__restrict__ ushare,
+                                  float2 *__restrict__ qnorm, int32_t *__restrict__ cnt, int32_t *__restrict__ ucnt,
                                   int32_t *__restrict__ err, unsigned long long *counters, int64_t n) {
     const int64_t row = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
@@ -467,7 +481,7 @@ __global__ void dense_prep_kernel(const float *__restrict__ q, int64_t nq, int32
     if (lane == 0) {
         qnorm[row] = make_float2(norm_up(st), norm_up(se));
         cnt[row] = 0;
-        ushare[row] = 0xff800000u;  // ordered +inf
+        ucnt[row] = 0;
     }
 }
 
@@ -491,17 +505,24 @@ __global__ void dense_operand_kernel(const float *__restrict__ x, int64_t n, int
     if (lane == 0) out[row] = make_float4((float)sx, norm_up(sx), norm_up(se), 0.f);
 }
 
-// T*[q] = k-th smallest value of ubuf[q][0..L): a radix select over the
-// order-preserving uint32 keys, 11 + 11 + 10 bits, one CTA per query. Every
-// vector among the k smallest upper bounds of the whole collection is among
-// the k smallest of its own sub-tile, so this is the k-th smallest upper
-// bound over all vectors (+inf when fewer than k are finite).
-__global__ void __launch_bounds__(256) dense_select_kernel(const float *__restrict__ ubuf, int64_t L, int32_t k,
-                                                           float *__restrict__ tstar) {
+// T*[q] = k-th smallest value appended to ubuf[q]: a radix select over the
+// order-preserving uint32 keys, 11 + 11 + 10 bits, one CTA per query. The
+// runs partition the collection and each appended its k smallest upper
+// bounds, so every vector among the k smallest upper bounds of the whole
+// collection is there: this is the k-th smallest upper bound over all vectors
+// (+inf when fewer than k were appended). If the buffer overflowed, the k-th
+// of what it holds is larger, which only lengthens the candidate list.
+__global__ void __launch_bounds__(256) dense_select_kernel(const float *__restrict__ ubuf, const int32_t *__restrict__ ucnt,
+                                                           int32_t ucap, int32_t k, float *__restrict__ tstar) {
     __shared__ int hist[2048];
     __shared__ uint32_t s_prefix, s_want;
     const int64_t row = blockIdx.x;
-    const float *u = ubuf + row * L;
+    const float *u = ubuf + row * ucap;
+    const int64_t L = min(ucnt[row], ucap);
+    if (L < k) {  // fewer than k upper bounds: every vector is a candidate
+        if (threadIdx.x == 0) tstar[row] = __int_as_float(0x7f800000);
+        return;
+    }
     uint32_t prefix = 0, mask = 0;
     if (threadIdx.x == 0) s_want = (uint32_t)k;
     const int shifts[3] = {21, 10, 0};
@@ -698,8 +719,21 @@ cudaError_t launch_finish(const FinishParams &f, cudaStream_t st) {
     return counted(cudaGetLastError());
 }
 
-// sub-tiles of the bound pass: EW per TN-vector tile
-int64_t sub_tiles(int64_t n, int32_t k) { return (int64_t)ew_for(k <= 16 ? 16 : 64) * ((n + TN - 1) / TN); }
+// Appended upper bounds per query: k per (CTA, column part) run; with the
+// grid a multiple of the query tiles every CTA keeps one query tile, so
+// grid * EW * k bounds the count (a smaller buffer would only loosen T*).
+int32_t bound_cap(int sms, int32_t k) {
+    const int64_t c = (int64_t)sms * ew_for(k <= 16 ? 16 : 64) * k;
+    return (int32_t)std::min<int64_t>(std::max<int64_t>(c, 1024), 1 << 16);
+}
+
+// Persistent grid: a multiple of the query tiles (each CTA then serves one
+// query tile), at most one CTA per SM.
+int dense_grid(int64_t ntiles, int nqt, int sms) {
+    int g = (int)std::min<int64_t>(ntiles, (int64_t)sms);
+    if (nqt <= g) g -= g % nqt;
+    return std::max(g, 1);
+}
 
 }  // namespace
 
@@ -725,10 +759,10 @@ int dense_cap(int64_t n, int32_t k) {
     return p;
 }
 
-size_t dense_scratch_bytes(int64_t nq, int32_t d, int32_t k, int32_t cap, int64_t n) {
+size_t dense_scratch_bytes(int64_t nq, int32_t d, int32_t k, int32_t cap, int64_t n, int sms) {
     auto rup = [](size_t b) { return (b + 255) & ~size_t(255); };
     return rup((size_t)nq * d * 4) + rup((size_t)nq * 8) + 3 * rup((size_t)nq * 4) +
-           rup((size_t)nq * sub_tiles(n, k) * k * 4) +
+           rup((size_t)nq * bound_cap(sms, k) * 4) +
            rup((size_t)nq * cap * 4) + rup((size_t)nq * k * 8) + rup(8);
 }
 
@@ -736,7 +770,7 @@ pdx_status dense_run(const pdx_index *ix, const float *qd, int64_t nq, int32_t k
                      unsigned char *scratch, size_t bytes, int cap, float *od, int64_t *oi, unsigned long long *counters,
                      int sms, void *ev_start, void *ev_stop, cudaStream_t st) {
     const int d = ix->d;
-    const int64_t nsub = sub_tiles(ix->n, k);
+    const int32_t ucap = bound_cap(sms, k);
     auto rup = [](size_t b) { return (b + 255) & ~size_t(255); };
     size_t off = 0;
     auto take = [&](size_t b) {
@@ -748,8 +782,8 @@ pdx_status dense_run(const pdx_index *ix, const float *qd, int64_t nq, int32_t k
     float2 *qnorm = reinterpret_cast<float2 *>(take((size_t)nq * 8));
     float *tstar = reinterpret_cast<float *>(take((size_t)nq * 4));
     int32_t *cnt = reinterpret_cast<int32_t *>(take((size_t)nq * 4));
-    uint32_t *ushare = reinterpret_cast<uint32_t *>(take((size_t)nq * 4));
-    float *ubuf = reinterpret_cast<float *>(take((size_t)nq * nsub * k * 4));
+    int32_t *ucnt = reinterpret_cast<int32_t *>(take((size_t)nq * 4));
+    float *ubuf = reinterpret_cast<float *>(take((size_t)nq * ucap * 4));
     int32_t *ent_id = reinterpret_cast<int32_t *>(take((size_t)nq * cap * 4));
     uint64_t *keys = reinterpret_cast<uint64_t *>(take((size_t)nq * k * 8));
     int32_t *err = reinterpret_cast<int32_t *>(take(8));
@@ -760,7 +794,7 @@ pdx_status dense_run(const pdx_index *ix, const float *qd, int64_t nq, int32_t k
     if (nq == 0) return PDX_OK;
     {
         const unsigned grid = (unsigned)((nq * 32 + 255) / 256);
-        dense_prep_kernel<<<grid, 256, 0, st>>>(qd, nq, d, qs, qnorm, cnt, ushare, err, counters, ix->n);
+        dense_prep_kernel<<<grid, 256, 0, st>>>(qd, nq, d, qs, qnorm, cnt, ucnt, err, counters, ix->n);
         cudaError_t e = counted(cudaGetLastError());
         if (e != cudaSuccess) return cuda_status_ext(e, "dense_prep_kernel");
     }
@@ -776,11 +810,11 @@ pdx_status dense_run(const pdx_index *ix, const float *qd, int64_t nq, int32_t k
     p.k = k;
     p.nqt = (int32_t)((nq + TM - 1) / TM);
     p.ntiles = (int64_t)p.nqt * ((ix->n + TN - 1) / TN);
-    p.nsub = nsub;
     p.qnorm = qnorm;
     p.xnorm = reinterpret_cast<const float4 *>(ix->xnorm);
     p.ubuf = ubuf;
-    p.ushare = ushare;
+    p.ucnt = ucnt;
+    p.ucap = ucap;
     p.tstar = tstar;
     p.cnt = cnt;
     p.cap = cap;
@@ -796,14 +830,14 @@ pdx_status dense_run(const pdx_index *ix, const float *qd, int64_t nq, int32_t k
     p.c_xx = (float)(u);
     p.c_rel = (float)(4.0 * u);
     p.err = err;
-    const int grid = (int)std::min<int64_t>(p.ntiles, (int64_t)sms);
+    const int grid = dense_grid(p.ntiles, p.nqt, sms);
     cudaError_t e;
     if (ev_start && (e = cudaEventRecord(static_cast<cudaEvent_t>(ev_start), st)) != cudaSuccess)
         return cuda_status_ext(e, "cudaEventRecord");
-    // pass 1: per sub-tile, the k smallest upper bounds; then T* per query
+    // pass 1: per run, the k smallest upper bounds; then T* per query
     if ((e = launch_tc_any<0>(mq, mx, p, grid, metric, st)) != cudaSuccess)
         return cuda_status_ext(e, "dense_tc_kernel (bound pass)");
-    dense_select_kernel<<<(unsigned)nq, 256, 0, st>>>(ubuf, nsub * k, k, tstar);
+    dense_select_kernel<<<(unsigned)nq, 256, 0, st>>>(ubuf, ucnt, ucap, k, tstar);
     if ((e = counted(cudaGetLastError())) != cudaSuccess) return cuda_status_ext(e, "dense_select_kernel");
     // pass 2: emit the vectors whose lower bound is within T*
     if ((e = launch_tc_any<1>(mq, mx, p, grid, metric, st)) != cudaSuccess)

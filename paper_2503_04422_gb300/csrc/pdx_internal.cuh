@@ -265,7 +265,7 @@ void fill_stats(pdx_search_stats *so, const unsigned long long *c, const pdx_ind
 // Tensor-core dense engine (pdx_dense.cu).
 bool dense_supported(const pdx_index *ix, int32_t k, const char **why);
 int dense_cap(int64_t n, int32_t k);
-size_t dense_scratch_bytes(int64_t nq, int32_t d, int32_t k, int32_t cap, int64_t n);
+size_t dense_scratch_bytes(int64_t nq, int32_t d, int32_t k, int32_t cap, int64_t n, int sms);
 pdx_status dense_run(const pdx_index *ix, const float *qd, int64_t nq, int32_t k, int metric, int out_mode,
                      unsigned char *scratch, size_t bytes, int cap, float *od, int64_t *oi, unsigned long long *counters,
                      int sms, void *ev_start, void *ev_stop, cudaStream_t st);
