@@ -46,6 +46,7 @@
 #include <algorithm>
 #include <atomic>
 #include <cmath>
+#include <cstdlib>
 #include <mutex>
 
 #include "pdx_internal.cuh"
@@ -192,6 +193,8 @@ struct DenseParams {
     int32_t *ent_id;             // [nq][cap] emitted vector ids
     float k2, c_acc, c_xx, c_rel;  // margin coefficients (see dense_bounds)
     int32_t *err;                // set when a wait gave up
+    int32_t stall_test;          // test hook: the producer issues no loads, so the
+                                 // first wait of the MMA thread runs out
 };
 
 // Error margin of est for one (query, vector) pair. Both operands are
@@ -265,7 +268,7 @@ __global__ void __launch_bounds__(Epi<EW>::threads, 1)
 
     if (warp == 0) {
         // ---- TMA producer ----
-        if (lane == 0) {
+        if (lane == 0 && !p.stall_test) {
             int s = 0;
             uint32_t ph = 0;
             uint32_t issued = 0, last_par = 0;  // per stage: loads issued, parity of the last one
@@ -830,6 +833,12 @@ pdx_status dense_run(const pdx_index *ix, const float *qd, int64_t nq, int32_t k
     p.c_xx = (float)(u);
     p.c_rel = (float)(4.0 * u);
     p.err = err;
+    // test hook for the bounded waits (tests/test_gpu_dense.py): with
+    // PDX_TEST_DENSE_STALL=1 no tile is loaded, every GEMM wait runs out after
+    // its limit, the kernel releases TMEM and flags the error, and the finish
+    // kernel answers every query by the plain FP32 scan
+    const char *stall = std::getenv("PDX_TEST_DENSE_STALL");
+    p.stall_test = (stall && stall[0] == '1') ? 1 : 0;
     const int grid = dense_grid(p.ntiles, p.nqt, sms);
     cudaError_t e;
     if (ev_start && (e = cudaEventRecord(static_cast<cudaEvent_t>(ev_start), st)) != cudaSuccess)

@@ -171,3 +171,22 @@ def test_full_size_1m_d768_sampled(P, torch):
     assert st["dense_fallbacks"] == 0
     rows = np.random.default_rng(2).choice(q.shape[0], size=6, replace=False)
     check_topk(x, q, 10, d, i, rows=rows)
+
+
+def test_gemm_wait_timeout_is_reported_and_answered(P, torch, monkeypatch):
+    # test hook: the GEMM's producer loads nothing, so its MMA thread's first
+    # wait runs out after its 2 s limit. The kernel releases TMEM and flags the
+    # error; the finish kernel then answers every query by the plain FP32 scan.
+    # No fault is involved, and the context stays usable.
+    rng = np.random.default_rng(16)
+    x = rng.standard_normal((3000, 64)).astype(np.float32)
+    q = rng.standard_normal((8, 64)).astype(np.float32)
+    ix = P.pdx_build_layout(_dev(torch, x), dense_rows=True)
+    monkeypatch.setenv("PDX_TEST_DENSE_STALL", "1")
+    d, i, st = _search(P, torch, ix, q, 10)
+    assert st["dense_fallbacks"] == q.shape[0]
+    check_topk(x, q, 10, d, i)
+    monkeypatch.delenv("PDX_TEST_DENSE_STALL")
+    d, i, st = _search(P, torch, ix, q, 10)
+    assert st["dense_fallbacks"] == 0
+    check_topk(x, q, 10, d, i)
