@@ -119,7 +119,12 @@ typedef struct pdx_build_opts {
                                   that the index keeps (n*d*4 bytes); L2 and unit-norm IP  */
     uint32_t partition_size;   /* exact search: at most this many vectors per PDXearch
                                   block, equal horizontal partitions (Sec. 6.6; 10000)    */
-    int32_t keep_fp32_rerank;  /* low-precision storage: keep an FP32 copy (default 1)     */
+    int32_t keep_rows;         /* keep the vectors row-major in FP32 (n*d*4 bytes, default
+                                  1). BF16/FP8 storage always keeps them: they are its
+                                  rerank source. With FP32 storage the scan uses them to
+                                  finish PRUNE phases that start with at most 8 survivors
+                                  (exact distances from contiguous rows instead of one
+                                  memory sector per value of the dimension-major block). */
     int32_t dense_rows;        /* keep, for the tensor-core dense engine, the vectors
                                   row-major in FP32 (the rerank source), a copy rounded to
                                   TF32 (the GEMM operand) and per-row norms: n*(2d+4)*4

@@ -224,6 +224,16 @@ static pdx_status finish_low_precision(pdx_index *ix, const float *xrows, cudaSt
     return PDX_OK;
 }
 
+// Row-major FP32 vectors by id (the scan finishes few-survivor PRUNE phases
+// from them; low-precision storage keeps them as its rerank source).
+static pdx_status keep_rows(pdx_index *ix, const float *xrows, cudaStream_t st) {
+    if (ix->xnary) return PDX_OK;
+    PDX_TRY(dalloc(ix, &ix->xnary, (size_t)ix->n * ix->d));
+    PDX_TRY(cudaMemcpyAsync(ix->xnary, xrows, (size_t)ix->n * ix->d * 4, cudaMemcpyDeviceToDevice, st));
+    PDX_TRY(cudaStreamSynchronize(st));
+    return PDX_OK;
+}
+
 // Tensor-core dense engine: the exact row-major FP32 vectors (rerank; already
 // there for low-precision storage), their TF32-rounded copy (the GEMM
 // operand) and per-row norms.
@@ -253,7 +263,7 @@ void pdx_default_build_opts(pdx_build_opts *o) {
     o->metric = PDX_L2;
     o->storage = PDX_F32;
     o->partition_size = 10000;
-    o->keep_fp32_rerank = 1;
+    o->keep_rows = 1;
 }
 
 void pdx_default_ivf_opts(pdx_ivf_opts *o) {
@@ -422,6 +432,7 @@ pdx_status pdx_build_layout(const float *x, int64_t n, int32_t d, const pdx_buil
             if (e != cudaSuccess) s = cuda_status(e, "cudaStreamSynchronize", __LINE__);
         }
         if (s == PDX_OK && o.storage != PDX_F32) s = finish_low_precision(ix, xd, st);
+        if (s == PDX_OK && o.storage == PDX_F32 && o.keep_rows) s = keep_rows(ix, xd, st);
         if (s == PDX_OK && o.dense_rows) s = keep_dense_rows(ix, xd, st);
     }
     if (s != PDX_OK) {
@@ -754,10 +765,12 @@ pdx_status exact_run(const pdx_index *ix, const float *qd, int64_t nq, int32_t k
     PDX_TRY(launch_scan(pl.pruner, pl.metric, p, sms, st));
     if (o.scan_event_stop) PDX_TRY(cudaEventRecord(static_cast<cudaEvent_t>(o.scan_event_stop), st));
     PDX_TRY(launch_select_k_tau(cand, nq, (int64_t)ep.nslots * k, k, tau, p.gamma, topk, st));
-    if (ix->storage == PDX_F32)
-        PDX_TRY(launch_refine(topk, nq, k, qd, d, ix->data, ix->slot_of, ix->metric, refined, st));
-    else
+    // canonical distances: from the contiguous rows when the index keeps them
+    // (same lanes, order and reduction as from the blocks, so the same bits)
+    if (ix->xnary && ix->metric != PDX_L1)
         PDX_TRY(launch_refine_rows(topk, nq, k, qd, d, ix->xnary, ix->metric, refined, st));
+    else
+        PDX_TRY(launch_refine(topk, nq, k, qd, d, ix->data, ix->slot_of, ix->metric, refined, st));
     PDX_TRY(launch_select_k(refined, nq, k, k, final_keys, st));
     PDX_TRY(launch_write_out(final_keys, nq, k, pl.out_mode, qd, d, od, oi, st));
     return PDX_OK;
@@ -1030,6 +1043,7 @@ static pdx_status ivf_build_impl(pdx_index *ix, const float *x, const pdx_ivf_op
     }
     PDX_TRY(cudaStreamSynchronize(st));
     if (ix->storage != PDX_F32) return finish_low_precision(ix, xt, st);
+    if (o.base.keep_rows) return keep_rows(ix, xt, st);
     return PDX_OK;
 }
 
@@ -1257,10 +1271,10 @@ extern "C" pdx_status pdx_search_ivf(const pdx_index *ix, const float *q, int64_
     }
     if (o.scan_event_stop) PDX_TRY(cudaEventRecord(static_cast<cudaEvent_t>(o.scan_event_stop), st));
     PDX_TRY(launch_select_k(cand, nq, (int64_t)nprobe * k, k, topk, st));
-    if (ix->storage == PDX_F32)
-        PDX_TRY(launch_refine(topk, nq, k, qt, d, ix->data, ix->slot_of, ix->metric, refined, st));
-    else
+    if (ix->xnary && ix->metric != PDX_L1)
         PDX_TRY(launch_refine_rows(topk, nq, k, qt, d, ix->xnary, ix->metric, refined, st));
+    else
+        PDX_TRY(launch_refine(topk, nq, k, qt, d, ix->data, ix->slot_of, ix->metric, refined, st));
     PDX_TRY(launch_select_k(refined, nq, k, k, final_keys, st));
     PDX_TRY(launch_write_out(final_keys, nq, k, pl.out_mode, qt, d, od, oi, st));
     if (!o_dev) {

@@ -387,6 +387,34 @@ __device__ __forceinline__ uint32_t pool_kth(const ScanParams &a, int64_t qi, in
     return prefix;
 }
 
+// Full distance of one stored vector from its row of the row-major FP32 copy
+// (warp-uniform result): lanes take dimensions j = lane, lane + 32, ..., so
+// each request reads 128 contiguous bytes. The predicate is kept: every 128
+// dimensions the warp compares the row's partial sum (a lower bound of the
+// distance for L2 / L1, whatever dimensions it covers) with thr and gives up
+// once it is above. Returns the full distance, or +inf for a pruned vector;
+// *read counts the values read.
+template <int MET>
+__device__ __forceinline__ float row_dist_pruned(const float *__restrict__ xrow, const float *__restrict__ qrow,
+                                                 int D, int lane, float thr, int *read) {
+    float acc = 0.f;
+    int j0 = 0;
+    for (; j0 < D; j0 += 128) {
+        const int j1 = min(D, j0 + 128);
+        for (int j = j0 + lane; j < j1; j += 32) acc = term<MET>(qrow[j], __ldg(xrow + j), acc);
+        if (MET != MT_IP && j1 < D && warp_sum(acc) > thr) {
+            *read = j1;
+            return __int_as_float(0x7f800000);
+        }
+    }
+    *read = D;
+    return rank_dist<MET>(warp_sum(acc));
+}
+
+// PRUNE phases that start with at most this many survivors finish from the
+// row-major copy when the index keeps one (see the kernel).
+constexpr int kRowFinish = 8;
+
 template <int PR, int MET, int ST>
 __global__ void __launch_bounds__(256, PDX_SCAN_MIN_CTAS) pdxsearch_kernel(ScanParams a) {
     using ET = typename Elem<ST>::T;
@@ -564,11 +592,18 @@ __global__ void __launch_bounds__(256, PDX_SCAN_MIN_CTAS) pdxsearch_kernel(ScanP
                 }
             }
             // ---------------- PRUNE ----------------
-            // Survivor m owns G = 32 / pow2(nsurv) consecutive lanes; its lanes
+            // A few survivors: in the dimension-major block every remaining value
+            // of one vector sits in its own 256-byte slice, one memory sector per
+            // 4-byte value. With a row-major FP32 copy of the vectors their exact
+            // distances are finished from contiguous rows instead (D / 32 coalesced
+            // 128-byte requests per vector); the merge below takes them as full
+            // distances, as it does after the last PRUNE step.
+            const bool rows = nsurv > 0 && nsurv <= kRowFinish && a.xnary != nullptr;
+            // Otherwise survivor m owns G = 32 / pow2(nsurv) consecutive lanes; its lanes
             // stride over the step's dimensions, so all lanes stay busy for any
             // mix of survivor count and step size, and a log2(G) shuffle tree
             // reduces each survivor's step sum.
-            if (nsurv > 0) {
+            if (nsurv > 0 && !rows) {
                 int G = 32 / pow2_ceil(nsurv);
                 int m = lane / G, g = lane % G;
                 if (m < nsurv) {
@@ -687,6 +722,28 @@ __global__ void __launch_bounds__(256, PDX_SCAN_MIN_CTAS) pdxsearch_kernel(ScanP
                 unsigned m2 = __ballot_sync(kFull, alive & 4u) & 0xffffu;
                 unsigned m3 = __ballot_sync(kFull, alive & 8u) & 0xffffu;
                 nfinal = __popc(m0) + __popc(m1) + __popc(m2) + __popc(m3);
+            } else if (rows) {
+                // the predicate threshold, the same for the whole warp
+                const float rthr = __shfl_sync(kFull, slack(fminf(tau_loc, o2f(*tau_g_ptr)), a.gamma), 0);
+                int rows_pruned = 0;
+                for (int m = 0; m < nsurv; ++m) {
+                    const int v = w.sv[m];
+                    const int id = a.ids[(int64_t)b * kBlock + v];
+                    int read = 0;
+                    const float dd = row_dist_pruned<MET>(a.xnary + (int64_t)id * D, qrow, D, lane, rthr, &read);
+                    c_values += (lane == 0) ? (unsigned long long)read : 0ull;
+                    if (read < D) ++rows_pruned;
+                    // lane 0 reads the shared threshold and the warp follows it
+                    if (__shfl_sync(kFull, (int)(dd <= slack(o2f(*tau_g_ptr), a.gamma)), 0)) {
+                        topk_insert(w.topk, cnt, k, make_key(dd, id), lane);
+                        ++c_cand;
+                        if (a.pool && __shfl_sync(kFull, (int)(f2o(dd) < *tau_g_ptr), 0)) {
+                            pool_push(a, qi, dd, lane);
+                            pushed = true;
+                        }
+                    }
+                }
+                nfinal = nsurv - rows_pruned;
             } else if (nsurv > 0) {
                 float dist = rank_dist<MET>(my_p);
                 bool cand = (lane < nsurv) && (dist <= slack(o2f(*tau_g_ptr), a.gamma));

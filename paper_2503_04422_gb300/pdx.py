@@ -33,7 +33,7 @@ STATUS_NAMES = {0: "PDX_OK", 1: "PDX_ERR_ARG", 2: "PDX_ERR_OOM", 3: "PDX_ERR_CUD
 
 class pdx_build_opts(ctypes.Structure):
     _fields_ = [("struct_size", ctypes.c_uint32), ("metric", ctypes.c_int), ("storage", ctypes.c_int),
-                ("partition_size", ctypes.c_uint32), ("keep_fp32_rerank", ctypes.c_int32),
+                ("partition_size", ctypes.c_uint32), ("keep_rows", ctypes.c_int32),
                 ("dense_rows", ctypes.c_int32)]
 
 
@@ -199,14 +199,14 @@ class Index:
             pass
 
 
-def build_opts(metric="l2", storage="f32", partition_size=10000, keep_fp32_rerank=True,
+def build_opts(metric="l2", storage="f32", partition_size=10000, keep_rows=True,
                dense_rows=False) -> pdx_build_opts:
     o = pdx_build_opts()
     lib().pdx_default_build_opts(ctypes.byref(o))
     o.metric = METRIC[metric]
     o.storage = DTYPE[storage]
     o.partition_size = partition_size
-    o.keep_fp32_rerank = int(bool(keep_fp32_rerank))
+    o.keep_rows = int(bool(keep_rows))
     o.dense_rows = int(bool(dense_rows))
     return o
 
