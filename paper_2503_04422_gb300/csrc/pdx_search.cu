@@ -389,31 +389,21 @@ __device__ __forceinline__ uint32_t pool_kth(const ScanParams &a, int64_t qi, in
 
 // Full distance of one stored vector from its row of the row-major FP32 copy
 // (warp-uniform result): lanes take dimensions j = lane, lane + 32, ..., so
-// each request reads 128 contiguous bytes. The predicate is kept: every 128
-// dimensions the warp compares the row's partial sum (a lower bound of the
-// distance for L2 / L1, whatever dimensions it covers) with thr and gives up
-// once it is above. Returns the full distance, or +inf for a pruned vector;
-// *read counts the values read.
+// each request reads 128 contiguous bytes.
 template <int MET>
-__device__ __forceinline__ float row_dist_pruned(const float *__restrict__ xrow, const float *__restrict__ qrow,
-                                                 int D, int lane, float thr, int *read) {
+__device__ __forceinline__ float row_dist(const float *__restrict__ xrow, const float *__restrict__ qrow, int D,
+                                          int lane) {
     float acc = 0.f;
-    int j0 = 0;
-    for (; j0 < D; j0 += 128) {
-        const int j1 = min(D, j0 + 128);
-        for (int j = j0 + lane; j < j1; j += 32) acc = term<MET>(qrow[j], __ldg(xrow + j), acc);
-        if (MET != MT_IP && j1 < D && warp_sum(acc) > thr) {
-            *read = j1;
-            return __int_as_float(0x7f800000);
-        }
-    }
-    *read = D;
+    for (int j = lane; j < D; j += 32) acc = term<MET>(qrow[j], __ldg(xrow + j), acc);
     return rank_dist<MET>(warp_sum(acc));
 }
 
-// PRUNE phases that start with at most this many survivors finish from the
-// row-major copy when the index keeps one (see the kernel).
+// PRUNE phases with at most this many survivors finish from the row-major
+// copy when the index keeps one: at once when every survivor is far below the
+// threshold, else once kPruneBudget further dimensions have not pruned them
+// (see the kernel).
 constexpr int kRowFinish = 8;
+constexpr int kPruneBudget = 32;
 
 template <int PR, int MET, int ST>
 __global__ void __launch_bounds__(256, PDX_SCAN_MIN_CTAS) pdxsearch_kernel(ScanParams a) {
@@ -598,12 +588,23 @@ __global__ void __launch_bounds__(256, PDX_SCAN_MIN_CTAS) pdxsearch_kernel(ScanP
             // distances are finished from contiguous rows instead (D / 32 coalesced
             // 128-byte requests per vector); the merge below takes them as full
             // distances, as it does after the last PRUNE step.
-            const bool rows = nsurv > 0 && nsurv <= kRowFinish && a.xnary != nullptr;
+            // Only survivors still far below the threshold (partial < thr / 2 after
+            // the dimensions visited so far, e.g. cluster-mates of the query,
+            // which need nearly all dimensions) go to the rows; a block with a
+            // survivor near the threshold keeps the PRUNE phase, whose visit
+            // order prunes such vectors within a few more dimensions.
+            bool rows = false;
+            if (nsurv > 0 && nsurv <= kRowFinish && a.xnary != nullptr) {
+                float spmax = 0.f;
+                for (int m = 0; m < nsurv; ++m) spmax = fmaxf(spmax, w.sp[m]);
+                rows = __shfl_sync(kFull, (int)(spmax < 0.5f * thr), 0) != 0;
+            }
             // Otherwise survivor m owns G = 32 / pow2(nsurv) consecutive lanes; its lanes
             // stride over the step's dimensions, so all lanes stay busy for any
             // mix of survivor count and step size, and a log2(G) shuffle tree
             // reduces each survivor's step sum.
             if (nsurv > 0 && !rows) {
+                const int prune_pos0 = pos;
                 int G = 32 / pow2_ceil(nsurv);
                 int m = lane / G, g = lane % G;
                 if (m < nsurv) {
@@ -676,6 +677,12 @@ __global__ void __launch_bounds__(256, PDX_SCAN_MIN_CTAS) pdxsearch_kernel(ScanP
                         m = mn;
                         g = lane % Gn;
                     }
+                    // survivors that kPruneBudget more dimensions did not prune
+                    // need most of the remaining ones: finish them from the rows
+                    if (a.xnary != nullptr && nsurv <= kRowFinish && pos - prune_pos0 >= kPruneBudget) {
+                        rows = true;
+                        break;
+                    }
                 }
                 // survivors' leaders hold (my_v, my_p) at lanes m*G; gather them
                 // to lanes 0..nsurv-1 for the merge below
@@ -685,6 +692,10 @@ __global__ void __launch_bounds__(256, PDX_SCAN_MIN_CTAS) pdxsearch_kernel(ScanP
                     int nv = __shfl_sync(kFull, my_v, src & 31);
                     my_p = np;
                     my_v = nv;
+                    if (rows) {
+                        if (lane < nsurv) w.sv[lane] = my_v;
+                        __syncwarp();
+                    }
                 }
             }
             // ---------------- merge ----------------
@@ -723,16 +734,11 @@ __global__ void __launch_bounds__(256, PDX_SCAN_MIN_CTAS) pdxsearch_kernel(ScanP
                 unsigned m3 = __ballot_sync(kFull, alive & 8u) & 0xffffu;
                 nfinal = __popc(m0) + __popc(m1) + __popc(m2) + __popc(m3);
             } else if (rows) {
-                // the predicate threshold, the same for the whole warp
-                const float rthr = __shfl_sync(kFull, slack(fminf(tau_loc, o2f(*tau_g_ptr)), a.gamma), 0);
-                int rows_pruned = 0;
                 for (int m = 0; m < nsurv; ++m) {
                     const int v = w.sv[m];
                     const int id = a.ids[(int64_t)b * kBlock + v];
-                    int read = 0;
-                    const float dd = row_dist_pruned<MET>(a.xnary + (int64_t)id * D, qrow, D, lane, rthr, &read);
-                    c_values += (lane == 0) ? (unsigned long long)read : 0ull;
-                    if (read < D) ++rows_pruned;
+                    const float dd = row_dist<MET>(a.xnary + (int64_t)id * D, qrow, D, lane);
+                    c_values += (lane == 0) ? (unsigned long long)D : 0ull;
                     // lane 0 reads the shared threshold and the warp follows it
                     if (__shfl_sync(kFull, (int)(dd <= slack(o2f(*tau_g_ptr), a.gamma)), 0)) {
                         topk_insert(w.topk, cnt, k, make_key(dd, id), lane);
@@ -743,7 +749,7 @@ __global__ void __launch_bounds__(256, PDX_SCAN_MIN_CTAS) pdxsearch_kernel(ScanP
                         }
                     }
                 }
-                nfinal = nsurv - rows_pruned;
+                nfinal = nsurv;
             } else if (nsurv > 0) {
                 float dist = rank_dist<MET>(my_p);
                 bool cand = (lane < nsurv) && (dist <= slack(o2f(*tau_g_ptr), a.gamma));
