@@ -498,7 +498,7 @@ pdx_status check_search_args(const pdx_index *ix, const float *q, int64_t nq, in
     // resolve the automatic choices
     if (o->means_scope == PDX_MEANS_AUTO) o->means_scope = ix->is_ivf ? PDX_MEANS_BLOCK : PDX_MEANS_COLLECTION;
     if (o->zone_dims == 0) o->zone_dims = (o->means_scope == PDX_MEANS_COLLECTION) ? 1 : 8;
-    if (o->ctas_per_sm == 0) o->ctas_per_sm = 3;
+    // ctas_per_sm 0: the scan's own default (4 for FP32 blocks, 3 for BF16/FP8)
     return PDX_OK;
 }
 

@@ -330,11 +330,10 @@ __device__ __forceinline__ bool prune_test(float partial, float thr, int dv, int
     }
 }
 
-// Minimum resident CTAs per SM the register allocation must allow (a build-time
-// tuning knob; 1 leaves the compiler free).
-#ifndef PDX_SCAN_MIN_CTAS
-#define PDX_SCAN_MIN_CTAS 3
-#endif
+// Resident CTAs per SM the register allocation is built for (OCC): 3 (80
+// registers, 24 warps per SM) or, for FP32 blocks, 4 (64 registers, 32 warps).
+// BF16/FP8 blocks stay at 3: their lower-bound arithmetic would spill at 64.
+// The launcher takes 4 when four CTAs' shared memory still leaves room for L1.
 
 // Exact FP32 L2 distance of one stored vector (row of the N-ary FP32 copy)
 // to the query; lanes take dimensions j = lane, lane + 32, ... (warp-uniform).
@@ -405,8 +404,8 @@ __device__ __forceinline__ float row_dist(const float *__restrict__ xrow, const 
 constexpr int kRowFinish = 8;
 constexpr int kPruneBudget = 32;
 
-template <int PR, int MET, int ST>
-__global__ void __launch_bounds__(256, PDX_SCAN_MIN_CTAS) pdxsearch_kernel(ScanParams a) {
+template <int PR, int MET, int ST, int OCC>
+__global__ void __launch_bounds__(256, OCC) pdxsearch_kernel(ScanParams a) {
     using ET = typename Elem<ST>::T;
     constexpr bool kLB = (PR == PR_BOND || PR == PR_NONE);  // low-precision: prune on a lower bound
     extern __shared__ __align__(16) unsigned char smem[];
@@ -807,13 +806,16 @@ static cudaError_t launch_scan_t(const ScanParams &p, int num_sms, cudaStream_t 
     while (warps > 1 && per_warp * warps > 200 * 1024) warps >>= 1;
     const size_t smem = per_warp * warps;
     if (smem > 227 * 1024) return cudaErrorInvalidValue;
-    auto kern = pdxsearch_kernel<PR, MET, ST>;
+    // 4 resident CTAs (the 64-register build) when the storage allows it and
+    // four CTAs' shared memory leaves at least 32 KB of the SM for L1
+    const bool four = ST == ST_F32 && p.ctas_per_sm != 3 && 4 * (smem + 1024) + 32 * 1024 <= 228 * 1024;
+    auto kern = four ? pdxsearch_kernel<PR, MET, ST, (ST == ST_F32 ? 4 : 3)> : pdxsearch_kernel<PR, MET, ST, 3>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     // Shared-memory carveout sized for the requested number of resident CTAs
     // (1 KB reserved per CTA); what remains of the SM's on-chip memory is L1,
     // which holds the lines of the scan's loads in flight.
-    const int want = p.ctas_per_sm > 0 ? p.ctas_per_sm : 3;
+    const int want = p.ctas_per_sm > 0 ? (int)p.ctas_per_sm : (four ? 4 : 3);
     int pct = (int)((want * (smem + 1024) * 100 + 228 * 1024 - 1) / (228 * 1024));
     if (pct > 100) pct = 100;
     if (pct < 1) pct = 1;
