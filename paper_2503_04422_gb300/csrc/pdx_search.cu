@@ -448,6 +448,15 @@ __global__ void __launch_bounds__(256, OCC) pdxsearch_kernel(ScanParams a) {
         int cnt = 0;
         float tau_loc = __int_as_float(0x7f800000);
         const float *qaux = (PR == PR_BSA) ? a.qaux + qi * a.nchk * 2 : nullptr;
+        // PDX-BOND: blocks in pairs for the first fetch step (4 dimensions):
+        // both blocks' loads go out together, and the second block's partials
+        // wait in registers for the next iteration, so blocks that end after
+        // this step (most of them, in exact search) cost half a round trip to
+        // L2. ADSampling and BSA bounds are loose after 4 dimensions, blocks
+        // rarely end there, and the kernels skip the pairing.
+        const bool pair = (PR == PR_BOND) && a.first_step == 4 && D > 4;
+        bool pre_valid = false;
+        float4 pre = make_float4(0.f, 0.f, 0.f, 0.f);
 
         for (int b = b0; b < b1; ++b) {
             const ET *xb = xbase + (int64_t)b * D * kBlock;
@@ -465,10 +474,66 @@ __global__ void __launch_bounds__(256, OCC) pdxsearch_kernel(ScanParams a) {
             int nsurv = -1;  // -1: still in WARMUP
             float my_p = 0.f;
             int my_v = 0;
+            bool first_done = false;
+            if (pair) {
+                if (pre_valid) {
+                    acc = pre;
+                    pre_valid = false;
+                } else {
+                    // positions h and 2 + h of the order: the same terms, in the
+                    // same order, as the generic first step below
+                    const int j0 = w.ord[h], j1 = w.ord[2 + h];
+                    const float q0 = w.qo[h], q1 = w.qo[2 + h];
+                    const float s0 = (ST == ST_FP8) ? w.s2o[h] : 1.f, s1 = (ST == ST_FP8) ? w.s2o[2 + h] : 1.f;
+                    const bool nxt = b + 1 < b1;
+                    const float4 x0 = Elem<ST>::load4(xb + j0 * kBlock + 4 * sl);
+                    const float4 x1 = Elem<ST>::load4(xb + j1 * kBlock + 4 * sl);
+                    float4 y0 = make_float4(0.f, 0.f, 0.f, 0.f), y1 = y0;
+                    if (nxt) {
+                        const ET *xn = xb + (int64_t)D * kBlock;
+                        y0 = Elem<ST>::load4(xn + j0 * kBlock + 4 * sl);
+                        y1 = Elem<ST>::load4(xn + j1 * kBlock + 4 * sl);
+                    }
+                    float4 pn = make_float4(0.f, 0.f, 0.f, 0.f);
+                    if (ST == ST_F32) {
+                        acc.x = term<MET>(q0, x0.x, acc.x);
+                        acc.y = term<MET>(q0, x0.y, acc.y);
+                        acc.z = term<MET>(q0, x0.z, acc.z);
+                        acc.w = term<MET>(q0, x0.w, acc.w);
+                        acc.x = term<MET>(q1, x1.x, acc.x);
+                        acc.y = term<MET>(q1, x1.y, acc.y);
+                        acc.z = term<MET>(q1, x1.z, acc.z);
+                        acc.w = term<MET>(q1, x1.w, acc.w);
+                        pn.x = term<MET>(q1, y1.x, term<MET>(q0, y0.x, 0.f));
+                        pn.y = term<MET>(q1, y1.y, term<MET>(q0, y0.y, 0.f));
+                        pn.z = term<MET>(q1, y1.z, term<MET>(q0, y0.z, 0.f));
+                        pn.w = term<MET>(q1, y1.w, term<MET>(q0, y0.w, 0.f));
+                    } else {
+                        acc.x = lp_term<ST, kLB>(q0, x0.x, acc.x, s0);
+                        acc.y = lp_term<ST, kLB>(q0, x0.y, acc.y, s0);
+                        acc.z = lp_term<ST, kLB>(q0, x0.z, acc.z, s0);
+                        acc.w = lp_term<ST, kLB>(q0, x0.w, acc.w, s0);
+                        acc.x = lp_term<ST, kLB>(q1, x1.x, acc.x, s1);
+                        acc.y = lp_term<ST, kLB>(q1, x1.y, acc.y, s1);
+                        acc.z = lp_term<ST, kLB>(q1, x1.z, acc.z, s1);
+                        acc.w = lp_term<ST, kLB>(q1, x1.w, acc.w, s1);
+                        pn.x = lp_term<ST, kLB>(q1, y1.x, lp_term<ST, kLB>(q0, y0.x, 0.f, s0), s1);
+                        pn.y = lp_term<ST, kLB>(q1, y1.y, lp_term<ST, kLB>(q0, y0.y, 0.f, s0), s1);
+                        pn.z = lp_term<ST, kLB>(q1, y1.z, lp_term<ST, kLB>(q0, y0.z, 0.f, s0), s1);
+                        pn.w = lp_term<ST, kLB>(q1, y1.w, lp_term<ST, kLB>(q0, y0.w, 0.f, s0), s1);
+                    }
+                    if (nxt) {
+                        pre = pn;
+                        pre_valid = true;
+                    }
+                }
+                first_done = true;
+            }
             // ---------------- WARMUP ----------------
             while (pos < D) {
                 const int e = min(D, pos + step);
-                int i = pos;
+                int i = first_done ? e : pos;  // the paired first step is already in acc
+                first_done = false;
                 for (; i + 8 <= e; i += 8) {
                     float4 x[4];
                     float qv[4], s2[4];
