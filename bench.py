@@ -252,7 +252,8 @@ def run_ours(args, rank, world, local_rank):
     stats_dev = torch.zeros(16, dtype=torch.int64, device="cuda")
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")   # > 129 MB L2
     opts = pdx.search_opts(pruner=pruner, engine=engine if pruner == "none" else "auto",
-                           first_step=args.first_step, ctas_per_sm=args.ctas_per_sm)
+                           first_step=args.first_step, ctas_per_sm=args.ctas_per_sm,
+                           start_vectors=args.start_vectors)
     stream = torch.cuda.current_stream()
 
     def step(ev_scan=None):
@@ -454,7 +455,7 @@ def run_ivf(args, rank, world, local_rank):
         ix = built[tr]
         rows = []
         for nprobe in (8, 16, 32, 64, 128):
-            opts = pdx.search_opts(pruner=pruner)
+            opts = pdx.search_opts(pruner=pruner, first_step=args.first_step, ctas_per_sm=args.ctas_per_sm)
             for _ in range(args.warmup):
                 pdx.pdx_search_ivf(ix, qd, k, nprobe, opts=opts, out=(od, oi))
             ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
@@ -772,9 +773,10 @@ def main():
     ap.add_argument("--traces", type=int, default=None, help="learned-order workload: training queries")
     ap.add_argument("--epochs", type=int, default=30, help="learned-order workload: training epochs")
     ap.add_argument("--no-f32-compare", action="store_true", help="serving workload: skip the FP32-storage stream")
-    ap.add_argument("--first-step", type=int, default=None, help="exact workloads: first fetch step (default 4)")
+    ap.add_argument("--first-step", type=int, default=None, help="exact and IVF workloads: first fetch step (default 4)")
     ap.add_argument("--no-alt", action="store_true", help="exact workload: skip the tensor-engine companion line")
-    ap.add_argument("--ctas-per-sm", type=int, default=None, help="exact workloads: resident scan CTAs per SM")
+    ap.add_argument("--ctas-per-sm", type=int, default=None, help="exact and IVF workloads: resident scan CTAs per SM")
+    ap.add_argument("--start-vectors", type=int, default=None, help="exact workloads: START scan size (default 4096)")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3

@@ -174,7 +174,7 @@ typedef struct pdx_search_opts {
     uint32_t first_step;       /* first fetch step in dimensions, then doubling (default 4;
                                   the paper's CPU setting is 2). BSA searches always use the
                                   schedule their index stored residual norms for (4).      */
-    uint32_t start_vectors;    /* exact search: vectors of the START scan (0 = one block)  */
+    uint32_t start_vectors;    /* exact search: vectors of the START scan (default 1024; 0 = one block) */
     uint32_t blocks_per_item;  /* 64-vector blocks per GPU work item (0 = automatic)       */
     pdx_search_stats *stats_out; /* optional host pointer; filled after the search (the call
                                   then synchronises `stream`)                               */

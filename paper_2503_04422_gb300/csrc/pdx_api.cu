@@ -291,7 +291,7 @@ void pdx_default_search_opts(pdx_search_opts *o) {
     o->first_step = 4;
     o->means_scope = PDX_MEANS_AUTO;
     o->ctas_per_sm = 0;
-    o->start_vectors = 4096;
+    o->start_vectors = 1024;
     o->blocks_per_item = 0;
     o->stats_out = nullptr;
 }

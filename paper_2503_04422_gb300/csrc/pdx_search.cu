@@ -139,7 +139,12 @@ struct WarpSmem {
     uint64_t *topk;     // [k]
     int32_t *sv;        // [kMaxSurv] survivor slot indices
     float *sp;          // [kMaxSurv] survivor partial distances
+    unsigned long long *ctr;  // [kStats] the warp's statistics; lane 0 adds to them
 };
+
+// Statistics a scan warp keeps in shared memory (registers are the scarce
+// resource of the scan) and adds to the launch counters when it ends.
+enum ScanStat { S_VALUES = 0, S_SCANNED, S_PRUNED, S_PBLOCKS, S_CAND, S_ITEMS, kStats };
 
 // The scan kernel sorts at most kMaxSortUnits zone keys itself, in registers
 // (8 per lane); finer orders are computed once per query (or per query and
@@ -164,7 +169,7 @@ __host__ __device__ inline int sort_units(int d, int zone_dims, int order, int p
 
 __host__ __device__ inline size_t warp_smem_bytes(int d, int k, bool scaled) {
     return align16((size_t)d * 2) + align16((size_t)d * 4) * (scaled ? 2 : 1) + align16((size_t)k * 8) +
-           align16(kMaxSurv * 4) * 2;
+           align16(kMaxSurv * 4) * 2 + align16(kStats * 8);
 }
 
 size_t scan_warp_smem(int d, int k, int zone_dims, int order) {
@@ -190,6 +195,8 @@ __device__ __forceinline__ WarpSmem carve(unsigned char *base, int d, int k, boo
     w.sv = reinterpret_cast<int32_t *>(base + o);
     o += align16(kMaxSurv * 4);
     w.sp = reinterpret_cast<float *>(base + o);
+    o += align16(kMaxSurv * 4);
+    w.ctr = reinterpret_cast<unsigned long long *>(base + o);
     return w;
 }
 
@@ -417,7 +424,8 @@ __global__ void __launch_bounds__(256, OCC) pdxsearch_kernel(ScanParams a) {
     const int h = lane >> 4, sl = lane & 15;
     const int k = a.k;
     const int chunks = a.chunks_per_part;
-    unsigned long long c_values = 0, c_scanned = 0, c_pruned = 0, c_pblocks = 0, c_cand = 0, c_items = 0;
+    if (lane < kStats) w.ctr[lane] = 0;
+    __syncwarp();
 
     while (true) {
         unsigned long long wi = 0;
@@ -438,13 +446,20 @@ __global__ void __launch_bounds__(256, OCC) pdxsearch_kernel(ScanParams a) {
             for (int i = lane; i < k; i += 32) out[i] = kEmptyKey;
             continue;
         }
-        ++c_items;
+        if (lane == 0) w.ctr[S_ITEMS] += 1;
         const float *qrow = a.q + qi * D;
         const uint16_t *given = nullptr;
         if (a.qorder) given = a.qorder + (a.qorder_per_part ? (qi * (a.nslots / chunks) + pr) : qi) * (int64_t)D;
+        volatile uint32_t *tau_g_ptr = reinterpret_cast<volatile uint32_t *>(a.tau) + qi;
+        // The query's shared τ is read one block ahead: the read a block uses
+        // went out with the previous block's loads (the first one before the
+        // visit order is built), so a block whose first step is already in
+        // registers waits for no load at all. τ only decreases, so a value one
+        // block old still bounds the final k-th distance, and the warp's own
+        // candidates are in tau_loc.
+        float tau_ahead = o2f(*tau_g_ptr);
         build_order(w, qrow, a.means ? a.means + (int64_t)part * D : nullptr, given,
                     (ST == ST_FP8) ? a.scale : nullptr, D, a.zone_dims, nunits, lane);
-        volatile uint32_t *tau_g_ptr = reinterpret_cast<volatile uint32_t *>(a.tau) + qi;
         int cnt = 0;
         float tau_loc = __int_as_float(0x7f800000);
         const float *qaux = (PR == PR_BSA) ? a.qaux + qi * a.nchk * 2 : nullptr;
@@ -461,13 +476,14 @@ __global__ void __launch_bounds__(256, OCC) pdxsearch_kernel(ScanParams a) {
         for (int b = b0; b < b1; ++b) {
             const ET *xb = xbase + (int64_t)b * D * kBlock;
             const int nvalid = a.blk_cnt[b];
-            const float tau_g = o2f(*tau_g_ptr);
+            const float tau_g = tau_ahead;
+            tau_ahead = o2f(*tau_g_ptr);
             const float thr = slack(fminf(tau_loc, tau_g), a.gamma);
             unsigned alive = 0;
 #pragma unroll
             for (int c = 0; c < 4; ++c)
                 if (4 * sl + c < nvalid) alive |= 1u << c;
-            c_scanned += (lane == 0) ? nvalid : 0;
+            if (lane == 0) w.ctr[S_SCANNED] += nvalid;
             float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
             int pos = 0, step = (PR == PR_NONE) ? D : max(1, a.first_step);
             int chk = 0;
@@ -595,7 +611,7 @@ __global__ void __launch_bounds__(256, OCC) pdxsearch_kernel(ScanParams a) {
                         }
                     }
                 }
-                c_values += (lane == 0) ? (unsigned long long)(e - pos) * nvalid : 0ull;
+                if (lane == 0) w.ctr[S_VALUES] += (unsigned long long)(e - pos) * nvalid;
                 pos = e;
                 step <<= 1;
                 if (PR == PR_NONE || pos >= D) break;
@@ -641,7 +657,7 @@ __global__ void __launch_bounds__(256, OCC) pdxsearch_kernel(ScanParams a) {
                     }
                     __syncwarp();
                     nsurv = nalive;
-                    ++c_pblocks;
+                    if (lane == 0) w.ctr[S_PBLOCKS] += 1;
                     break;
                 }
             }
@@ -709,7 +725,7 @@ __global__ void __launch_bounds__(256, OCC) pdxsearch_kernel(ScanParams a) {
                     }
                     for (int o = G >> 1; o; o >>= 1) acc1 += __shfl_xor_sync(kFull, acc1, o);
                     my_p += acc1;
-                    c_values += (lane == 0) ? (unsigned long long)(e - pos) * nsurv : 0ull;
+                    if (lane == 0) w.ctr[S_VALUES] += (unsigned long long)(e - pos) * nsurv;
                     pos = e;
                     step <<= 1;
                     if (pos >= D) break;
@@ -784,7 +800,7 @@ __global__ void __launch_bounds__(256, OCC) pdxsearch_kernel(ScanParams a) {
                         if (ST != ST_F32) dd = rerank_l2(a.xnary + (int64_t)id * D, qrow, D, lane);  // exact FP32
                         uint64_t key = make_key(dd, id);
                         topk_insert(w.topk, cnt, k, key, lane);
-                        ++c_cand;
+                        if (lane == 0) w.ctr[S_CAND] += 1;
                         // lane 0 reads the shared threshold and the warp follows it
                         if (a.pool && __shfl_sync(kFull, (int)(f2o(dd) < *tau_g_ptr), 0)) {
                             pool_push(a, qi, dd, lane);
@@ -802,11 +818,11 @@ __global__ void __launch_bounds__(256, OCC) pdxsearch_kernel(ScanParams a) {
                     const int v = w.sv[m];
                     const int id = a.ids[(int64_t)b * kBlock + v];
                     const float dd = row_dist<MET>(a.xnary + (int64_t)id * D, qrow, D, lane);
-                    c_values += (lane == 0) ? (unsigned long long)D : 0ull;
+                    if (lane == 0) w.ctr[S_VALUES] += (unsigned long long)D;
                     // lane 0 reads the shared threshold and the warp follows it
                     if (__shfl_sync(kFull, (int)(dd <= slack(o2f(*tau_g_ptr), a.gamma)), 0)) {
                         topk_insert(w.topk, cnt, k, make_key(dd, id), lane);
-                        ++c_cand;
+                        if (lane == 0) w.ctr[S_CAND] += 1;
                         if (a.pool && __shfl_sync(kFull, (int)(f2o(dd) < *tau_g_ptr), 0)) {
                             pool_push(a, qi, dd, lane);
                             pushed = true;
@@ -827,7 +843,7 @@ __global__ void __launch_bounds__(256, OCC) pdxsearch_kernel(ScanParams a) {
                     if (ST != ST_F32) dd = rerank_l2(a.xnary + (int64_t)id * D, qrow, D, lane);  // exact FP32
                     uint64_t key = make_key(dd, id);
                     topk_insert(w.topk, cnt, k, key, lane);
-                    ++c_cand;
+                    if (lane == 0) w.ctr[S_CAND] += 1;
                     if (a.pool && __shfl_sync(kFull, (int)(f2o(dd) < *tau_g_ptr), 0)) {
                         pool_push(a, qi, dd, lane);
                         pushed = true;
@@ -835,7 +851,7 @@ __global__ void __launch_bounds__(256, OCC) pdxsearch_kernel(ScanParams a) {
                 }
                 nfinal = nsurv;
             }
-            c_pruned += (lane == 0) ? (unsigned long long)(nvalid - nfinal) : 0ull;
+            if (lane == 0) w.ctr[S_PRUNED] += (unsigned long long)(nvalid - nfinal);
             if (cnt == k) {
                 float t = key_dist(w.topk[k - 1]);
                 if (t < tau_loc) {
@@ -852,13 +868,14 @@ __global__ void __launch_bounds__(256, OCC) pdxsearch_kernel(ScanParams a) {
         for (int i = lane; i < k; i += 32) out[i] = (i < cnt) ? w.topk[i] : kEmptyKey;
         __syncwarp();
     }
+    __syncwarp();
     if (lane == 0 && a.counters) {
-        atomicAdd(a.counters + C_VALUES, c_values);
-        atomicAdd(a.counters + C_SCANNED, c_scanned);
-        atomicAdd(a.counters + C_PRUNED, c_pruned);
-        atomicAdd(a.counters + C_PRUNE_BLOCKS, c_pblocks);
-        atomicAdd(a.counters + C_CANDIDATES, c_cand);
-        atomicAdd(a.counters + C_ITEMS, c_items);
+        atomicAdd(a.counters + C_VALUES, w.ctr[S_VALUES]);
+        atomicAdd(a.counters + C_SCANNED, w.ctr[S_SCANNED]);
+        atomicAdd(a.counters + C_PRUNED, w.ctr[S_PRUNED]);
+        atomicAdd(a.counters + C_PRUNE_BLOCKS, w.ctr[S_PBLOCKS]);
+        atomicAdd(a.counters + C_CANDIDATES, w.ctr[S_CAND]);
+        atomicAdd(a.counters + C_ITEMS, w.ctr[S_ITEMS]);
     }
 }
 
