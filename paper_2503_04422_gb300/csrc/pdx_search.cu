@@ -458,8 +458,18 @@ __global__ void __launch_bounds__(256, OCC) pdxsearch_kernel(ScanParams a) {
         // block old still bounds the final k-th distance, and the warp's own
         // candidates are in tau_loc.
         float tau_ahead = o2f(*tau_g_ptr);
+        // Every block of a part but its last holds 64 vectors (parts fill their
+        // blocks in order), so only an item's last block reads its count. The
+        // item's vectors count as scanned and as pruned up front; blocks take
+        // back from the pruned count the vectors that reach the merge.
+        const int last_cnt = a.blk_cnt[b1 - 1];
         build_order(w, qrow, a.means ? a.means + (int64_t)part * D : nullptr, given,
                     (ST == ST_FP8) ? a.scale : nullptr, D, a.zone_dims, nunits, lane);
+        if (lane == 0) {
+            const unsigned long long nv = (unsigned long long)(b1 - b0 - 1) * kBlock + (unsigned)last_cnt;
+            w.ctr[S_SCANNED] += nv;
+            w.ctr[S_PRUNED] += nv;
+        }
         int cnt = 0;
         float tau_loc = __int_as_float(0x7f800000);
         const float *qaux = (PR == PR_BSA) ? a.qaux + qi * a.nchk * 2 : nullptr;
@@ -475,7 +485,7 @@ __global__ void __launch_bounds__(256, OCC) pdxsearch_kernel(ScanParams a) {
 
         for (int b = b0; b < b1; ++b) {
             const ET *xb = xbase + (int64_t)b * D * kBlock;
-            const int nvalid = a.blk_cnt[b];
+            const int nvalid = (b == b1 - 1) ? a.blk_cnt[b] : kBlock;
             const float tau_g = tau_ahead;
             tau_ahead = o2f(*tau_g_ptr);
             const float thr = slack(fminf(tau_loc, tau_g), a.gamma);
@@ -483,7 +493,6 @@ __global__ void __launch_bounds__(256, OCC) pdxsearch_kernel(ScanParams a) {
 #pragma unroll
             for (int c = 0; c < 4; ++c)
                 if (4 * sl + c < nvalid) alive |= 1u << c;
-            if (lane == 0) w.ctr[S_SCANNED] += nvalid;
             float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
             int pos = 0, step = (PR == PR_NONE) ? D : max(1, a.first_step);
             int chk = 0;
@@ -611,7 +620,6 @@ __global__ void __launch_bounds__(256, OCC) pdxsearch_kernel(ScanParams a) {
                         }
                     }
                 }
-                if (lane == 0) w.ctr[S_VALUES] += (unsigned long long)(e - pos) * nvalid;
                 pos = e;
                 step <<= 1;
                 if (PR == PR_NONE || pos >= D) break;
@@ -632,15 +640,15 @@ __global__ void __launch_bounds__(256, OCC) pdxsearch_kernel(ScanParams a) {
                     if (prune_test<PR>(sel4(f, c), thr, pos, D, a.eps0, rx2, rq2, sd2, a.bsa_m)) alive &= ~(1u << c);
                 }
                 ++chk;
+                if (!__any_sync(kFull, alive != 0u)) {
+                    nsurv = 0;
+                    break;
+                }
                 unsigned m0 = __ballot_sync(kFull, alive & 1u) & 0xffffu;
                 unsigned m1 = __ballot_sync(kFull, alive & 2u) & 0xffffu;
                 unsigned m2 = __ballot_sync(kFull, alive & 4u) & 0xffffu;
                 unsigned m3 = __ballot_sync(kFull, alive & 8u) & 0xffffu;
                 int nalive = __popc(m0) + __popc(m1) + __popc(m2) + __popc(m3);
-                if (nalive == 0) {
-                    nsurv = 0;
-                    break;
-                }
                 if (nalive <= a.sel_count) {
                     // PRUNE: positions array of the survivors, in slot order
                     unsigned below = (1u << sl) - 1u;
@@ -661,6 +669,8 @@ __global__ void __launch_bounds__(256, OCC) pdxsearch_kernel(ScanParams a) {
                     break;
                 }
             }
+            // values of the WARMUP steps: the first pos dimensions of every vector
+            if (lane == 0) w.ctr[S_VALUES] += (unsigned long long)pos * nvalid;
             // ---------------- PRUNE ----------------
             // A few survivors: in the dimension-major block every remaining value
             // of one vector sits in its own 256-byte slice, one memory sector per
@@ -851,7 +861,7 @@ __global__ void __launch_bounds__(256, OCC) pdxsearch_kernel(ScanParams a) {
                 }
                 nfinal = nsurv;
             }
-            if (lane == 0) w.ctr[S_PRUNED] += (unsigned long long)(nvalid - nfinal);
+            if (nfinal > 0 && lane == 0) w.ctr[S_PRUNED] -= (unsigned long long)nfinal;
             if (cnt == k) {
                 float t = key_dist(w.topk[k - 1]);
                 if (t < tau_loc) {
