@@ -425,7 +425,8 @@ void pdx_free(pdx_index *index);
 pdx_status pdx_merge_topk(const float *dist, const int64_t *idx, int32_t nshards, int64_t nq, int32_t k,
                           pdx_metric metric, float *out_dist, int64_t *out_idx, void *stream);
 
-/* Number of CUDA kernels this process has launched through the library. */
+/* Number of CUDA kernels this process has launched through the library; a
+ * server's graph replay counts each kernel node of the graph. */
 uint64_t pdx_kernel_launches(void);
 
 /* Message of the last non-OK status on this thread ("" if none). */

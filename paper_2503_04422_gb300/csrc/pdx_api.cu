@@ -17,7 +17,8 @@ namespace pdx {
 static thread_local std::string g_err;
 static std::atomic<unsigned long long> g_launches{0};
 
-void count_launches(int n) { g_launches.fetch_add((unsigned long long)n, std::memory_order_relaxed); }
+// n < 0 takes back launches that a stream capture recorded (modular arithmetic)
+void count_launches(int n) { g_launches.fetch_add((unsigned long long)(long long)n, std::memory_order_relaxed); }
 
 void set_error(const char *fmt, ...) {
     char buf[1024];

@@ -465,10 +465,14 @@ __global__ void __launch_bounds__(256, OCC) pdxsearch_kernel(ScanParams a) {
         const int last_cnt = a.blk_cnt[b1 - 1];
         build_order(w, qrow, a.means ? a.means + (int64_t)part * D : nullptr, given,
                     (ST == ST_FP8) ? a.scale : nullptr, D, a.zone_dims, nunits, lane);
+        // every vector takes the first fetch step: its values are counted here,
+        // those of later WARMUP steps by the blocks that take them
+        const int s0 = min(D, (PR == PR_NONE) ? D : max(1, a.first_step));
         if (lane == 0) {
             const unsigned long long nv = (unsigned long long)(b1 - b0 - 1) * kBlock + (unsigned)last_cnt;
             w.ctr[S_SCANNED] += nv;
             w.ctr[S_PRUNED] += nv;
+            w.ctr[S_VALUES] += nv * (unsigned)s0;
         }
         int cnt = 0;
         float tau_loc = __int_as_float(0x7f800000);
@@ -489,10 +493,13 @@ __global__ void __launch_bounds__(256, OCC) pdxsearch_kernel(ScanParams a) {
             const float tau_g = tau_ahead;
             tau_ahead = o2f(*tau_g_ptr);
             const float thr = slack(fminf(tau_loc, tau_g), a.gamma);
-            unsigned alive = 0;
+            unsigned alive = 0xfu;
+            if (nvalid < kBlock) {
+                alive = 0;
 #pragma unroll
-            for (int c = 0; c < 4; ++c)
-                if (4 * sl + c < nvalid) alive |= 1u << c;
+                for (int c = 0; c < 4; ++c)
+                    if (4 * sl + c < nvalid) alive |= 1u << c;
+            }
             float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
             int pos = 0, step = (PR == PR_NONE) ? D : max(1, a.first_step);
             int chk = 0;
@@ -669,8 +676,8 @@ __global__ void __launch_bounds__(256, OCC) pdxsearch_kernel(ScanParams a) {
                     break;
                 }
             }
-            // values of the WARMUP steps: the first pos dimensions of every vector
-            if (lane == 0) w.ctr[S_VALUES] += (unsigned long long)pos * nvalid;
+            // values of the WARMUP steps after the first: dimensions s0..pos of every vector
+            if (pos > s0 && lane == 0) w.ctr[S_VALUES] += (unsigned long long)(pos - s0) * nvalid;
             // ---------------- PRUNE ----------------
             // A few survivors: in the dimension-major block every remaining value
             // of one vector sits in its own 256-byte slice, one memory sector per
@@ -862,7 +869,7 @@ __global__ void __launch_bounds__(256, OCC) pdxsearch_kernel(ScanParams a) {
                 nfinal = nsurv;
             }
             if (nfinal > 0 && lane == 0) w.ctr[S_PRUNED] -= (unsigned long long)nfinal;
-            if (cnt == k) {
+            if (nfinal > 0 && cnt == k) {  // the list changes only through vectors that reach the merge
                 float t = key_dist(w.topk[k - 1]);
                 if (t < tau_loc) {
                     tau_loc = t;

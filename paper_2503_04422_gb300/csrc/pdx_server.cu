@@ -30,6 +30,7 @@ struct ServerEntry {
     ExactPlan ep;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
+    int kernels = 0;  // kernel nodes of the graph: each replay launches them all
     float tuned_ms = 0.f;
 };
 
@@ -218,7 +219,11 @@ static pdx_status prepare_entry(pdx_server *s, int c, int bk) {
         if (r != PDX_OK) return r;
         cudaError_t e = cudaStreamBeginCapture(s->st, cudaStreamCaptureModeThreadLocal);
         if (e != cudaSuccess) return cuda_status_ext(e, "cudaStreamBeginCapture");
+        // captured launches run only when the graph is replayed, and are
+        // counted then
+        const uint64_t before = pdx_kernel_launches();
         r = exact_run(ix, s->qbuf, B, s->o.k, o, pl, E.ep, s->work, s->obuf_d, s->obuf_i, nullptr, s->sms, s->st);
+        count_launches(-(int)(pdx_kernel_launches() - before));
         cudaGraph_t g = nullptr;
         e = cudaStreamEndCapture(s->st, &g);
         if (r != PDX_OK) {
@@ -227,6 +232,19 @@ static pdx_status prepare_entry(pdx_server *s, int c, int bk) {
         }
         if (e != cudaSuccess) return cuda_status_ext(e, "cudaStreamEndCapture");
         E.graph = g;
+        size_t nn = 0;
+        e = cudaGraphGetNodes(g, nullptr, &nn);
+        if (e != cudaSuccess) return cuda_status_ext(e, "cudaGraphGetNodes");
+        std::vector<cudaGraphNode_t> nodes(nn);
+        if (nn > 0) {
+            e = cudaGraphGetNodes(g, nodes.data(), &nn);
+            if (e != cudaSuccess) return cuda_status_ext(e, "cudaGraphGetNodes");
+        }
+        E.kernels = 0;
+        for (cudaGraphNode_t n : nodes) {
+            cudaGraphNodeType t;
+            if (cudaGraphNodeGetType(n, &t) == cudaSuccess && t == cudaGraphNodeTypeKernel) ++E.kernels;
+        }
         e = cudaGraphInstantiate(&E.exec, g, 0);
         if (e != cudaSuccess) return cuda_status_ext(e, "cudaGraphInstantiate");
     }
@@ -391,6 +409,7 @@ extern "C" pdx_status pdx_server_search(pdx_server *s, int32_t collection, const
     }
     if (E.exec) {
         SRV_TRY(cudaGraphLaunch(E.exec, s->st));
+        count_launches(E.kernels);
         s->graph_launches += 1;
     } else {
         pdx_status r = exact_run(ix, s->qbuf, (int64_t)1 << bk, k, E.opts, E.pl, E.ep, s->work, s->obuf_d, s->obuf_i,

@@ -47,6 +47,7 @@ def test_server_batches_are_exact(P, torch, collections, graphs, tune, tmp_path)
                    tune_cache=cache if tune else None)
     rng = np.random.default_rng(1)
     stream = [(int(rng.integers(0, 3)), int(b)) for b in [1, 3, 17, 64, 5, 3, 64, 33, 1]]
+    launches0 = P.pdx_kernel_launches()
     for coll, b in stream:
         x, q, _ = collections[coll]
         sel = rng.choice(q.shape[0], size=b, replace=False)
@@ -57,6 +58,8 @@ def test_server_batches_are_exact(P, torch, collections, graphs, tune, tmp_path)
         dh, ih = srv.search(coll, qq)                 # host buffers
         assert np.array_equal(ih, i.cpu().numpy())
     info = srv.info
+    # every batch runs the library's kernels, graph replays included
+    assert P.pdx_kernel_launches() - launches0 >= 2 * len(stream)
     if graphs:
         assert info["graph_launches"] > 0 and info["direct_launches"] == 0
     else:
