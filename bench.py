@@ -559,7 +559,8 @@ def run_learned(args, rank, world, local_rank):
     train_s = time.perf_counter() - t0
     heur = pdx.search_opts(pruner="bond")
     learned = pdx.search_opts(pruner="bond", order="learned", mlp=net, mlp_centroids=cent)
-    # fallback / judge on a validation split
+    # the heuristic order is the fallback: the learned one is used only if it
+    # visits fewer values on a validation split
     _, iv_h, sv_h = pdx.pdx_search_exact(ix, q_val, k, opts=pdx.search_opts(pruner="bond"), stats=True)
     _, iv_l, sv_l = pdx.pdx_search_exact(ix, q_val, k, opts=pdx.search_opts(pruner="bond", order="learned", mlp=net,
                                                                              mlp_centroids=cent), stats=True)

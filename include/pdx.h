@@ -51,7 +51,7 @@ typedef enum pdx_status {
     PDX_ERR_OOM = 2,          /* device allocation failed                     */
     PDX_ERR_CUDA = 3,         /* a CUDA call failed                           */
     PDX_ERR_TIMEOUT = 4,      /* a bounded device wait ran out                */
-    PDX_ERR_UNSUPPORTED = 5   /* valid request this build does not implement  */
+    PDX_ERR_UNSUPPORTED = 5   /* valid request the library does not implement */
 } pdx_status;
 
 /* Sec. 2.1: squared Euclidean distance, inner product (similarity, larger is

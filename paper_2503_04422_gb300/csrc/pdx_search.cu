@@ -467,12 +467,12 @@ __global__ void __launch_bounds__(256, OCC) pdxsearch_kernel(ScanParams a) {
                     (ST == ST_FP8) ? a.scale : nullptr, D, a.zone_dims, nunits, lane);
         // every vector takes the first fetch step: its values are counted here,
         // those of later WARMUP steps by the blocks that take them
-        const int s0 = min(D, (PR == PR_NONE) ? D : max(1, a.first_step));
+        const int fs0 = min(D, (PR == PR_NONE) ? D : max(1, a.first_step));
         if (lane == 0) {
             const unsigned long long nv = (unsigned long long)(b1 - b0 - 1) * kBlock + (unsigned)last_cnt;
             w.ctr[S_SCANNED] += nv;
             w.ctr[S_PRUNED] += nv;
-            w.ctr[S_VALUES] += nv * (unsigned)s0;
+            w.ctr[S_VALUES] += nv * (unsigned)fs0;
         }
         int cnt = 0;
         float tau_loc = __int_as_float(0x7f800000);
@@ -676,8 +676,8 @@ __global__ void __launch_bounds__(256, OCC) pdxsearch_kernel(ScanParams a) {
                     break;
                 }
             }
-            // values of the WARMUP steps after the first: dimensions s0..pos of every vector
-            if (pos > s0 && lane == 0) w.ctr[S_VALUES] += (unsigned long long)(pos - s0) * nvalid;
+            // values of the WARMUP steps after the first: dimensions fs0..pos of every vector
+            if (pos > fs0 && lane == 0) w.ctr[S_VALUES] += (unsigned long long)(pos - fs0) * nvalid;
             // ---------------- PRUNE ----------------
             // A few survivors: in the dimension-major block every remaining value
             // of one vector sits in its own 256-byte slice, one memory sector per
