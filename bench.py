@@ -384,7 +384,7 @@ def run_ours(args, rank, world, local_rank):
                        "order": "dist_to_means",
                        "means": "collection (automatic for exact search)", "zone_dims": "1 (automatic)",
                        "first_step": int(opts.first_step), "selection_threshold": round(float(opts.selection_threshold), 3),
-                       "start_vectors": int(opts.start_vectors), "ctas_per_sm": int(opts.ctas_per_sm) or "automatic (4 for FP32 blocks when they fit with 32 KB of L1, else 3)",
+                       "start_vectors": int(opts.start_vectors), "ctas_per_sm": int(opts.ctas_per_sm) or "automatic (4 when four CTAs fit with 32 KB of L1, else 3)",
                        "l2": (f"collection {n * d * 4 / 1e9:.3g} GB; 256 MB L2 flush between timed steps "
                               "(untimed)")},
             "roofline": roofline,

@@ -185,11 +185,11 @@ typedef struct pdx_search_opts {
                                   PDXearch scan kernel                                        */
     void *scan_event_stop;     /* optional cudaEvent_t recorded just after it                 */
     pdx_means_scope means_scope; /* distance-to-means order: block or collection means (AUTO) */
-    uint32_t ctas_per_sm;      /* resident scan CTAs per SM (0 = 4 for FP32 blocks when four
-                                  CTAs' shared memory leaves 32 KB for L1, else 3). The
-                                  shared-memory carveout
-                                  is sized for exactly this many, and the rest of each SM's
-                                  on-chip memory serves as L1 for the loads in flight.     */
+    uint32_t ctas_per_sm;      /* resident scan CTAs per SM (0 = 4 when four CTAs' shared
+                                  memory leaves 32 KB for L1, else 3). The shared-memory
+                                  carveout is sized for exactly this many, and the rest of
+                                  each SM's on-chip memory serves as L1 for the loads in
+                                  flight.                                                  */
     pdx_mlp *mlp;              /* PDX_ORDER_LEARNED: the network (exact indexes)           */
     const float *mlp_centroids;/* PDX_ORDER_LEARNED: device [mlp_ncentroids][d]; each query
                                   is paired with its nearest one as the network input      */

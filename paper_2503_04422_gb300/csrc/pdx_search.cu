@@ -905,10 +905,10 @@ static cudaError_t launch_scan_t(const ScanParams &p, int num_sms, cudaStream_t 
     while (warps > 1 && per_warp * warps > 200 * 1024) warps >>= 1;
     const size_t smem = per_warp * warps;
     if (smem > 227 * 1024) return cudaErrorInvalidValue;
-    // 4 resident CTAs (the 64-register build) when the storage allows it and
-    // four CTAs' shared memory leaves at least 32 KB of the SM for L1
-    const bool four = ST == ST_F32 && p.ctas_per_sm != 3 && 4 * (smem + 1024) + 32 * 1024 <= 228 * 1024;
-    auto kern = four ? pdxsearch_kernel<PR, MET, ST, (ST == ST_F32 ? 4 : 3)> : pdxsearch_kernel<PR, MET, ST, 3>;
+    // 4 resident CTAs (the 64-register build) when four CTAs' shared memory
+    // leaves at least 32 KB of the SM for L1
+    const bool four = p.ctas_per_sm != 3 && 4 * (smem + 1024) + 32 * 1024 <= 228 * 1024;
+    auto kern = four ? pdxsearch_kernel<PR, MET, ST, 4> : pdxsearch_kernel<PR, MET, ST, 3>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     // Shared-memory carveout sized for the requested number of resident CTAs
