@@ -64,3 +64,40 @@ def test_adam_lowers_loss():
 
 def test_order_from_scores():
     assert M.order_from_scores(np.array([0.5, 2.0, 2.0, -1.0])).tolist() == [1, 2, 0, 3]
+
+
+def test_adam_two_steps_hand_worked():
+    # tests/golden/ads_bsa_worked.json "adam": two steps worked out by hand
+    import json
+    import os
+    g = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "ads_bsa_worked.json")))["adam"]
+    p = [np.array([g["p0"]])]
+    m = [np.zeros(1)]
+    v = [np.zeros(1)]
+    for t, (gr, want) in enumerate(zip(g["grads"], g["p_after"]), start=1):
+        M.adam_step(p, [np.array([gr])], m, v, t, lr=g["lr"])
+        assert abs(p[0][0] - want) < 1e-6
+
+
+def test_adam_constant_gradient_moves_lr_per_step():
+    # with bias correction, a constant gradient g gives m_hat = g and
+    # v_hat = g^2 at every step, so each step moves exactly lr against sign(g)
+    # (up to eps); without the correction the first step would be 3.16 lr
+    p = [np.array([0.0, 1.0, -2.0])]
+    g = np.array([0.3, -7.0, 0.5])
+    m, v = [np.zeros(3)], [np.zeros(3)]
+    for t in range(1, 6):
+        M.adam_step(p, [g], m, v, t, lr=0.01)
+        np.testing.assert_allclose(p[0], np.array([0.0, 1.0, -2.0]) - 0.01 * t * np.sign(g), rtol=0, atol=1e-8)
+
+
+def test_adam_is_gradient_scale_invariant():
+    rng = np.random.default_rng(3)
+    g1, g2 = rng.standard_normal(5), rng.standard_normal(5)
+    out = []
+    for s in (1.0, 1000.0):
+        p, m, v = [np.ones(5)], [np.zeros(5)], [np.zeros(5)]
+        M.adam_step(p, [s * g1], m, v, 1, lr=0.05)
+        M.adam_step(p, [s * g2], m, v, 2, lr=0.05)
+        out.append(p[0].copy())
+    np.testing.assert_allclose(out[0], out[1], rtol=0, atol=1e-7)

@@ -272,3 +272,43 @@ def test_random_orthogonal_is_orthogonal():
     np.testing.assert_allclose(p.T @ p, np.eye(48), atol=1e-6)
     v = np.random.default_rng(0).standard_normal(48)
     assert abs(np.linalg.norm(p @ v) - np.linalg.norm(v)) < 1e-6 * np.linalg.norm(v)
+
+
+def _worked(name):
+    return _gold("ads_bsa_worked.json")[name]
+
+
+def test_ads_predicate_hand_worked_events():
+    # tests/golden/ads_bsa_worked.json "ads": every prune event worked out by
+    # hand from Sec. 2.3's hypothesis test at a fixed tau. A predicate that
+    # never fires, an inverted D/d, a dropped square or eps0/d instead of
+    # eps0/sqrt(d) each moves or removes one of the two events.
+    g = _worked("ads")
+    x = np.array(g["vectors"], np.float64)
+    q = np.array(g["query"], np.float64)
+    d, i, st = ops.pdxearch(x, q, g["k"], [np.arange(x.shape[0])], pruner="ads", eps0=g["eps0"],
+                            first_step=g["first_step"], tau0=g["tau0"])
+    assert [list(e) for e in st.prune_events] == g["prune_events"]
+    assert i.tolist() == g["top_ids"]
+    assert d.tolist() == g["top_dists"]
+    # a larger eps0 widens the test: x2 is no longer pruned at d=6
+    _, _, st2 = ops.pdxearch(x, q, g["k"], [np.arange(x.shape[0])], pruner="ads", eps0=4.0,
+                             first_step=g["first_step"], tau0=g["tau0"])
+    assert [e[1] for e in st2.prune_events] == []
+
+
+def test_bsa_predicate_hand_worked_events():
+    # "bsa": one vector pruned only by the error-quantile test (x0), one only
+    # by the Cauchy-Schwarz bound at each check point (x3 at d=2, x5 at d=6),
+    # and one (x4) that survives only if ||q_r|| enters with the right sign.
+    # F(d) differs from d/D here, so a fraction of dimensions in place of the
+    # fraction of variance moves x0's event.
+    g = _worked("bsa")
+    x = np.array(g["vectors"], np.float64)
+    q = np.array(g["query"], np.float64)
+    d, i, st = ops.pdxearch(x, q, g["k"], [np.arange(x.shape[0])], pruner="bsa", bsa_m=g["m"],
+                            bsa_lambda=np.array(g["variances"], np.float64), first_step=g["first_step"],
+                            tau0=g["tau0"])
+    assert [list(e) for e in st.prune_events] == g["prune_events"]
+    assert i.tolist() == g["top_ids"]
+    assert d.tolist() == g["top_dists"]
