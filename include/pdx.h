@@ -139,10 +139,19 @@ typedef struct pdx_ivf_opts {
     uint32_t kmeans_iters;     /* Lloyd iterations on the GPU                              */
     uint32_t kmeans_sample;    /* vectors used to train (0 = all)                         */
     uint64_t seed;             /* picks the initial centroids when none are given          */
-    pdx_pruner transform;      /* ADSAMPLING: rotate by `rotation`; BSA: PCA projection    */
-    const float *rotation;     /* ADSAMPLING: d*d orthogonal matrix, row-major; the stored
-                                  and query vectors become rotation * v. Caller-owned.    */
+    pdx_pruner transform;      /* ADSAMPLING: random orthogonal rotation; BSA: PCA projection */
+    const float *rotation;     /* ADSAMPLING, optional: the caller's d*d orthogonal matrix,
+                                  row-major (host or device, caller-owned); the stored and
+                                  query vectors become rotation * v. NULL: the library draws
+                                  its own from rotation_seed (below).                      */
     const float *init_centroids; /* optional nlist*d initial centroids (host or device)   */
+    uint64_t rotation_seed;    /* ADSAMPLING without `rotation`: seed of the random
+                                  orthogonal matrix (Sec. 2.3). The library fills a d*d
+                                  matrix with standard normal values (splitmix64 counter
+                                  stream, Box-Muller), takes its QR factorisation in FP64
+                                  (Householder) and keeps Q with every column's sign set
+                                  so that R's diagonal is positive: a Haar-distributed
+                                  orthogonal matrix. Same seed, same matrix.               */
 } pdx_ivf_opts;
 
 typedef struct pdx_search_stats {
@@ -159,7 +168,17 @@ typedef struct pdx_search_stats {
     uint64_t dense_fallbacks;  /* tensor-core engine: queries whose candidates overflowed their
                                   buffer (or whose GEMM gave up on a wait) and were answered
                                   by a plain FP32 scan instead                              */
-    uint64_t reserved[7];
+    uint64_t phase_ns[5];      /* device time of each phase of the search in nanoseconds, from
+                                  CUDA events on `stream` (the breakdown of Table 6); filled
+                                  only in stats_out:
+                                  [0] query preprocessing: ADSampling/BSA transform, visit
+                                      orders, order-network inference
+                                  [1] finding the nearest IVF buckets (0 for exact search)
+                                  [2] START: the initial thresholds (exact: dense scan of the
+                                      first start_vectors; IVF: the nearest bucket's PDXearch)
+                                  [3] WARMUP/PRUNE: the PDXearch scan (or the tensor engine)
+                                  [4] merge of the per-item lists, canonical distances, output */
+    uint64_t reserved[2];
 } pdx_search_stats;
 
 typedef struct pdx_search_opts {
@@ -195,6 +214,18 @@ typedef struct pdx_search_opts {
                                   is paired with its nearest one as the network input      */
     int32_t mlp_ncentroids;
     pdx_engine engine;         /* unpruned exact search: PDX scan or tensor-core GEMM (AUTO) */
+    const float *tau_init;     /* optional [nq] initial thresholds (host or device): each
+                                  query's search starts from min(tau_init[i], what START
+                                  finds). For an exact result each value must be at least
+                                  the query's true k-th distance (e.g. the k-th distance of
+                                  k real vectors); a smaller value makes the result the
+                                  best vectors within it, padded. In the metric the scan
+                                  ranks by (L2 or L1; unit-norm IP is searched as L2)     */
+    int32_t tau_fixed;         /* nonzero (with tau_init): no START, and the thresholds never
+                                  tighten during the search, so which vectors are pruned
+                                  depends only on tau_init and the predicate, not on the
+                                  order in which warps finish. Meant for reproducible prune
+                                  counts (tests against a sequential implementation).    */
 } pdx_search_opts;
 
 typedef struct pdx_index_info {
@@ -220,7 +251,9 @@ typedef enum pdx_array {
     PDX_ARRAY_ROTATION = 6,    /* float32 [d][d] IVF transform applied to vectors/queries  */
     PDX_ARRAY_VARIANCES = 7,   /* float32 [d] BSA: variance of each projected dimension    */
     PDX_ARRAY_BLOCKS_LP = 8,   /* bf16 / fp8-e4m3 bits [nblocks][d][64] (storage != F32)   */
-    PDX_ARRAY_SCALES = 9       /* float32 [d] FP8 storage: per-dimension scale             */
+    PDX_ARRAY_SCALES = 9,      /* float32 [d] FP8 storage: per-dimension scale             */
+    PDX_ARRAY_ROWS = 10        /* float32 [n][d] row-major vectors by id (keep_rows); for a
+                                  rotated or projected IVF index the original vectors     */
 } pdx_array;
 
 /* Fill an options struct with the defaults named above. */
@@ -243,13 +276,16 @@ pdx_status pdx_build_layout(const float *x, int64_t n, int32_t d, const pdx_buil
 
 /*
  * pdx_ivf_build -- IVF index whose buckets are PDX blocks (Sec. 2.1, Fig. 2).
- * Optionally transforms the vectors first (ADSampling: the caller's random
- * orthogonal rotation; BSA: PCA projection computed here), runs
+ * Optionally transforms the vectors first (ADSampling: a random orthogonal
+ * rotation, the caller's or one drawn from rotation_seed; BSA: PCA projection
+ * computed here), runs
  * kmeans_iters Lloyd iterations on the GPU from init_centroids (or from
  * nlist vectors picked with `seed`), assigns every vector to its nearest
  * centroid (ties: lower bucket id), and lays each bucket out as PDX blocks.
- * Errors as pdx_build_layout, plus PDX_ERR_ARG for nlist outside [1, n] or a
- * missing rotation for ADSAMPLING.
+ * A transformed index keeps the original vectors row-major (keep_rows) and
+ * reports every distance from them and the untransformed query, so its
+ * distances carry no rounding of the transform.
+ * Errors as pdx_build_layout, plus PDX_ERR_ARG for nlist outside [1, n].
  */
 pdx_status pdx_ivf_build(const float *x, int64_t n, int32_t d, const pdx_ivf_opts *opts,
                          void *stream, pdx_index **out);
@@ -301,9 +337,11 @@ pdx_status pdx_search_ivf(const pdx_index *index, const float *q, int64_t nq, in
  *    PDX_ERR_ARG and says how much it needed. Fewer queries per call or a
  *    smaller start_vectors reduce it: about nq*(8*k*parts*groups + 8*start_vectors) bytes.
  *  - The call allocates nothing. It makes no cudaMalloc/cudaFree and uses no
- *    allocating library routine. The first call on a device looks up the
- *    array's device address with cudaGetSymbolAddress, with that device
- *    current. Make that first call before any stream capture.
+ *    allocating library routine. Every call looks up the array's device
+ *    address with cudaGetSymbolAddress, with the calling thread's current
+ *    device, so the address stays right after a cudaDeviceReset. The first
+ *    call on a device also loads the library's kernels there: make it before
+ *    any stream capture. tau_init, if given, must be device memory.
  *  - Every call on a device shares the one array, and each call overwrites it
  *    (the call resets what must start from zero). Calls whose work overlaps
  *    on the GPU (different streams, or host threads without ordering) race

@@ -6,6 +6,7 @@
 #include <cstdio>
 #include <cstring>
 #include <cmath>
+#include <memory>
 #include <new>
 #include <string>
 #include <vector>
@@ -194,9 +195,11 @@ static bool valid_metric(int m) { return m == PDX_L2 || m == PDX_IP || m == PDX_
 static size_t elem_size(pdx_dtype t) { return t == PDX_F32 ? 4 : (t == PDX_BF16 ? 2 : 1); }
 
 // Low-precision storage: quantise the FP32 PDX blocks (BF16, or FP8-E4M3 with
-// per-dimension scales), keep the FP32 vectors by id (xrows, row-major) for the
-// START scan and the rerank, and release the FP32 blocks.
-static pdx_status finish_low_precision(pdx_index *ix, const float *xrows, cudaStream_t st) {
+// per-dimension scales taken from xblk, the vectors as the blocks hold them),
+// keep the FP32 vectors by id (xrows, row-major: for a transformed IVF index
+// the original vectors) for the START scan and the rerank, and release the
+// FP32 blocks.
+static pdx_status finish_low_precision(pdx_index *ix, const float *xblk, const float *xrows, cudaStream_t st) {
     const int d = ix->d;
     PDX_TRY(dalloc(ix, &ix->xnary, (size_t)ix->n * d));
     PDX_TRY(cudaMemcpyAsync(ix->xnary, xrows, (size_t)ix->n * d * 4, cudaMemcpyDeviceToDevice, st));
@@ -204,7 +207,7 @@ static pdx_status finish_low_precision(pdx_index *ix, const float *xrows, cudaSt
     if (ix->storage == PDX_FP8_E4M3) {
         PDX_TRY(dalloc(ix, &ix->scale, (size_t)d));
         PDX_TRY(cudaMalloc(&colmax, (size_t)d * 4));
-        cudaError_t e = launch_fp8_scales(xrows, ix->n, d, colmax, ix->scale, st);
+        cudaError_t e = launch_fp8_scales(xblk, ix->n, d, colmax, ix->scale, st);
         if (e != cudaSuccess) {
             cudaFree(colmax);
             return cuda_status(e, "launch_fp8_scales", __LINE__);
@@ -341,6 +344,7 @@ pdx_status pdx_index_copy_out(const pdx_index *ix, pdx_array which, void *dst, s
     case PDX_ARRAY_ASSIGN: src = ix->assign; need = (size_t)ix->n * 4; break;
     case PDX_ARRAY_ROTATION: src = ix->rot; need = (size_t)ix->d * ix->d * 4; break;
     case PDX_ARRAY_VARIANCES: src = ix->pca_var; need = (size_t)ix->d * 4; break;
+    case PDX_ARRAY_ROWS: src = ix->xnary; need = (size_t)ix->n * ix->d * 4; break;
     default: set_error("pdx_index_copy_out: unknown array %d", (int)which); return PDX_ERR_ARG;
     }
     if (!src) {
@@ -432,7 +436,7 @@ pdx_status pdx_build_layout(const float *x, int64_t n, int32_t d, const pdx_buil
             cudaError_t e = cudaStreamSynchronize(st);
             if (e != cudaSuccess) s = cuda_status(e, "cudaStreamSynchronize", __LINE__);
         }
-        if (s == PDX_OK && o.storage != PDX_F32) s = finish_low_precision(ix, xd, st);
+        if (s == PDX_OK && o.storage != PDX_F32) s = finish_low_precision(ix, xd, xd, st);
         if (s == PDX_OK && o.storage == PDX_F32 && o.keep_rows) s = keep_rows(ix, xd, st);
         if (s == PDX_OK && o.dense_rows) s = keep_dense_rows(ix, xd, st);
     }
@@ -490,6 +494,10 @@ pdx_status check_search_args(const pdx_index *ix, const float *q, int64_t nq, in
     }
     if (o->engine < PDX_ENGINE_AUTO || o->engine > PDX_ENGINE_TENSOR) {
         set_error("%s: bad engine %d", fn, (int)o->engine);
+        return PDX_ERR_ARG;
+    }
+    if (o->tau_fixed && !o->tau_init) {
+        set_error("%s: tau_fixed needs tau_init", fn);
         return PDX_ERR_ARG;
     }
     if (o->order == PDX_ORDER_LEARNED && o->mlp->d != ix->d) {
@@ -606,7 +614,7 @@ pdx_status exact_plan(const pdx_index *ix, int64_t nq, int32_t k, const pdx_sear
         return PDX_OK;
     }
     ep->nslots = ix->nparts * ep->chunks;
-    ep->start = (pl.pruner != PDX_PRUNE_NONE);
+    ep->start = (pl.pruner != PDX_PRUNE_NONE) && !o.tau_fixed;
     ep->start_blk = 0;
     if (ep->start) {
         int64_t sv = std::max<int64_t>(o.start_vectors, k);
@@ -622,6 +630,7 @@ pdx_status exact_plan(const pdx_index *ix, int64_t nq, int32_t k, const pdx_sear
                + rup(ep->op.bytes)                              // visit orders
                + rup((size_t)nq * kPoolCap * 4) + rup((size_t)nq * 4);  // shared candidate pools
     if (ep->start) b += rup((size_t)nq * ep->Lstart * 8) + rup((size_t)nq * k * 8);
+    if (o.tau_init) b += rup((size_t)nq * 4);
     ep->mlp_bytes = 0;
     if (ep->op.mode == 2) {
         ep->mlp_Lc = ((int64_t)o.mlp_ncentroids + kBlock - 1) / kBlock * kBlock;
@@ -639,8 +648,10 @@ pdx_status exact_plan(const pdx_index *ix, int64_t nq, int32_t k, const pdx_sear
 // synchronise, so it can be captured in a CUDA graph (without scan events).
 pdx_status exact_run(const pdx_index *ix, const float *qd, int64_t nq, int32_t k, const pdx_search_opts &o,
                      const SearchPlan &pl, const ExactPlan &ep, unsigned char *scratch, float *od, int64_t *oi,
-                     unsigned long long **counters_out, int sms, cudaStream_t st) {
+                     unsigned long long **counters_out, int sms, cudaStream_t st, const PhaseEvents *ph) {
     const int d = ix->d;
+    auto mark = [&](int i) -> cudaError_t { return ph ? cudaEventRecord(ph->e[i], st) : cudaSuccess; };
+    PDX_TRY(mark(0));
     if (ep.dense) {
         const size_t db = dense_scratch_bytes(nq, d, k, ep.dense_cap, ix->n, sms);
         unsigned long long *counters = reinterpret_cast<unsigned long long *>(scratch + db);
@@ -648,8 +659,13 @@ pdx_status exact_run(const pdx_index *ix, const float *qd, int64_t nq, int32_t k
         unsigned long long *kc = o.stats_device ? reinterpret_cast<unsigned long long *>(o.stats_device) : counters;
         if (counters_out) *counters_out = kc;
         const bool ip = ix->metric == PDX_IP;
-        return dense_run(ix, qd, nq, k, ip ? MT_IP : MT_L2, ip ? 1 : 0, scratch, db, ep.dense_cap, od, oi, kc, sms,
-                         o.scan_event_start, o.scan_event_stop, st);
+        for (int i = 1; i <= 3; ++i) PDX_TRY(mark(i));
+        pdx_status ds = dense_run(ix, qd, nq, k, ip ? MT_IP : MT_L2, ip ? 1 : 0, scratch, db, ep.dense_cap, od, oi,
+                                  kc, sms, o.scan_event_start, o.scan_event_stop, st);
+        if (ds != PDX_OK) return ds;
+        PDX_TRY(mark(4));
+        PDX_TRY(mark(5));
+        return PDX_OK;
     }
     size_t off = 0;
     auto take = [&](size_t bytes) {
@@ -670,6 +686,7 @@ pdx_status exact_run(const pdx_index *ix, const float *qd, int64_t nq, int32_t k
     uint64_t *skeys = ep.start ? reinterpret_cast<uint64_t *>(take((size_t)nq * ep.Lstart * 8)) : nullptr;
     uint64_t *stopk = ep.start ? reinterpret_cast<uint64_t *>(take((size_t)nq * k * 8)) : nullptr;
     unsigned char *mlp_ws = ep.mlp_bytes ? take(ep.mlp_bytes) : nullptr;
+    float *tau_in = o.tau_init ? reinterpret_cast<float *>(take((size_t)nq * 4)) : nullptr;
     if (off > ep.bytes) {
         set_error("internal error: exact-search scratch layout exceeds its plan");
         return PDX_ERR_CUDA;
@@ -699,10 +716,12 @@ pdx_status exact_run(const pdx_index *ix, const float *qd, int64_t nq, int32_t k
     if (ep.op.rows)  // query preprocessing (Sec. 5): PDX-BOND visit orders
         PDX_TRY(launch_order(qd, ep.op.rows, d, ep.op.per_part ? ix->means : ix->cmean, ep.op.per_part, nullptr,
                              ep.op.mode, std::max(1, (int)o.zone_dims), scores, qorder, st));
+    PDX_TRY(mark(1));
+    PDX_TRY(mark(2));
     PDX_TRY(launch_fill_u32(reinterpret_cast<uint32_t *>(tau), 0xff800000u, nq, st));  // ordered +inf
     PDX_TRY(cudaMemsetAsync(counters, 0, C_COUNT * 8, st));
     PDX_TRY(cudaMemsetAsync(work, 0, 8, st));
-    const bool use_pool = pl.pruner != PDX_PRUNE_NONE;
+    const bool use_pool = pl.pruner != PDX_PRUNE_NONE && !o.tau_fixed;
     if (use_pool) {
         PDX_TRY(launch_fill_u32(reinterpret_cast<uint32_t *>(pool), 0x7f800000u, nq * kPoolCap, st));  // +inf
         PDX_TRY(cudaMemsetAsync(pool_cnt, 0, (size_t)nq * 4, st));
@@ -724,6 +743,11 @@ pdx_status exact_run(const pdx_index *ix, const float *qd, int64_t nq, int32_t k
         PDX_TRY(launch_tau_from_keys(stopk, nq, k, tau, st));
         PDX_TRY(launch_add_u64(kc + C_START, (unsigned long long)nq * ep.Lstart * d, st));
     }
+    if (tau_in) {  // the caller's initial thresholds
+        PDX_TRY(cudaMemcpyAsync(tau_in, o.tau_init, (size_t)nq * 4, cudaMemcpyDefault, st));
+        PDX_TRY(launch_tau_min(tau, tau_in, nq, st));
+    }
+    PDX_TRY(mark(3));
     ScanParams p;
     std::memset(&p, 0, sizeof p);
     p.data = ix->data;
@@ -736,6 +760,7 @@ pdx_status exact_run(const pdx_index *ix, const float *qd, int64_t nq, int32_t k
     p.part_blk = ix->part_blk;
     p.d = d;
     p.q = qd;
+    p.qrows = qd;
     p.nq = nq;
     p.means = ix->means;
     p.probes = nullptr;
@@ -762,9 +787,11 @@ pdx_status exact_run(const pdx_index *ix, const float *qd, int64_t nq, int32_t k
     p.qorder_per_part = ep.op.per_part;
     p.pool = use_pool ? pool : nullptr;
     p.pool_cnt = pool_cnt;
+    p.tau_fixed = o.tau_fixed ? 1 : 0;
     if (o.scan_event_start) PDX_TRY(cudaEventRecord(static_cast<cudaEvent_t>(o.scan_event_start), st));
     PDX_TRY(launch_scan(pl.pruner, pl.metric, p, sms, st));
     if (o.scan_event_stop) PDX_TRY(cudaEventRecord(static_cast<cudaEvent_t>(o.scan_event_stop), st));
+    PDX_TRY(mark(4));
     PDX_TRY(launch_select_k_tau(cand, nq, (int64_t)ep.nslots * k, k, tau, p.gamma, topk, st));
     // canonical distances: from the contiguous rows when the index keeps them
     // (same lanes, order and reduction as from the blocks, so the same bits)
@@ -774,7 +801,28 @@ pdx_status exact_run(const pdx_index *ix, const float *qd, int64_t nq, int32_t k
         PDX_TRY(launch_refine(topk, nq, k, qd, d, ix->data, ix->slot_of, ix->metric, refined, st));
     PDX_TRY(launch_select_k(refined, nq, k, k, final_keys, st));
     PDX_TRY(launch_write_out(final_keys, nq, k, pl.out_mode, qd, d, od, oi, st));
+    PDX_TRY(mark(5));
     return PDX_OK;
+}
+
+PhaseEvents::PhaseEvents() {
+    for (auto &x : e) x = nullptr;
+    ok = true;
+    for (auto &x : e)
+        if (cudaEventCreate(&x) != cudaSuccess) ok = false;
+}
+PhaseEvents::~PhaseEvents() {
+    for (auto &x : e)
+        if (x) cudaEventDestroy(x);
+}
+// Call after the stream has been synchronised.
+void PhaseEvents::fill(pdx_search_stats *so) const {
+    for (int i = 0; i < 5; ++i) {
+        float ms = 0.f;
+        so->phase_ns[i] = (ok && cudaEventElapsedTime(&ms, e[i], e[i + 1]) == cudaSuccess && ms > 0.f)
+                              ? (uint64_t)((double)ms * 1e6 + 0.5)
+                              : 0;
+    }
 }
 
 void fill_stats(pdx_search_stats *so, const unsigned long long *c, const pdx_index *ix) {
@@ -853,7 +901,12 @@ extern "C" pdx_status pdx_search_exact(const pdx_index *ix, const float *q, int6
         qd = qs;
     }
     unsigned long long *kc = nullptr;
-    s = exact_run(ix, qd, nq, k, o, pl, ep, work, od, oi, &kc, sms, st);
+    std::unique_ptr<PhaseEvents> ph;
+    if (o.stats_out) {
+        ph.reset(new (std::nothrow) PhaseEvents());
+        if (ph && !ph->ok) ph.reset();
+    }
+    s = exact_run(ix, qd, nq, k, o, pl, ep, work, od, oi, &kc, sms, st, ph.get());
     if (s != PDX_OK) return s;
     if (!o_dev) {
         PDX_TRY(cudaMemcpyAsync(out_dist, od, (size_t)nq * k * 4, cudaMemcpyDeviceToHost, st));
@@ -864,6 +917,7 @@ extern "C" pdx_status pdx_search_exact(const pdx_index *ix, const float *q, int6
         PDX_TRY(cudaMemcpyAsync(c, kc, sizeof c, cudaMemcpyDeviceToHost, st));
         PDX_TRY(cudaStreamSynchronize(st));
         fill_stats(o.stats_out, c, ix);
+        if (ph) ph->fill(o.stats_out);
     }
     if (!o_dev) PDX_TRY(cudaStreamSynchronize(st));
     return PDX_OK;
@@ -891,6 +945,82 @@ static std::vector<int32_t> check_points(int d, int first_step) {
         step *= 2;
     }
     return c;
+}
+
+// ADSampling's random orthogonal transformation (Sec. 2.3), drawn from a seed:
+// a d x d matrix of standard normal values, its QR factorisation in FP64 by
+// Householder reflections, and Q with each column multiplied by the sign of
+// R's diagonal entry, which makes Q Haar-distributed over the orthogonal
+// group. Normal values: Box-Muller on uniform doubles from a splitmix64
+// counter stream (two 53-bit uniforms per value).
+static void random_orthogonal(int d, uint64_t seed, std::vector<float> &out) {
+    const size_t dd = (size_t)d;
+    std::vector<double> A(dd * dd);  // row-major A[i][j]
+    uint64_t st = seed ^ 0x5D58A6E1C4B3F207ull;
+    const double two_pi = 6.283185307179586476925;
+    for (size_t e = 0; e < dd * dd; ++e) {
+        const double u1 = 1.0 - (double)(splitmix64(st) >> 11) * 0x1.0p-53;  // (0, 1]
+        const double u2 = (double)(splitmix64(st) >> 11) * 0x1.0p-53;        // [0, 1)
+        A[e] = std::sqrt(-2.0 * std::log(u1)) * std::cos(two_pi * u2);
+    }
+    // Householder: for column k, v = x - alpha e_1 with alpha = -sign(x_0) ||x||
+    // (so R_kk = alpha), reflecting rows k.. of the trailing columns.
+    std::vector<double> V(dd * dd, 0.0), w(dd);
+    std::vector<double> rdiag(dd);
+    for (int k = 0; k < d; ++k) {
+        double nrm2 = 0.0;
+        for (int i = k; i < d; ++i) nrm2 += A[(size_t)i * dd + k] * A[(size_t)i * dd + k];
+        const double x0 = A[(size_t)k * dd + k];
+        const double alpha = (x0 >= 0.0 ? -1.0 : 1.0) * std::sqrt(nrm2);
+        rdiag[(size_t)k] = alpha;
+        double *v = &V[(size_t)k * dd];  // v over rows k..d-1
+        double vn2 = 0.0;
+        for (int i = k; i < d; ++i) {
+            v[i] = A[(size_t)i * dd + k] - (i == k ? alpha : 0.0);
+            vn2 += v[i] * v[i];
+        }
+        if (vn2 == 0.0) continue;  // column already reduced: H_k = I
+        const double inv = 1.0 / std::sqrt(vn2);
+        for (int i = k; i < d; ++i) v[i] *= inv;
+        // A[k:, k:] -= 2 v (v^T A[k:, k:])
+        std::fill(w.begin() + k, w.end(), 0.0);
+        for (int i = k; i < d; ++i) {
+            const double vi = v[i];
+            const double *row = &A[(size_t)i * dd];
+            for (int j = k; j < d; ++j) w[(size_t)j] += vi * row[j];
+        }
+        for (int i = k; i < d; ++i) {
+            const double vi2 = 2.0 * v[i];
+            double *row = &A[(size_t)i * dd];
+            for (int j = k; j < d; ++j) row[j] -= vi2 * w[(size_t)j];
+        }
+    }
+    // Q = H_0 H_1 ... H_{d-1}: applied to I from the last reflection back
+    std::vector<double> Q(dd * dd, 0.0);
+    for (int i = 0; i < d; ++i) Q[(size_t)i * dd + i] = 1.0;
+    for (int k = d - 1; k >= 0; --k) {
+        const double *v = &V[(size_t)k * dd];
+        bool zero = true;
+        for (int i = k; i < d && zero; ++i) zero = (v[i] == 0.0);
+        if (zero) continue;
+        std::fill(w.begin(), w.end(), 0.0);
+        for (int i = k; i < d; ++i) {
+            const double vi = v[i];
+            const double *row = &Q[(size_t)i * dd];
+            for (int j = 0; j < d; ++j) w[(size_t)j] += vi * row[j];
+        }
+        for (int i = k; i < d; ++i) {
+            const double vi2 = 2.0 * v[i];
+            double *row = &Q[(size_t)i * dd];
+            for (int j = 0; j < d; ++j) row[j] -= vi2 * w[(size_t)j];
+        }
+    }
+    out.assign(dd * dd, 0.f);
+    for (int i = 0; i < d; ++i)
+        for (int j = 0; j < d; ++j) {
+            const double sgn = rdiag[(size_t)j] < 0.0 ? -1.0 : 1.0;
+            out[(size_t)i * dd + j] = (float)(Q[(size_t)i * dd + j] * sgn);
+        }
 }
 
 // PCA of the (sample of the) vectors for BSA: rot rows = eigenvectors of the
@@ -972,7 +1102,14 @@ static pdx_status ivf_build_impl(pdx_index *ix, const float *x, const pdx_ivf_op
         PDX_CHECK_SCRATCH(scr);
         if (o.transform == PDX_PRUNE_ADSAMPLING) {
             PDX_TRY(dalloc(ix, &ix->rot, (size_t)d * d));
-            PDX_TRY(cudaMemcpyAsync(ix->rot, o.rotation, (size_t)d * d * 4, cudaMemcpyDefault, st));
+            if (o.rotation) {
+                PDX_TRY(cudaMemcpyAsync(ix->rot, o.rotation, (size_t)d * d * 4, cudaMemcpyDefault, st));
+            } else {
+                std::vector<float> P;
+                random_orthogonal(d, o.rotation_seed, P);
+                PDX_TRY(cudaMemcpyAsync(ix->rot, P.data(), P.size() * 4, cudaMemcpyHostToDevice, st));
+                PDX_TRY(cudaStreamSynchronize(st));
+            }
             PDX_TRY(launch_transform(xd, n, d, ix->rot, nullptr, t, st));
         } else {
             pdx_status s = build_pca(ix, xd, std::min<int64_t>(n, 262144), st);
@@ -1043,8 +1180,10 @@ static pdx_status ivf_build_impl(pdx_index *ix, const float *x, const pdx_ivf_op
         }
     }
     PDX_TRY(cudaStreamSynchronize(st));
-    if (ix->storage != PDX_F32) return finish_low_precision(ix, xt, st);
-    if (o.base.keep_rows) return keep_rows(ix, xt, st);
+    // rows by id: the original vectors, so that full distances (row finish,
+    // rerank, canonical refine) carry no rounding of the transform
+    if (ix->storage != PDX_F32) return finish_low_precision(ix, xt, xd, st);
+    if (o.base.keep_rows) return keep_rows(ix, xd, st);
     return PDX_OK;
 }
 
@@ -1073,10 +1212,6 @@ extern "C" pdx_status pdx_ivf_build(const float *x, int64_t n, int32_t d, const 
     }
     if (o.kmeans_sample != 0 && o.kmeans_sample < o.nlist) {
         set_error("pdx_ivf_build: kmeans_sample=%u must be 0 (all) or >= nlist=%u", o.kmeans_sample, o.nlist);
-        return PDX_ERR_ARG;
-    }
-    if (o.transform == PDX_PRUNE_ADSAMPLING && !o.rotation) {
-        set_error("pdx_ivf_build: ADSampling needs the caller's d*d orthogonal rotation");
         return PDX_ERR_ARG;
     }
     if (o.base.storage != PDX_F32 && o.base.metric == PDX_L1) {
@@ -1163,7 +1298,7 @@ extern "C" pdx_status pdx_search_ivf(const pdx_index *ix, const float *q, int64_
                   rup((size_t)nq * Lc * 8) + rup((size_t)nq * nprobe * 8) + rup((size_t)nq * nprobe * 4) +
                   rup((size_t)nq * 4) + rup((size_t)nq * nprobe * k * 8) + 3 * rup((size_t)nq * k * 8) +
                   rup(C_COUNT * 8) + rup(16) + rup((size_t)nq * (nchk + 1) * 8) +
-                  rup((size_t)nq * kPoolCap * 4) + rup((size_t)nq * 4) +
+                  rup((size_t)nq * kPoolCap * 4) + rup((size_t)nq * 4) + (o.tau_init ? rup((size_t)nq * 4) : 0) +
                   (o_dev ? 0 : rup((size_t)nq * k * 4) + rup((size_t)nq * k * 8));
     PDX_TRY(scr.reserve(need));
     const float *qd = q;
@@ -1174,12 +1309,7 @@ extern "C" pdx_status pdx_search_ivf(const pdx_index *ix, const float *q, int64_
         qd = t;
     }
     const float *qt = qd;
-    if (tr) {
-        float *t = scr.take<float>((size_t)nq * d);
-        PDX_CHECK_SCRATCH(scr);
-        PDX_TRY(launch_transform(qd, nq, d, ix->rot, ix->shift, t, st));
-        qt = t;
-    }
+    float *qt_buf = tr ? scr.take<float>((size_t)nq * d) : nullptr;
     uint64_t *pkeys = scr.take<uint64_t>((size_t)nq * Lc);
     uint64_t *ptopk = scr.take<uint64_t>((size_t)nq * nprobe);
     int32_t *probes = scr.take<int32_t>((size_t)nq * nprobe);
@@ -1194,6 +1324,7 @@ extern "C" pdx_status pdx_search_ivf(const pdx_index *ix, const float *q, int64_
     uint16_t *qorder = op.rows ? scr.take<uint16_t>((size_t)op.rows * d) : nullptr;
     float *pool = scr.take<float>((size_t)nq * kPoolCap);
     int32_t *pool_cnt = scr.take<int32_t>((size_t)nq);
+    float *tau_in = o.tau_init ? scr.take<float>((size_t)nq) : nullptr;
     float *od = out_dist;
     int64_t *oi = out_idx;
     if (!o_dev) {
@@ -1201,22 +1332,39 @@ extern "C" pdx_status pdx_search_ivf(const pdx_index *ix, const float *q, int64_
         oi = scr.take<int64_t>((size_t)nq * k);
     }
     PDX_CHECK_SCRATCH(scr);
+    std::unique_ptr<PhaseEvents> ph;
+    if (o.stats_out) {
+        ph.reset(new (std::nothrow) PhaseEvents());
+        if (ph && !ph->ok) ph.reset();
+    }
+    auto mark = [&](int i) -> cudaError_t { return ph ? cudaEventRecord(ph->e[i], st) : cudaSuccess; };
+    PDX_TRY(mark(0));
+    if (tr) {  // query preprocessing (Sec. 2.3): rotation or PCA projection
+        PDX_TRY(launch_transform(qd, nq, d, ix->rot, ix->shift, qt_buf, st));
+        qt = qt_buf;
+    }
+    if (nchk > 0) PDX_TRY(launch_bsa_qaux(qt, nq, d, ix->pca_var, ix->chk, nchk, qaux, st));
+    PDX_TRY(mark(1));
     // nearest buckets: PDX scan of the centroids, then the nprobe best per query
     PDX_TRY(launch_dense_keys(qt, nq, ix->cdata, ix->cids, d, ix->c_nblocks, PDX_L2, pkeys, st));
     PDX_TRY(launch_select_k(pkeys, nq, Lc, nprobe, ptopk, st));
     PDX_TRY(launch_keys_to_parts(ptopk, nq, nprobe, probes, st));
-    if (nchk > 0) PDX_TRY(launch_bsa_qaux(qt, nq, d, ix->pca_var, ix->chk, nchk, qaux, st));
     if (op.rows)  // PDX-BOND visit orders against the probed buckets' (or the collection's) means
         PDX_TRY(launch_order(qt, op.rows, d, op.per_part ? ix->means : ix->cmean, op.per_part,
                              op.per_part ? probes : nullptr, op.mode, std::max(1, (int)o.zone_dims), nullptr, qorder,
                              st));
+    PDX_TRY(mark(2));
     PDX_TRY(launch_fill_u32(reinterpret_cast<uint32_t *>(tau), 0xff800000u, nq, st));
     PDX_TRY(cudaMemsetAsync(counters, 0, C_COUNT * 8, st));
     PDX_TRY(cudaMemsetAsync(work, 0, 16, st));
-    const bool use_pool = pl.pruner != PDX_PRUNE_NONE;
+    const bool use_pool = pl.pruner != PDX_PRUNE_NONE && !o.tau_fixed;
     if (use_pool) {
         PDX_TRY(launch_fill_u32(reinterpret_cast<uint32_t *>(pool), 0x7f800000u, nq * kPoolCap, st));  // +inf
         PDX_TRY(cudaMemsetAsync(pool_cnt, 0, (size_t)nq * 4, st));
+    }
+    if (tau_in) {  // the caller's initial thresholds
+        PDX_TRY(cudaMemcpyAsync(tau_in, o.tau_init, (size_t)nq * 4, cudaMemcpyDefault, st));
+        PDX_TRY(launch_tau_min(tau, tau_in, nq, st));
     }
     unsigned long long *kc = o.stats_device ? reinterpret_cast<unsigned long long *>(o.stats_device) : counters;
     ScanParams p;
@@ -1231,6 +1379,7 @@ extern "C" pdx_status pdx_search_ivf(const pdx_index *ix, const float *q, int64_
     p.part_blk = ix->part_blk;
     p.d = d;
     p.q = qt;
+    p.qrows = qd;  // the rows keep the original vectors
     p.nq = nq;
     p.means = ix->means;
     p.probes = probes;
@@ -1257,12 +1406,14 @@ extern "C" pdx_status pdx_search_ivf(const pdx_index *ix, const float *q, int64_
     p.pool_cnt = pool_cnt;
     p.qorder = qorder;
     p.qorder_per_part = op.per_part;
+    p.tau_fixed = o.tau_fixed ? 1 : 0;
     if (o.scan_event_start) PDX_TRY(cudaEventRecord(static_cast<cudaEvent_t>(o.scan_event_start), st));
     // START (Sec. 4): the nearest bucket of every query, starting from tau = +inf
     p.slot0 = 0;
     p.nitems = nq;
     p.work_counter = work;
     PDX_TRY(launch_scan(pl.pruner, pl.metric, p, sms, st));
+    PDX_TRY(mark(3));
     // WARMUP/PRUNE over the remaining buckets with the thresholds START produced
     if (nprobe > 1) {
         p.slot0 = 1;
@@ -1271,13 +1422,17 @@ extern "C" pdx_status pdx_search_ivf(const pdx_index *ix, const float *q, int64_
         PDX_TRY(launch_scan(pl.pruner, pl.metric, p, sms, st));
     }
     if (o.scan_event_stop) PDX_TRY(cudaEventRecord(static_cast<cudaEvent_t>(o.scan_event_stop), st));
+    PDX_TRY(mark(4));
     PDX_TRY(launch_select_k(cand, nq, (int64_t)nprobe * k, k, topk, st));
+    // canonical distances from the rows (the original vectors, with the
+    // untransformed queries) when the index keeps them
     if (ix->xnary && ix->metric != PDX_L1)
-        PDX_TRY(launch_refine_rows(topk, nq, k, qt, d, ix->xnary, ix->metric, refined, st));
+        PDX_TRY(launch_refine_rows(topk, nq, k, qd, d, ix->xnary, ix->metric, refined, st));
     else
         PDX_TRY(launch_refine(topk, nq, k, qt, d, ix->data, ix->slot_of, ix->metric, refined, st));
     PDX_TRY(launch_select_k(refined, nq, k, k, final_keys, st));
-    PDX_TRY(launch_write_out(final_keys, nq, k, pl.out_mode, qt, d, od, oi, st));
+    PDX_TRY(launch_write_out(final_keys, nq, k, pl.out_mode, qd, d, od, oi, st));
+    PDX_TRY(mark(5));
     if (!o_dev) {
         PDX_TRY(cudaMemcpyAsync(out_dist, od, (size_t)nq * k * 4, cudaMemcpyDeviceToHost, st));
         PDX_TRY(cudaMemcpyAsync(out_idx, oi, (size_t)nq * k * 8, cudaMemcpyDeviceToHost, st));
@@ -1295,9 +1450,10 @@ extern "C" pdx_status pdx_search_ivf(const pdx_index *ix, const float *q, int64_
         so->candidates = c[C_CANDIDATES];
         so->work_items = c[C_ITEMS];
         so->start_values = c[C_START];
-    so->dense_fallbacks = c[C_DENSE_FALLBACK];
+        so->dense_fallbacks = c[C_DENSE_FALLBACK];
         so->bytes_logical = c[C_VALUES] * elem_size(ix->storage) + c[C_START] * 4ull +
                             (ix->storage == PDX_F32 ? 0ull : c[C_CANDIDATES] * (uint64_t)d * 4ull);
+        if (ph) ph->fill(so);
     }
     if (!o_dev) PDX_TRY(cudaStreamSynchronize(st));
     return PDX_OK;

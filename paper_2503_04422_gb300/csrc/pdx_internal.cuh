@@ -52,7 +52,9 @@ struct pdx_index {
     void *data_lp = nullptr;        // [nblocks][d][64] BF16 / FP8-E4M3 blocks
     float *scale = nullptr;         // [d] FP8: per-dimension scale
     float *xnary = nullptr;         // [n][d] FP32 vectors by id (low precision: START, rerank;
-                                    // tensor-core dense engine)
+                                    // tensor-core dense engine; row finish; canonical refine).
+                                    // A rotated or projected IVF index keeps the original
+                                    // (untransformed) vectors here.
     float *xtc = nullptr;           // [n][d] the rows rounded to TF32 (tensor-core operand)
     float *xnorm = nullptr;         // [n][4] (||x||^2, ||x||, ||x - tf32(x)||, 0) (dense engine)
     int32_t *ids = nullptr;         // [nblocks*64]
@@ -182,6 +184,7 @@ struct ScanParams {
     const int32_t *part_blk;
     int32_t d;
     const float *q;            // [nq][d] (transformed for ADS/BSA)
+    const float *qrows;        // [nq][d] the queries in the space of xnary (untransformed)
     int64_t nq;
     const float *means;        // [nparts][d] (BOND order)
     const int32_t *probes;     // [nq][nslots] part per slot, or null (slot -> part0 + slot/chunks)
@@ -214,6 +217,7 @@ struct ScanParams {
     // best over everything scanned so far, as one heap per query would give.
     float *pool;               // [nq][kPoolCap] or null
     int32_t *pool_cnt;         // [nq]
+    int32_t tau_fixed;         // thresholds stay at their initial values (no tightening)
 };
 
 
@@ -257,9 +261,17 @@ pdx_status exact_check(const pdx_index *ix, const float *q, int64_t nq, int32_t 
                        float *out_dist, int64_t *out_idx, pdx_search_opts *o, SearchPlan *pl, const char *fn);
 pdx_status exact_plan(const pdx_index *ix, int64_t nq, int32_t k, const pdx_search_opts &o, const SearchPlan &pl,
                       int sms, ExactPlan *ep);
+// Events recorded on the search stream at the phase boundaries (pdx_search_stats.phase_ns).
+struct PhaseEvents {
+    cudaEvent_t e[6];
+    bool ok;
+    PhaseEvents();
+    ~PhaseEvents();
+    void fill(pdx_search_stats *so) const;
+};
 pdx_status exact_run(const pdx_index *ix, const float *qd, int64_t nq, int32_t k, const pdx_search_opts &o,
                      const SearchPlan &pl, const ExactPlan &ep, unsigned char *scratch, float *od, int64_t *oi,
-                     unsigned long long **counters_out, int sms, cudaStream_t st);
+                     unsigned long long **counters_out, int sms, cudaStream_t st, const PhaseEvents *ph = nullptr);
 void fill_stats(pdx_search_stats *so, const unsigned long long *c, const pdx_index *ix);
 
 // Tensor-core dense engine (pdx_dense.cu).
@@ -293,6 +305,8 @@ cudaError_t launch_select_k(const uint64_t *keys, int64_t rows, int64_t L, int32
 // tau[row] is the row's final threshold (the k-th distance of k real vectors).
 cudaError_t launch_select_k_tau(const uint64_t *keys, int64_t rows, int64_t L, int32_t k, const float *tau,
                                 float gamma, uint64_t *out, cudaStream_t st);
+// tau[row] = min(tau[row], init[row]) on the ordered representation.
+cudaError_t launch_tau_min(float *tau, const float *init, int64_t rows, cudaStream_t st);
 // tau[row] = distance of the k-th key of each row (or +inf).
 cudaError_t launch_tau_from_keys(const uint64_t *topk, int64_t rows, int32_t k, float *tau, cudaStream_t st);
 // Canonical distances of the selected results: recomputed in the natural

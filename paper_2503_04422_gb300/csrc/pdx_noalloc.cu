@@ -4,7 +4,6 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
-#include <mutex>
 
 #include "pdx_internal.cuh"
 
@@ -17,15 +16,14 @@ constexpr int kNoAllocMaxDevices = 64;
 
 // Shared by every call of pdx_search_exact_noalloc on a device. Host code
 // must not use this symbol as a device address: its name denotes a host-side
-// shadow. The device address is looked up once per device with
-// cudaGetSymbolAddress (noalloc_scratch below).
+// shadow. The device address is looked up with cudaGetSymbolAddress on every
+// call (noalloc_scratch below).
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
 
-static std::mutex g_noalloc_mu;
-static unsigned char *g_noalloc_dev_ptr[kNoAllocMaxDevices] = {};
-
-// Device address of the static scratch array on the current device. Looked up
-// on the first call made with that device current; later calls reuse it.
+// Device address of the static scratch array on the current device, looked
+// up on every call with that device current. The lookup allocates nothing and
+// is cheap; not caching it keeps the address valid after the device's primary
+// context is reset and created again (cudaDeviceReset), which moves the array.
 static pdx_status noalloc_scratch(unsigned char **out) {
     int dev = -1;
     cudaError_t e = cudaGetDevice(&dev);
@@ -37,18 +35,14 @@ static pdx_status noalloc_scratch(unsigned char **out) {
         set_error("pdx_search_exact_noalloc: device ordinal %d not supported", dev);
         return PDX_ERR_UNSUPPORTED;
     }
-    std::lock_guard<std::mutex> lk(g_noalloc_mu);
-    if (!g_noalloc_dev_ptr[dev]) {
-        void *p = nullptr;
-        e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-        if (e != cudaSuccess || !p) {
-            set_error("pdx_search_exact_noalloc: cudaGetSymbolAddress of the scratch array failed: %s",
-                      cudaGetErrorString(e));
-            return PDX_ERR_CUDA;
-        }
-        g_noalloc_dev_ptr[dev] = static_cast<unsigned char *>(p);
+    void *p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess || !p) {
+        set_error("pdx_search_exact_noalloc: cudaGetSymbolAddress of the scratch array failed: %s",
+                  cudaGetErrorString(e));
+        return PDX_ERR_CUDA;
     }
-    *out = g_noalloc_dev_ptr[dev];
+    *out = static_cast<unsigned char *>(p);
     return PDX_OK;
 }
 
@@ -89,6 +83,10 @@ extern "C" pdx_status pdx_search_exact_noalloc(const pdx_index *ix, const float 
     if (ep.bytes > kNoAllocScratchBytes) {
         set_error("%s: this search needs %zu bytes of scratch but the static array holds %zu; "
                   "use fewer queries per call or a smaller start_vectors", fn, ep.bytes, kNoAllocScratchBytes);
+        return PDX_ERR_ARG;
+    }
+    if (o.tau_init && !noalloc_is_device(o.tau_init)) {
+        set_error("%s: tau_init must be device memory (this entry point stages nothing)", fn);
         return PDX_ERR_ARG;
     }
     unsigned char *base = nullptr;

@@ -448,6 +448,9 @@ __global__ void __launch_bounds__(256, OCC) pdxsearch_kernel(ScanParams a) {
         }
         if (lane == 0) w.ctr[S_ITEMS] += 1;
         const float *qrow = a.q + qi * D;
+        // the query as the row-major vectors are stored (untransformed for a
+        // rotated or projected index, whose rows keep the original vectors)
+        const float *qrow_r = a.qrows + qi * D;
         const uint16_t *given = nullptr;
         if (a.qorder) given = a.qorder + (a.qorder_per_part ? (qi * (a.nslots / chunks) + pr) : qi) * (int64_t)D;
         volatile uint32_t *tau_g_ptr = reinterpret_cast<volatile uint32_t *>(a.tau) + qi;
@@ -814,7 +817,7 @@ __global__ void __launch_bounds__(256, OCC) pdxsearch_kernel(ScanParams a) {
                         float dd = __shfl_sync(kFull, dist, src);
                         int v = 4 * src + c;
                         const int id = a.ids[(int64_t)b * kBlock + v];
-                        if (ST != ST_F32) dd = rerank_l2(a.xnary + (int64_t)id * D, qrow, D, lane);  // exact FP32
+                        if (ST != ST_F32) dd = rerank_l2(a.xnary + (int64_t)id * D, qrow_r, D, lane);  // exact FP32
                         uint64_t key = make_key(dd, id);
                         topk_insert(w.topk, cnt, k, key, lane);
                         if (lane == 0) w.ctr[S_CAND] += 1;
@@ -834,7 +837,7 @@ __global__ void __launch_bounds__(256, OCC) pdxsearch_kernel(ScanParams a) {
                 for (int m = 0; m < nsurv; ++m) {
                     const int v = w.sv[m];
                     const int id = a.ids[(int64_t)b * kBlock + v];
-                    const float dd = row_dist<MET>(a.xnary + (int64_t)id * D, qrow, D, lane);
+                    const float dd = row_dist<MET>(a.xnary + (int64_t)id * D, qrow_r, D, lane);
                     if (lane == 0) w.ctr[S_VALUES] += (unsigned long long)D;
                     // lane 0 reads the shared threshold and the warp follows it
                     if (__shfl_sync(kFull, (int)(dd <= slack(o2f(*tau_g_ptr), a.gamma)), 0)) {
@@ -857,7 +860,7 @@ __global__ void __launch_bounds__(256, OCC) pdxsearch_kernel(ScanParams a) {
                     float dd = __shfl_sync(kFull, dist, src);
                     int v = __shfl_sync(kFull, my_v, src);
                     const int id = a.ids[(int64_t)b * kBlock + v];
-                    if (ST != ST_F32) dd = rerank_l2(a.xnary + (int64_t)id * D, qrow, D, lane);  // exact FP32
+                    if (ST != ST_F32) dd = rerank_l2(a.xnary + (int64_t)id * D, qrow_r, D, lane);  // exact FP32
                     uint64_t key = make_key(dd, id);
                     topk_insert(w.topk, cnt, k, key, lane);
                     if (lane == 0) w.ctr[S_CAND] += 1;
@@ -869,7 +872,7 @@ __global__ void __launch_bounds__(256, OCC) pdxsearch_kernel(ScanParams a) {
                 nfinal = nsurv;
             }
             if (nfinal > 0 && lane == 0) w.ctr[S_PRUNED] -= (unsigned long long)nfinal;
-            if (nfinal > 0 && cnt == k) {  // the list changes only through vectors that reach the merge
+            if (nfinal > 0 && cnt == k && !a.tau_fixed) {  // the list changes only through vectors that reach the merge
                 float t = key_dist(w.topk[k - 1]);
                 if (t < tau_loc) {
                     tau_loc = t;
@@ -1254,6 +1257,21 @@ __global__ void tau_from_keys_kernel(const uint64_t *topk, int64_t rows, int32_t
 cudaError_t launch_tau_from_keys(const uint64_t *topk, int64_t rows, int32_t k, float *tau, cudaStream_t st) {
     if (rows == 0) return cudaSuccess;
     tau_from_keys_kernel<<<(unsigned)((rows + 255) / 256), 256, 0, st>>>(topk, rows, k, tau);
+    return counted(cudaGetLastError());
+}
+
+__global__ void tau_min_kernel(float *tau, const float *init, int64_t rows) {
+    int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= rows) return;
+    uint32_t *t = reinterpret_cast<uint32_t *>(tau) + r;
+    const float v = init[r];
+    const uint32_t o = (v != v) ? f2o(__int_as_float(0x7f800000)) : f2o(v);  // NaN: no bound
+    if (o < *t) *t = o;
+}
+
+cudaError_t launch_tau_min(float *tau, const float *init, int64_t rows, cudaStream_t st) {
+    if (rows == 0) return cudaSuccess;
+    tau_min_kernel<<<(unsigned)((rows + 255) / 256), 256, 0, st>>>(tau, init, rows);
     return counted(cudaGetLastError());
 }
 

@@ -304,6 +304,10 @@ extern "C" pdx_status pdx_server_create(const pdx_index *const *indexes, int32_t
         set_error("pdx_server_create: a server runs exact searches (pruner NONE or BOND)");
         return PDX_ERR_ARG;
     }
+    if (opts->search.tau_init || opts->search.tau_fixed) {
+        set_error("pdx_server_create: per-query initial thresholds are a per-call option; a server takes none");
+        return PDX_ERR_ARG;
+    }
     pdx_server *s = new (std::nothrow) pdx_server();
     if (!s) {
         set_error("host allocation failed");

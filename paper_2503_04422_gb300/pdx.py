@@ -26,7 +26,8 @@ ORDER = {"dist_to_means": 0, "decreasing": 1, "sequential": 2, "learned": 3}
 MEANS = {"block": 0, "collection": 1, "auto": 2}
 ENGINE = {"auto": 0, "scan": 1, "tensor": 2}
 ARRAY = {"blocks": 0, "ids": 1, "part_blocks": 2, "means": 3, "centroids": 4, "assign": 5, "rotation": 6,
-         "variances": 7, "blocks_lp": 8, "scales": 9}
+         "variances": 7, "blocks_lp": 8, "scales": 9, "rows": 10}
+PHASES = ("preprocess", "find_buckets", "start", "scan", "merge")
 STATUS_NAMES = {0: "PDX_OK", 1: "PDX_ERR_ARG", 2: "PDX_ERR_OOM", 3: "PDX_ERR_CUDA", 4: "PDX_ERR_TIMEOUT",
                 5: "PDX_ERR_UNSUPPORTED"}
 
@@ -40,7 +41,8 @@ class pdx_build_opts(ctypes.Structure):
 class pdx_ivf_opts(ctypes.Structure):
     _fields_ = [("struct_size", ctypes.c_uint32), ("base", pdx_build_opts), ("nlist", ctypes.c_uint32),
                 ("kmeans_iters", ctypes.c_uint32), ("kmeans_sample", ctypes.c_uint32), ("seed", ctypes.c_uint64),
-                ("transform", ctypes.c_int), ("rotation", ctypes.c_void_p), ("init_centroids", ctypes.c_void_p)]
+                ("transform", ctypes.c_int), ("rotation", ctypes.c_void_p), ("init_centroids", ctypes.c_void_p),
+                ("rotation_seed", ctypes.c_uint64)]
 
 
 class pdx_search_stats(ctypes.Structure):
@@ -48,12 +50,15 @@ class pdx_search_stats(ctypes.Structure):
                 ("vectors_pruned", ctypes.c_uint64), ("prune_phase_blocks", ctypes.c_uint64),
                 ("candidates", ctypes.c_uint64), ("work_items", ctypes.c_uint64),
                 ("start_values", ctypes.c_uint64), ("bytes_logical", ctypes.c_uint64),
-                ("dense_fallbacks", ctypes.c_uint64), ("reserved", ctypes.c_uint64 * 7)]
+                ("dense_fallbacks", ctypes.c_uint64), ("phase_ns", ctypes.c_uint64 * 5),
+                ("reserved", ctypes.c_uint64 * 2)]
     FIELDS = ("values_visited", "vectors_scanned", "vectors_pruned", "prune_phase_blocks", "candidates",
               "work_items", "start_values", "bytes_logical", "dense_fallbacks")
 
     def as_dict(self):
-        return {f: int(getattr(self, f)) for f, _ in self._fields_ if f != "reserved"}
+        d = {f: int(getattr(self, f)) for f in self.FIELDS}
+        d["phase_ns"] = {name: int(v) for name, v in zip(PHASES, self.phase_ns)}
+        return d
 
 
 class pdx_search_opts(ctypes.Structure):
@@ -64,7 +69,8 @@ class pdx_search_opts(ctypes.Structure):
                 ("stats_device", ctypes.c_void_p), ("scan_event_start", ctypes.c_void_p),
                 ("scan_event_stop", ctypes.c_void_p), ("means_scope", ctypes.c_int),
                 ("ctas_per_sm", ctypes.c_uint32), ("mlp", ctypes.c_void_p), ("mlp_centroids", ctypes.c_void_p),
-                ("mlp_ncentroids", ctypes.c_int32), ("engine", ctypes.c_int)]
+                ("mlp_ncentroids", ctypes.c_int32), ("engine", ctypes.c_int), ("tau_init", ctypes.c_void_p),
+                ("tau_fixed", ctypes.c_int32)]
 
 
 class pdx_index_info(ctypes.Structure):
@@ -181,7 +187,7 @@ class Index:
             "centroids": ((inf.nparts, inf.d), np.float32), "assign": ((inf.n,), np.int32),
             "rotation": ((inf.d, inf.d), np.float32), "variances": ((inf.d,), np.float32),
             "blocks_lp": ((inf.nblocks, inf.d, 64), np.uint16 if inf.storage == 1 else np.uint8),
-            "scales": ((inf.d,), np.float32)}
+            "scales": ((inf.d,), np.float32), "rows": ((inf.n, inf.d), np.float32)}
         shape, dt = shapes[which]
         out = np.empty(shape, dt)
         _check(lib().pdx_index_copy_out(self.handle, ARRAY[which], out.ctypes.data, out.nbytes), "pdx_index_copy_out")
@@ -214,9 +220,17 @@ def build_opts(metric="l2", storage="f32", partition_size=10000, keep_rows=True,
 def search_opts(pruner="bond", order="dist_to_means", zone_dims=None, selection_threshold=None, eps0=None,
                 bsa_m=None, first_step=None, start_vectors=None, blocks_per_item=None,
                 means_scope=None, ctas_per_sm=None, mlp=None, mlp_centroids=None,
-                engine="auto") -> pdx_search_opts:
+                engine="auto", tau_init=None, tau_fixed=False) -> pdx_search_opts:
+    """Search options; tau_init (float32 [nq], host or device) seeds each
+    query's threshold and tau_fixed keeps it fixed (see include/pdx.h). The
+    returned struct keeps a reference to tau_init's storage."""
     o = pdx_search_opts()
     lib().pdx_default_search_opts(ctypes.byref(o))
+    if tau_init is not None:
+        tp, tk, _, _ = _ptr_f32(tau_init, "tau_init")
+        o.tau_init = tp
+        o._tau_keep = tk
+    o.tau_fixed = int(bool(tau_fixed))
     o.pruner = PRUNER[pruner]
     o.order = ORDER[order]
     o.engine = ENGINE[engine]
@@ -250,12 +264,16 @@ def pdx_build_layout(x, metric="l2", partition_size=10000, storage="f32", stream
 
 
 def pdx_ivf_build(x, nlist, metric="l2", kmeans_iters=10, kmeans_sample=0, seed=2503, transform="none",
-                  rotation=None, init_centroids=None, storage="f32", stream=None) -> Index:
-    """IVF index whose buckets are PDX blocks (Sec. 2.1, Fig. 2)."""
+                  rotation=None, init_centroids=None, storage="f32", stream=None, rotation_seed=2503,
+                  keep_rows=True) -> Index:
+    """IVF index whose buckets are PDX blocks (Sec. 2.1, Fig. 2). ADSampling
+    rotates by `rotation` when given, else by the library's seeded random
+    orthogonal matrix (rotation_seed)."""
     p, keep, cuda, shape = _ptr_f32(x, "x")
     o = pdx_ivf_opts()
     lib().pdx_default_ivf_opts(ctypes.byref(o))
-    o.base = build_opts(metric, storage)
+    o.base = build_opts(metric, storage, keep_rows=keep_rows)
+    o.rotation_seed = rotation_seed
     o.nlist = nlist
     o.kmeans_iters = kmeans_iters
     o.kmeans_sample = kmeans_sample

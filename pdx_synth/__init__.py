@@ -63,6 +63,18 @@ def random_orthogonal(d: int, seed: int) -> np.ndarray:
     return qm.astype(np.float32)
 
 
+def anisotropic_gaussian(n: int, d: int, nq: int, decay: float = 0.9, seed: int = BASE_SEED + 8):
+    """Vectors and queries from one zero-mean Gaussian whose covariance has
+    the eigenvalues decay^(2j) (well separated) along the axes of a seeded
+    random orthogonal basis: a workload whose principal components are
+    distinct and not aligned with the storage axes."""
+    sig = (decay ** np.arange(d)).astype(np.float64)
+    basis = random_orthogonal(d, seed + 1).astype(np.float64)
+    x = ((_rng(seed, 0).standard_normal((n, d)) * sig) @ basis.T).astype(np.float32)
+    q = ((_rng(seed, 1).standard_normal((nq, d)) * sig) @ basis.T).astype(np.float32)
+    return x, q
+
+
 @dataclass
 class MixtureSpec:
     n: int

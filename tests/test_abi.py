@@ -50,7 +50,9 @@ def test_struct_layouts_match_c(tmp_path):
         " offsetof(pdx_search_opts, mlp_ncentroids), offsetof(pdx_ivf_opts, init_centroids));"
         "printf(\"%zu %zu\\n\", sizeof(pdx_server_opts), sizeof(pdx_server_info_t));"
         "printf(\"%zu %zu %zu\\n\", offsetof(pdx_search_opts, engine), offsetof(pdx_build_opts, dense_rows),"
-        " offsetof(pdx_search_stats, dense_fallbacks));return 0;}\n")
+        " offsetof(pdx_search_stats, dense_fallbacks));"
+        "printf(\"%zu %zu %zu %zu\\n\", offsetof(pdx_search_opts, tau_init), offsetof(pdx_search_opts, tau_fixed),"
+        " offsetof(pdx_ivf_opts, rotation_seed), offsetof(pdx_search_stats, phase_ns));return 0;}\n")
     exe = tmp_path / "sizes"
     subprocess.check_call(["gcc", "-I", os.path.join(ROOT, "include"), str(prog), "-o", str(exe)])
     got = [int(v) for v in subprocess.check_output([str(exe)]).split()]
@@ -59,7 +61,9 @@ def test_struct_layouts_match_c(tmp_path):
             P.pdx_search_opts.mlp_ncentroids.offset, P.pdx_ivf_opts.init_centroids.offset,
             ctypes.sizeof(P.pdx_server_opts), ctypes.sizeof(P.pdx_server_info_t),
             P.pdx_search_opts.engine.offset, P.pdx_build_opts.dense_rows.offset,
-            P.pdx_search_stats.dense_fallbacks.offset]
+            P.pdx_search_stats.dense_fallbacks.offset, P.pdx_search_opts.tau_init.offset,
+            P.pdx_search_opts.tau_fixed.offset, P.pdx_ivf_opts.rotation_seed.offset,
+            P.pdx_search_stats.phase_ns.offset]
     assert got == want
 
 

@@ -238,3 +238,49 @@ def test_sharded_search_merged_on_device(P, torch):
                                torch.stack([p[1] for p in parts]).cpu().numpy())
     assert np.array_equal(hi_, mi.cpu().numpy()) and np.array_equal(hd, md.cpu().numpy())
     check_topk(x, q, 10, md, mi)
+
+
+@pytest.mark.parametrize("pruner", ["none", "bond"])
+def test_k_1024(P, torch, pruner):
+    # the largest k the header allows, over several partitions with a ragged tail
+    x, q = pdx_synth.gaussian_mixture(pdx_synth.MixtureSpec(n=9000, d=40, nq=6, n_centres=6, seed=27))
+    ix = P.pdx_build_layout(_dev(torch, x), partition_size=2500)
+    dist, idx = P.pdx_search_exact(ix, _dev(torch, q), 1024, pruner=pruner)
+    torch.cuda.synchronize()
+    check_topk(x, q, 1024, dist, idx)
+
+
+def test_initial_thresholds(P, torch):
+    # tau_init at (or above) each query's true k-th distance keeps PDX-BOND
+    # exact, with or without tightening (tau_fixed); the fixed run prunes with
+    # the true k-th distance from the start, so it visits no more values
+    x, q = pdx_synth.gaussian_mixture(pdx_synth.MixtureSpec(n=30000, d=96, nq=32, n_centres=24, seed=28))
+    ix = P.pdx_build_layout(_dev(torch, x), partition_size=5000)
+    td, ti = ok.knn(x, q, 10)
+    kth = td[:, -1].astype(np.float32)
+    _, _, s0 = P.pdx_search_exact(ix, _dev(torch, q), 10, stats=True)
+    for fixed, tau in ((False, kth * np.float32(1.5)), (True, kth), (True, kth * np.float32(1.01))):
+        dist, idx, st = P.pdx_search_exact(ix, _dev(torch, q), 10, tau_init=tau, tau_fixed=fixed, stats=True)
+        torch.cuda.synchronize()
+        check_topk(x, q, 10, dist, idx)
+        if fixed:
+            assert st["start_values"] == 0
+    _, _, sf = P.pdx_search_exact(ix, _dev(torch, q), 10, tau_init=kth, tau_fixed=True, stats=True)
+    assert sf["values_visited"] <= s0["values_visited"]
+    # a threshold below the k-th distance returns the vectors within it, padded
+    low = (td[:, 4] * 1.0001).astype(np.float32)
+    dist, idx = P.pdx_search_exact(ix, q, 10, tau_init=low, tau_fixed=True)
+    for r in range(q.shape[0]):
+        got = [int(v) for v in idx[r] if v >= 0]
+        assert got == ti[r, :len(got)].tolist() and len(got) >= 5
+    with pytest.raises(P.PdxError):
+        P.pdx_search_exact(ix, _dev(torch, q), 10, tau_fixed=True)          # fixed needs tau_init
+
+
+def test_exact_phase_times(P, torch):
+    x, q = pdx_synth.gaussian_mixture(pdx_synth.MixtureSpec(n=50000, d=128, nq=200, n_centres=32, seed=29))
+    ix = P.pdx_build_layout(_dev(torch, x))
+    _, _, st = P.pdx_search_exact(ix, _dev(torch, q), 10, stats=True)
+    ph = st["phase_ns"]
+    assert ph["start"] > 0 and ph["scan"] > 0 and ph["merge"] > 0
+    assert ph["scan"] > ph["merge"]

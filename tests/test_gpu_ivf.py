@@ -1,12 +1,19 @@
 """GPU parity of the IVF path (Sec. 2.1, Fig. 2; PDXearch over buckets, Sec. 4;
 ADSampling and BSA, Sec. 2.3) against the FP64 oracle. The oracle works in the
 original space: ADSampling's rotation and BSA's PCA are orthogonal, so
-distances, bucket assignments and probe orders are the same there."""
+distances, bucket assignments and probe orders are the same there. A
+transformed index reports its distances from the original vectors, so they
+are held to the same 1e-5 as every other search. The approximate predicates
+are compared prune for prune with the sequential PDXearch oracle at fixed
+thresholds."""
+import math
+
 import numpy as np
 import pytest
 
 import pdx_synth
 from oracle import knn as ok
+from oracle import pdxearch as ops
 from tests._parity import check_topk
 
 pytestmark = pytest.mark.gpu
@@ -120,25 +127,27 @@ def test_transformed_indexes_reduce_to_probed_exact(P, torch, transform, pruner,
     dist, idx = P.pdx_search_ivf(ix, _dev(torch, q), 10, nprobe, pruner=pruner, **knob)
     torch.cuda.synchronize()
     rows = _probe_margin_ok(q, init, nprobe)
-    check_topk(x, q, 10, dist, idx, truth=(truth[0][rows], truth[1][rows]), rows=rows, rtol=2e-5, atol=1e-4)
+    check_topk(x, q, 10, dist, idx, truth=(truth[0][rows], truth[1][rows]), rows=rows)
 
 
 def _recall_setup(P, torch, transform):
     x, q = pdx_synth.gaussian_mixture(pdx_synth.MixtureSpec(n=40000, d=96, nq=64, n_centres=64, seed=36,
                                                             rotate=True))
     init = np.ascontiguousarray(x[np.random.default_rng(1).choice(40000, size=64, replace=False)])
-    rot = pdx_synth.random_orthogonal(96, 6) if transform == "ads" else None
-    ix = P.pdx_ivf_build(_dev(torch, x), nlist=64, kmeans_iters=4, init_centroids=init, transform=transform,
-                         rotation=rot)
+    # the library draws ADSampling's rotation itself (rotation_seed); k-means is
+    # skipped so that the oracle can assign buckets from the same centroids
+    ix = P.pdx_ivf_build(_dev(torch, x), nlist=64, kmeans_iters=0, init_centroids=init, transform=transform,
+                         rotation_seed=6)
     qd = _dev(torch, q)
-    ref_d, ref_i = P.pdx_search_ivf(ix, qd, 10, 8, pruner="bond")
+    oa, _ = ok.assign(x, init)
+    ref_i = ok.knn_probed(x, q, 10, oa, init, 8)[1]     # FP64 oracle over the 8 probed buckets
     _, _, sn = P.pdx_search_ivf(ix, qd, 10, 8, pruner="none", stats=True)
-    return x, q, ix, qd, ref_i.cpu().numpy(), sn["values_visited"]
+    return x, q, ix, qd, ref_i, sn["values_visited"]
 
 
 def test_adsampling_keeps_recall(P, torch):
-    # eps0 = 2.1 (Sec. 6.1): recall against the exact search over the same
-    # buckets stays high while most values are skipped
+    # eps0 = 2.1 (Sec. 6.1): recall against the oracle's exact search over the
+    # same buckets stays high while most values are skipped
     x, q, ix, qd, ref_i, none_vals = _recall_setup(P, torch, "ads")
     _, i, st = P.pdx_search_ivf(ix, qd, 10, 8, pruner="ads", eps0=2.1, stats=True)
     assert ok.recall_at_k(ref_i, i.cpu().numpy()) >= 0.99
@@ -155,7 +164,7 @@ def test_bsa_multiplier_trades_pruning_for_recall(P, torch):
     for m in (0.25, 0.5, 1.0, 2.0, 4.0, 1e30):
         _, i, st = P.pdx_search_ivf(ix, qd, 10, 8, pruner="bsa", bsa_m=m, stats=True)
         res.append((m, ok.recall_at_k(ref_i, i.cpu().numpy()), st["values_visited"]))
-    assert res[-1][1] == 1.0
+    assert res[-1][1] >= 0.995            # the exact bound alone (probe near-ties aside)
     for (m0, r0, v0), (m1, r1, v1) in zip(res, res[1:]):
         assert r1 >= r0 - 0.02, res          # recall grows with m
         assert v1 >= v0 * 0.98, res          # pruning shrinks with m
@@ -184,9 +193,116 @@ def test_ivf_argument_errors(P, torch):
     with pytest.raises(P.PdxError):
         P.pdx_search_ivf(ix, _dev(torch, q), 5, 2, pruner="ads")        # index not rotated
     with pytest.raises(P.PdxError):
-        P.pdx_ivf_build(_dev(torch, x), nlist=8, transform="ads")      # rotation missing
-    with pytest.raises(P.PdxError):
         P.pdx_ivf_build(_dev(torch, x), nlist=501)
     exact = P.pdx_build_layout(_dev(torch, x))
     with pytest.raises(P.PdxError):
         P.pdx_search_ivf(exact, _dev(torch, q), 5, 1)
+
+
+def test_library_rotation_is_seeded_orthogonal(P, torch):
+    # Sec. 2.3: ADSampling's random orthogonal transformation, drawn by the
+    # library from rotation_seed when the caller gives none
+    x, q, init = _data(n=3000, d=96, nq=16, nlist=12, seed=39)
+    ix = P.pdx_ivf_build(_dev(torch, x), nlist=12, kmeans_iters=0, init_centroids=init, transform="ads",
+                         rotation_seed=7)
+    R = ix.copy_out("rotation").astype(np.float64)
+    np.testing.assert_allclose(R.T @ R, np.eye(96), atol=2e-6)
+    np.testing.assert_allclose(R @ R.T, np.eye(96), atol=2e-6)
+    v = np.random.default_rng(3).standard_normal((5, 96))
+    np.testing.assert_allclose(np.linalg.norm(v @ R.T, axis=1), np.linalg.norm(v, axis=1), rtol=2e-6)
+    assert abs(np.linalg.det(R)) == pytest.approx(1.0, abs=1e-4)
+    # entries of a Haar matrix: mean 0, variance 1/d
+    assert abs(R.mean()) < 3.0 / 96 and abs(R.var() * 96 - 1.0) < 0.05
+    again = P.pdx_ivf_build(_dev(torch, x), nlist=12, kmeans_iters=0, init_centroids=init, transform="ads",
+                            rotation_seed=7).copy_out("rotation")
+    other = P.pdx_ivf_build(_dev(torch, x), nlist=12, kmeans_iters=0, init_centroids=init, transform="ads",
+                            rotation_seed=8).copy_out("rotation")
+    assert np.array_equal(again, R.astype(np.float32))
+    assert np.abs(other - R).max() > 0.1
+    # the rows keep the original vectors; searches report original-space distances
+    np.testing.assert_array_equal(ix.copy_out("rows"), x)
+    oa, _ = ok.assign(x, init)
+    truth = ok.knn_probed(x, q, 10, oa, init, 4)
+    dist, idx = P.pdx_search_ivf(ix, _dev(torch, q), 10, 4, pruner="bond")
+    torch.cuda.synchronize()
+    rows = _probe_margin_ok(q, init, 4)
+    check_topk(x, q, 10, dist, idx, truth=(truth[0][rows], truth[1][rows]), rows=rows)
+
+
+def _oracle_fixed_tau(xs, qs, k, tau0, pruner, **kw):
+    """Per query: (vectors pruned, top-k ids among survivors within tau0) of
+    the sequential PDXearch oracle at a fixed threshold. With tau fixed, which
+    vectors are pruned depends only on tau and the predicate, not on blocks or
+    their order, so one block holding every vector is used."""
+    out = []
+    allv = [np.arange(xs.shape[0])]
+    for r in range(qs.shape[0]):
+        d, i, st = ops.pdxearch(xs, qs[r], k, allv, pruner=pruner, first_step=4, tau0=float(tau0[r]), **kw)
+        keep = [int(v) for v, dd in zip(i, d) if v >= 0 and dd <= tau0[r]]
+        out.append((st.vectors_pruned, keep))
+    return out
+
+
+@pytest.mark.parametrize("pruner,knob", [("ads", dict(eps0=2.1)), ("ads", dict(eps0=1.0)),
+                                         ("bsa", dict(bsa_m=1.0)), ("bsa", dict(bsa_m=0.5))])
+def test_approximate_predicates_prune_like_the_oracle(P, torch, pruner, knob):
+    # Sec. 2.3 at fixed thresholds: the GPU's ADSampling / BSA tests prune the
+    # same vectors as the sequential oracle (which follows the paper's steps).
+    # Thresholds within 2e-4 (relative) of a decision may go either way; they
+    # are covered by running the oracle at tau0 * (1 -/+ 2e-4).
+    n, d, nq, k = 4000, 48, 12, 10
+    x, q = pdx_synth.anisotropic_gaussian(n, d, nq, decay=0.93, seed=71)
+    x64, q64 = x.astype(np.float64), q.astype(np.float64)
+    truth_d, _ = ok.knn(x, q, 3 * k)
+    tau0 = truth_d[:, -1].astype(np.float32)          # the 3k-th distance: a real k-th bound
+    init = np.ascontiguousarray(x[np.random.default_rng(5).choice(n, size=8, replace=False)])
+    if pruner == "ads":
+        rot = pdx_synth.random_orthogonal(d, 17)
+        ix = P.pdx_ivf_build(_dev(torch, x), nlist=8, kmeans_iters=0, init_centroids=init, transform="ads",
+                             rotation=rot, keep_rows=False)
+        R = rot.astype(np.float64)
+        xs, qs, extra = x64 @ R.T, q64 @ R.T, dict(eps0=knob["eps0"])
+    else:
+        ix = P.pdx_ivf_build(_dev(torch, x), nlist=8, kmeans_iters=0, init_centroids=init, transform="bsa",
+                             keep_rows=False)
+        mean = x64.mean(axis=0)
+        lam, vec = np.linalg.eigh(np.cov(x64.T, bias=True))
+        order = np.argsort(-lam, kind="stable")
+        lam, vec = np.maximum(lam[order], 0.0), vec[:, order]
+        xs, qs = (x64 - mean) @ vec, (q64 - mean) @ vec
+        extra = dict(bsa_m=knob["bsa_m"], bsa_lambda=lam)
+    lo = _oracle_fixed_tau(xs, qs, k, tau0 * (1 - 2e-4), pruner, **extra)
+    mid = _oracle_fixed_tau(xs, qs, k, tau0, pruner, **extra)
+    hi = _oracle_fixed_tau(xs, qs, k, tau0 * (1 + 2e-4), pruner, **extra)
+    dist, idx, st = P.pdx_search_ivf(ix, _dev(torch, q), k, 8, pruner=pruner, tau_init=_dev(torch, tau0),
+                                     tau_fixed=True, stats=True, **knob)
+    torch.cuda.synchronize()
+    idx = idx.cpu().numpy()
+    pruned_hi = sum(p for p, _ in hi)
+    pruned_lo = sum(p for p, _ in lo)
+    assert pruned_hi <= st["vectors_pruned"] <= pruned_lo, (pruned_hi, st["vectors_pruned"], pruned_lo)
+    assert st["vectors_scanned"] == n * nq
+    # the predicate prunes a real share at this threshold (not a vacuous test)
+    assert sum(p for p, _ in mid) > 0.3 * n * nq
+    agree = 0
+    for r in range(nq):
+        if lo[r][1] != hi[r][1]:
+            continue                                      # a decision within the tolerance changes the result
+        agree += 1
+        got = [int(v) for v in idx[r] if v >= 0]
+        assert got == mid[r][1], (r, got, mid[r][1])
+    assert agree >= nq // 2
+
+
+def test_phase_times_cover_the_search(P, torch):
+    # pdx_search_stats.phase_ns: the Table 6 breakdown, every phase timed on the stream
+    x, q, init = _data(n=20000, d=64, nq=256, nlist=32, seed=43)
+    ix = P.pdx_ivf_build(_dev(torch, x), nlist=32, kmeans_iters=2, init_centroids=init, transform="ads")
+    _, _, st = P.pdx_search_ivf(ix, _dev(torch, q), 10, 8, pruner="ads", stats=True)
+    ph = st["phase_ns"]
+    assert set(ph) == {"preprocess", "find_buckets", "start", "scan", "merge"}
+    assert all(v > 0 for v in ph.values()), ph
+    ex = P.pdx_build_layout(_dev(torch, x))
+    _, _, se = P.pdx_search_exact(ex, _dev(torch, q), 10, stats=True)
+    assert se["phase_ns"]["find_buckets"] < se["phase_ns"]["scan"]
+    assert se["phase_ns"]["start"] > 0 and se["phase_ns"]["scan"] > 0 and se["phase_ns"]["merge"] > 0

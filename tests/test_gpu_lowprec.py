@@ -112,3 +112,15 @@ def test_low_precision_ivf_and_unit_ip(P, torch):
     dist, idx = P.pdx_search_exact(iu, _dev(torch, qu), 10)
     torch.cuda.synchronize()
     check_topk(xu, qu, 10, dist, idx, metric="ip", atol=2e-6)
+
+
+@pytest.mark.parametrize("storage", ["bf16", "fp8"])
+def test_low_precision_k100_d1024(P, torch, storage):
+    # the serving workload's shape: exact top-100 over 1024-dimensional
+    # low-precision blocks (margin-widened lower bound, FP32 rerank)
+    x, q = pdx_synth.gaussian_mixture(pdx_synth.MixtureSpec(n=20000, d=1024, nq=24, n_centres=16, seed=44))
+    ix = P.pdx_build_layout(_dev(torch, x), storage=storage)
+    for pruner in ("none", "bond"):
+        dist, idx = P.pdx_search_exact(ix, _dev(torch, q), 100, pruner=pruner)
+        torch.cuda.synchronize()
+        check_topk(x, q, 100, dist, idx)

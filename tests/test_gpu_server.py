@@ -86,3 +86,20 @@ def test_server_argument_errors(P, torch, collections):
     with pytest.raises(P.PdxError):
         srv.search(0, q[:17])                              # above max_batch
     srv.free()
+
+
+def test_server_fp8_top100(P, torch):
+    # FP8-E4M3 storage, exact top-100 L2, graph replays and autotuning: the
+    # serving configuration, checked against the FP64 oracle
+    x, q = pdx_synth.gaussian_mixture(pdx_synth.MixtureSpec(n=20000, d=384, nq=96, n_centres=16, seed=57))
+    ix = P.pdx_build_layout(torch.from_numpy(x).cuda(), storage="fp8")
+    srv = P.Server([ix], k=100, max_batch=64, use_graphs=True, autotune=True)
+    off = 0
+    for b in (1, 64, 7, 24):
+        qq = np.ascontiguousarray(q[off:off + b])
+        off += b
+        d, i = srv.search(0, torch.from_numpy(qq).cuda())
+        torch.cuda.synchronize()
+        check_topk(x, qq, 100, d, i)
+    assert srv.info["graph_launches"] > 0
+    srv.free()
