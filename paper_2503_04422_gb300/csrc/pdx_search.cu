@@ -480,17 +480,110 @@ __global__ void __launch_bounds__(256, OCC) pdxsearch_kernel(ScanParams a) {
         int cnt = 0;
         float tau_loc = __int_as_float(0x7f800000);
         const float *qaux = (PR == PR_BSA) ? a.qaux + qi * a.nchk * 2 : nullptr;
-        // PDX-BOND: blocks in pairs for the first fetch step (4 dimensions):
-        // both blocks' loads go out together, and the second block's partials
-        // wait in registers for the next iteration, so blocks that end after
-        // this step (most of them, in exact search) cost half a round trip to
-        // L2. ADSampling and BSA bounds are loose after 4 dimensions, blocks
-        // rarely end there, and the kernels skip the pairing.
-        const bool pair = (PR == PR_BOND) && a.first_step == 4 && D > 4;
-        bool pre_valid = false;
-        float4 pre = make_float4(0.f, 0.f, 0.f, 0.f);
+        // PDX-BOND skim of the first fetch step (4 dimensions). In exact search
+        // nearly every block ends there: each of its vectors' partial over the
+        // query's first 4 dimensions already exceeds the threshold. The skim
+        // takes two blocks per warp iteration: lanes h = 0 / 1 take blocks sb
+        // and sb + 1, lane sl holds vectors 4*sl..4*sl+3 and loads their 4
+        // first-step values (one 16-byte load per dimension), so a vector's
+        // partial needs no exchange between lanes, and one vote tells whether
+        // either block keeps a vector. Only blocks that do enter the generic
+        // WARMUP/PRUNE code below, with their first step already in acc (the
+        // other block of the pair waits in sk). ADSampling and BSA bounds are
+        // loose after 4 dimensions, blocks rarely end there, and those kernels
+        // take every block through the generic code.
+        const bool skim = (PR == PR_BOND) && a.first_step == 4 && D > 4;
+        int sj0 = 0, sj1 = 0, sj2 = 0, sj3 = 0;
+        float sq0 = 0.f, sq1 = 0.f, sq2 = 0.f, sq3 = 0.f;
+        float ss0 = 1.f, ss1 = 1.f, ss2 = 1.f, ss3 = 1.f;
+        if (skim) {
+            sj0 = w.ord[0] * kBlock + 4 * sl;
+            sj1 = w.ord[1] * kBlock + 4 * sl;
+            sj2 = w.ord[2] * kBlock + 4 * sl;
+            sj3 = w.ord[3] * kBlock + 4 * sl;
+            sq0 = w.qo[0];
+            sq1 = w.qo[1];
+            sq2 = w.qo[2];
+            sq3 = w.qo[3];
+            if (ST == ST_FP8) {
+                ss0 = w.s2o[0];
+                ss1 = w.s2o[1];
+                ss2 = w.s2o[2];
+                ss3 = w.s2o[3];
+            }
+        }
+        int bnext = b0;   // next block the skim (or the plain loop) takes
+        int pend = -1;    // block whose skim partials wait in sk (lanes 16..31)
+        float4 sk = make_float4(0.f, 0.f, 0.f, 0.f);
 
-        for (int b = b0; b < b1; ++b) {
+        while (true) {
+            int b;
+            bool first_done = false;
+            float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (!skim) {
+                if (bnext >= b1) break;
+                b = bnext++;
+            } else {
+                if (pend >= 0) {
+                    b = pend;
+                    pend = -1;
+                } else {
+                    unsigned vote = 0;
+                    while (bnext < b1) {
+                        const float thr_s = slack(fminf(tau_loc, tau_ahead), a.gamma);
+                        tau_ahead = o2f(*tau_g_ptr);
+                        const int bb = bnext + h;
+                        float4 s4 = make_float4(0.f, 0.f, 0.f, 0.f);
+                        unsigned al = 0;
+                        if (bb < b1) {
+                            const ET *xs = xbase + (int64_t)bb * D * kBlock;
+                            const float4 x0 = Elem<ST>::load4(xs + sj0);
+                            const float4 x1 = Elem<ST>::load4(xs + sj1);
+                            const float4 x2 = Elem<ST>::load4(xs + sj2);
+                            const float4 x3 = Elem<ST>::load4(xs + sj3);
+                            if (ST == ST_F32) {
+                                s4.x = term<MET>(sq3, x3.x, term<MET>(sq2, x2.x, term<MET>(sq1, x1.x, term<MET>(sq0, x0.x, 0.f))));
+                                s4.y = term<MET>(sq3, x3.y, term<MET>(sq2, x2.y, term<MET>(sq1, x1.y, term<MET>(sq0, x0.y, 0.f))));
+                                s4.z = term<MET>(sq3, x3.z, term<MET>(sq2, x2.z, term<MET>(sq1, x1.z, term<MET>(sq0, x0.z, 0.f))));
+                                s4.w = term<MET>(sq3, x3.w, term<MET>(sq2, x2.w, term<MET>(sq1, x1.w, term<MET>(sq0, x0.w, 0.f))));
+                            } else {
+                                s4.x = lp_term<ST, kLB>(sq3, x3.x, lp_term<ST, kLB>(sq2, x2.x, lp_term<ST, kLB>(sq1, x1.x, lp_term<ST, kLB>(sq0, x0.x, 0.f, ss0), ss1), ss2), ss3);
+                                s4.y = lp_term<ST, kLB>(sq3, x3.y, lp_term<ST, kLB>(sq2, x2.y, lp_term<ST, kLB>(sq1, x1.y, lp_term<ST, kLB>(sq0, x0.y, 0.f, ss0), ss1), ss2), ss3);
+                                s4.z = lp_term<ST, kLB>(sq3, x3.z, lp_term<ST, kLB>(sq2, x2.z, lp_term<ST, kLB>(sq1, x1.z, lp_term<ST, kLB>(sq0, x0.z, 0.f, ss0), ss1), ss2), ss3);
+                                s4.w = lp_term<ST, kLB>(sq3, x3.w, lp_term<ST, kLB>(sq2, x2.w, lp_term<ST, kLB>(sq1, x1.w, lp_term<ST, kLB>(sq0, x0.w, 0.f, ss0), ss1), ss2), ss3);
+                            }
+                            const int nv = (bb == b1 - 1) ? last_cnt : kBlock;
+                            al = (unsigned)(s4.x <= thr_s && 4 * sl < nv) | ((unsigned)(s4.y <= thr_s && 4 * sl + 1 < nv) << 1) |
+                                 ((unsigned)(s4.z <= thr_s && 4 * sl + 2 < nv) << 2) |
+                                 ((unsigned)(s4.w <= thr_s && 4 * sl + 3 < nv) << 3);
+                        }
+                        vote = __ballot_sync(kFull, al != 0u);
+                        if (vote) {
+                            sk = s4;
+                            break;
+                        }
+                        bnext += 2;
+                    }
+                    if (!vote) break;
+                    if (vote & 0xffffu) {
+                        b = bnext;
+                        if (vote >> 16) pend = bnext + 1;
+                    } else {
+                        b = bnext + 1;
+                    }
+                    bnext += 2;
+                }
+                // this block's first-step partials, in the layout of the generic
+                // code (lanes h = 0 hold the sums, lanes h = 1 add zero)
+                const bool upper = (b != bnext - 2);  // block sb + 1 of its skim pair
+                const int from = upper ? sl + 16 : sl;
+                acc.x = __shfl_sync(kFull, sk.x, from);
+                acc.y = __shfl_sync(kFull, sk.y, from);
+                acc.z = __shfl_sync(kFull, sk.z, from);
+                acc.w = __shfl_sync(kFull, sk.w, from);
+                if (h) acc = make_float4(0.f, 0.f, 0.f, 0.f);
+                first_done = true;
+            }
             const ET *xb = xbase + (int64_t)b * D * kBlock;
             const int nvalid = (b == b1 - 1) ? a.blk_cnt[b] : kBlock;
             const float tau_g = tau_ahead;
@@ -503,67 +596,11 @@ __global__ void __launch_bounds__(256, OCC) pdxsearch_kernel(ScanParams a) {
                 for (int c = 0; c < 4; ++c)
                     if (4 * sl + c < nvalid) alive |= 1u << c;
             }
-            float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
             int pos = 0, step = (PR == PR_NONE) ? D : max(1, a.first_step);
             int chk = 0;
             int nsurv = -1;  // -1: still in WARMUP
             float my_p = 0.f;
             int my_v = 0;
-            bool first_done = false;
-            if (pair) {
-                if (pre_valid) {
-                    acc = pre;
-                    pre_valid = false;
-                } else {
-                    // positions h and 2 + h of the order: the same terms, in the
-                    // same order, as the generic first step below
-                    const int j0 = w.ord[h], j1 = w.ord[2 + h];
-                    const float q0 = w.qo[h], q1 = w.qo[2 + h];
-                    const float s0 = (ST == ST_FP8) ? w.s2o[h] : 1.f, s1 = (ST == ST_FP8) ? w.s2o[2 + h] : 1.f;
-                    const bool nxt = b + 1 < b1;
-                    const float4 x0 = Elem<ST>::load4(xb + j0 * kBlock + 4 * sl);
-                    const float4 x1 = Elem<ST>::load4(xb + j1 * kBlock + 4 * sl);
-                    float4 y0 = make_float4(0.f, 0.f, 0.f, 0.f), y1 = y0;
-                    if (nxt) {
-                        const ET *xn = xb + (int64_t)D * kBlock;
-                        y0 = Elem<ST>::load4(xn + j0 * kBlock + 4 * sl);
-                        y1 = Elem<ST>::load4(xn + j1 * kBlock + 4 * sl);
-                    }
-                    float4 pn = make_float4(0.f, 0.f, 0.f, 0.f);
-                    if (ST == ST_F32) {
-                        acc.x = term<MET>(q0, x0.x, acc.x);
-                        acc.y = term<MET>(q0, x0.y, acc.y);
-                        acc.z = term<MET>(q0, x0.z, acc.z);
-                        acc.w = term<MET>(q0, x0.w, acc.w);
-                        acc.x = term<MET>(q1, x1.x, acc.x);
-                        acc.y = term<MET>(q1, x1.y, acc.y);
-                        acc.z = term<MET>(q1, x1.z, acc.z);
-                        acc.w = term<MET>(q1, x1.w, acc.w);
-                        pn.x = term<MET>(q1, y1.x, term<MET>(q0, y0.x, 0.f));
-                        pn.y = term<MET>(q1, y1.y, term<MET>(q0, y0.y, 0.f));
-                        pn.z = term<MET>(q1, y1.z, term<MET>(q0, y0.z, 0.f));
-                        pn.w = term<MET>(q1, y1.w, term<MET>(q0, y0.w, 0.f));
-                    } else {
-                        acc.x = lp_term<ST, kLB>(q0, x0.x, acc.x, s0);
-                        acc.y = lp_term<ST, kLB>(q0, x0.y, acc.y, s0);
-                        acc.z = lp_term<ST, kLB>(q0, x0.z, acc.z, s0);
-                        acc.w = lp_term<ST, kLB>(q0, x0.w, acc.w, s0);
-                        acc.x = lp_term<ST, kLB>(q1, x1.x, acc.x, s1);
-                        acc.y = lp_term<ST, kLB>(q1, x1.y, acc.y, s1);
-                        acc.z = lp_term<ST, kLB>(q1, x1.z, acc.z, s1);
-                        acc.w = lp_term<ST, kLB>(q1, x1.w, acc.w, s1);
-                        pn.x = lp_term<ST, kLB>(q1, y1.x, lp_term<ST, kLB>(q0, y0.x, 0.f, s0), s1);
-                        pn.y = lp_term<ST, kLB>(q1, y1.y, lp_term<ST, kLB>(q0, y0.y, 0.f, s0), s1);
-                        pn.z = lp_term<ST, kLB>(q1, y1.z, lp_term<ST, kLB>(q0, y0.z, 0.f, s0), s1);
-                        pn.w = lp_term<ST, kLB>(q1, y1.w, lp_term<ST, kLB>(q0, y0.w, 0.f, s0), s1);
-                    }
-                    if (nxt) {
-                        pre = pn;
-                        pre_valid = true;
-                    }
-                }
-                first_done = true;
-            }
             // ---------------- WARMUP ----------------
             while (pos < D) {
                 const int e = min(D, pos + step);
