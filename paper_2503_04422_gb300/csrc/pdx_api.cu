@@ -107,6 +107,12 @@ struct Scratch {
     } while (0)
 static size_t rup(size_t b) { return (b + 255) & ~size_t(255); }
 
+// The scan may read rows (and the matching query rows) as float4 when every
+// row starts on a 16-byte boundary.
+static int rows_vec4(const pdx_index *ix, const float *qrows) {
+    return (ix->d % 4 == 0 && ((uintptr_t)ix->xnary & 15u) == 0 && ((uintptr_t)qrows & 15u) == 0) ? 1 : 0;
+}
+
 static void free_index(pdx_index *ix) {
     if (!ix) return;
     void *ptrs[] = {ix->data, ix->data_lp, ix->scale, ix->xnary, ix->xtc, ix->xnorm, ix->ids, ix->slot_of, ix->blk_cnt, ix->part_blk, ix->means, ix->cmean, ix->centroids, ix->centroid_norms,
@@ -788,6 +794,7 @@ pdx_status exact_run(const pdx_index *ix, const float *qd, int64_t nq, int32_t k
     p.pool = use_pool ? pool : nullptr;
     p.pool_cnt = pool_cnt;
     p.tau_fixed = o.tau_fixed ? 1 : 0;
+    p.rows_vec4 = rows_vec4(ix, p.qrows);
     if (o.scan_event_start) PDX_TRY(cudaEventRecord(static_cast<cudaEvent_t>(o.scan_event_start), st));
     PDX_TRY(launch_scan(pl.pruner, pl.metric, p, sms, st));
     if (o.scan_event_stop) PDX_TRY(cudaEventRecord(static_cast<cudaEvent_t>(o.scan_event_stop), st));
@@ -1407,6 +1414,7 @@ extern "C" pdx_status pdx_search_ivf(const pdx_index *ix, const float *q, int64_
     p.qorder = qorder;
     p.qorder_per_part = op.per_part;
     p.tau_fixed = o.tau_fixed ? 1 : 0;
+    p.rows_vec4 = rows_vec4(ix, p.qrows);
     if (o.scan_event_start) PDX_TRY(cudaEventRecord(static_cast<cudaEvent_t>(o.scan_event_start), st));
     // START (Sec. 4): the nearest bucket of every query, starting from tau = +inf
     p.slot0 = 0;

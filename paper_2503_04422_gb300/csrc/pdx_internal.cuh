@@ -218,6 +218,7 @@ struct ScanParams {
     float *pool;               // [nq][kPoolCap] or null
     int32_t *pool_cnt;         // [nq]
     int32_t tau_fixed;         // thresholds stay at their initial values (no tightening)
+    int32_t rows_vec4;         // d % 4 == 0 and xnary, qrows 16-byte aligned: rows read as float4
 };
 
 

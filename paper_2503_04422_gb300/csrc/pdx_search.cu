@@ -342,17 +342,6 @@ __device__ __forceinline__ bool prune_test(float partial, float thr, int dv, int
 // BF16/FP8 blocks stay at 3: their lower-bound arithmetic would spill at 64.
 // The launcher takes 4 when four CTAs' shared memory still leaves room for L1.
 
-// Exact FP32 L2 distance of one stored vector (row of the N-ary FP32 copy)
-// to the query; lanes take dimensions j = lane, lane + 32, ... (warp-uniform).
-__device__ __forceinline__ float rerank_l2(const float *__restrict__ xrow, const float *__restrict__ qrow, int D,
-                                          int lane) {
-    float acc = 0.f;
-    for (int j = lane; j < D; j += 32) {
-        float t = qrow[j] - __ldg(xrow + j);
-        acc = fmaf(t, t, acc);
-    }
-    return warp_sum(acc);
-}
 
 // Offer a full distance to the query's shared pool (lane 0 writes). The pool
 // is a ring: once full, new distances (only those below the current
@@ -394,13 +383,47 @@ __device__ __forceinline__ uint32_t pool_kth(const ScanParams &a, int64_t qi, in
 }
 
 // Full distance of one stored vector from its row of the row-major FP32 copy
-// (warp-uniform result): lanes take dimensions j = lane, lane + 32, ..., so
-// each request reads 128 contiguous bytes.
+// (warp-uniform result). With vec4 (d a multiple of 4 and both rows 16-byte
+// aligned) lanes take 16-byte pieces i = lane, lane + 32, ... and issue
+// kRowUnroll of them (512 bytes per warp each) before the first is consumed;
+// otherwise lanes take dimensions j = lane, lane + 32, ... (128 contiguous
+// bytes per request).
+#ifndef PDX_ROW_UNROLL
+#define PDX_ROW_UNROLL 4
+#endif
+constexpr int kRowUnroll = PDX_ROW_UNROLL;
 template <int MET>
 __device__ __forceinline__ float row_dist(const float *__restrict__ xrow, const float *__restrict__ qrow, int D,
-                                          int lane) {
+                                          int lane, bool vec4) {
     float acc = 0.f;
-    for (int j = lane; j < D; j += 32) acc = term<MET>(qrow[j], __ldg(xrow + j), acc);
+    if (vec4) {
+        const float4 *x4 = reinterpret_cast<const float4 *>(xrow);
+        const float4 *q4 = reinterpret_cast<const float4 *>(qrow);
+        const int n4 = D >> 2;
+        for (int base = lane; base < n4; base += 32 * kRowUnroll) {
+            float4 xv[kRowUnroll];
+#pragma unroll
+            for (int u = 0; u < kRowUnroll; ++u) {
+                const int i = base + 32 * u;
+                xv[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+                if (i < n4) xv[u] = __ldg(x4 + i);
+            }
+            // the query row is re-read for every row of the item: an L1 hit
+#pragma unroll
+            for (int u = 0; u < kRowUnroll; ++u) {
+                const int i = base + 32 * u;
+                if (i < n4) {
+                    const float4 qv = __ldg(q4 + i);
+                    acc = term<MET>(qv.x, xv[u].x, acc);
+                    acc = term<MET>(qv.y, xv[u].y, acc);
+                    acc = term<MET>(qv.z, xv[u].z, acc);
+                    acc = term<MET>(qv.w, xv[u].w, acc);
+                }
+            }
+        }
+    } else {
+        for (int j = lane; j < D; j += 32) acc = term<MET>(qrow[j], __ldg(xrow + j), acc);
+    }
     return rank_dist<MET>(warp_sum(acc));
 }
 
@@ -496,20 +519,16 @@ __global__ void __launch_bounds__(256, OCC) pdxsearch_kernel(ScanParams a) {
         int sj0 = 0, sj1 = 0, sj2 = 0, sj3 = 0;
         float sq0 = 0.f, sq1 = 0.f, sq2 = 0.f, sq3 = 0.f;
         float ss0 = 1.f, ss1 = 1.f, ss2 = 1.f, ss3 = 1.f;
-        if (skim) {
+        if (skim && ST == ST_F32) {  // low precision reads them from shared memory (registers)
             sj0 = w.ord[0] * kBlock + 4 * sl;
             sj1 = w.ord[1] * kBlock + 4 * sl;
             sj2 = w.ord[2] * kBlock + 4 * sl;
             sj3 = w.ord[3] * kBlock + 4 * sl;
-            sq0 = w.qo[0];
-            sq1 = w.qo[1];
-            sq2 = w.qo[2];
-            sq3 = w.qo[3];
-            if (ST == ST_FP8) {
-                ss0 = w.s2o[0];
-                ss1 = w.s2o[1];
-                ss2 = w.s2o[2];
-                ss3 = w.s2o[3];
+            {
+                sq0 = w.qo[0];
+                sq1 = w.qo[1];
+                sq2 = w.qo[2];
+                sq3 = w.qo[3];
             }
         }
         int bnext = b0;   // next block the skim (or the plain loop) takes
@@ -537,10 +556,28 @@ __global__ void __launch_bounds__(256, OCC) pdxsearch_kernel(ScanParams a) {
                         unsigned al = 0;
                         if (bb < b1) {
                             const ET *xs = xbase + (int64_t)bb * D * kBlock;
+                            if (ST != ST_F32) {
+                                sj0 = w.ord[0] * kBlock + 4 * sl;
+                                sj1 = w.ord[1] * kBlock + 4 * sl;
+                                sj2 = w.ord[2] * kBlock + 4 * sl;
+                                sj3 = w.ord[3] * kBlock + 4 * sl;
+                            }
                             const float4 x0 = Elem<ST>::load4(xs + sj0);
                             const float4 x1 = Elem<ST>::load4(xs + sj1);
                             const float4 x2 = Elem<ST>::load4(xs + sj2);
                             const float4 x3 = Elem<ST>::load4(xs + sj3);
+                            if (ST != ST_F32) {
+                                sq0 = w.qo[0];
+                                sq1 = w.qo[1];
+                                sq2 = w.qo[2];
+                                sq3 = w.qo[3];
+                                if (ST == ST_FP8) {
+                                    ss0 = w.s2o[0];
+                                    ss1 = w.s2o[1];
+                                    ss2 = w.s2o[2];
+                                    ss3 = w.s2o[3];
+                                }
+                            }
                             if (ST == ST_F32) {
                                 s4.x = term<MET>(sq3, x3.x, term<MET>(sq2, x2.x, term<MET>(sq1, x1.x, term<MET>(sq0, x0.x, 0.f))));
                                 s4.y = term<MET>(sq3, x3.y, term<MET>(sq2, x2.y, term<MET>(sq1, x1.y, term<MET>(sq0, x0.y, 0.f))));
@@ -854,7 +891,7 @@ __global__ void __launch_bounds__(256, OCC) pdxsearch_kernel(ScanParams a) {
                         float dd = __shfl_sync(kFull, dist, src);
                         int v = 4 * src + c;
                         const int id = a.ids[(int64_t)b * kBlock + v];
-                        if (ST != ST_F32) dd = rerank_l2(a.xnary + (int64_t)id * D, qrow_r, D, lane);  // exact FP32
+                        if (ST != ST_F32) dd = row_dist<MT_L2>(a.xnary + (int64_t)id * D, qrow_r, D, lane, a.rows_vec4);  // exact FP32
                         uint64_t key = make_key(dd, id);
                         topk_insert(w.topk, cnt, k, key, lane);
                         if (lane == 0) w.ctr[S_CAND] += 1;
@@ -874,7 +911,7 @@ __global__ void __launch_bounds__(256, OCC) pdxsearch_kernel(ScanParams a) {
                 for (int m = 0; m < nsurv; ++m) {
                     const int v = w.sv[m];
                     const int id = a.ids[(int64_t)b * kBlock + v];
-                    const float dd = row_dist<MET>(a.xnary + (int64_t)id * D, qrow_r, D, lane);
+                    const float dd = row_dist<MET>(a.xnary + (int64_t)id * D, qrow_r, D, lane, a.rows_vec4);
                     if (lane == 0) w.ctr[S_VALUES] += (unsigned long long)D;
                     // lane 0 reads the shared threshold and the warp follows it
                     if (__shfl_sync(kFull, (int)(dd <= slack(o2f(*tau_g_ptr), a.gamma)), 0)) {
@@ -897,7 +934,7 @@ __global__ void __launch_bounds__(256, OCC) pdxsearch_kernel(ScanParams a) {
                     float dd = __shfl_sync(kFull, dist, src);
                     int v = __shfl_sync(kFull, my_v, src);
                     const int id = a.ids[(int64_t)b * kBlock + v];
-                    if (ST != ST_F32) dd = rerank_l2(a.xnary + (int64_t)id * D, qrow_r, D, lane);  // exact FP32
+                    if (ST != ST_F32) dd = row_dist<MT_L2>(a.xnary + (int64_t)id * D, qrow_r, D, lane, a.rows_vec4);  // exact FP32
                     uint64_t key = make_key(dd, id);
                     topk_insert(w.topk, cnt, k, key, lane);
                     if (lane == 0) w.ctr[S_CAND] += 1;

@@ -1,8 +1,9 @@
 """Rank body of the sharded-search test: one CPU process per rank, gloo
 collectives. Each rank answers the queries over its own id range of the
 collection with the FP64 oracle (standing in for that rank's GPU search),
-makes its ids global, all-gathers the per-shard lists and merges them with
-the library's pdx_merge_topk (host path)."""
+and hands its lists to paper_2503_04422_gb300.shard.gather_merge (global
+ids, all-gather, the library's pdx_merge_topk on the host path), the same
+exchange step the bench's sharded mode runs over NCCL."""
 import os
 
 import numpy as np
@@ -17,19 +18,15 @@ def rank_main(rank, world, port, x, q, k, metric, out_path):
     dist.init_process_group("gloo", rank=rank, world_size=world)
     try:
         from oracle import knn as ok
-        from paper_2503_04422_gb300 import pdx
+        from paper_2503_04422_gb300 import shard
 
         n = x.shape[0]
-        lo, hi = rank * n // world, (rank + 1) * n // world
+        lo, hi = shard.shard_range(n, rank, world)
         d_, i_ = ok.knn(x[lo:hi], q, k, metric)
-        i_ = np.where(i_ >= 0, i_ + lo, -1).astype(np.int64)
-        dt = torch.from_numpy(d_.astype(np.float32))
-        it = torch.from_numpy(i_)
-        gd = [torch.empty_like(dt) for _ in range(world)]
-        gi = [torch.empty_like(it) for _ in range(world)]
-        dist.all_gather(gd, dt)
-        dist.all_gather(gi, it)
-        md, mi = pdx.pdx_merge_topk(torch.stack(gd).numpy(), torch.stack(gi).numpy(), metric)
+        # the bench's exchange step: global ids, all-gather, pdx_merge_topk
+        md, mi = shard.gather_merge(torch.from_numpy(d_.astype(np.float32)), torch.from_numpy(i_.astype(np.int64)),
+                                    lo, metric)
+        md, mi = md.numpy(), mi.numpy()
         # every rank holds the same merged answer
         chk = torch.from_numpy(mi.copy())
         ref = chk.clone()
