@@ -36,6 +36,7 @@ WORKLOADS = {
     "ivf_1m_d960": dict(k=10, pruner="ads", nlist=1024),
     "learned_order_2m_d1536": dict(k=10, pruner="bond", metric="ip", nclusters=1024, traces=50_000),
     "serving_64_fp8": dict(k=100, pruner="bond", storage="fp8", batches=1000, max_batch=4096),
+    "layouts": dict(k=10),
 }
 PROFILE_TRAFFIC = os.path.join(ROOT, "profiles", "traffic.json")
 
@@ -783,6 +784,71 @@ def run_serving(args, rank, world, local_rank):
         pass
 
 
+def run_layouts(args, rank, world, local_rank):
+    """The layout comparison (Sec. 3 Fig. 3, Table 3's kernel study, N-ary +
+    gather and DSM in Sec. 7) on one workload: exact top-k by a linear scan
+    (no pruning) over PDX blocks, N-ary rows, N-ary rows transposed on the fly
+    through shared memory, and the fully dimension-major DSM copy, all with
+    the same lean kernel shape (layout scans), plus the library's PDX scan.
+    Every layout must return the same ids. The line reports each layout's
+    queries/s and logical GB/s (n * d * 4 bytes per query) and the PDX
+    speedup over N-ary, the paper's Table 3 ratio."""
+    import numpy as np
+    import torch
+
+    import pdx_synth
+    from paper_2503_04422_gb300 import build as pbuild
+    pbuild.build()
+    from paper_2503_04422_gb300 import pdx
+
+    torch.cuda.set_device(local_rank)
+    base = args.layout_workload
+    k = WORKLOADS[base]["k"]
+    nq = args.nq or pdx_synth.WORKLOADS[base]["nq"]
+    x, q = pdx_synth.make(base, n=args.n, nq=nq)
+    n, d = x.shape
+    ix = pdx.pdx_build_layout(torch.from_numpy(x).cuda(), keep_dsm=True)
+    torch.cuda.synchronize()
+    qd = torch.from_numpy(q).cuda()
+    od = torch.empty((nq, k), dtype=torch.float32, device="cuda")
+    oi = torch.empty((nq, k), dtype=torch.int64, device="cuda")
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    peak, peak_kind = _peak_hbm()
+    res, ref = {}, None
+    for layout in ("pdx", "pdx_kernel", "nary", "nary_gather", "dsm"):
+        opts = pdx.search_opts(pruner="none", engine="scan", layout=layout)
+        for _ in range(args.warmup):
+            pdx.pdx_search_exact(ix, qd, k, opts=opts, out=(od, oi))
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+        torch.cuda.synchronize()
+        for i in range(args.steps):
+            flush.zero_()
+            ev[i][0].record()
+            pdx.pdx_search_exact(ix, qd, k, opts=opts, out=(od, oi))
+            ev[i][1].record()
+        torch.cuda.synchronize()
+        ms = sum(a.elapsed_time(b) for a, b in ev) / args.steps
+        ids = oi.cpu().numpy()
+        if ref is None:
+            ref = ids
+        gbs = nq * n * d * 4.0 / (ms / 1e3) / 1e9
+        res[layout] = {"qps": nq / (ms / 1e3), "ms": ms, "logical_gbs": gbs, "frac_of_hbm": gbs / peak,
+                       "same_ids": bool(np.array_equal(ids, ref))}
+        print(json.dumps({"layout": layout, **res[layout]}), file=sys.stderr, flush=True)
+    best = res["pdx_kernel"]
+    line = {"metric": METRIC, "value": best["qps"], "unit": "queries/s", "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": best["ms"], "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"layouts_{base}", "n": n, "d": d, "nq": nq, "k": k, "pruner": "none",
+                       "l2": "256 MB L2 flush between timed steps (untimed)"},
+            "layouts": res,
+            "pdx_over_nary": res["pdx_kernel"]["qps"] / res["nary"]["qps"],
+            "pdx_over_gather": res["pdx_kernel"]["qps"] / res["nary_gather"]["qps"],
+            "pdx_over_dsm": res["pdx_kernel"]["qps"] / res["dsm"]["qps"],
+            "peak": peak, "peak_kind": peak_kind}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -809,7 +875,10 @@ def main():
     ap.add_argument("--first-step", type=int, default=None, help="exact and IVF workloads: first fetch step (default 4)")
     ap.add_argument("--no-alt", action="store_true", help="exact workload: skip the tensor-engine companion line")
     ap.add_argument("--ctas-per-sm", type=int, default=None, help="exact and IVF workloads: resident scan CTAs per SM")
-    ap.add_argument("--start-vectors", type=int, default=None, help="exact workloads: START scan size (default 4096)")
+    ap.add_argument("--start-vectors", type=int, default=None, help="exact workloads: START scan size (default 1024)")
+    ap.add_argument("--layout-workload", default="plain_scan_10k_d128",
+                    choices=["plain_scan_10k_d128", "bond_exact_1m_d768"],
+                    help="layouts workload: the collection the layouts are compared on")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3
@@ -824,6 +893,8 @@ def main():
         run_learned(args, rank, world, local_rank)
     elif args.workload.startswith("serving"):
         run_serving(args, rank, world, local_rank)
+    elif args.workload == "layouts":
+        run_layouts(args, rank, world, local_rank)
     else:
         run_ours(args, rank, world, local_rank)
 

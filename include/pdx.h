@@ -110,6 +110,30 @@ typedef enum pdx_engine {
     PDX_ENGINE_TENSOR = 2
 } pdx_engine;
 
+/*
+ * Storage layouts of the linear scan (pruner PDX_PRUNE_NONE, engine SCAN),
+ * for comparing layouts on one workload (Sec. 3 Fig. 3, the kernel study of
+ * Sec. 6.2 / Table 3, N-ary + gather and DSM in Sec. 7). Every layout gives
+ * the same exact results.
+ * PDX          the index's PDX blocks (the default scan path)
+ * PDX_KERNEL   the PDX blocks through the same minimal kernel the other
+ *              layouts use (no phases, no threshold sharing)
+ * NARY         row-major vectors (keep_rows): a warp reduces each vector's
+ *              partial sums across its lanes
+ * NARY_GATHER  row-major vectors staged into shared memory as 64-vector x
+ *              32-dimension tiles, transposed on the fly, then the PDX kernel
+ * DSM          the whole collection dimension-major (keep_dsm)
+ * The layout kernels need FP32 storage, an exact index, k <= 256 and (N-ary
+ * forms) d a multiple of 4; otherwise the search returns PDX_ERR_UNSUPPORTED.
+ */
+typedef enum pdx_layout {
+    PDX_LAYOUT_PDX = 0,
+    PDX_LAYOUT_PDX_KERNEL = 1,
+    PDX_LAYOUT_NARY = 2,
+    PDX_LAYOUT_NARY_GATHER = 3,
+    PDX_LAYOUT_DSM = 4
+} pdx_layout;
+
 typedef struct pdx_build_opts {
     uint32_t struct_size;      /* = sizeof(pdx_build_opts)                                */
     pdx_metric metric;         /* metric the index will be searched with                   */
@@ -130,6 +154,9 @@ typedef struct pdx_build_opts {
                                   TF32 (the GEMM operand) and per-row norms: n*(2d+4)*4
                                   bytes. Low-precision storage keeps the FP32 rows anyway
                                   and adds n*(d+4)*4 bytes (default 0)                     */
+    int32_t keep_dsm;          /* also keep the collection fully dimension-major (DSM: d
+                                  columns of ceil(n/64)*64 floats) for the PDX_LAYOUT_DSM
+                                  scan (default 0)                                          */
 } pdx_build_opts;
 
 typedef struct pdx_ivf_opts {
@@ -226,6 +253,8 @@ typedef struct pdx_search_opts {
                                   depends only on tau_init and the predicate, not on the
                                   order in which warps finish. Meant for reproducible prune
                                   counts (tests against a sequential implementation).    */
+    pdx_layout layout;         /* unpruned exact search on the SCAN engine: which storage
+                                  layout the linear scan reads (default PDX)               */
 } pdx_search_opts;
 
 typedef struct pdx_index_info {

@@ -115,7 +115,7 @@ static int rows_vec4(const pdx_index *ix, const float *qrows) {
 
 static void free_index(pdx_index *ix) {
     if (!ix) return;
-    void *ptrs[] = {ix->data, ix->data_lp, ix->scale, ix->xnary, ix->xtc, ix->xnorm, ix->ids, ix->slot_of, ix->blk_cnt, ix->part_blk, ix->means, ix->cmean, ix->centroids, ix->centroid_norms,
+    void *ptrs[] = {ix->data, ix->data_lp, ix->scale, ix->xnary, ix->dsm, ix->xtc, ix->xnorm, ix->ids, ix->slot_of, ix->blk_cnt, ix->part_blk, ix->means, ix->cmean, ix->centroids, ix->centroid_norms,
                     ix->assign, ix->rot, ix->shift, ix->pca_var, ix->resid, ix->chk, ix->cdata, ix->cids};
     for (void *p : ptrs)
         if (p) cudaFree(p);
@@ -442,6 +442,13 @@ pdx_status pdx_build_layout(const float *x, int64_t n, int32_t d, const pdx_buil
             cudaError_t e = cudaStreamSynchronize(st);
             if (e != cudaSuccess) s = cuda_status(e, "cudaStreamSynchronize", __LINE__);
         }
+        if (s == PDX_OK && o.keep_dsm) {  // the fully dimension-major copy (DSM layout scan)
+            const int64_t n_pad = (n + kBlock - 1) / kBlock * kBlock;
+            cudaError_t e = dalloc(ix, &ix->dsm, (size_t)n_pad * d);
+            if (e == cudaSuccess) e = launch_dsm_transpose(xd, n, d, n_pad, ix->dsm, st);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+            if (e != cudaSuccess) s = cuda_status(e, "DSM copy", __LINE__);
+        }
         if (s == PDX_OK && o.storage != PDX_F32) s = finish_low_precision(ix, xd, xd, st);
         if (s == PDX_OK && o.storage == PDX_F32 && o.keep_rows) s = keep_rows(ix, xd, st);
         if (s == PDX_OK && o.dense_rows) s = keep_dense_rows(ix, xd, st);
@@ -500,6 +507,10 @@ pdx_status check_search_args(const pdx_index *ix, const float *q, int64_t nq, in
     }
     if (o->engine < PDX_ENGINE_AUTO || o->engine > PDX_ENGINE_TENSOR) {
         set_error("%s: bad engine %d", fn, (int)o->engine);
+        return PDX_ERR_ARG;
+    }
+    if (o->layout < PDX_LAYOUT_PDX || o->layout > PDX_LAYOUT_DSM) {
+        set_error("%s: bad layout %d", fn, (int)o->layout);
         return PDX_ERR_ARG;
     }
     if (o->tau_fixed && !o->tau_init) {
@@ -600,6 +611,21 @@ pdx_status exact_plan(const pdx_index *ix, int64_t nq, int32_t k, const pdx_sear
     if (bpi < 1) bpi = 1;
     ep->bpi = bpi;
     ep->chunks = (max_blk + bpi - 1) / bpi;
+    // linear scan over another storage layout (the layout comparison)
+    if (o.layout != PDX_LAYOUT_PDX) {
+        const char *why = nullptr;
+        if (pl.pruner != PDX_PRUNE_NONE || o.engine == PDX_ENGINE_TENSOR) {
+            set_error("layout %d: layout scans are unpruned scans (pruner NONE, engine SCAN or AUTO)", (int)o.layout);
+            return PDX_ERR_UNSUPPORTED;
+        }
+        if (!layout_supported(ix, o.layout, k, &why)) {
+            set_error("layout %d: %s", (int)o.layout, why);
+            return PDX_ERR_UNSUPPORTED;
+        }
+        ep->layout = (int)o.layout;
+        ep->bytes = layout_scratch_bytes(ix, nq, k) + rup(C_COUNT * 8);
+        return PDX_OK;
+    }
     // unpruned search: the tensor-core engine when the index supports it
     const char *why = nullptr;
     const bool can_dense = pl.pruner == PDX_PRUNE_NONE && dense_supported(ix, k, &why);
@@ -658,6 +684,23 @@ pdx_status exact_run(const pdx_index *ix, const float *qd, int64_t nq, int32_t k
     const int d = ix->d;
     auto mark = [&](int i) -> cudaError_t { return ph ? cudaEventRecord(ph->e[i], st) : cudaSuccess; };
     PDX_TRY(mark(0));
+    if (ep.layout != PDX_LAYOUT_PDX) {
+        const size_t lb = layout_scratch_bytes(ix, nq, k);
+        unsigned long long *counters = reinterpret_cast<unsigned long long *>(scratch + lb);
+        PDX_TRY(cudaMemsetAsync(counters, 0, C_COUNT * 8, st));
+        unsigned long long *kc = o.stats_device ? reinterpret_cast<unsigned long long *>(o.stats_device) : counters;
+        if (counters_out) *counters_out = kc;
+        // every value of every vector is visited
+        PDX_TRY(launch_add_u64(kc + C_VALUES, (unsigned long long)nq * ix->n * d, st));
+        PDX_TRY(launch_add_u64(kc + C_SCANNED, (unsigned long long)nq * ix->n, st));
+        for (int i = 1; i <= 3; ++i) PDX_TRY(mark(i));
+        pdx_status ls = layout_run(ix, qd, nq, k, ep.layout, pl.metric, pl.out_mode, scratch, od, oi, sms,
+                                   o.scan_event_start, o.scan_event_stop, st);
+        if (ls != PDX_OK) return ls;
+        PDX_TRY(mark(4));
+        PDX_TRY(mark(5));
+        return PDX_OK;
+    }
     if (ep.dense) {
         const size_t db = dense_scratch_bytes(nq, d, k, ep.dense_cap, ix->n, sms);
         unsigned long long *counters = reinterpret_cast<unsigned long long *>(scratch + db);

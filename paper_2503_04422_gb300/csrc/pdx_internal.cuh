@@ -55,6 +55,8 @@ struct pdx_index {
                                     // tensor-core dense engine; row finish; canonical refine).
                                     // A rotated or projected IVF index keeps the original
                                     // (untransformed) vectors here.
+    float *dsm = nullptr;           // [d][n_pad] fully dimension-major copy (keep_dsm), n_pad = nblocks*64
+                                    // for an unpartitioned count: ceil(n/64)*64
     float *xtc = nullptr;           // [n][d] the rows rounded to TF32 (tensor-core operand)
     float *xnorm = nullptr;         // [n][4] (||x||^2, ||x||, ||x - tf32(x)||, 0) (dense engine)
     int32_t *ids = nullptr;         // [nblocks*64]
@@ -254,6 +256,7 @@ struct ExactPlan {
     OrderPlan op;
     size_t mlp_bytes = 0;      // learned order: centroid keys, nearest, inputs, hidden, scores
     int64_t mlp_Lc = 0;
+    int layout = 0;            // pdx_layout of an unpruned scan (0: the PDX scan path)
     bool dense = false;        // tensor-core engine (pdx_dense.cu) instead of the scan
     int dense_cap = 0;         // its candidate entries per query
     size_t bytes = 0;
@@ -274,6 +277,15 @@ pdx_status exact_run(const pdx_index *ix, const float *qd, int64_t nq, int32_t k
                      const SearchPlan &pl, const ExactPlan &ep, unsigned char *scratch, float *od, int64_t *oi,
                      unsigned long long **counters_out, int sms, cudaStream_t st, const PhaseEvents *ph = nullptr);
 void fill_stats(pdx_search_stats *so, const unsigned long long *c, const pdx_index *ix);
+
+// Layout scans (pdx_layouts.cu): linear scans over PDX, N-ary, N-ary + gather
+// or DSM storage, merged like the PDX scan's per-item lists.
+bool layout_supported(const pdx_index *ix, int layout, int32_t k, const char **why);
+size_t layout_scratch_bytes(const pdx_index *ix, int64_t nq, int32_t k);
+pdx_status layout_run(const pdx_index *ix, const float *qd, int64_t nq, int32_t k, int layout, int metric,
+                      int out_mode, unsigned char *scratch, float *od, int64_t *oi, int sms, void *ev_start,
+                      void *ev_stop, cudaStream_t st);
+cudaError_t launch_dsm_transpose(const float *x, int64_t n, int32_t d, int64_t n_pad, float *out, cudaStream_t st);
 
 // Tensor-core dense engine (pdx_dense.cu).
 bool dense_supported(const pdx_index *ix, int32_t k, const char **why);

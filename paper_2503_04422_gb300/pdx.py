@@ -25,6 +25,7 @@ PRUNER = {"none": 0, "bond": 1, "ads": 2, "adsampling": 2, "bsa": 3}
 ORDER = {"dist_to_means": 0, "decreasing": 1, "sequential": 2, "learned": 3}
 MEANS = {"block": 0, "collection": 1, "auto": 2}
 ENGINE = {"auto": 0, "scan": 1, "tensor": 2}
+LAYOUT = {"pdx": 0, "pdx_kernel": 1, "nary": 2, "nary_gather": 3, "dsm": 4}
 ARRAY = {"blocks": 0, "ids": 1, "part_blocks": 2, "means": 3, "centroids": 4, "assign": 5, "rotation": 6,
          "variances": 7, "blocks_lp": 8, "scales": 9, "rows": 10}
 PHASES = ("preprocess", "find_buckets", "start", "scan", "merge")
@@ -35,7 +36,7 @@ STATUS_NAMES = {0: "PDX_OK", 1: "PDX_ERR_ARG", 2: "PDX_ERR_OOM", 3: "PDX_ERR_CUD
 class pdx_build_opts(ctypes.Structure):
     _fields_ = [("struct_size", ctypes.c_uint32), ("metric", ctypes.c_int), ("storage", ctypes.c_int),
                 ("partition_size", ctypes.c_uint32), ("keep_rows", ctypes.c_int32),
-                ("dense_rows", ctypes.c_int32)]
+                ("dense_rows", ctypes.c_int32), ("keep_dsm", ctypes.c_int32)]
 
 
 class pdx_ivf_opts(ctypes.Structure):
@@ -70,7 +71,7 @@ class pdx_search_opts(ctypes.Structure):
                 ("scan_event_stop", ctypes.c_void_p), ("means_scope", ctypes.c_int),
                 ("ctas_per_sm", ctypes.c_uint32), ("mlp", ctypes.c_void_p), ("mlp_centroids", ctypes.c_void_p),
                 ("mlp_ncentroids", ctypes.c_int32), ("engine", ctypes.c_int), ("tau_init", ctypes.c_void_p),
-                ("tau_fixed", ctypes.c_int32)]
+                ("tau_fixed", ctypes.c_int32), ("layout", ctypes.c_int)]
 
 
 class pdx_index_info(ctypes.Structure):
@@ -206,7 +207,7 @@ class Index:
 
 
 def build_opts(metric="l2", storage="f32", partition_size=10000, keep_rows=True,
-               dense_rows=False) -> pdx_build_opts:
+               dense_rows=False, keep_dsm=False) -> pdx_build_opts:
     o = pdx_build_opts()
     lib().pdx_default_build_opts(ctypes.byref(o))
     o.metric = METRIC[metric]
@@ -214,13 +215,14 @@ def build_opts(metric="l2", storage="f32", partition_size=10000, keep_rows=True,
     o.partition_size = partition_size
     o.keep_rows = int(bool(keep_rows))
     o.dense_rows = int(bool(dense_rows))
+    o.keep_dsm = int(bool(keep_dsm))
     return o
 
 
 def search_opts(pruner="bond", order="dist_to_means", zone_dims=None, selection_threshold=None, eps0=None,
                 bsa_m=None, first_step=None, start_vectors=None, blocks_per_item=None,
                 means_scope=None, ctas_per_sm=None, mlp=None, mlp_centroids=None,
-                engine="auto", tau_init=None, tau_fixed=False) -> pdx_search_opts:
+                engine="auto", tau_init=None, tau_fixed=False, layout="pdx") -> pdx_search_opts:
     """Search options; tau_init (float32 [nq], host or device) seeds each
     query's threshold and tau_fixed keeps it fixed (see include/pdx.h). The
     returned struct keeps a reference to tau_init's storage."""
@@ -231,6 +233,7 @@ def search_opts(pruner="bond", order="dist_to_means", zone_dims=None, selection_
         o.tau_init = tp
         o._tau_keep = tk
     o.tau_fixed = int(bool(tau_fixed))
+    o.layout = LAYOUT[layout]
     o.pruner = PRUNER[pruner]
     o.order = ORDER[order]
     o.engine = ENGINE[engine]
@@ -249,14 +252,15 @@ def search_opts(pruner="bond", order="dist_to_means", zone_dims=None, selection_
 
 
 def pdx_build_layout(x, metric="l2", partition_size=10000, storage="f32", stream=None,
-                     dense_rows=False) -> Index:
+                     dense_rows=False, keep_dsm=False, keep_rows=True) -> Index:
     """Exact-search index over x [n][d] (Sec. 3, Sec. 6.6); dense_rows also
-    keeps the row-major FP32 vectors the tensor-core engine reads."""
+    keeps the row-major FP32 vectors the tensor-core engine reads, keep_dsm a
+    fully dimension-major copy for the DSM layout scan."""
     p, keep, cuda, shape = _ptr_f32(x, "x")
     if len(shape) != 2:
         raise ValueError("x must be [n][d]")
     h = ctypes.c_void_p()
-    o = build_opts(metric, storage, partition_size, dense_rows=dense_rows)
+    o = build_opts(metric, storage, partition_size, keep_rows=keep_rows, dense_rows=dense_rows, keep_dsm=keep_dsm)
     _check(lib().pdx_build_layout(p, shape[0], shape[1], ctypes.byref(o), _stream(cuda, stream), ctypes.byref(h)),
            "pdx_build_layout")
     del keep
