@@ -11,7 +11,10 @@ and the SM clocks seen during the timed region.
 Usage: python bench.py [--gpus N --steps K --warmup W --impl ours|reference]
 For N > 1 launch under torchrun: every rank holds a replica of the
 collection and searches its own batch of queries (weak scaling, no
-collective on the data path).
+collective on the data path). With --shard the collection is split by id
+range instead: every rank answers the same queries over its shard, and the
+per-shard top-k lists are all-gathered over NCCL and merged on the device
+(strong scaling).
 """
 from __future__ import annotations
 
@@ -237,8 +240,20 @@ def run_ours(args, rank, world, local_rank):
     spec = WORKLOADS[args.workload]
     k = spec["k"]
     base_nq = args.nq or pdx_synth.WORKLOADS[args.workload]["nq"]
-    x, q_all = pdx_synth.make(args.workload, n=args.n, nq=base_nq * world)
-    q = np.ascontiguousarray(q_all[rank * base_nq:(rank + 1) * base_nq])
+    if args.shard:
+        # sharded collection: every rank holds the id range [lo, hi) and answers
+        # the same queries; the per-shard lists are all-gathered and merged
+        from paper_2503_04422_gb300 import shard
+        x_all, q_all = pdx_synth.make(args.workload, n=args.n, nq=base_nq)
+        q = np.ascontiguousarray(q_all)
+        lo, hi = shard.shard_range(x_all.shape[0], rank, world)
+        x = np.ascontiguousarray(x_all[lo:hi])
+        n_total = x_all.shape[0]
+        del x_all
+    else:
+        x, q_all = pdx_synth.make(args.workload, n=args.n, nq=base_nq * world)
+        q = np.ascontiguousarray(q_all[rank * base_nq:(rank + 1) * base_nq])
+        lo, n_total = 0, x.shape[0]
     n, d = x.shape
     nq = q.shape[0]
     pruner = args.pruner or spec["pruner"]
@@ -265,6 +280,9 @@ def run_ours(args, rank, world, local_rank):
         else:
             opts.scan_event_start = opts.scan_event_stop = opts.stats_device = None
         pdx.pdx_search_exact(ix, q_dev, k, opts=opts, out=(od, oi))
+        if args.shard:   # the exchange step: global ids, NCCL all-gather, device merge
+            return shard.gather_merge(od, oi, lo)
+        return od, oi
 
     for _ in range(args.warmup):
         step()
@@ -301,7 +319,9 @@ def run_ours(args, rank, world, local_rank):
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         tot_ms = float(t.item())
     ms_per_step = tot_ms / K
-    value = nq * world * K / (tot_ms / 1e3)
+    # replicas: every rank answers its own queries (weak scaling); shards: all
+    # ranks answer the same queries over their part of the collection (strong)
+    value = nq * (1 if args.shard else world) * K / (tot_ms / 1e3)
 
     # roofline of the dominant kernel from its event-timed launches: the
     # PDXearch scan (logical bytes read) or the tensor-core GEMM (2 nq n d FLOP)
@@ -339,13 +359,36 @@ def run_ours(args, rank, world, local_rank):
 
     # end to end through the C ABI with host (pinned) buffers
     e2e = None
-    if not args.no_e2e:
+    if not args.no_e2e and not args.shard:
         e2e = _e2e(pdx, ix, q, k, opts, stream, flush, K, world, dist)
+    elif not args.no_e2e:
+        # shards: host queries in, search, exchange, merged results back to the host
+        q_host = torch.from_numpy(q).pin_memory()
+        rd = torch.empty((nq, k), dtype=torch.float32).pin_memory()
+        ri = torch.empty((nq, k), dtype=torch.int64).pin_memory()
+        ev_e = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+        torch.cuda.synchronize()
+        for i in range(K):
+            flush.zero_()
+            ev_e[i][0].record(stream)
+            q_dev.copy_(q_host, non_blocking=True)
+            md, mi = step()
+            rd.copy_(md, non_blocking=True)
+            ri.copy_(mi, non_blocking=True)
+            ev_e[i][1].record(stream)
+        torch.cuda.synchronize()
+        e_ms = sum(a_.elapsed_time(b_) for a_, b_ in ev_e)
+        if dist:
+            t = torch.tensor([e_ms], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            e_ms = float(t.item())
+        e2e = {"value": nq * K / (e_ms / 1e3), "unit": "queries/s", "h2d_bytes_per_step": nq * d * 4,
+               "d2h_bytes_per_step": nq * k * 12}
 
     # the other exact engine on the same workload: no pruning, the L2
     # decomposition's q.x on the tensor cores (same exact results)
     alt = None
-    if pruner == "bond" and args.storage == "f32" and not args.no_alt:
+    if pruner == "bond" and args.storage == "f32" and not args.no_alt and not args.shard:
         ix_t = pdx.pdx_build_layout(torch.from_numpy(x).cuda(), dense_rows=True)
         torch.cuda.synchronize()
         opts_t = pdx.search_opts(pruner="none", engine="tensor")
@@ -378,9 +421,14 @@ def run_ours(args, rank, world, local_rank):
         pruned = float(st[2]) / max(1.0, float(st[1]))
         line = {
             "metric": METRIC, "value": value, "unit": "queries/s", "n_gpus": world, "steps": K,
-            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
+            "scaling": "strong" if args.shard else "weak",
             "vs_baseline": None, "dtype": args.storage, "data": "synthetic",
-            "config": {"workload": args.workload, "n": n, "d": d, "nq_per_gpu": nq, "k": k, "storage": args.storage,
+            "config": {"workload": args.workload, "n": n_total, "d": d, "nq_per_gpu": nq, "k": k,
+                       "storage": args.storage,
+                       "parallelism": (f"shard{world}: ids [lo, hi) per rank, NCCL all-gather of the "
+                                       "per-shard top-k, pdx_merge_topk on the device") if args.shard
+                       else f"replicas{world}: every rank searches its own queries over the whole collection",
                        "pruner": pruner, "engine": "tensor (TF32 GEMM + FP32 rerank)" if tensor else "pdx scan",
                        "order": "dist_to_means",
                        "means": "collection (automatic for exact search)", "zone_dims": "1 (automatic)",
@@ -876,6 +924,8 @@ def main():
     ap.add_argument("--no-alt", action="store_true", help="exact workload: skip the tensor-engine companion line")
     ap.add_argument("--ctas-per-sm", type=int, default=None, help="exact and IVF workloads: resident scan CTAs per SM")
     ap.add_argument("--start-vectors", type=int, default=None, help="exact workloads: START scan size (default 1024)")
+    ap.add_argument("--shard", action="store_true",
+                    help="exact workload: split the collection over the ranks by id range (strong scaling)")
     ap.add_argument("--layout-workload", default="plain_scan_10k_d128",
                     choices=["plain_scan_10k_d128", "bond_exact_1m_d768"],
                     help="layouts workload: the collection the layouts are compared on")

@@ -1341,12 +1341,26 @@ extern "C" pdx_status pdx_search_ivf(const pdx_index *ix, const float *q, int64_
     const int nchk = (o.pruner == PDX_PRUNE_BSA) ? ix->bsa_nchk : 0;
     int max_blk = 0;
     for (int p = 0; p < ix->nparts; ++p) max_blk = std::max(max_blk, ix->h_part_blk[p + 1] - ix->h_part_blk[p]);
+    max_blk = std::max(1, max_blk);
+    // work items: (query, probed bucket, group of its blocks). Buckets are
+    // split into groups when the START launch (one nearest bucket per query)
+    // would leave too few items to fill the GPU; every group of a query
+    // shares its threshold through the query's candidate pool.
+    int ivf_bpi = (int)o.blocks_per_item;
+    if (ivf_bpi <= 0) {
+        const int64_t target = (int64_t)sms * 64 * 3;
+        const int64_t want = std::max<int64_t>(1, (target + nq - 1) / nq);
+        const int ch = (int)std::min<int64_t>(max_blk, std::min<int64_t>(want, 8));
+        ivf_bpi = (max_blk + ch - 1) / ch;
+    }
+    const int ivf_chunks = (max_blk + ivf_bpi - 1) / ivf_bpi;
+    const int nslots = nprobe * ivf_chunks;
     const OrderPlan op = plan_orders(ix, o, pl.pruner, nq, nprobe);
 
     Scratch scr(st);
     size_t need = rup(op.bytes) + (q_dev ? 0 : rup((size_t)nq * d * 4)) + (tr ? rup((size_t)nq * d * 4) : 0) +
                   rup((size_t)nq * Lc * 8) + rup((size_t)nq * nprobe * 8) + rup((size_t)nq * nprobe * 4) +
-                  rup((size_t)nq * 4) + rup((size_t)nq * nprobe * k * 8) + 3 * rup((size_t)nq * k * 8) +
+                  rup((size_t)nq * 4) + rup((size_t)nq * nslots * k * 8) + 3 * rup((size_t)nq * k * 8) +
                   rup(C_COUNT * 8) + rup(16) + rup((size_t)nq * (nchk + 1) * 8) +
                   rup((size_t)nq * kPoolCap * 4) + rup((size_t)nq * 4) + (o.tau_init ? rup((size_t)nq * 4) : 0) +
                   (o_dev ? 0 : rup((size_t)nq * k * 4) + rup((size_t)nq * k * 8));
@@ -1364,7 +1378,7 @@ extern "C" pdx_status pdx_search_ivf(const pdx_index *ix, const float *q, int64_
     uint64_t *ptopk = scr.take<uint64_t>((size_t)nq * nprobe);
     int32_t *probes = scr.take<int32_t>((size_t)nq * nprobe);
     float *tau = scr.take<float>((size_t)nq);
-    uint64_t *cand = scr.take<uint64_t>((size_t)nq * nprobe * k);
+    uint64_t *cand = scr.take<uint64_t>((size_t)nq * nslots * k);
     uint64_t *topk = scr.take<uint64_t>((size_t)nq * k);
     uint64_t *refined = scr.take<uint64_t>((size_t)nq * k);
     uint64_t *final_keys = scr.take<uint64_t>((size_t)nq * k);
@@ -1433,9 +1447,9 @@ extern "C" pdx_status pdx_search_ivf(const pdx_index *ix, const float *q, int64_
     p.nq = nq;
     p.means = ix->means;
     p.probes = probes;
-    p.nslots = nprobe;
-    p.chunks_per_part = 1;
-    p.blocks_per_item = std::max(1, max_blk);
+    p.nslots = nslots;
+    p.chunks_per_part = ivf_chunks;
+    p.blocks_per_item = ivf_bpi;
     p.k = k;
     p.tau = tau;
     p.cand = cand;
@@ -1461,20 +1475,20 @@ extern "C" pdx_status pdx_search_ivf(const pdx_index *ix, const float *q, int64_
     if (o.scan_event_start) PDX_TRY(cudaEventRecord(static_cast<cudaEvent_t>(o.scan_event_start), st));
     // START (Sec. 4): the nearest bucket of every query, starting from tau = +inf
     p.slot0 = 0;
-    p.nitems = nq;
+    p.nitems = nq * (int64_t)ivf_chunks;
     p.work_counter = work;
     PDX_TRY(launch_scan(pl.pruner, pl.metric, p, sms, st));
     PDX_TRY(mark(3));
     // WARMUP/PRUNE over the remaining buckets with the thresholds START produced
     if (nprobe > 1) {
-        p.slot0 = 1;
-        p.nitems = nq * (int64_t)(nprobe - 1);
+        p.slot0 = ivf_chunks;
+        p.nitems = nq * (int64_t)(nprobe - 1) * ivf_chunks;
         p.work_counter = work + 2;
         PDX_TRY(launch_scan(pl.pruner, pl.metric, p, sms, st));
     }
     if (o.scan_event_stop) PDX_TRY(cudaEventRecord(static_cast<cudaEvent_t>(o.scan_event_stop), st));
     PDX_TRY(mark(4));
-    PDX_TRY(launch_select_k(cand, nq, (int64_t)nprobe * k, k, topk, st));
+    PDX_TRY(launch_select_k(cand, nq, (int64_t)nslots * k, k, topk, st));
     // canonical distances from the rows (the original vectors, with the
     // untransformed queries) when the index keeps them
     if (ix->xnary && ix->metric != PDX_L1)

@@ -28,8 +28,10 @@ def gather_merge(dist_local, idx_local, lo: int, metric: str = "l2", group=None)
 
     from . import pdx
 
-    world = dist.get_world_size(group)
     idx_g = torch.where(idx_local >= 0, idx_local + lo, idx_local).to(torch.int64).contiguous()
+    if not dist.is_available() or not dist.is_initialized() or dist.get_world_size(group) == 1:
+        return dist_local, idx_g                      # one shard: nothing to exchange
+    world = dist.get_world_size(group)
     dist_local = dist_local.contiguous()
     gd = [torch.empty_like(dist_local) for _ in range(world)]
     gi = [torch.empty_like(idx_g) for _ in range(world)]
