@@ -623,7 +623,7 @@ pdx_status exact_plan(const pdx_index *ix, int64_t nq, int32_t k, const pdx_sear
             return PDX_ERR_UNSUPPORTED;
         }
         ep->layout = (int)o.layout;
-        ep->bytes = layout_scratch_bytes(ix, nq, k) + rup(C_COUNT * 8);
+        ep->bytes = layout_scratch_bytes(ix, o.layout, nq, k) + rup(C_COUNT * 8);
         return PDX_OK;
     }
     // unpruned search: the tensor-core engine when the index supports it
@@ -685,7 +685,7 @@ pdx_status exact_run(const pdx_index *ix, const float *qd, int64_t nq, int32_t k
     auto mark = [&](int i) -> cudaError_t { return ph ? cudaEventRecord(ph->e[i], st) : cudaSuccess; };
     PDX_TRY(mark(0));
     if (ep.layout != PDX_LAYOUT_PDX) {
-        const size_t lb = layout_scratch_bytes(ix, nq, k);
+        const size_t lb = layout_scratch_bytes(ix, ep.layout, nq, k);
         unsigned long long *counters = reinterpret_cast<unsigned long long *>(scratch + lb);
         PDX_TRY(cudaMemsetAsync(counters, 0, C_COUNT * 8, st));
         unsigned long long *kc = o.stats_device ? reinterpret_cast<unsigned long long *>(o.stats_device) : counters;

@@ -281,7 +281,7 @@ void fill_stats(pdx_search_stats *so, const unsigned long long *c, const pdx_ind
 // Layout scans (pdx_layouts.cu): linear scans over PDX, N-ary, N-ary + gather
 // or DSM storage, merged like the PDX scan's per-item lists.
 bool layout_supported(const pdx_index *ix, int layout, int32_t k, const char **why);
-size_t layout_scratch_bytes(const pdx_index *ix, int64_t nq, int32_t k);
+size_t layout_scratch_bytes(const pdx_index *ix, int layout, int64_t nq, int32_t k);
 pdx_status layout_run(const pdx_index *ix, const float *qd, int64_t nq, int32_t k, int layout, int metric,
                       int out_mode, unsigned char *scratch, float *od, int64_t *oi, int sms, void *ev_start,
                       void *ev_stop, cudaStream_t st);

@@ -39,6 +39,8 @@ struct LayoutParams {
     const int32_t *ids;        // PDX: slot -> id (-1 padding)
     int64_t n;
     int64_t n_pad;             // DSM column length (multiple of 64)
+    int64_t nblk;              // 64-vector blocks scanned (PDX: the index's blocks, whose
+                               // partitions each end in a padded block; else ceil(n/64))
     int32_t d;
     const float *q;
     int64_t nq;
@@ -105,7 +107,7 @@ __global__ void __launch_bounds__(kLayoutWarps * 32) layout_scan_kernel(LayoutPa
     uint64_t *list = reinterpret_cast<uint64_t *>(wbase);
     float *qs = reinterpret_cast<float *>(wbase + list_bytes);
     float *tile = reinterpret_cast<float *>(wbase + list_bytes + q_bytes);
-    const int64_t nblk = (a.n + kBlock - 1) / kBlock;
+    const int64_t nblk = a.nblk;
 
     while (true) {
         unsigned long long wi = 0;
@@ -309,8 +311,14 @@ bool layout_supported(const pdx_index *ix, int layout, int32_t k, const char **w
     return w == nullptr;
 }
 
-size_t layout_scratch_bytes(const pdx_index *ix, int64_t nq, int32_t k) {
-    const int64_t nchunks = ((ix->n + kBlock - 1) / kBlock + kChunkBlocks - 1) / kChunkBlocks;
+// 64-vector blocks a layout scan walks: the PDX blocks (each partition ends
+// in a padded block) or ceil(n/64) groups of rows / DSM columns.
+static int64_t layout_blocks(const pdx_index *ix, int layout) {
+    return layout == PDX_LAYOUT_PDX_KERNEL ? ix->nblocks : (ix->n + kBlock - 1) / kBlock;
+}
+
+size_t layout_scratch_bytes(const pdx_index *ix, int layout, int64_t nq, int32_t k) {
+    const int64_t nchunks = (layout_blocks(ix, layout) + kChunkBlocks - 1) / kChunkBlocks;
     auto rup = [](size_t b) { return (b + 255) & ~size_t(255); };
     return rup((size_t)nq * nchunks * k * 8) + 3 * rup((size_t)nq * k * 8) + rup(8);
 }
@@ -318,7 +326,7 @@ size_t layout_scratch_bytes(const pdx_index *ix, int64_t nq, int32_t k) {
 pdx_status layout_run(const pdx_index *ix, const float *qd, int64_t nq, int32_t k, int layout, int metric,
                       int out_mode, unsigned char *scratch, float *od, int64_t *oi, int sms, void *ev_start,
                       void *ev_stop, cudaStream_t st) {
-    const int64_t nblk = (ix->n + kBlock - 1) / kBlock;
+    const int64_t nblk = layout_blocks(ix, layout);
     const int64_t nchunks = (nblk + kChunkBlocks - 1) / kChunkBlocks;
     auto rup = [](size_t b) { return (b + 255) & ~size_t(255); };
     size_t off = 0;
@@ -339,7 +347,8 @@ pdx_status layout_run(const pdx_index *ix, const float *qd, int64_t nq, int32_t 
     p.x = layout == PDX_LAYOUT_PDX_KERNEL ? ix->data : (layout == PDX_LAYOUT_DSM ? ix->dsm : ix->xnary);
     p.ids = ix->ids;
     p.n = ix->n;
-    p.n_pad = nblk * kBlock;
+    p.n_pad = (ix->n + kBlock - 1) / kBlock * kBlock;
+    p.nblk = nblk;
     p.d = ix->d;
     p.q = qd;
     p.nq = nq;
