@@ -157,6 +157,14 @@ typedef struct pdx_build_opts {
     int32_t keep_dsm;          /* also keep the collection fully dimension-major (DSM: d
                                   columns of ceil(n/64)*64 floats) for the PDX_LAYOUT_DSM
                                   scan (default 0)                                          */
+    int32_t start_clusters;    /* exact indexes: centroids that seed START (Sec. 4). The build
+                                  runs k-means over a sample and keeps, per centroid, the 64
+                                  vectors nearest to it; a pruned L2 search then takes its
+                                  initial threshold from exact distances to the members of
+                                  the query's 4 nearest centroids (real vectors near the
+                                  query) instead of from the first start_vectors stored
+                                  vectors. 0 = automatic (n/1024 centroids, at most 1024,
+                                  for n >= 65536; none below), -1 = none                  */
 } pdx_build_opts;
 
 typedef struct pdx_ivf_opts {

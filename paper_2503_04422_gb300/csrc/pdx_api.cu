@@ -115,7 +115,7 @@ static int rows_vec4(const pdx_index *ix, const float *qrows) {
 
 static void free_index(pdx_index *ix) {
     if (!ix) return;
-    void *ptrs[] = {ix->data, ix->data_lp, ix->scale, ix->xnary, ix->dsm, ix->xtc, ix->xnorm, ix->ids, ix->slot_of, ix->blk_cnt, ix->part_blk, ix->means, ix->cmean, ix->centroids, ix->centroid_norms,
+    void *ptrs[] = {ix->sc_cent, ix->sc_members, ix->data, ix->data_lp, ix->scale, ix->xnary, ix->dsm, ix->xtc, ix->xnorm, ix->ids, ix->slot_of, ix->blk_cnt, ix->part_blk, ix->means, ix->cmean, ix->centroids, ix->centroid_norms,
                     ix->assign, ix->rot, ix->shift, ix->pca_var, ix->resid, ix->chk, ix->cdata, ix->cids};
     for (void *p : ptrs)
         if (p) cudaFree(p);
@@ -241,6 +241,60 @@ static pdx_status keep_rows(pdx_index *ix, const float *xrows, cudaStream_t st) 
     PDX_TRY(dalloc(ix, &ix->xnary, (size_t)ix->n * ix->d));
     PDX_TRY(cudaMemcpyAsync(ix->xnary, xrows, (size_t)ix->n * ix->d * 4, cudaMemcpyDeviceToDevice, st));
     PDX_TRY(cudaStreamSynchronize(st));
+    return PDX_OK;
+}
+
+// START clusters of an exact index: Lloyd's k-means (8 iterations, the IVF
+// kernels) over an evenly strided sample of 64 vectors per centroid, every
+// vector assigned to its nearest centroid, and per centroid the ids of the
+// kStartMembers assigned vectors nearest to it (ties: lower id). A search's
+// START takes exact distances to the members of the query's kStartProbe
+// nearest centroids: real vectors near the query, so the initial threshold is
+// already close to the final k-th distance.
+static pdx_status build_start_clusters(pdx_index *ix, const float *xd, int32_t C, cudaStream_t st) {
+    const int64_t n = ix->n;
+    const int d = ix->d;
+    const int64_t m = std::min<int64_t>(n, (int64_t)C * 64);
+    const int64_t stride = n / m;
+    Scratch scr(st);
+    PDX_TRY(scr.reserve(rup((size_t)m * d * 4) + rup((size_t)C * d * 4) + rup((size_t)C * 4) + rup((size_t)n * 4) +
+                        rup((size_t)n * 4)));
+    float *sample = scr.take<float>((size_t)m * d);
+    float *sums = scr.take<float>((size_t)C * d);
+    int32_t *counts = scr.take<int32_t>((size_t)C);
+    int32_t *assign = scr.take<int32_t>((size_t)n);
+    float *best = scr.take<float>((size_t)n);
+    PDX_CHECK_SCRATCH(scr);
+    PDX_TRY(cudaMemcpy2DAsync(sample, (size_t)d * 4, xd, (size_t)stride * d * 4, (size_t)d * 4, (size_t)m,
+                              cudaMemcpyDeviceToDevice, st));
+    PDX_TRY(dalloc(ix, &ix->sc_cent, (size_t)C * d));
+    PDX_TRY(cudaMemcpy2DAsync(ix->sc_cent, (size_t)d * 4, sample, (size_t)(m / C) * d * 4, (size_t)d * 4, (size_t)C,
+                              cudaMemcpyDeviceToDevice, st));
+    for (int it = 0; it < 8; ++it) {
+        PDX_TRY(launch_nearest_centroids(sample, m, d, ix->sc_cent, nullptr, C, assign, nullptr, st));
+        PDX_TRY(launch_kmeans_update(sample, m, d, assign, C, sums, counts, ix->sc_cent, st));
+    }
+    PDX_TRY(launch_nearest_centroids(xd, n, d, ix->sc_cent, nullptr, C, assign, best, st));
+    std::vector<int32_t> ha((size_t)n);
+    std::vector<float> hb((size_t)n);
+    PDX_TRY(cudaMemcpyAsync(ha.data(), assign, (size_t)n * 4, cudaMemcpyDeviceToHost, st));
+    PDX_TRY(cudaMemcpyAsync(hb.data(), best, (size_t)n * 4, cudaMemcpyDeviceToHost, st));
+    PDX_TRY(cudaStreamSynchronize(st));
+    std::vector<std::vector<std::pair<float, int32_t>>> per((size_t)C);
+    for (int64_t i = 0; i < n; ++i) per[(size_t)ha[(size_t)i]].push_back({hb[(size_t)i], (int32_t)i});
+    const int M = kStartMembers;
+    std::vector<int32_t> mem((size_t)C * M, -1);
+    for (int c = 0; c < C; ++c) {
+        auto &v = per[(size_t)c];
+        const size_t take = std::min<size_t>(v.size(), (size_t)M);
+        std::partial_sort(v.begin(), v.begin() + take, v.end());
+        for (size_t i = 0; i < take; ++i) mem[(size_t)c * M + i] = v[i].second;
+    }
+    PDX_TRY(dalloc(ix, &ix->sc_members, mem.size()));
+    PDX_TRY(cudaMemcpyAsync(ix->sc_members, mem.data(), mem.size() * 4, cudaMemcpyHostToDevice, st));
+    PDX_TRY(cudaStreamSynchronize(st));
+    ix->sc_c = C;
+    ix->sc_m = M;
     return PDX_OK;
 }
 
@@ -394,6 +448,10 @@ pdx_status pdx_build_layout(const float *x, int64_t n, int32_t d, const pdx_buil
         return PDX_ERR_UNSUPPORTED;
     }
     if (o.partition_size == 0) o.partition_size = 10000;
+    if (o.start_clusters < -1) {
+        set_error("pdx_build_layout: start_clusters=%d (0 automatic, -1 none, or a count)", o.start_clusters);
+        return PDX_ERR_ARG;
+    }
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     pdx_index *ix = new (std::nothrow) pdx_index();
     if (!ix) {
@@ -441,6 +499,11 @@ pdx_status pdx_build_layout(const float *x, int64_t n, int32_t d, const pdx_buil
         if (s == PDX_OK) {
             cudaError_t e = cudaStreamSynchronize(st);
             if (e != cudaSuccess) s = cuda_status(e, "cudaStreamSynchronize", __LINE__);
+        }
+        if (s == PDX_OK) {  // START clusters (0: automatic, one per 1024 vectors from 64k vectors on)
+            int32_t C = o.start_clusters;
+            if (C == 0) C = n >= 65536 ? (int32_t)std::min<int64_t>(1024, n / 1024) : 0;
+            if (C > 0) s = build_start_clusters(ix, xd, (int32_t)std::min<int64_t>(C, n), st);
         }
         if (s == PDX_OK && o.keep_dsm) {  // the fully dimension-major copy (DSM layout scan)
             const int64_t n_pad = (n + kBlock - 1) / kBlock * kBlock;
@@ -648,7 +711,11 @@ pdx_status exact_plan(const pdx_index *ix, int64_t nq, int32_t k, const pdx_sear
     ep->nslots = ix->nparts * ep->chunks;
     ep->start = (pl.pruner != PDX_PRUNE_NONE) && !o.tau_fixed;
     ep->start_blk = 0;
-    if (ep->start) {
+    // START from the query's nearest start clusters when the index has them
+    // (L2 ranking), else from the first start_vectors stored vectors
+    ep->start_clusters = ep->start && ix->sc_c > 0 && pl.metric == PDX_L2;
+    ep->sc_ld = ep->start_clusters ? ((int64_t)ix->sc_c + kBlock - 1) / kBlock * kBlock : 0;
+    if (ep->start && !ep->start_clusters) {
         int64_t sv = std::max<int64_t>(o.start_vectors, k);
         ep->start_blk = (int)std::min<int64_t>(ix->nblocks, (sv + kBlock - 1) / kBlock);
     }
@@ -662,6 +729,9 @@ pdx_status exact_plan(const pdx_index *ix, int64_t nq, int32_t k, const pdx_sear
                + rup(ep->op.bytes)                              // visit orders
                + rup((size_t)nq * kPoolCap * 4) + rup((size_t)nq * 4);  // shared candidate pools
     if (ep->start) b += rup((size_t)nq * ep->Lstart * 8) + rup((size_t)nq * k * 8);
+    if (ep->start_clusters)
+        b += rup((size_t)nq * ep->sc_ld * 8) + rup((size_t)nq * kStartProbe * 8) +
+             rup((size_t)nq * kStartProbe * ix->sc_m * 8);
     if (o.tau_init) b += rup((size_t)nq * 4);
     ep->mlp_bytes = 0;
     if (ep->op.mode == 2) {
@@ -734,6 +804,10 @@ pdx_status exact_run(const pdx_index *ix, const float *qd, int64_t nq, int32_t k
     int32_t *pool_cnt = reinterpret_cast<int32_t *>(take((size_t)nq * 4));
     uint64_t *skeys = ep.start ? reinterpret_cast<uint64_t *>(take((size_t)nq * ep.Lstart * 8)) : nullptr;
     uint64_t *stopk = ep.start ? reinterpret_cast<uint64_t *>(take((size_t)nq * k * 8)) : nullptr;
+    uint64_t *sc_keys = ep.start_clusters ? reinterpret_cast<uint64_t *>(take((size_t)nq * ep.sc_ld * 8)) : nullptr;
+    uint64_t *sc_near = ep.start_clusters ? reinterpret_cast<uint64_t *>(take((size_t)nq * kStartProbe * 8)) : nullptr;
+    uint64_t *sc_mkeys =
+        ep.start_clusters ? reinterpret_cast<uint64_t *>(take((size_t)nq * kStartProbe * ix->sc_m * 8)) : nullptr;
     unsigned char *mlp_ws = ep.mlp_bytes ? take(ep.mlp_bytes) : nullptr;
     float *tau_in = o.tau_init ? reinterpret_cast<float *>(take((size_t)nq * 4)) : nullptr;
     if (off > ep.bytes) {
@@ -778,7 +852,19 @@ pdx_status exact_run(const pdx_index *ix, const float *qd, int64_t nq, int32_t k
     // kernels accumulate into the caller's device stats when given, else into scratch
     unsigned long long *kc = o.stats_device ? reinterpret_cast<unsigned long long *>(o.stats_device) : counters;
     if (counters_out) *counters_out = kc;
-    if (ep.start) {
+    if (ep.start_clusters) {
+        // START (Sec. 4) from the query's kStartProbe nearest start clusters:
+        // exact distances to their members give every query an initial
+        // k-th-best threshold of real vectors near it
+        const int P = kStartProbe, M = ix->sc_m;
+        PDX_TRY(launch_dense_keys_rows(qd, nq, ix->sc_cent, ix->sc_c, d, ep.sc_ld, sc_keys, st));
+        PDX_TRY(launch_select_k(sc_keys, nq, ep.sc_ld, P, sc_near, st));
+        PDX_TRY(launch_member_keys(qd, nq, d, ix->xnary, ix->data, ix->slot_of, sc_near, P, ix->sc_members, M, sc_mkeys,
+                                   st));
+        PDX_TRY(launch_select_k(sc_mkeys, nq, (int64_t)P * M, k, stopk, st));
+        PDX_TRY(launch_tau_from_keys(stopk, nq, k, tau, st));
+        PDX_TRY(launch_add_u64(kc + C_START, (unsigned long long)nq * ((uint64_t)ix->sc_c + (uint64_t)P * M) * d, st));
+    } else if (ep.start) {
         // START (Sec. 4): exact distances of the first start_vectors stored
         // vectors give every query an initial k-th-best threshold
         if (ix->storage == PDX_F32) {

@@ -18,6 +18,8 @@ constexpr int kMaxK = 1024;
 constexpr int kMaxD = 4096;
 constexpr int kMaxSortUnits = 256;  // zone keys a scan warp sorts in-kernel (8 per lane)
 constexpr int kPoolCap = 256;       // shared candidate distances per query (8 per lane)
+constexpr int kStartProbe = 4;      // start clusters a query's START reads
+constexpr int kStartMembers = 64;   // member vectors kept per start cluster
 
 // Device counters, in the order of the first fields of pdx_search_stats
 // (slot 7 is bytes_logical, which the host derives and no kernel writes).
@@ -55,8 +57,12 @@ struct pdx_index {
                                     // tensor-core dense engine; row finish; canonical refine).
                                     // A rotated or projected IVF index keeps the original
                                     // (untransformed) vectors here.
-    float *dsm = nullptr;           // [d][n_pad] fully dimension-major copy (keep_dsm), n_pad = nblocks*64
-                                    // for an unpartitioned count: ceil(n/64)*64
+    float *dsm = nullptr;           // [d][n_pad] fully dimension-major copy (keep_dsm), n_pad = ceil(n/64)*64
+    // START clusters (exact indexes): k-means centroids over a sample and, for
+    // each, the ids of the sc_m vectors nearest to it among those assigned to it
+    int32_t sc_c = 0, sc_m = 0;
+    float *sc_cent = nullptr;       // [sc_c][d] row-major
+    int32_t *sc_members = nullptr;  // [sc_c][sc_m], -1 = padding
     float *xtc = nullptr;           // [n][d] the rows rounded to TF32 (tensor-core operand)
     float *xnorm = nullptr;         // [n][4] (||x||^2, ||x||, ||x - tf32(x)||, 0) (dense engine)
     int32_t *ids = nullptr;         // [nblocks*64]
@@ -257,6 +263,8 @@ struct ExactPlan {
     size_t mlp_bytes = 0;      // learned order: centroid keys, nearest, inputs, hidden, scores
     int64_t mlp_Lc = 0;
     int layout = 0;            // pdx_layout of an unpruned scan (0: the PDX scan path)
+    bool start_clusters = false;  // START from the query's nearest start clusters
+    int64_t sc_ld = 0;         // padded centroid count of the centroid keys
     bool dense = false;        // tensor-core engine (pdx_dense.cu) instead of the scan
     int dense_cap = 0;         // its candidate entries per query
     size_t bytes = 0;
@@ -303,6 +311,11 @@ size_t scan_warp_smem(int d, int k, int zone_dims, int order);
 // as (distance, id) keys [nq][nvec_pad].
 cudaError_t launch_dense_keys(const float *q, int64_t nq, const float *data, const int32_t *ids,
                               int32_t d, int32_t nblk, int metric, uint64_t *keys, cudaStream_t st);
+// START from start clusters: exact distances to the members of each query's
+// P nearest clusters (nearest: [nq][P] centroid keys), keys [nq][P*M].
+cudaError_t launch_member_keys(const float *q, int64_t nq, int32_t d, const float *rows, const float *data,
+                               const int32_t *slot_of, const uint64_t *nearest, int32_t P, const int32_t *members,
+                               int32_t M, uint64_t *keys, cudaStream_t st);
 // START over row-major FP32 vectors: keys[qi*ld + r] for r < nrows <= ld.
 cudaError_t launch_dense_keys_rows(const float *q, int64_t nq, const float *x, int32_t nrows, int32_t d, int64_t ld,
                                    uint64_t *keys, cudaStream_t st);

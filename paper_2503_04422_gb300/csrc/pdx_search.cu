@@ -1161,6 +1161,56 @@ cudaError_t launch_dense_keys_rows(const float *q, int64_t nq, const float *x, i
     return counted(cudaGetLastError());
 }
 
+// START from the query's nearest start clusters: one CTA per query, a warp
+// per member vector, exact FP32 L2 from the row-major vectors (or the PDX
+// blocks through slot_of when the index keeps no rows). keys[qi][p*M + m] =
+// (distance, id) of member m of the query's p-th nearest cluster (empty for
+// padding). Each vector belongs to one cluster, so the keys are distinct
+// vectors and their k-th smallest distance bounds the final k-th from above.
+__global__ void member_keys_kernel(const float *__restrict__ q, int64_t nq, int32_t d, const float *__restrict__ rows,
+                                   const float *__restrict__ data, const int32_t *__restrict__ slot_of,
+                                   const uint64_t *__restrict__ nearest, int32_t P, const int32_t *__restrict__ members,
+                                   int32_t M, uint64_t *__restrict__ keys) {
+    const int64_t qi = blockIdx.x;
+    if (qi >= nq) return;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    const float *qrow = q + qi * d;
+    for (int e = warp; e < P * M; e += nw) {
+        const int p = e / M, m = e % M;
+        const uint64_t ck = nearest[qi * P + p];
+        int32_t id = -1;
+        if (ck != kEmptyKey) id = members[(int64_t)key_id(ck) * M + m];
+        uint64_t key = kEmptyKey;
+        if (id >= 0) {
+            float acc = 0.f;
+            if (rows) {
+                const float *xr = rows + (int64_t)id * d;
+                for (int j = lane; j < d; j += 32) {
+                    const float t = qrow[j] - __ldg(xr + j);
+                    acc = fmaf(t, t, acc);
+                }
+            } else {
+                const int32_t slot = slot_of[id];
+                const float *xb = data + (int64_t)(slot / kBlock) * d * kBlock + (slot % kBlock);
+                for (int j = lane; j < d; j += 32) {
+                    const float t = qrow[j] - __ldg(xb + (int64_t)j * kBlock);
+                    acc = fmaf(t, t, acc);
+                }
+            }
+            key = make_key(warp_sum(acc), id);
+        }
+        if (lane == 0) keys[qi * (int64_t)P * M + e] = key;
+    }
+}
+
+cudaError_t launch_member_keys(const float *q, int64_t nq, int32_t d, const float *rows, const float *data,
+                               const int32_t *slot_of, const uint64_t *nearest, int32_t P, const int32_t *members,
+                               int32_t M, uint64_t *keys, cudaStream_t st) {
+    if (nq == 0) return cudaSuccess;
+    member_keys_kernel<<<(unsigned)nq, 256, 0, st>>>(q, nq, d, rows, data, slot_of, nearest, P, members, M, keys);
+    return counted(cudaGetLastError());
+}
+
 cudaError_t launch_dense_keys(const float *q, int64_t nq, const float *data, const int32_t *ids, int32_t d,
                               int32_t nblk, int metric, uint64_t *keys, cudaStream_t st) {
     if (nq == 0 || nblk == 0) return cudaSuccess;

@@ -36,7 +36,7 @@ STATUS_NAMES = {0: "PDX_OK", 1: "PDX_ERR_ARG", 2: "PDX_ERR_OOM", 3: "PDX_ERR_CUD
 class pdx_build_opts(ctypes.Structure):
     _fields_ = [("struct_size", ctypes.c_uint32), ("metric", ctypes.c_int), ("storage", ctypes.c_int),
                 ("partition_size", ctypes.c_uint32), ("keep_rows", ctypes.c_int32),
-                ("dense_rows", ctypes.c_int32), ("keep_dsm", ctypes.c_int32)]
+                ("dense_rows", ctypes.c_int32), ("keep_dsm", ctypes.c_int32), ("start_clusters", ctypes.c_int32)]
 
 
 class pdx_ivf_opts(ctypes.Structure):
@@ -207,7 +207,7 @@ class Index:
 
 
 def build_opts(metric="l2", storage="f32", partition_size=10000, keep_rows=True,
-               dense_rows=False, keep_dsm=False) -> pdx_build_opts:
+               dense_rows=False, keep_dsm=False, start_clusters=0) -> pdx_build_opts:
     o = pdx_build_opts()
     lib().pdx_default_build_opts(ctypes.byref(o))
     o.metric = METRIC[metric]
@@ -216,6 +216,7 @@ def build_opts(metric="l2", storage="f32", partition_size=10000, keep_rows=True,
     o.keep_rows = int(bool(keep_rows))
     o.dense_rows = int(bool(dense_rows))
     o.keep_dsm = int(bool(keep_dsm))
+    o.start_clusters = int(start_clusters)
     return o
 
 
@@ -252,7 +253,7 @@ def search_opts(pruner="bond", order="dist_to_means", zone_dims=None, selection_
 
 
 def pdx_build_layout(x, metric="l2", partition_size=10000, storage="f32", stream=None,
-                     dense_rows=False, keep_dsm=False, keep_rows=True) -> Index:
+                     dense_rows=False, keep_dsm=False, keep_rows=True, start_clusters=0) -> Index:
     """Exact-search index over x [n][d] (Sec. 3, Sec. 6.6); dense_rows also
     keeps the row-major FP32 vectors the tensor-core engine reads, keep_dsm a
     fully dimension-major copy for the DSM layout scan."""
@@ -260,7 +261,8 @@ def pdx_build_layout(x, metric="l2", partition_size=10000, storage="f32", stream
     if len(shape) != 2:
         raise ValueError("x must be [n][d]")
     h = ctypes.c_void_p()
-    o = build_opts(metric, storage, partition_size, keep_rows=keep_rows, dense_rows=dense_rows, keep_dsm=keep_dsm)
+    o = build_opts(metric, storage, partition_size, keep_rows=keep_rows, dense_rows=dense_rows, keep_dsm=keep_dsm,
+                   start_clusters=start_clusters)
     _check(lib().pdx_build_layout(p, shape[0], shape[1], ctypes.byref(o), _stream(cuda, stream), ctypes.byref(h)),
            "pdx_build_layout")
     del keep
