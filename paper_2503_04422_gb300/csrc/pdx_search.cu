@@ -1161,53 +1161,69 @@ cudaError_t launch_dense_keys_rows(const float *q, int64_t nq, const float *x, i
     return counted(cudaGetLastError());
 }
 
-// START from the query's nearest start clusters: one CTA per query, a warp
-// per member vector, exact FP32 L2 from the row-major vectors (or the PDX
-// blocks through slot_of when the index keeps no rows). keys[qi][p*M + m] =
-// (distance, id) of member m of the query's p-th nearest cluster (empty for
-// padding). Each vector belongs to one cluster, so the keys are distinct
-// vectors and their k-th smallest distance bounds the final k-th from above.
+// START from the query's nearest start clusters: a warp per (query, member)
+// vector, exact FP32 L2 from the row-major vectors (16-byte pieces, eight in
+// flight per lane, when d is a multiple of 4 and the rows are aligned), or
+// from the PDX blocks through slot_of when the index keeps no rows.
+// keys[qi][p*M + m] = (distance, id) of member m of the query's p-th nearest
+// cluster (empty for padding). Each vector belongs to one cluster, so the keys
+// are distinct vectors and their k-th smallest distance bounds the final k-th
+// from above.
 __global__ void member_keys_kernel(const float *__restrict__ q, int64_t nq, int32_t d, const float *__restrict__ rows,
                                    const float *__restrict__ data, const int32_t *__restrict__ slot_of,
                                    const uint64_t *__restrict__ nearest, int32_t P, const int32_t *__restrict__ members,
-                                   int32_t M, uint64_t *__restrict__ keys) {
+                                   int32_t M, int vec4, uint64_t *__restrict__ keys) {
     const int64_t qi = blockIdx.x;
-    if (qi >= nq) return;
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-    const float *qrow = q + qi * d;
-    for (int e = warp; e < P * M; e += nw) {
-        const int p = e / M, m = e % M;
-        const uint64_t ck = nearest[qi * P + p];
-        int32_t id = -1;
-        if (ck != kEmptyKey) id = members[(int64_t)key_id(ck) * M + m];
-        uint64_t key = kEmptyKey;
-        if (id >= 0) {
-            float acc = 0.f;
-            if (rows) {
-                const float *xr = rows + (int64_t)id * d;
-                for (int j = lane; j < d; j += 32) {
-                    const float t = qrow[j] - __ldg(xr + j);
-                    acc = fmaf(t, t, acc);
-                }
-            } else {
-                const int32_t slot = slot_of[id];
-                const float *xb = data + (int64_t)(slot / kBlock) * d * kBlock + (slot % kBlock);
-                for (int j = lane; j < d; j += 32) {
-                    const float t = qrow[j] - __ldg(xb + (int64_t)j * kBlock);
-                    acc = fmaf(t, t, acc);
+    const int lane = threadIdx.x & 31;
+    const int e = blockIdx.y * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (qi >= nq || e >= P * M) return;
+    const int p = e / M, m = e % M;
+    const uint64_t ck = nearest[qi * P + p];
+    const int32_t id = (ck != kEmptyKey) ? members[(int64_t)key_id(ck) * M + m] : -1;
+    uint64_t key = kEmptyKey;
+    if (id >= 0) {
+        const float *qrow = q + qi * d;
+        float acc = 0.f;
+        if (rows && vec4) {
+            const float4 *x4 = reinterpret_cast<const float4 *>(rows + (int64_t)id * d);
+            const float4 *q4 = reinterpret_cast<const float4 *>(qrow);
+            const int n4 = d >> 2;
+            for (int base = lane; base < n4; base += 256) {
+                float4 xv[8];
+#pragma unroll
+                for (int u = 0; u < 8; ++u)
+                    xv[u] = (base + 32 * u < n4) ? __ldg(x4 + base + 32 * u) : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    if (base + 32 * u < n4) {
+                        const float4 qv = __ldg(q4 + base + 32 * u);
+                        acc = term<MT_L2>(qv.x, xv[u].x, acc);
+                        acc = term<MT_L2>(qv.y, xv[u].y, acc);
+                        acc = term<MT_L2>(qv.z, xv[u].z, acc);
+                        acc = term<MT_L2>(qv.w, xv[u].w, acc);
+                    }
                 }
             }
-            key = make_key(warp_sum(acc), id);
+        } else if (rows) {
+            const float *xr = rows + (int64_t)id * d;
+            for (int j = lane; j < d; j += 32) acc = term<MT_L2>(qrow[j], __ldg(xr + j), acc);
+        } else {
+            const int32_t slot = slot_of[id];
+            const float *xb = data + (int64_t)(slot / kBlock) * d * kBlock + (slot % kBlock);
+            for (int j = lane; j < d; j += 32) acc = term<MT_L2>(qrow[j], __ldg(xb + (int64_t)j * kBlock), acc);
         }
-        if (lane == 0) keys[qi * (int64_t)P * M + e] = key;
+        key = make_key(warp_sum(acc), id);
     }
+    if (lane == 0) keys[qi * (int64_t)P * M + e] = key;
 }
 
 cudaError_t launch_member_keys(const float *q, int64_t nq, int32_t d, const float *rows, const float *data,
                                const int32_t *slot_of, const uint64_t *nearest, int32_t P, const int32_t *members,
                                int32_t M, uint64_t *keys, cudaStream_t st) {
-    if (nq == 0) return cudaSuccess;
-    member_keys_kernel<<<(unsigned)nq, 256, 0, st>>>(q, nq, d, rows, data, slot_of, nearest, P, members, M, keys);
+    if (nq == 0 || P * M == 0) return cudaSuccess;
+    const int vec4 = (d % 4 == 0 && ((uintptr_t)rows & 15u) == 0 && ((uintptr_t)q & 15u) == 0) ? 1 : 0;
+    dim3 grid((unsigned)nq, (unsigned)((P * M + 7) / 8));
+    member_keys_kernel<<<grid, 256, 0, st>>>(q, nq, d, rows, data, slot_of, nearest, P, members, M, vec4, keys);
     return counted(cudaGetLastError());
 }
 
