@@ -388,10 +388,7 @@ __device__ __forceinline__ uint32_t pool_kth(const ScanParams &a, int64_t qi, in
 // kRowUnroll of them (512 bytes per warp each) before the first is consumed;
 // otherwise lanes take dimensions j = lane, lane + 32, ... (128 contiguous
 // bytes per request).
-#ifndef PDX_ROW_UNROLL
-#define PDX_ROW_UNROLL 4
-#endif
-constexpr int kRowUnroll = PDX_ROW_UNROLL;
+constexpr int kRowUnroll = 4;
 template <int MET>
 __device__ __forceinline__ float row_dist(const float *__restrict__ xrow, const float *__restrict__ qrow, int D,
                                           int lane, bool vec4) {
@@ -423,6 +420,63 @@ __device__ __forceinline__ float row_dist(const float *__restrict__ xrow, const 
         }
     } else {
         for (int j = lane; j < D; j += 32) acc = term<MET>(qrow[j], __ldg(xrow + j), acc);
+    }
+    return rank_dist<MET>(warp_sum(acc));
+}
+
+// The same with an early exit (L2 / L1, whose partial sums only grow): after
+// each round of loads but the last, the partial over the dimensions read so
+// far is compared with thr (already slack-widened); above it the vector is
+// pruned and *visited < D tells the caller how far it got.
+template <int MET>
+__device__ __forceinline__ float row_dist_bounded(const float *__restrict__ xrow, const float *__restrict__ qrow,
+                                                  int D, int lane, bool vec4, float thr, int *visited) {
+    float acc = 0.f;
+    *visited = D;
+    if (vec4) {
+        const float4 *x4 = reinterpret_cast<const float4 *>(xrow);
+        const float4 *q4 = reinterpret_cast<const float4 *>(qrow);
+        const int n4 = D >> 2;
+        for (int base = lane; base < n4; base += 32 * kRowUnroll) {
+            float4 xv[kRowUnroll];
+#pragma unroll
+            for (int u = 0; u < kRowUnroll; ++u) {
+                const int i = base + 32 * u;
+                xv[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+                if (i < n4) xv[u] = __ldg(x4 + i);
+            }
+#pragma unroll
+            for (int u = 0; u < kRowUnroll; ++u) {
+                const int i = base + 32 * u;
+                if (i < n4) {
+                    const float4 qv = __ldg(q4 + i);
+                    acc = term<MET>(qv.x, xv[u].x, acc);
+                    acc = term<MET>(qv.y, xv[u].y, acc);
+                    acc = term<MET>(qv.z, xv[u].z, acc);
+                    acc = term<MET>(qv.w, xv[u].w, acc);
+                }
+            }
+            const int done = (base - lane + 32 * kRowUnroll) * 4;  // dimensions read so far
+            if (MET != MT_IP && done < D) {
+                const float part = warp_sum(acc);
+                if (part > thr) {
+                    *visited = done;
+                    return part;
+                }
+            }
+        }
+    } else {
+        for (int j0 = 0; j0 < D; j0 += 512) {
+            const int j1 = min(D, j0 + 512);
+            for (int j = j0 + lane; j < j1; j += 32) acc = term<MET>(qrow[j], __ldg(xrow + j), acc);
+            if (MET != MT_IP && j1 < D) {
+                const float part = warp_sum(acc);
+                if (part > thr) {
+                    *visited = j1;
+                    return part;
+                }
+            }
+        }
     }
     return rank_dist<MET>(warp_sum(acc));
 }
@@ -908,11 +962,19 @@ __global__ void __launch_bounds__(256, OCC) pdxsearch_kernel(ScanParams a) {
                 unsigned m3 = __ballot_sync(kFull, alive & 8u) & 0xffffu;
                 nfinal = __popc(m0) + __popc(m1) + __popc(m2) + __popc(m3);
             } else if (rows) {
+                int finished = 0;
                 for (int m = 0; m < nsurv; ++m) {
                     const int v = w.sv[m];
                     const int id = a.ids[(int64_t)b * kBlock + v];
-                    const float dd = row_dist<MET>(a.xnary + (int64_t)id * D, qrow_r, D, lane, a.rows_vec4);
-                    if (lane == 0) w.ctr[S_VALUES] += (unsigned long long)D;
+                    // the row is read in rounds; a partial above the current
+                    // threshold ends it early (the vector is pruned)
+                    const float thr_r = slack(fminf(tau_loc, o2f(*tau_g_ptr)), a.gamma);
+                    int vis;
+                    const float dd = row_dist_bounded<MET>(a.xnary + (int64_t)id * D, qrow_r, D, lane, a.rows_vec4,
+                                                           thr_r, &vis);
+                    if (lane == 0) w.ctr[S_VALUES] += (unsigned long long)vis;
+                    if (vis < D) continue;
+                    ++finished;
                     // lane 0 reads the shared threshold and the warp follows it
                     if (__shfl_sync(kFull, (int)(dd <= slack(o2f(*tau_g_ptr), a.gamma)), 0)) {
                         topk_insert(w.topk, cnt, k, make_key(dd, id), lane);
@@ -923,7 +985,7 @@ __global__ void __launch_bounds__(256, OCC) pdxsearch_kernel(ScanParams a) {
                         }
                     }
                 }
-                nfinal = nsurv;
+                nfinal = finished;
             } else if (nsurv > 0) {
                 float dist = rank_dist<MET>(my_p);
                 bool cand = (lane < nsurv) && (dist <= slack(o2f(*tau_g_ptr), a.gamma));
