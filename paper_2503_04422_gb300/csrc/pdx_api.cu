@@ -500,9 +500,9 @@ pdx_status pdx_build_layout(const float *x, int64_t n, int32_t d, const pdx_buil
             cudaError_t e = cudaStreamSynchronize(st);
             if (e != cudaSuccess) s = cuda_status(e, "cudaStreamSynchronize", __LINE__);
         }
-        if (s == PDX_OK) {  // START clusters (0: automatic, one per 1024 vectors from 64k vectors on)
+        if (s == PDX_OK) {  // START clusters (0: automatic, one per 4096 vectors from 64k vectors on)
             int32_t C = o.start_clusters;
-            if (C == 0) C = n >= 65536 ? (int32_t)std::min<int64_t>(1024, n / 1024) : 0;
+            if (C == 0) C = n >= 65536 ? (int32_t)std::min<int64_t>(1024, n / 4096) : 0;
             if (C > 0) s = build_start_clusters(ix, xd, (int32_t)std::min<int64_t>(C, n), st);
         }
         if (s == PDX_OK && o.keep_dsm) {  // the fully dimension-major copy (DSM layout scan)

@@ -18,7 +18,7 @@ constexpr int kMaxK = 1024;
 constexpr int kMaxD = 4096;
 constexpr int kMaxSortUnits = 256;  // zone keys a scan warp sorts in-kernel (8 per lane)
 constexpr int kPoolCap = 256;       // shared candidate distances per query (8 per lane)
-constexpr int kStartProbe = 4;      // start clusters a query's START reads
+constexpr int kStartProbe = 2;      // start clusters a query's START reads
 constexpr int kStartMembers = 64;   // member vectors kept per start cluster
 
 // Device counters, in the order of the first fields of pdx_search_stats

@@ -927,6 +927,11 @@ __global__ void __launch_bounds__(256, OCC) pdxsearch_kernel(ScanParams a) {
                 }
             }
             // ---------------- merge ----------------
+            // Candidates are tested against this block's threshold thr (its
+            // shared part read one block ahead): tau only decreases, so a
+            // distance above thr cannot be among the final k, and one below
+            // it that the current tau would reject costs a list entry only.
+            // No test waits for a fresh read of the shared tau.
             int nfinal = 0;
             bool pushed = false;
             if (nsurv < 0) {
@@ -937,7 +942,7 @@ __global__ void __launch_bounds__(256, OCC) pdxsearch_kernel(ScanParams a) {
                                               acc.w + __shfl_xor_sync(kFull, acc.w, 16));
                 for (int c = 0; c < 4; ++c) {
                     float dist = rank_dist<MET>(sel4(fm, c));
-                    bool cand = (h == 0) && (alive & (1u << c)) && (dist <= slack(o2f(*tau_g_ptr), a.gamma));
+                    bool cand = (h == 0) && (alive & (1u << c)) && (dist <= thr);
                     unsigned cm = __ballot_sync(kFull, cand);
                     while (cm) {
                         int src = __ffs(cm) - 1;
@@ -950,7 +955,7 @@ __global__ void __launch_bounds__(256, OCC) pdxsearch_kernel(ScanParams a) {
                         topk_insert(w.topk, cnt, k, key, lane);
                         if (lane == 0) w.ctr[S_CAND] += 1;
                         // lane 0 reads the shared threshold and the warp follows it
-                        if (a.pool && __shfl_sync(kFull, (int)(f2o(dd) < *tau_g_ptr), 0)) {
+                        if (a.pool && dd < thr) {
                             pool_push(a, qi, dd, lane);
                             pushed = true;
                         }
@@ -963,23 +968,22 @@ __global__ void __launch_bounds__(256, OCC) pdxsearch_kernel(ScanParams a) {
                 nfinal = __popc(m0) + __popc(m1) + __popc(m2) + __popc(m3);
             } else if (rows) {
                 int finished = 0;
+                // all survivors' ids in one round of loads (lane m: survivor m)
+                const int myid = (lane < nsurv) ? a.ids[(int64_t)b * kBlock + w.sv[lane]] : 0;
                 for (int m = 0; m < nsurv; ++m) {
-                    const int v = w.sv[m];
-                    const int id = a.ids[(int64_t)b * kBlock + v];
-                    // the row is read in rounds; a partial above the current
+                    const int id = __shfl_sync(kFull, myid, m);
+                    // the row is read in rounds; a partial above the block's
                     // threshold ends it early (the vector is pruned)
-                    const float thr_r = slack(fminf(tau_loc, o2f(*tau_g_ptr)), a.gamma);
                     int vis;
                     const float dd = row_dist_bounded<MET>(a.xnary + (int64_t)id * D, qrow_r, D, lane, a.rows_vec4,
-                                                           thr_r, &vis);
+                                                           thr, &vis);
                     if (lane == 0) w.ctr[S_VALUES] += (unsigned long long)vis;
                     if (vis < D) continue;
                     ++finished;
-                    // lane 0 reads the shared threshold and the warp follows it
-                    if (__shfl_sync(kFull, (int)(dd <= slack(o2f(*tau_g_ptr), a.gamma)), 0)) {
+                    if (dd <= thr) {
                         topk_insert(w.topk, cnt, k, make_key(dd, id), lane);
                         if (lane == 0) w.ctr[S_CAND] += 1;
-                        if (a.pool && __shfl_sync(kFull, (int)(f2o(dd) < *tau_g_ptr), 0)) {
+                        if (a.pool && dd < thr) {
                             pool_push(a, qi, dd, lane);
                             pushed = true;
                         }
@@ -988,7 +992,7 @@ __global__ void __launch_bounds__(256, OCC) pdxsearch_kernel(ScanParams a) {
                 nfinal = finished;
             } else if (nsurv > 0) {
                 float dist = rank_dist<MET>(my_p);
-                bool cand = (lane < nsurv) && (dist <= slack(o2f(*tau_g_ptr), a.gamma));
+                bool cand = (lane < nsurv) && (dist <= thr);
                 unsigned cm = __ballot_sync(kFull, cand);
                 while (cm) {
                     int src = __ffs(cm) - 1;
@@ -1000,7 +1004,7 @@ __global__ void __launch_bounds__(256, OCC) pdxsearch_kernel(ScanParams a) {
                     uint64_t key = make_key(dd, id);
                     topk_insert(w.topk, cnt, k, key, lane);
                     if (lane == 0) w.ctr[S_CAND] += 1;
-                    if (a.pool && __shfl_sync(kFull, (int)(f2o(dd) < *tau_g_ptr), 0)) {
+                    if (a.pool && dd < thr) {
                         pool_push(a, qi, dd, lane);
                         pushed = true;
                     }
@@ -1335,9 +1339,53 @@ __global__ void __launch_bounds__(512) select_k_kernel(const uint64_t *__restric
     for (int i = tid; i < k; i += nt) out[row * k + i] = buf[i];
 }
 
+// k <= 8 smallest keys of each row, a warp per row: every lane keeps the
+// smallest keys of its stride of the row in a sorted register list, then k
+// rounds of a warp-wide minimum pop them in order.
+__global__ void select_small_kernel(const uint64_t *__restrict__ keys, int64_t rows, int64_t L, int32_t k,
+                                    uint64_t *__restrict__ out) {
+    const int64_t row = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (row >= rows) return;
+    uint64_t best[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) best[i] = kEmptyKey;
+    const uint64_t *kr = keys + row * L;
+    for (int64_t i = lane; i < L; i += 32) {
+        uint64_t v = kr[i];
+        if (v >= best[7]) continue;
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {  // insertion into the sorted list
+            const uint64_t lo = v < best[j] ? v : best[j];
+            v = v < best[j] ? best[j] : v;
+            best[j] = lo;
+        }
+    }
+    for (int r = 0; r < k; ++r) {
+        uint64_t m = best[0];
+#pragma unroll
+        for (int o = 16; o; o >>= 1) {
+            const uint64_t t = __shfl_xor_sync(kFull, m, o);
+            m = t < m ? t : m;
+        }
+        // the lane holding the minimum (the lowest such lane) pops it
+        const unsigned own = __ballot_sync(kFull, best[0] == m);
+        if (lane == __ffs(own) - 1) {
+#pragma unroll
+            for (int j = 0; j < 7; ++j) best[j] = best[j + 1];
+            best[7] = kEmptyKey;
+        }
+        if (lane == 0) out[row * k + r] = m;
+    }
+}
+
 cudaError_t launch_select_k(const uint64_t *keys, int64_t rows, int64_t L, int32_t k, uint64_t *out,
                             cudaStream_t st) {
     if (rows == 0) return cudaSuccess;
+    if (k <= 8 && L <= 4096) {  // a warp per row
+        select_small_kernel<<<(unsigned)((rows * 32 + 255) / 256), 256, 0, st>>>(keys, rows, L, k, out);
+        return counted(cudaGetLastError());
+    }
     int kpad = pow2_ceil(k);
     int64_t want = (int64_t)kpad + L;
     int sb = pow2_ceil((int)(want < 8192 ? want : 8192));
