@@ -537,7 +537,9 @@ __global__ void __launch_bounds__(256, OCC) pdxsearch_kernel(ScanParams a) {
         // registers waits for no load at all. τ only decreases, so a value one
         // block old still bounds the final k-th distance, and the warp's own
         // candidates are in tau_loc.
-        float tau_ahead = o2f(*tau_g_ptr);
+        // The raw ordered value is kept and converted only when used, so no
+        // instruction waits for the read before the next loads go out.
+        uint32_t tau_ahead = *tau_g_ptr;
         // Every block of a part but its last holds 64 vectors (parts fill their
         // blocks in order), so only an item's last block reads its count. The
         // item's vectors count as scanned and as pruned up front; blocks take
@@ -602,9 +604,11 @@ __global__ void __launch_bounds__(256, OCC) pdxsearch_kernel(ScanParams a) {
                     pend = -1;
                 } else {
                     unsigned vote = 0;
+                    int since = 0;
                     while (bnext < b1) {
-                        const float thr_s = slack(fminf(tau_loc, tau_ahead), a.gamma);
-                        tau_ahead = o2f(*tau_g_ptr);
+                        const float thr_s = slack(fminf(tau_loc, o2f(tau_ahead)), a.gamma);
+                        // the shared tau moves slowly: re-read every 4th pair
+                        if ((++since & 3) == 0) tau_ahead = *tau_g_ptr;
                         const int bb = bnext + h;
                         float4 s4 = make_float4(0.f, 0.f, 0.f, 0.f);
                         unsigned al = 0;
@@ -677,8 +681,8 @@ __global__ void __launch_bounds__(256, OCC) pdxsearch_kernel(ScanParams a) {
             }
             const ET *xb = xbase + (int64_t)b * D * kBlock;
             const int nvalid = (b == b1 - 1) ? a.blk_cnt[b] : kBlock;
-            const float tau_g = tau_ahead;
-            tau_ahead = o2f(*tau_g_ptr);
+            const float tau_g = o2f(tau_ahead);
+            tau_ahead = *tau_g_ptr;
             const float thr = slack(fminf(tau_loc, tau_g), a.gamma);
             unsigned alive = 0xfu;
             if (nvalid < kBlock) {
