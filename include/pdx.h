@@ -395,8 +395,9 @@ pdx_status pdx_search_exact_noalloc(const pdx_index *index, const float *q, int6
  * dimensionality). Each (collection, power-of-two batch bucket) pair is
  * prepared on first use. The search is captured as a CUDA graph and replayed
  * afterwards (use_graphs). Its launch shape (resident scan CTAs per SM, first
- * fetch step, START size) is first chosen by timing candidates on that first
- * batch (autotune). Exact results are identical for every candidate. Tuning
+ * fetch step, i.e. the first prune-check interval, and work-item size in
+ * 64-vector blocks: the automatic size, its half and its double) is first
+ * chosen by timing candidates on that first batch (autotune). Exact results are identical for every candidate. Tuning
  * results persist in the JSON file tune_cache (optional).
  *
  * The server owns one device workspace sized for its largest plan, plus

@@ -7,8 +7,9 @@
 // queries runs in the smallest bucket B >= nq, and rows nq..B-1 of the input
 // buffer hold earlier (valid) queries whose results are ignored. On first use
 // of an entry the tuner times candidate launch shapes on the caller's batch.
-// The shapes are the resident CTAs per SM, the first fetch step and the START
-// size. Every candidate gives the same exact result. The entry then captures
+// The shapes are the resident CTAs per SM, the first fetch step and the size
+// of a work item in 64-vector blocks. Every candidate gives the same exact
+// result. The entry then captures
 // the search into a CUDA graph, and later batches replay it after one copy-in.
 #include <algorithm>
 #include <cstdio>
@@ -35,7 +36,7 @@ struct ServerEntry {
 };
 
 struct TuneRecord {
-    uint32_t ctas, first_step, start_vectors;
+    uint32_t ctas, first_step, blocks_per_item;
     float ms;
 };
 
@@ -70,7 +71,7 @@ static std::string cache_key(const pdx_index *ix, int64_t bucket, int k) {
 }
 
 // Tuner cache file: one JSON object whose keys are cache_key() strings and
-// whose values are {"ctas":..,"first_step":..,"start_vectors":..,"ms":..}.
+// whose values are {"ctas":..,"first_step":..,"blocks_per_item":..,"ms":..}.
 static void load_cache(pdx_server *s) {
     if (!s->o.tune_cache) return;
     FILE *f = fopen(s->o.tune_cache, "r");
@@ -91,11 +92,11 @@ static void load_cache(pdx_server *s) {
         TuneRecord t{};
         unsigned a = 0, b = 0, c = 0;
         float ms = 0.f;
-        if (sscanf(body.c_str(), "{\"ctas\": %u, \"first_step\": %u, \"start_vectors\": %u, \"ms\": %f}", &a, &b, &c,
-                   &ms) == 4) {
+        if (sscanf(body.c_str(), "{\"ctas\": %u, \"first_step\": %u, \"blocks_per_item\": %u, \"ms\": %f}", &a,
+                   &b, &c, &ms) == 4) {
             t.ctas = a;
             t.first_step = b;
-            t.start_vectors = c;
+            t.blocks_per_item = c;
             t.ms = ms;
             s->cache[key] = t;
         }
@@ -111,13 +112,35 @@ static void save_cache(pdx_server *s) {
     fprintf(f, "{\n");
     size_t i = 0;
     for (auto &kv : s->cache) {
-        fprintf(f, "  \"%s\": {\"ctas\": %u, \"first_step\": %u, \"start_vectors\": %u, \"ms\": %.4f}%s\n",
-                kv.first.c_str(), kv.second.ctas, kv.second.first_step, kv.second.start_vectors, kv.second.ms,
+        fprintf(f, "  \"%s\": {\"ctas\": %u, \"first_step\": %u, \"blocks_per_item\": %u, \"ms\": %.4f}%s\n",
+                kv.first.c_str(), kv.second.ctas, kv.second.first_step, kv.second.blocks_per_item, kv.second.ms,
                 ++i < s->cache.size() ? "," : "");
     }
     fprintf(f, "}\n");
     fclose(f);
     std::rename(tmp.c_str(), s->o.tune_cache);
+}
+
+// Work-item sizes the tuner tries: the automatic one and its half and double.
+static std::vector<uint32_t> item_sizes(const pdx_index *ix, int64_t B, int k, const pdx_search_opts &o,
+                                        const SearchPlan &pl, int sms) {
+    pdx_search_opts a = o;
+    a.blocks_per_item = 0;
+    ExactPlan ep;
+    std::vector<uint32_t> out;
+    if (exact_plan(ix, B, k, a, pl, sms, &ep) != PDX_OK || ep.dense || ep.layout) return {o.blocks_per_item};
+    for (int b : {ep.bpi, std::max(1, ep.bpi / 2), ep.bpi * 2})
+        if (std::find(out.begin(), out.end(), (uint32_t)b) == out.end()) out.push_back((uint32_t)b);
+    return out;
+}
+
+// A candidate is tried only if its plan fits the server's workspace.
+static bool plan_fits(pdx_server *s, const pdx_index *ix, int64_t B, const pdx_search_opts &o, const SearchPlan &pl,
+                      uint32_t bpi) {
+    pdx_search_opts c = o;
+    c.blocks_per_item = bpi;
+    ExactPlan ep;
+    return exact_plan(ix, B, s->o.k, c, pl, s->sms, &ep) == PDX_OK && ep.bytes <= s->work_bytes;
 }
 
 static int bucket_of(int64_t nq) {
@@ -172,32 +195,37 @@ static pdx_status prepare_entry(pdx_server *s, int c, int bk) {
         if (it != s->cache.end()) {
             o.ctas_per_sm = it->second.ctas;
             o.first_step = it->second.first_step;
-            o.start_vectors = it->second.start_vectors;
+            o.blocks_per_item = it->second.blocks_per_item;
             E.tuned_ms = it->second.ms;
         } else {
+            // candidates: resident CTAs per SM x first fetch step (the first
+            // prune-check interval) x work-item size in 64-vector blocks (the
+            // automatic size, half of it, twice it), each within the workspace
             float best = 1e30f;
-            TuneRecord bt{o.ctas_per_sm, o.first_step, o.start_vectors, 0.f};
+            TuneRecord bt{o.ctas_per_sm, o.first_step, o.blocks_per_item, 0.f};
             const uint32_t ctas[] = {3, 4};
             const uint32_t steps[] = {4, 8};
-            const uint32_t starts[] = {1024, 4096};
+            std::vector<uint32_t> bpis;
+            for (uint32_t b : item_sizes(ix, B, s->o.k, o, pl, s->sms))
+                if (plan_fits(s, ix, B, o, pl, b)) bpis.push_back(b);
             for (uint32_t ct : ctas)
                 for (uint32_t fs : steps)
-                    for (uint32_t sv : starts) {
+                    for (uint32_t bp : bpis) {
                         pdx_search_opts c2 = o;
                         c2.ctas_per_sm = ct;
                         c2.first_step = fs;
-                        c2.start_vectors = sv;
+                        c2.blocks_per_item = bp;
                         float ms = 0.f;
                         r = time_candidate(s, ix, B, c2, &ms);
                         if (r != PDX_OK) return r;
                         if (ms < best) {
                             best = ms;
-                            bt = TuneRecord{ct, fs, sv, ms};
+                            bt = TuneRecord{ct, fs, bp, ms};
                         }
                     }
             o.ctas_per_sm = bt.ctas;
             o.first_step = bt.first_step;
-            o.start_vectors = bt.start_vectors;
+            o.blocks_per_item = bt.blocks_per_item;
             E.tuned_ms = best;
             s->cache[key] = bt;
             s->tunings += 1;
@@ -334,19 +362,29 @@ extern "C" pdx_status pdx_server_create(const pdx_index *const *indexes, int32_t
         pdx_search_opts o;
         SearchPlan pl;
         pdx_search_opts base = opts->search;
-        for (uint32_t sv : {base.start_vectors, 1024u, 4096u}) {
-            base.start_vectors = sv;
-            pdx_status r = check_search_args(ix, nullptr, 0, opts->k, &base, nullptr, nullptr, &o, "pdx_server_create");
-            if (r == PDX_OK) r = plan_metric(ix, o.pruner, &pl, "pdx_server_create");
-            if (r != PDX_OK) {
-                pdx_server_free(s);
-                return r;
+        pdx_status r = check_search_args(ix, nullptr, 0, opts->k, &base, nullptr, nullptr, &o, "pdx_server_create");
+        if (r == PDX_OK) r = plan_metric(ix, o.pruner, &pl, "pdx_server_create");
+        if (r != PDX_OK) {
+            pdx_server_free(s);
+            return r;
+        }
+        for (int bk = 0; bk <= s->max_bucket_log2; ++bk) {
+            // the automatic plan always fits; the tuner's other item sizes fit
+            // when their lists stay within 256 MB more
+            const int64_t B = (int64_t)1 << bk;
+            ExactPlan ep;
+            exact_plan(ix, B, opts->k, o, pl, s->sms, &ep);
+            size_t need = ep.bytes;
+            if (opts->autotune) {
+                for (uint32_t b : item_sizes(ix, B, opts->k, o, pl, s->sms)) {
+                    pdx_search_opts c = o;
+                    c.blocks_per_item = b;
+                    ExactPlan e2;
+                    if (exact_plan(ix, B, opts->k, c, pl, s->sms, &e2) == PDX_OK && e2.bytes <= ep.bytes + ((size_t)256 << 20))
+                        need = std::max(need, e2.bytes);
+                }
             }
-            for (int bk = 0; bk <= s->max_bucket_log2; ++bk) {
-                ExactPlan ep;
-                exact_plan(ix, (int64_t)1 << bk, opts->k, o, pl, s->sms, &ep);
-                s->work_bytes = std::max(s->work_bytes, ep.bytes);
-            }
+            s->work_bytes = std::max(s->work_bytes, need);
         }
     }
     s->entries.assign(count, std::vector<ServerEntry>(s->max_bucket_log2 + 1));
