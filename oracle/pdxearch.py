@@ -40,6 +40,19 @@ while ``oracle.knn`` is the reference for the exact *result*:
     so partial / F(d) estimates the full distance; m -> infinity leaves only
     the exact test.
 
+* ADSampling with PDX-BOND's query-aware order (the fusion the paper names
+  as future work, Sec. 8; the reading is this build's): on rotated data the
+  dimensions are visited by PDX-BOND's distance-to-means order against the
+  block's means, and after d visited dimensions the vector is pruned when
+  either test fires:
+  - PDX-BOND (exact): partial > tau;
+  - the hypothesis test, calibrated to the visited share of the expected
+    distance: partial > tau * F_q(d) * (1 + eps0 / sqrt(d))^2, where
+    E_j = (q_j - mu_j)^2 + var_j is the expected (q_j - x_j)^2 for a vector of
+    the block (mean mu_j, population variance var_j) and F_q(d) is the sum of
+    E over the visited dimensions over the sum of E over all of them. With
+    storage order and equal E_j, F_q(d) = d / D and the test is ADSampling's.
+
 Returns the top-k plus per-query counters: values accumulated (the paper's
 pruning power is 1 - visited / (n*D)), vectors pruned, and the phase at which
 each block ended.
@@ -137,9 +150,13 @@ def pdxearch(x, q, k, blocks, pruner="bond", order="dist_to_means", zone_dims=1,
                 started = True
             continue
         tau = min(heap.tau, tau_seed)
-        if pruner in ("bond", "none"):
+        mass = None
+        if pruner in ("bond", "none", "ads_bond"):
             mu = xb.mean(axis=0)
             dims = visit_order(q, mu, order, zone_dims)
+            if pruner == "ads_bond":
+                e = (q - mu) ** 2 + xb.var(axis=0)
+                mass = np.concatenate([[0.0], np.cumsum(e[dims])]) / e.sum()
         else:
             dims = np.arange(d)
         partial = np.zeros(ids.size)
@@ -155,7 +172,8 @@ def pdxearch(x, q, k, blocks, pruner="bond", order="dist_to_means", zone_dims=1,
             pos += s
             if pos >= d:
                 break
-            test = _predicate(pruner, partial[rows], tau, pos, d, xb[rows], q, dims, pos, eps0, bsa_m, bsa_lambda)
+            test = _predicate(pruner, partial[rows], tau, pos, d, xb[rows], q, dims, pos, eps0, bsa_m, bsa_lambda,
+                              None if mass is None else mass[pos])
             newly = test & ~pruned[rows]
             for r in rows[newly]:
                 st.prune_events.append((bi, int(ids[r]), pos))
@@ -176,11 +194,13 @@ def pdxearch(x, q, k, blocks, pruner="bond", order="dist_to_means", zone_dims=1,
     return np.array([v for v, _ in items]), np.array([i for _, i in items], np.int64), st
 
 
-def _predicate(pruner, partial, tau, dvis, d, xrows, q, dims, pos, eps0, bsa_m, bsa_lambda):
+def _predicate(pruner, partial, tau, dvis, d, xrows, q, dims, pos, eps0, bsa_m, bsa_lambda, mass=None):
     if pruner == "none" or not math.isfinite(tau):
         return np.zeros(partial.shape, bool)
     if pruner == "bond":
         return partial > tau
+    if pruner == "ads_bond":
+        return (partial > tau) | (partial > tau * mass * (1.0 + eps0 / math.sqrt(dvis)) ** 2)
     if pruner == "ads":
         return partial * (d / dvis) > tau * (1.0 + eps0 / math.sqrt(dvis)) ** 2
     if pruner == "bsa":

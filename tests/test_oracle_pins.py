@@ -312,3 +312,41 @@ def test_bsa_predicate_hand_worked_events():
     assert [list(e) for e in st.prune_events] == g["prune_events"]
     assert i.tolist() == g["top_ids"]
     assert d.tolist() == g["top_dists"]
+
+
+def test_ads_bond_predicate_hand_worked_events():
+    # "ads_bond": the fused predicate (PDX-BOND order + mass-calibrated
+    # hypothesis test + PDX-BOND's exact test). At tau = 4.01 x0 is pruned by
+    # the test alone at d=1; at tau = 4.2 it survives d=1 and BOND prunes it
+    # at d=3. Dropping the variance term from E_j, the square of the factor,
+    # or the query-aware order each changes one of the two event lists.
+    g = _worked("ads_bond")
+    x = np.array(g["vectors"], np.float64)
+    q = np.array(g["query"], np.float64)
+    for case in g["cases"]:
+        d, i, st = ops.pdxearch(x, q, g["k"], [np.arange(x.shape[0])], pruner="ads_bond", eps0=g["eps0"],
+                                first_step=g["first_step"], tau0=case["tau0"])
+        assert [list(e) for e in st.prune_events] == case["prune_events"]
+        assert i.tolist() == g["top_ids"] and d.tolist() == g["top_dists"]
+
+
+def test_ads_bond_reduces_to_adsampling_without_reordering():
+    # equal expected contributions and storage order: F_q(d) = d / D, so the
+    # fused statistical test is ADSampling's; the fused predicate prunes every
+    # vector ADSampling prunes, and any other vector it prunes is one whose
+    # distance exceeds tau (PDX-BOND's exact test)
+    rng = np.random.default_rng(8)
+    x = rng.standard_normal((300, 16))
+    q = np.zeros(16)
+    x -= x.mean(axis=0)
+    x /= x.std(axis=0)                      # mean 0, variance 1 in every dimension
+    blocks = [np.arange(300)]
+    for tau in (8.0, 14.0):
+        _, _, a = ops.pdxearch(x, q, 5, blocks, pruner="ads_bond", order="sequential", eps0=1.5, first_step=2,
+                               tau0=tau)
+        _, _, b = ops.pdxearch(x, q, 5, blocks, pruner="ads", eps0=1.5, first_step=2, tau0=tau)
+        bond_only = {(e[1]) for e in a.prune_events} - {(e[1]) for e in b.prune_events}
+        # every extra prune of the fused test is one PDX-BOND's exact test makes
+        for v in bond_only:
+            assert ((x[v] - q) ** 2).sum() > tau
+        assert {e[1] for e in b.prune_events} <= {e[1] for e in a.prune_events}
