@@ -67,7 +67,19 @@ typedef enum pdx_pruner {
     PDX_PRUNE_NONE = 0,
     PDX_PRUNE_BOND = 1,        /* exact: partial distance > tau              */
     PDX_PRUNE_ADSAMPLING = 2,  /* approximate: hypothesis test, eps0         */
-    PDX_PRUNE_BSA = 3          /* approximate: error quantile, multiplier m  */
+    PDX_PRUNE_BSA = 3,         /* approximate: error quantile, multiplier m  */
+    PDX_PRUNE_ADS_BOND = 4     /* approximate: ADSampling on a rotated index with
+                                  PDX-BOND's query-aware visit order (the fusion
+                                  Sec. 8 proposes as future work). Dimensions are
+                                  visited by distance to the probed bucket's means
+                                  (zones of zone_dims); after d of them a vector is
+                                  pruned when partial > tau (PDX-BOND, exact) or
+                                  partial > tau * F_q(d) * (1 + eps0/sqrt(d))^2,
+                                  where F_q(d) is the visited share of the expected
+                                  distance sum_j (q_j - mu_j)^2 + var_j over the
+                                  bucket (mu, var: the bucket's means and
+                                  variances). With storage order and equal
+                                  expected terms it is ADSampling's test.       */
 } pdx_pruner;
 
 /* Order in which PDX-BOND visits dimensions (Sec. 5, Fig. 6). */

@@ -115,7 +115,7 @@ static int rows_vec4(const pdx_index *ix, const float *qrows) {
 
 static void free_index(pdx_index *ix) {
     if (!ix) return;
-    void *ptrs[] = {ix->sc_cent, ix->sc_members, ix->data, ix->data_lp, ix->scale, ix->xnary, ix->dsm, ix->xtc, ix->xnorm, ix->ids, ix->slot_of, ix->blk_cnt, ix->part_blk, ix->means, ix->cmean, ix->centroids, ix->centroid_norms,
+    void *ptrs[] = {ix->sc_cent, ix->sc_members, ix->data, ix->data_lp, ix->scale, ix->xnary, ix->dsm, ix->xtc, ix->xnorm, ix->ids, ix->slot_of, ix->blk_cnt, ix->part_blk, ix->means, ix->vars, ix->cmean, ix->centroids, ix->centroid_norms,
                     ix->assign, ix->rot, ix->shift, ix->pca_var, ix->resid, ix->chk, ix->cdata, ix->cids};
     for (void *p : ptrs)
         if (p) cudaFree(p);
@@ -547,7 +547,7 @@ pdx_status check_search_args(const pdx_index *ix, const float *q, int64_t nq, in
         }
         *o = *opts;
     }
-    if (o->pruner < PDX_PRUNE_NONE || o->pruner > PDX_PRUNE_BSA || o->order < PDX_ORDER_DIST_TO_MEANS ||
+    if (o->pruner < PDX_PRUNE_NONE || o->pruner > PDX_PRUNE_ADS_BOND || o->order < PDX_ORDER_DIST_TO_MEANS ||
         o->order > PDX_ORDER_LEARNED) {
         set_error("%s: bad pruner %d or order %d", fn, (int)o->pruner, (int)o->order);
         return PDX_ERR_ARG;
@@ -630,8 +630,17 @@ pdx_status plan_metric(const pdx_index *ix, int pruner, SearchPlan *pl, const ch
 // block means (more than kMaxSortUnits zones) once per (query, part rank).
 OrderPlan plan_orders(const pdx_index *ix, const pdx_search_opts &o, int pruner, int64_t nq, int parts_per_query) {
     OrderPlan pl;
-    if (pruner != PDX_PRUNE_BOND || o.order == PDX_ORDER_SEQUENTIAL) return pl;
     const int d = ix->d;
+    if (pruner == PDX_PRUNE_ADS_BOND) {
+        // the fused pruner: distance-to-means zones against each probed
+        // bucket's means, one row per (query, bucket), for the scan and F_q
+        pl.mode = 0;
+        pl.per_part = parts_per_query;
+        pl.rows = nq * pl.per_part;
+        pl.bytes = (size_t)pl.rows * d * 2;
+        return pl;
+    }
+    if (pruner != PDX_PRUNE_BOND || o.order == PDX_ORDER_SEQUENTIAL) return pl;
     if (o.order == PDX_ORDER_LEARNED) {
         pl.mode = 2;
     } else if (o.order == PDX_ORDER_DECREASING) {
@@ -1297,6 +1306,9 @@ static pdx_status ivf_build_impl(pdx_index *ix, const float *x, const pdx_ivf_op
     for (int64_t i = 0; i < n; ++i) rows[(size_t)fill[(size_t)ha[(size_t)i]]++] = (int32_t)i;
     pdx_status s = layout_parts(ix, xt, rows, part_row, st);
     if (s != PDX_OK) return s;
+    // per-bucket variances (the fused pruner's expected contributions)
+    PDX_TRY(dalloc(ix, &ix->vars, (size_t)nlist * d));
+    PDX_TRY(launch_part_vars(ix->data, ix->blk_cnt, ix->part_blk, nlist, d, ix->means, ix->vars, st));
     // centroids in PDX layout too (Sec. 6.4: the bucket search uses the PDX kernel)
     ix->c_nblocks = (nlist + kBlock - 1) / kBlock;
     std::vector<int32_t> cids((size_t)ix->c_nblocks * kBlock, -1);
@@ -1397,7 +1409,8 @@ extern "C" pdx_status pdx_search_ivf(const pdx_index *ix, const float *q, int64_
         set_error("%s: nprobe=%d outside [1, min(nlist=%d, 4096)]", fn, nprobe, ix->nparts);
         return PDX_ERR_ARG;
     }
-    if ((o.pruner == PDX_PRUNE_ADSAMPLING && ix->transform != PDX_PRUNE_ADSAMPLING) ||
+    if (((o.pruner == PDX_PRUNE_ADSAMPLING || o.pruner == PDX_PRUNE_ADS_BOND) &&
+         ix->transform != PDX_PRUNE_ADSAMPLING) ||
         (o.pruner == PDX_PRUNE_BSA && ix->transform != PDX_PRUNE_BSA)) {
         set_error("%s: pruner %d needs an index built with that transform", fn, (int)o.pruner);
         return PDX_ERR_ARG;
@@ -1424,7 +1437,15 @@ extern "C" pdx_status pdx_search_ivf(const pdx_index *ix, const float *q, int64_
     const bool tr = ix->transform != PDX_PRUNE_NONE;
     const int sms = num_sms();
     const int64_t Lc = (int64_t)ix->c_nblocks * kBlock;
-    const int nchk = (o.pruner == PDX_PRUNE_BSA) ? ix->bsa_nchk : 0;
+    // check points: BSA's stored schedule, or (fused pruner) the search's own
+    const std::vector<int32_t> adsb_chk =
+        o.pruner == PDX_PRUNE_ADS_BOND ? check_points(d, (int)o.first_step) : std::vector<int32_t>();
+    if ((int)adsb_chk.size() > kMaxChecks) {
+        set_error("%s: first_step=%u gives %zu check points (at most %d)", fn, o.first_step, adsb_chk.size(),
+                  kMaxChecks);
+        return PDX_ERR_ARG;
+    }
+    const int nchk = (o.pruner == PDX_PRUNE_BSA) ? ix->bsa_nchk : (int)adsb_chk.size();
     int max_blk = 0;
     for (int p = 0; p < ix->nparts; ++p) max_blk = std::max(max_blk, ix->h_part_blk[p + 1] - ix->h_part_blk[p]);
     max_blk = std::max(1, max_blk);
@@ -1448,6 +1469,7 @@ extern "C" pdx_status pdx_search_ivf(const pdx_index *ix, const float *q, int64_
                   rup((size_t)nq * Lc * 8) + rup((size_t)nq * nprobe * 8) + rup((size_t)nq * nprobe * 4) +
                   rup((size_t)nq * 4) + rup((size_t)nq * nslots * k * 8) + 3 * rup((size_t)nq * k * 8) +
                   rup(C_COUNT * 8) + rup(16) + rup((size_t)nq * (nchk + 1) * 8) +
+                  rup((size_t)nq * nprobe * std::max(1, nchk) * 4) + rup((size_t)kMaxChecks * 4) +
                   rup((size_t)nq * kPoolCap * 4) + rup((size_t)nq * 4) + (o.tau_init ? rup((size_t)nq * 4) : 0) +
                   (o_dev ? 0 : rup((size_t)nq * k * 4) + rup((size_t)nq * k * 8));
     PDX_TRY(scr.reserve(need));
@@ -1471,6 +1493,8 @@ extern "C" pdx_status pdx_search_ivf(const pdx_index *ix, const float *q, int64_
     unsigned long long *counters = scr.take<unsigned long long>(C_COUNT);
     int *work = scr.take<int>(4);
     float *qaux = scr.take<float>((size_t)nq * (nchk + 1) * 2);
+    float *mass = scr.take<float>((size_t)nq * nprobe * std::max(1, nchk));
+    int32_t *chk_dev = scr.take<int32_t>(kMaxChecks);
     uint16_t *qorder = op.rows ? scr.take<uint16_t>((size_t)op.rows * d) : nullptr;
     float *pool = scr.take<float>((size_t)nq * kPoolCap);
     int32_t *pool_cnt = scr.take<int32_t>((size_t)nq);
@@ -1493,7 +1517,7 @@ extern "C" pdx_status pdx_search_ivf(const pdx_index *ix, const float *q, int64_
         PDX_TRY(launch_transform(qd, nq, d, ix->rot, ix->shift, qt_buf, st));
         qt = qt_buf;
     }
-    if (nchk > 0) PDX_TRY(launch_bsa_qaux(qt, nq, d, ix->pca_var, ix->chk, nchk, qaux, st));
+    if (nchk > 0 && o.pruner == PDX_PRUNE_BSA) PDX_TRY(launch_bsa_qaux(qt, nq, d, ix->pca_var, ix->chk, nchk, qaux, st));
     PDX_TRY(mark(1));
     // nearest buckets: PDX scan of the centroids, then the nprobe best per query
     PDX_TRY(launch_dense_keys(qt, nq, ix->cdata, ix->cids, d, ix->c_nblocks, PDX_L2, pkeys, st));
@@ -1503,6 +1527,11 @@ extern "C" pdx_status pdx_search_ivf(const pdx_index *ix, const float *q, int64_
         PDX_TRY(launch_order(qt, op.rows, d, op.per_part ? ix->means : ix->cmean, op.per_part,
                              op.per_part ? probes : nullptr, op.mode, std::max(1, (int)o.zone_dims), nullptr, qorder,
                              st));
+    if (o.pruner == PDX_PRUNE_ADS_BOND && nchk > 0) {  // F_q at every check point of every (query, bucket)
+        PDX_TRY(cudaMemcpyAsync(chk_dev, adsb_chk.data(), adsb_chk.size() * 4, cudaMemcpyHostToDevice, st));
+        PDX_TRY(launch_mass(qt, (int64_t)nq * nprobe, d, nprobe, probes, ix->means, ix->vars, qorder, chk_dev, nchk,
+                            mass, st));
+    }
     PDX_TRY(mark(2));
     PDX_TRY(launch_fill_u32(reinterpret_cast<uint32_t *>(tau), 0xff800000u, nq, st));
     PDX_TRY(cudaMemsetAsync(counters, 0, C_COUNT * 8, st));
@@ -1549,7 +1578,7 @@ extern "C" pdx_status pdx_search_ivf(const pdx_index *ix, const float *q, int64_
     p.gamma = (float)d * 1.1920929e-7f;
     p.eps0 = o.eps0;
     p.bsa_m = o.bsa_m;
-    p.qaux = qaux;
+    p.qaux = (o.pruner == PDX_PRUNE_ADS_BOND) ? mass : qaux;
     p.resid = ix->resid;
     p.nchk = nchk;
     p.pool = use_pool ? pool : nullptr;

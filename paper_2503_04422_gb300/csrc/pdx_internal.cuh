@@ -19,6 +19,7 @@ constexpr int kMaxD = 4096;
 constexpr int kMaxSortUnits = 256;  // zone keys a scan warp sorts in-kernel (8 per lane)
 constexpr int kPoolCap = 256;       // shared candidate distances per query (8 per lane)
 constexpr int kStartProbe = 2;      // start clusters a query's START reads
+constexpr int kMaxChecks = 16;      // prune check points of one fetch schedule (doubling: log2(d) + 1)
 constexpr int kStartMembers = 64;   // member vectors kept per start cluster
 
 // Device counters, in the order of the first fields of pdx_search_stats
@@ -70,6 +71,7 @@ struct pdx_index {
     int32_t *blk_cnt = nullptr;     // [nblocks] valid lanes per block
     int32_t *part_blk = nullptr;    // [nparts+1]
     float *means = nullptr;         // [nparts][d]
+    float *vars = nullptr;          // [nparts][d] per-part population variances (IVF: the fused pruner)
     float *cmean = nullptr;         // [d] collection means
     float *centroids = nullptr;     // [nparts][d] (IVF)
     float *centroid_norms = nullptr;// [nparts]
@@ -175,6 +177,12 @@ cudaError_t launch_to_pdx(const float *x, int32_t d, const int32_t *ids, int64_t
                           float *data, cudaStream_t st);
 cudaError_t launch_part_means(const float *data, const int32_t *blk_cnt, const int32_t *part_blk,
                               int32_t nparts, int32_t d, float *means, cudaStream_t st);
+cudaError_t launch_part_vars(const float *data, const int32_t *blk_cnt, const int32_t *part_blk, int32_t nparts,
+                             int32_t d, const float *means, float *vars, cudaStream_t st);
+// Visited shares F_q of the expected distance at each check point (fused pruner).
+cudaError_t launch_mass(const float *q, int64_t rows, int32_t d, int32_t per_part, const int32_t *row_part,
+                        const float *means, const float *vars, const uint16_t *order, const int32_t *chk, int32_t nchk,
+                        float *out, cudaStream_t st);
 cudaError_t launch_unit_norm_check(const float *x, int64_t n, int32_t d, float tol, int *flag,
                                    cudaStream_t st);
 cudaError_t launch_fill_u32(uint32_t *p, uint32_t v, int64_t n, cudaStream_t st);

@@ -74,6 +74,44 @@ cudaError_t launch_part_means(const float *data, const int32_t *blk_cnt, const i
     return counted(cudaGetLastError());
 }
 
+// Population variance of every dimension over each part's vectors (the fused
+// pruner's expected contributions), one warp per (part, dimension).
+__global__ void part_vars_kernel(const float *__restrict__ data, const int32_t *__restrict__ blk_cnt,
+                                 const int32_t *__restrict__ part_blk, int32_t nparts, int32_t d,
+                                 const float *__restrict__ means, float *__restrict__ vars) {
+    const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (gw >= (int64_t)nparts * d) return;
+    const int p = (int)(gw / d), j = (int)(gw % d);
+    const float mu = means[(int64_t)p * d + j];
+    float s = 0.f;
+    int64_t cnt = 0;
+    for (int b = part_blk[p]; b < part_blk[p + 1]; ++b) {
+        const float *row = data + ((int64_t)b * d + j) * kBlock;
+        const int c = blk_cnt[b];
+        if (lane < c) {
+            const float t = row[lane] - mu;
+            s = fmaf(t, t, s);
+        }
+        if (lane + 32 < c) {
+            const float t = row[lane + 32] - mu;
+            s = fmaf(t, t, s);
+        }
+        cnt += c;
+    }
+    for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) vars[(int64_t)p * d + j] = cnt ? s / (float)cnt : 0.f;
+}
+
+cudaError_t launch_part_vars(const float *data, const int32_t *blk_cnt, const int32_t *part_blk, int32_t nparts,
+                             int32_t d, const float *means, float *vars, cudaStream_t st) {
+    const int64_t warps = (int64_t)nparts * d;
+    if (warps == 0) return cudaSuccess;
+    part_vars_kernel<<<(unsigned)((warps * 32 + 255) / 256), 256, 0, st>>>(data, blk_cnt, part_blk, nparts, d, means,
+                                                                           vars);
+    return counted(cudaGetLastError());
+}
+
 // flag is cleared when some row's squared norm differs from 1 by more than tol.
 __global__ void unit_norm_kernel(const float *__restrict__ x, int64_t n, int32_t d, float tol, int *flag) {
     const int64_t row = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;

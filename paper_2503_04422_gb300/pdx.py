@@ -21,7 +21,7 @@ LIB_PATH = os.path.join(_HERE, "_build", "libpdx.so")
 PDX_OK, PDX_ERR_ARG, PDX_ERR_OOM, PDX_ERR_CUDA, PDX_ERR_TIMEOUT, PDX_ERR_UNSUPPORTED = range(6)
 METRIC = {"l2": 0, "ip": 1, "l1": 2}
 DTYPE = {"f32": 0, "bf16": 1, "fp8": 2}
-PRUNER = {"none": 0, "bond": 1, "ads": 2, "adsampling": 2, "bsa": 3}
+PRUNER = {"none": 0, "bond": 1, "ads": 2, "adsampling": 2, "bsa": 3, "ads_bond": 4}
 ORDER = {"dist_to_means": 0, "decreasing": 1, "sequential": 2, "learned": 3}
 MEANS = {"block": 0, "collection": 1, "auto": 2}
 ENGINE = {"auto": 0, "scan": 1, "tensor": 2}
