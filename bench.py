@@ -510,7 +510,7 @@ def run_ivf(args, rank, world, local_rank):
     stats_dev = torch.zeros(16, dtype=torch.int64, device="cuda")
     results = {}
     pruners = [p.strip() for p in args.pruners.split(",")]
-    transforms = {"ads": "ads", "bsa": "bsa", "bond": "none", "none": "none"}
+    transforms = {"ads": "ads", "ads_bond": "ads", "bsa": "bsa", "bond": "none", "none": "none"}
     built = {}
     for pruner in pruners:
         tr = transforms[pruner]
