@@ -121,11 +121,12 @@ class _Heap:
 
 
 def pdxearch(x, q, k, blocks, pruner="bond", order="dist_to_means", zone_dims=1, first_step=2,
-             selection_threshold=0.20, eps0=2.1, bsa_m=None, bsa_lambda=None, tau0=None):
+             selection_threshold=0.20, eps0=2.1, bsa_m=None, bsa_lambda=None, tau0=None, tau_fixed=False):
     """One query. ``blocks`` is a list of int arrays (vector ids per PDXearch
     block, visited in list order). ``x`` is [n][D]; returns (dists, ids, stats).
     ``tau0`` optionally seeds the threshold (any k-th distance of k real
-    vectors keeps the search exact)."""
+    vectors keeps the search exact); with ``tau_fixed`` the threshold stays
+    tau0 instead of tightening as blocks merge into the heap."""
     x = np.asarray(x, np.float64)
     q = np.asarray(q, np.float64)
     n, d = x.shape
@@ -149,7 +150,7 @@ def pdxearch(x, q, k, blocks, pruner="bond", order="dist_to_means", zone_dims=1,
             if seen >= k:
                 started = True
             continue
-        tau = min(heap.tau, tau_seed)
+        tau = tau_seed if tau_fixed else min(heap.tau, tau_seed)
         mass = None
         if pruner in ("bond", "none", "ads_bond"):
             mu = xb.mean(axis=0)
