@@ -355,6 +355,10 @@ def run_ours(args, rank, world, local_rank):
                     "peak": peak, "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,
                     "traffic": traffic, "algorithmic_bytes_per_launch": bytes_per_launch,
                     "scan_ms_avg": scan_avg_ms,
+                    # DRAM bytes the kernel really moves (ncu, per launch) over its live duration:
+                    # the working set is L2-resident, so this stays far below the logical rate
+                    "dram_gbs": (traffic / (scan_avg_ms / 1e3) / 1e9) if traffic else None,
+                    "dram_frac": (traffic / (scan_avg_ms / 1e3) / 1e9 / peak) if traffic else None,
                     "per_unit": {"bytes_per_query": bytes_per_launch / nq, "units_per_launch": nq}}
 
     # end to end through the C ABI with host (pinned) buffers
