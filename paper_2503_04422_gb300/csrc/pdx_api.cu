@@ -824,6 +824,7 @@ pdx_status exact_run(const pdx_index *ix, const float *qd, int64_t nq, int32_t k
         return PDX_ERR_CUDA;
     }
     const float *scores = nullptr;
+    bool learned_done = false;
     if (ep.op.mode == 2) {
         // learned order: each query's nearest centroid, network input [q; c],
         // BF16 inference into per-dimension scores
@@ -841,11 +842,17 @@ pdx_status exact_run(const pdx_index *ix, const float *qd, int64_t nq, int32_t k
         PDX_TRY(launch_fill_u64(ckeys, kEmptyKey, nq * ep.mlp_Lc, st));
         PDX_TRY(launch_dense_keys_rows(qd, nq, o.mlp_centroids, o.mlp_ncentroids, d, ep.mlp_Lc, ckeys, st));
         PDX_TRY(launch_select_k(ckeys, nq, ep.mlp_Lc, 1, nearest, st));
-        PDX_TRY(launch_mlp_inputs(qd, nq, d, o.mlp_centroids, nearest, u, st));
-        PDX_TRY(mlp_scores(o.mlp, u, nq, zb, yb, st));
-        scores = yb;
+        if (hidden % 2 == 0) {
+            // inputs, both layers, the score and the sort in one launch
+            PDX_TRY(mlp_order(o.mlp, qd, nq, o.mlp_centroids, nearest, ix->cmean, qorder, st));
+            learned_done = true;
+        } else {
+            PDX_TRY(launch_mlp_inputs(qd, nq, d, o.mlp_centroids, nearest, u, st));
+            PDX_TRY(mlp_scores(o.mlp, u, nq, zb, yb, st));
+            scores = yb;
+        }
     }
-    if (ep.op.rows)  // query preprocessing (Sec. 5): PDX-BOND visit orders
+    if (ep.op.rows && !learned_done)  // query preprocessing (Sec. 5): PDX-BOND visit orders
         PDX_TRY(launch_order(qd, ep.op.rows, d, ep.op.per_part ? ix->means : ix->cmean, ep.op.per_part, nullptr,
                              ep.op.mode, std::max(1, (int)o.zone_dims), scores, qorder, st));
     PDX_TRY(mark(1));

@@ -249,6 +249,9 @@ cudaError_t launch_order(const float *q, int64_t rows, int32_t d, const float *m
 cudaError_t launch_mlp_inputs(const float *q, int64_t nq, int d, const float *cent, const uint64_t *nearest, float *u,
                               cudaStream_t st);
 cudaError_t mlp_scores(pdx_mlp *net, const float *U, int64_t B, float *Z, float *Y, cudaStream_t st);
+// learned visit orders [nq][d] in one launch: inputs [q; c], BF16 inference, scores, sort (even hidden size)
+cudaError_t mlp_order(pdx_mlp *net, const float *q, int64_t nq, const float *cent, const uint64_t *nearest,
+                      const float *mu, uint16_t *order, cudaStream_t st);
 
 // How a search gets its PDX-BOND visit orders (see plan_orders).
 struct OrderPlan {

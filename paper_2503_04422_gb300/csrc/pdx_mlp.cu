@@ -231,6 +231,113 @@ cudaError_t mlp_scores(pdx_mlp *net, const float *U, int64_t B, float *Z, float 
 
 
 // ---------------------------------------------------------------------------
+// The learned visit order in one launch ahead of the scan: one CTA per query
+// builds u = [q; c] (c: the nearest centroid, from its key), runs both layers
+// with the BF16 weights and FP32 accumulation (a warp per output: lanes take
+// pairs of BF16 weights, then a warp sum), adds the biases and the ReLU, forms
+// the score (q_j - mu_j)^2 + s_q y_j (mu: collection means, s_q: the query's
+// mean heuristic term), and sorts the dimensions by decreasing score (ties to
+// the lower dimension) into the query's row of the order array.
+__device__ __forceinline__ float bf16_lo(uint32_t v) { return __uint_as_float(v << 16); }
+__device__ __forceinline__ float bf16_hi(uint32_t v) { return __uint_as_float(v & 0xffff0000u); }
+
+__global__ void __launch_bounds__(256) mlp_order_kernel(const float *__restrict__ q, int64_t nq, int d, int H,
+                                                        const float *__restrict__ cent,
+                                                        const uint64_t *__restrict__ nearest,
+                                                        const uint16_t *__restrict__ w1h, const float *__restrict__ b1,
+                                                        const uint16_t *__restrict__ w2h, const float *__restrict__ b2,
+                                                        const float *__restrict__ mu, uint16_t *__restrict__ order) {
+    extern __shared__ __align__(16) unsigned char sm[];
+    const int64_t r = blockIdx.x;
+    if (r >= nq) return;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    const int npad = [&] { int p = 1; while (p < d) p <<= 1; return p; }();
+    uint64_t *keys = reinterpret_cast<uint64_t *>(sm);       // [npad]
+    float *u = reinterpret_cast<float *>(keys + npad);       // [2d]
+    float *h = u + 2 * d;                                    // [H]
+    __shared__ float red[32];
+    const int c = (int)(uint32_t)(nearest[r] & 0xffffffffu);
+    float part = 0.f;
+    for (int j = threadIdx.x; j < d; j += blockDim.x) {
+        const float qj = q[r * d + j];
+        u[j] = qj;
+        u[d + j] = cent[(int64_t)c * d + j];
+        const float t = qj - mu[j];
+        part = fmaf(t, t, part);
+    }
+    for (int o = 16; o; o >>= 1) part += __shfl_xor_sync(kFull, part, o);
+    if (lane == 0) red[warp] = part;
+    __syncthreads();
+    float sq = 0.f;
+    for (int i = 0; i < nw; ++i) sq += red[i];
+    sq /= (float)d;
+    // layer 1: h = relu(W1 u + b1), W1 [H][2d] in BF16 (2d even: pairs of weights)
+    for (int o = warp; o < H; o += nw) {
+        const uint32_t *wr = reinterpret_cast<const uint32_t *>(w1h + (int64_t)o * 2 * d);
+        float acc = 0.f;
+        for (int i = lane; i < d; i += 32) {
+            const uint32_t w = __ldg(wr + i);
+            acc = fmaf(bf16_lo(w), u[2 * i], acc);
+            acc = fmaf(bf16_hi(w), u[2 * i + 1], acc);
+        }
+        for (int s = 16; s; s >>= 1) acc += __shfl_xor_sync(kFull, acc, s);
+        if (lane == 0) h[o] = fmaxf(acc + b1[o], 0.f);
+    }
+    __syncthreads();
+    // layer 2 and the score: y = W2 h + b2, W2 [d][H] in BF16 (H even)
+    for (int j = warp; j < npad; j += nw) {
+        uint64_t key = kEmptyKey;
+        if (j < d) {
+            const uint32_t *wr = reinterpret_cast<const uint32_t *>(w2h + (int64_t)j * H);
+            float acc = 0.f;
+            for (int i = lane; i < H / 2; i += 32) {
+                const uint32_t w = __ldg(wr + i);
+                acc = fmaf(bf16_lo(w), h[2 * i], acc);
+                acc = fmaf(bf16_hi(w), h[2 * i + 1], acc);
+            }
+            for (int s = 16; s; s >>= 1) acc += __shfl_xor_sync(kFull, acc, s);
+            const float t = u[j] - mu[j];
+            const float sc = fmaf(t, t, sq * (acc + b2[j]));
+            key = ((uint64_t)f2o(-sc) << 32) | (uint32_t)j;
+        }
+        if (lane == 0) keys[j] = key;
+    }
+    __syncthreads();
+    for (int size = 2; size <= npad; size <<= 1) {
+        for (int stride = size >> 1; stride > 0; stride >>= 1) {
+            for (int i = threadIdx.x; i < (npad >> 1); i += blockDim.x) {
+                const int lo = 2 * i - (i & (stride - 1)), hi = lo + stride;
+                const bool asc = (lo & size) == 0;
+                const uint64_t a = keys[lo], b = keys[hi];
+                if ((a > b) == asc) {
+                    keys[lo] = b;
+                    keys[hi] = a;
+                }
+            }
+            __syncthreads();
+        }
+    }
+    for (int j = threadIdx.x; j < d; j += blockDim.x) order[r * d + j] = (uint16_t)(keys[j] & 0xffffu);
+}
+
+cudaError_t mlp_order(pdx_mlp *net, const float *q, int64_t nq, const float *cent, const uint64_t *nearest,
+                      const float *mu, uint16_t *order, cudaStream_t st) {
+    if (nq == 0) return cudaSuccess;
+    cudaError_t e = refresh_bf16(net, st);
+    if (e != cudaSuccess) return e;
+    const int d = net->d, H = net->hidden;
+    int npad = 1;
+    while (npad < d) npad <<= 1;
+    const size_t smem = (size_t)npad * 8 + (size_t)(2 * d + H) * 4;
+    if ((e = cudaFuncSetAttribute(mlp_order_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) !=
+        cudaSuccess)
+        return e;
+    mlp_order_kernel<<<(unsigned)nq, 256, smem, st>>>(q, nq, d, H, cent, nearest, net->w1h, net->b1(), net->w2h,
+                                                       net->b2(), mu, order);
+    return counted(cudaGetLastError());
+}
+
+// ---------------------------------------------------------------------------
 // u[r] = [q_r; c_(a_r)] with a_r the centroid id in keys[r] (nearest centroid)
 __global__ void mlp_inputs_kernel(const float *__restrict__ q, int64_t nq, int d, const float *__restrict__ cent,
                                   const uint64_t *__restrict__ nearest, float *__restrict__ u) {
