@@ -437,7 +437,10 @@ def run_ours(args, rank, world, local_rank):
                        "order": "dist_to_means",
                        "means": "collection (automatic for exact search)", "zone_dims": "1 (automatic)",
                        "first_step": int(opts.first_step), "selection_threshold": round(float(opts.selection_threshold), 3),
-                       "start_vectors": int(opts.start_vectors), "ctas_per_sm": int(opts.ctas_per_sm) or "automatic (4 when four CTAs fit with 32 KB of L1, else 3)",
+                       "start": (f"start clusters: {min(1024, n // 4096)} k-means centroids x 64 member vectors, "
+                                 "the 2 nearest per query" if n >= 65536 and pruner != "none"
+                                 else f"the first {int(opts.start_vectors)} stored vectors"),
+                       "ctas_per_sm": int(opts.ctas_per_sm) or "automatic (4 when four CTAs fit with 32 KB of L1, else 3)",
                        "l2": (f"collection {n * d * 4 / 1e9:.3g} GB; 256 MB L2 flush between timed steps "
                               "(untimed)")},
             "roofline": roofline,
@@ -516,6 +519,8 @@ def run_ivf(args, rank, world, local_rank):
     pruners = [p.strip() for p in args.pruners.split(",")]
     transforms = {"ads": "ads", "ads_bond": "ads", "bsa": "bsa", "bond": "none", "none": "none"}
     built = {}
+    clocks = ClockSampler(local_rank)
+    clocks.start()
     for pruner in pruners:
         tr = transforms[pruner]
         if tr not in built:
@@ -537,6 +542,7 @@ def run_ivf(args, rank, world, local_rank):
                 b_.record()
             stats_dev.zero_()
             torch.cuda.synchronize()
+            launches0 = pdx.pdx_kernel_launches()
             for i in range(args.steps):
                 opts.scan_event_start, opts.scan_event_stop = evs[i][0].cuda_event, evs[i][1].cuda_event
                 opts.stats_device = stats_dev.data_ptr()
@@ -544,6 +550,7 @@ def run_ivf(args, rank, world, local_rank):
                 pdx.pdx_search_ivf(ix, qd, k, nprobe, opts=opts, out=(od, oi))
                 ev[i][1].record()
             torch.cuda.synchronize()
+            launches = pdx.pdx_kernel_launches() - launches0
             ms = sum(a_.elapsed_time(b_) for a_, b_ in ev) / args.steps
             scan_ms = sum(a_.elapsed_time(b_) for a_, b_ in evs) / args.steps
             st = stats_dev.cpu().numpy().astype(np.float64)
@@ -551,7 +558,7 @@ def run_ivf(args, rank, world, local_rank):
             esize = {"f32": 4.0, "bf16": 2.0, "fp8": 1.0}[args.storage]
             byts = st[0] / args.steps * esize + (0.0 if args.storage == "f32" else st[4] / args.steps * d * 4.0)
             rows.append(dict(nprobe=nprobe, qps=nq / (ms / 1e3), ms=ms, recall=rec, scan_ms=scan_ms,
-                             scan_gbs=byts / (scan_ms / 1e3) / 1e9,
+                             scan_gbs=byts / (scan_ms / 1e3) / 1e9, gpu_launches=int(launches),
                              visited_fraction=st[0] / args.steps / (nq * nprobe * (n / nlist) * d)))
             print(json.dumps({"pruner": pruner, **rows[-1]}), file=sys.stderr, flush=True)
         ok_rows = [r for r in rows if r["recall"] >= 0.95]
@@ -565,6 +572,7 @@ def run_ivf(args, rank, world, local_rank):
             chosen["phases_ms"] = {p: v / 1e6 for p, v in ph.items()}
             chosen["phases_share"] = {p: v / tot for p, v in ph.items()}
         results[pruner] = dict(at_recall_095=chosen, sweep=rows)
+    clk = clocks.stop()
     main_p = pruners[0]
     best = results[main_p]["at_recall_095"] or results[main_p]["sweep"][-1]
     peak, peak_kind = _peak_hbm()
@@ -580,6 +588,7 @@ def run_ivf(args, rank, world, local_rank):
                          "peak": peak, "peak_kind": peak_kind, "unit": "GB/s", "frac": best["scan_gbs"] / peak,
                          "traffic": None},
             "pruners": {p: r["at_recall_095"] for p, r in results.items()},
+            "gpu_launches": best["gpu_launches"], "clocks": clk,
             "cpu_baseline": cpu,
             "sweeps": {p: r["sweep"] for p, r in results.items()}}
     print(json.dumps(line), flush=True)
@@ -669,8 +678,14 @@ def run_learned(args, rank, world, local_rank):
         st = stats_dev.cpu().numpy().astype(np.float64)
         return ms, st[0] / args.steps / (n_full * d * nq), oi.clone()
 
+    clocks = ClockSampler(local_rank)
+    clocks.start()
+    l0 = pdx.pdx_kernel_launches()
     ms_h, vis_h, res_h = timed(heur)
+    l1 = pdx.pdx_kernel_launches()
     ms_l, vis_l, res_l = timed(learned)
+    l2 = pdx.pdx_kernel_launches()
+    clk = clocks.stop()
     same = bool(torch.equal(res_h, res_l))
     chosen = ms_l if use_learned else ms_h
     line = {"metric": METRIC, "value": nq / (chosen / 1e3), "unit": "queries/s", "n_gpus": 1, "steps": args.steps,
@@ -682,7 +697,11 @@ def run_learned(args, rank, world, local_rank):
             "learned_vs_plain": {"learned_qps": nq / (ms_l / 1e3), "plain_qps": nq / (ms_h / 1e3),
                                  "learned_values_visited": vis_l, "plain_values_visited": vis_h,
                                  "identical_results": same, "validation_prefers_learned": bool(use_learned),
-                                 "train_loss": loss, "train_s": train_s, "trace_s": trace_s, "gen_s": gen_s}}
+                                 "train_loss": loss, "train_s": train_s, "trace_s": trace_s, "gen_s": gen_s},
+            # timed() launches the warm-up and the timed steps alike
+            "gpu_launches": int(((l2 - l1) if use_learned else (l1 - l0)) * args.steps / (args.steps + args.warmup)),
+            "gpu_launches_per_step": ((l2 - l1) if use_learned else (l1 - l0)) / (args.steps + args.warmup),
+            "clocks": clk}
     print(json.dumps(line), flush=True)
 
 

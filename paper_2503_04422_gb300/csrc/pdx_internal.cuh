@@ -146,6 +146,13 @@ constexpr unsigned kFull = 0xffffffffu;
 
 // One dimension's contribution to the distance (Sec. 2.1): squared
 // difference, product, or absolute difference.
+// Smallest power of two >= v (v >= 1).
+__host__ __device__ inline int pow2_ceil(int v) {
+    int p = 1;
+    while (p < v) p <<= 1;
+    return p;
+}
+
 template <int MET>
 __device__ __forceinline__ float term(float qv, float x, float acc) {
     if (MET == MT_L2) {
