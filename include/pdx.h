@@ -68,7 +68,7 @@ typedef enum pdx_pruner {
     PDX_PRUNE_BOND = 1,        /* exact: partial distance > tau              */
     PDX_PRUNE_ADSAMPLING = 2,  /* approximate: hypothesis test, eps0         */
     PDX_PRUNE_BSA = 3,         /* approximate: error quantile, multiplier m  */
-    PDX_PRUNE_ADS_BOND = 4     /* approximate: ADSampling on a rotated index with
+    PDX_PRUNE_ADS_BOND = 4,    /* approximate: ADSampling on a rotated index with
                                   PDX-BOND's query-aware visit order (the fusion
                                   Sec. 8 proposes as future work). Dimensions are
                                   visited by distance to the probed bucket's means
@@ -80,6 +80,19 @@ typedef enum pdx_pruner {
                                   bucket (mu, var: the bucket's means and
                                   variances). With storage order and equal
                                   expected terms it is ADSampling's test.       */
+    PDX_PRUNE_CS_IP = 5        /* exact: inner product with any vector norms.
+                                  Partial inner products are not monotone, so
+                                  PDX-BOND's test does not apply to them; after d
+                                  dimensions in storage order the unvisited part
+                                  q_r . x_r is at most ||q_r|| ||x_r||
+                                  (Cauchy-Schwarz, the exact bound BSA uses for L2
+                                  in Sec. 2.3), and a vector is pruned when
+                                  -(partial inner product) - ||q_r|| ||x_r|| > tau,
+                                  tau the k-th best -q.x so far, minus a rounding
+                                  margin of D * 2^-23 (||q_r|| ||x_r|| + ||q|| ||x||).
+                                  Exact search over an index built with
+                                  cs_first_step (its stored norms fix the fetch
+                                  schedule: the search's first_step is set to it) */
 } pdx_pruner;
 
 /* Order in which PDX-BOND visits dimensions (Sec. 5, Fig. 6). */
@@ -177,6 +190,13 @@ typedef struct pdx_build_opts {
                                   query) instead of from the first start_vectors stored
                                   vectors. 0 = automatic (n/4096 centroids, at most 1024,
                                   for n >= 65536; none below), -1 = none                  */
+    int32_t cs_first_step;     /* inner-product indexes: store, for the Cauchy-Schwarz bound
+                                  of PDX_PRUNE_CS_IP, every vector's norm and the norms of
+                                  its unvisited dimensions at the check points of the fetch
+                                  schedule that starts with this step (check points after
+                                  s, 3s, 7s, ... dimensions): 4 * (checks + 1) bytes per
+                                  vector. 0 = none (default); a non-zero value needs
+                                  metric PDX_IP and FP32 storage                           */
 } pdx_build_opts;
 
 typedef struct pdx_ivf_opts {

@@ -53,6 +53,16 @@ while ``oracle.knn`` is the reference for the exact *result*:
     E over the visited dimensions over the sum of E over all of them. With
     storage order and equal E_j, F_q(d) = d / D and the test is ADSampling's.
 
+* Exact inner-product pruning with the Cauchy-Schwarz bound (the exact half
+  of BSA's test in Sec. 2.3, carried over to the inner product; the paper
+  itself prunes only distances, and the reading is this build's): with
+  ``metric="ip"`` the distance is -q.x, and after the first d dimensions in
+  storage order the unvisited part q_r . x_r lies in [-||q_r|| ||x_r||,
+  ||q_r|| ||x_r||]. A vector is pruned when
+  partial - ||q_r|| ||x_r|| > tau, partial being the visited -sum q_j x_j and
+  tau the k-th best -q.x so far: even with the most favourable unvisited part
+  it cannot enter the top-k. It holds for any vector norms.
+
 Returns the top-k plus per-query counters: values accumulated (the paper's
 pruning power is 1 - visited / (n*D)), vectors pruned, and the phase at which
 each block ended.
@@ -121,12 +131,18 @@ class _Heap:
 
 
 def pdxearch(x, q, k, blocks, pruner="bond", order="dist_to_means", zone_dims=1, first_step=2,
-             selection_threshold=0.20, eps0=2.1, bsa_m=None, bsa_lambda=None, tau0=None, tau_fixed=False):
+             selection_threshold=0.20, eps0=2.1, bsa_m=None, bsa_lambda=None, tau0=None, tau_fixed=False,
+             metric="l2"):
     """One query. ``blocks`` is a list of int arrays (vector ids per PDXearch
     block, visited in list order). ``x`` is [n][D]; returns (dists, ids, stats).
     ``tau0`` optionally seeds the threshold (any k-th distance of k real
     vectors keeps the search exact); with ``tau_fixed`` the threshold stays
-    tau0 instead of tightening as blocks merge into the heap."""
+    tau0 instead of tightening as blocks merge into the heap. ``metric`` "ip"
+    ranks by -q.x (pruners "none" and "cs_ip" only)."""
+    if metric not in ("l2", "ip"):
+        raise ValueError(metric)
+    if (metric == "ip") != (pruner == "cs_ip") and pruner != "none":
+        raise ValueError("the Cauchy-Schwarz pruner ranks inner products; the other pruners squared distances")
     x = np.asarray(x, np.float64)
     q = np.asarray(q, np.float64)
     n, d = x.shape
@@ -142,7 +158,7 @@ def pdxearch(x, q, k, blocks, pruner="bond", order="dist_to_means", zone_dims=1,
         xb = x[ids]
         if not started:
             # START: linear scan until k vectors have been seen
-            full = ((xb - q) ** 2).sum(axis=1)
+            full = -(xb @ q) if metric == "ip" else ((xb - q) ** 2).sum(axis=1)
             st.values_visited += ids.size * d
             st.vectors_seen += ids.size
             heap.merge(full, ids)
@@ -167,7 +183,10 @@ def pdxearch(x, q, k, blocks, pruner="bond", order="dist_to_means", zone_dims=1,
         for s in step_schedule(d, first_step):
             js = dims[pos:pos + s]
             rows = np.arange(ids.size) if positions is None else positions
-            contrib = ((xb[np.ix_(rows, js)] - q[js]) ** 2).sum(axis=1)
+            if metric == "ip":
+                contrib = -(xb[np.ix_(rows, js)] @ q[js])
+            else:
+                contrib = ((xb[np.ix_(rows, js)] - q[js]) ** 2).sum(axis=1)
             partial[rows] += contrib
             st.values_visited += rows.size * js.size
             pos += s
@@ -213,6 +232,11 @@ def _predicate(pruner, partial, tau, dvis, d, xrows, q, dims, pos, eps0, bsa_m, 
         frac = float(lam[dims[:pos]].sum() / lam.sum())
         stat = partial > tau * frac * (1.0 + bsa_m / math.sqrt(dvis)) ** 2
         return cs | stat
+    if pruner == "cs_ip":
+        rest = dims[pos:]
+        rx = np.sqrt((xrows[:, rest] ** 2).sum(axis=1))
+        rq = math.sqrt(float((q[rest] ** 2).sum()))
+        return partial - rq * rx > tau
     raise ValueError(pruner)
 
 

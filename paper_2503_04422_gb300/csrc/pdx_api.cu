@@ -116,7 +116,8 @@ static int rows_vec4(const pdx_index *ix, const float *qrows) {
 static void free_index(pdx_index *ix) {
     if (!ix) return;
     void *ptrs[] = {ix->sc_cent, ix->sc_members, ix->data, ix->data_lp, ix->scale, ix->xnary, ix->dsm, ix->xtc, ix->xnorm, ix->ids, ix->slot_of, ix->blk_cnt, ix->part_blk, ix->means, ix->vars, ix->cmean, ix->centroids, ix->centroid_norms,
-                    ix->assign, ix->rot, ix->shift, ix->pca_var, ix->resid, ix->chk, ix->cdata, ix->cids};
+                    ix->assign, ix->rot, ix->shift, ix->pca_var, ix->resid, ix->chk, ix->cdata, ix->cids,
+                    ix->cs_chk, ix->cs_resid};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     delete[] ix->h_part_blk;
@@ -241,6 +242,37 @@ static pdx_status keep_rows(pdx_index *ix, const float *xrows, cudaStream_t st) 
     PDX_TRY(dalloc(ix, &ix->xnary, (size_t)ix->n * ix->d));
     PDX_TRY(cudaMemcpyAsync(ix->xnary, xrows, (size_t)ix->n * ix->d * 4, cudaMemcpyDeviceToDevice, st));
     PDX_TRY(cudaStreamSynchronize(st));
+    return PDX_OK;
+}
+
+// Check points of the doubling fetch schedule (dimensions visited at each
+// prune test): first_step, first_step*3, ... strictly below d.
+static std::vector<int32_t> check_points(int d, int first_step) {
+    std::vector<int32_t> c;
+    int pos = 0, step = std::max(1, first_step);
+    while (true) {
+        pos = std::min(d, pos + step);
+        if (pos >= d) break;
+        c.push_back(pos);
+        step *= 2;
+    }
+    return c;
+}
+
+// Norms for the Cauchy-Schwarz inner-product bound (PDX_PRUNE_CS_IP): the
+// squared norm of every vector (check 0) and of its dimensions from each
+// check point of the fetch schedule starting with first_step on.
+static pdx_status build_cs_norms(pdx_index *ix, int first_step, cudaStream_t st) {
+    std::vector<int32_t> chk = check_points(ix->d, first_step);
+    chk.insert(chk.begin(), 0);
+    PDX_TRY(dalloc(ix, &ix->cs_chk, chk.size()));
+    PDX_TRY(dalloc(ix, &ix->cs_resid, (size_t)ix->nblocks * chk.size() * kBlock));
+    PDX_TRY(cudaMemcpyAsync(ix->cs_chk, chk.data(), chk.size() * 4, cudaMemcpyHostToDevice, st));
+    PDX_TRY(launch_bsa_resid(ix->data, ix->blk_cnt, ix->nblocks, ix->d, ix->cs_chk, (int32_t)chk.size(), ix->cs_resid,
+                             st));
+    PDX_TRY(cudaStreamSynchronize(st));
+    ix->cs_first_step = first_step;
+    ix->cs_nchk = (int32_t)chk.size() - 1;
     return PDX_OK;
 }
 
@@ -452,6 +484,14 @@ pdx_status pdx_build_layout(const float *x, int64_t n, int32_t d, const pdx_buil
         set_error("pdx_build_layout: start_clusters=%d (0 automatic, -1 none, or a count)", o.start_clusters);
         return PDX_ERR_ARG;
     }
+    if (o.cs_first_step < 0 || o.cs_first_step > d) {
+        set_error("pdx_build_layout: cs_first_step=%d outside [0, d=%d]", o.cs_first_step, d);
+        return PDX_ERR_ARG;
+    }
+    if (o.cs_first_step > 0 && (o.metric != PDX_IP || o.storage != PDX_F32)) {
+        set_error("pdx_build_layout: cs_first_step needs metric PDX_IP and FP32 storage");
+        return PDX_ERR_UNSUPPORTED;
+    }
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     pdx_index *ix = new (std::nothrow) pdx_index();
     if (!ix) {
@@ -505,6 +545,7 @@ pdx_status pdx_build_layout(const float *x, int64_t n, int32_t d, const pdx_buil
             if (C == 0) C = n >= 65536 ? (int32_t)std::min<int64_t>(1024, n / 4096) : 0;
             if (C > 0) s = build_start_clusters(ix, xd, (int32_t)std::min<int64_t>(C, n), st);
         }
+        if (s == PDX_OK && o.cs_first_step > 0) s = build_cs_norms(ix, o.cs_first_step, st);
         if (s == PDX_OK && o.keep_dsm) {  // the fully dimension-major copy (DSM layout scan)
             const int64_t n_pad = (n + kBlock - 1) / kBlock * kBlock;
             cudaError_t e = dalloc(ix, &ix->dsm, (size_t)n_pad * d);
@@ -547,7 +588,7 @@ pdx_status check_search_args(const pdx_index *ix, const float *q, int64_t nq, in
         }
         *o = *opts;
     }
-    if (o->pruner < PDX_PRUNE_NONE || o->pruner > PDX_PRUNE_ADS_BOND || o->order < PDX_ORDER_DIST_TO_MEANS ||
+    if (o->pruner < PDX_PRUNE_NONE || o->pruner > PDX_PRUNE_CS_IP || o->order < PDX_ORDER_DIST_TO_MEANS ||
         o->order > PDX_ORDER_LEARNED) {
         set_error("%s: bad pruner %d or order %d", fn, (int)o->pruner, (int)o->order);
         return PDX_ERR_ARG;
@@ -595,9 +636,13 @@ pdx_status plan_metric(const pdx_index *ix, int pruner, SearchPlan *pl, const ch
     pl->pruner = pruner;
     pl->metric = ix->metric;
     pl->out_mode = 0;
+    if (pruner == PDX_PRUNE_CS_IP && ix->metric != PDX_IP) {
+        set_error("%s: the Cauchy-Schwarz bound (PDX_PRUNE_CS_IP) is for inner-product indexes", fn);
+        return PDX_ERR_UNSUPPORTED;
+    }
     if (ix->metric == PDX_IP) {
-        if (pruner == PDX_PRUNE_NONE) {
-            pl->out_mode = 1;
+        if (pruner == PDX_PRUNE_NONE || pruner == PDX_PRUNE_CS_IP) {
+            pl->out_mode = 1;   // ranks by -q.x, which holds for any norms under this bound
         } else if (ix->unit_norm) {
             // unit-norm vectors: ||q - x||^2 = ||q||^2 + 1 - 2 q.x ranks like -q.x
             pl->metric = PDX_L2;
@@ -742,6 +787,14 @@ pdx_status exact_plan(const pdx_index *ix, int64_t nq, int32_t k, const pdx_sear
         b += rup((size_t)nq * ep->sc_ld * 8) + rup((size_t)nq * kStartProbe * 8) +
              rup((size_t)nq * kStartProbe * ix->sc_m * 8);
     if (o.tau_init) b += rup((size_t)nq * 4);
+    if (pl.pruner == PDX_PRUNE_CS_IP) {
+        if ((int)o.first_step != ix->cs_first_step) {
+            set_error("PDX_PRUNE_CS_IP: first_step %u differs from the index's stored schedule (%d)", o.first_step,
+                      ix->cs_first_step);
+            return PDX_ERR_ARG;
+        }
+        b += rup((size_t)nq * (ix->cs_nchk + 1) * 2 * 4);  // the query's norms at the check points
+    }
     ep->mlp_bytes = 0;
     if (ep->op.mode == 2) {
         ep->mlp_Lc = ((int64_t)o.mlp_ncentroids + kBlock - 1) / kBlock * kBlock;
@@ -819,6 +872,9 @@ pdx_status exact_run(const pdx_index *ix, const float *qd, int64_t nq, int32_t k
         ep.start_clusters ? reinterpret_cast<uint64_t *>(take((size_t)nq * kStartProbe * ix->sc_m * 8)) : nullptr;
     unsigned char *mlp_ws = ep.mlp_bytes ? take(ep.mlp_bytes) : nullptr;
     float *tau_in = o.tau_init ? reinterpret_cast<float *>(take((size_t)nq * 4)) : nullptr;
+    float *cs_q = pl.pruner == PDX_PRUNE_CS_IP
+                      ? reinterpret_cast<float *>(take((size_t)nq * (ix->cs_nchk + 1) * 2 * 4))
+                      : nullptr;
     if (off > ep.bytes) {
         set_error("internal error: exact-search scratch layout exceeds its plan");
         return PDX_ERR_CUDA;
@@ -852,6 +908,8 @@ pdx_status exact_run(const pdx_index *ix, const float *qd, int64_t nq, int32_t k
             scores = yb;
         }
     }
+    if (cs_q)  // the query's whole and unvisited squared norms at the check points
+        PDX_TRY(launch_bsa_qaux(qd, nq, d, nullptr, ix->cs_chk, ix->cs_nchk + 1, cs_q, st));
     if (ep.op.rows && !learned_done)  // query preprocessing (Sec. 5): PDX-BOND visit orders
         PDX_TRY(launch_order(qd, ep.op.rows, d, ep.op.per_part ? ix->means : ix->cmean, ep.op.per_part, nullptr,
                              ep.op.mode, std::max(1, (int)o.zone_dims), scores, qorder, st));
@@ -940,6 +998,11 @@ pdx_status exact_run(const pdx_index *ix, const float *qd, int64_t nq, int32_t k
     p.pool_cnt = pool_cnt;
     p.tau_fixed = o.tau_fixed ? 1 : 0;
     p.rows_vec4 = rows_vec4(ix, p.qrows);
+    if (cs_q) {
+        p.qaux = cs_q;
+        p.resid = ix->cs_resid;
+        p.nchk = ix->cs_nchk;
+    }
     if (o.scan_event_start) PDX_TRY(cudaEventRecord(static_cast<cudaEvent_t>(o.scan_event_start), st));
     PDX_TRY(launch_scan(pl.pruner, pl.metric, p, sms, st));
     if (o.scan_event_stop) PDX_TRY(cudaEventRecord(static_cast<cudaEvent_t>(o.scan_event_stop), st));
@@ -999,9 +1062,17 @@ pdx_status exact_check(const pdx_index *ix, const float *q, int64_t nq, int32_t 
         set_error("%s: index was built by pdx_ivf_build", fn);
         return PDX_ERR_ARG;
     }
-    if (o->pruner != PDX_PRUNE_NONE && o->pruner != PDX_PRUNE_BOND) {
-        set_error("%s: only NONE or BOND keep the search exact", fn);
+    if (o->pruner != PDX_PRUNE_NONE && o->pruner != PDX_PRUNE_BOND && o->pruner != PDX_PRUNE_CS_IP) {
+        set_error("%s: only NONE, BOND or CS_IP keep the search exact", fn);
         return PDX_ERR_ARG;
+    }
+    if (o->pruner == PDX_PRUNE_CS_IP) {
+        if (ix->cs_first_step <= 0) {
+            set_error("%s: PDX_PRUNE_CS_IP needs an inner-product index built with cs_first_step", fn);
+            return PDX_ERR_UNSUPPORTED;
+        }
+        // the stored norms fix the fetch schedule (the check points)
+        o->first_step = (uint32_t)ix->cs_first_step;
     }
     if (q && (q == out_dist || (const void *)q == (const void *)out_idx)) {
         set_error("%s: outputs alias the queries", fn);
@@ -1083,20 +1154,6 @@ static uint64_t splitmix64(uint64_t &st) {
     z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
     z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
     return z ^ (z >> 31);
-}
-
-// Check points of the doubling fetch schedule (dimensions visited at each
-// prune test): first_step, first_step*3, ... strictly below d.
-static std::vector<int32_t> check_points(int d, int first_step) {
-    std::vector<int32_t> c;
-    int pos = 0, step = std::max(1, first_step);
-    while (true) {
-        pos = std::min(d, pos + step);
-        if (pos >= d) break;
-        c.push_back(pos);
-        step *= 2;
-    }
-    return c;
 }
 
 // ADSampling's random orthogonal transformation (Sec. 2.3), drawn from a seed:
@@ -1373,6 +1430,10 @@ extern "C" pdx_status pdx_ivf_build(const float *x, int64_t n, int32_t d, const 
         set_error("pdx_ivf_build: low-precision storage supports L2 (and unit-norm IP) only");
         return PDX_ERR_UNSUPPORTED;
     }
+    if (o.base.cs_first_step != 0) {
+        set_error("pdx_ivf_build: cs_first_step (the Cauchy-Schwarz inner-product norms) is for exact indexes");
+        return PDX_ERR_UNSUPPORTED;
+    }
     if (o.transform != PDX_PRUNE_NONE && o.base.metric != PDX_L2) {
         set_error("pdx_ivf_build: ADSampling/BSA transforms are defined for L2 only");
         return PDX_ERR_UNSUPPORTED;
@@ -1415,6 +1476,10 @@ extern "C" pdx_status pdx_search_ivf(const pdx_index *ix, const float *q, int64_
     if (nprobe < 1 || nprobe > ix->nparts || nprobe > 4096) {
         set_error("%s: nprobe=%d outside [1, min(nlist=%d, 4096)]", fn, nprobe, ix->nparts);
         return PDX_ERR_ARG;
+    }
+    if (o.pruner == PDX_PRUNE_CS_IP) {
+        set_error("%s: PDX_PRUNE_CS_IP serves exact inner-product indexes only", fn);
+        return PDX_ERR_UNSUPPORTED;
     }
     if (((o.pruner == PDX_PRUNE_ADSAMPLING || o.pruner == PDX_PRUNE_ADS_BOND) &&
          ix->transform != PDX_PRUNE_ADSAMPLING) ||

@@ -83,6 +83,11 @@ struct pdx_index {
     int32_t bsa_nchk = 0;           // BSA: number of check points stored
     int32_t bsa_first_step = 4;     // BSA: fetch schedule the residual norms were taken for
     int32_t *chk = nullptr;         // BSA: [bsa_nchk] dimensions visited at each check point
+    int32_t cs_first_step = 0;      // CS-IP: fetch schedule of the stored norms (0 = none)
+    int32_t cs_nchk = 0;            // CS-IP: check points of that schedule
+    int32_t *cs_chk = nullptr;      // CS-IP: [cs_nchk+1] 0, then the dimensions visited at each check
+    float *cs_resid = nullptr;      // CS-IP: [nblocks][cs_nchk+1][64] squared norms of the dimensions
+                                    //   from cs_chk[t] on (t = 0: the whole vector)
     float *cdata = nullptr;         // IVF centroids in PDX layout [c_nblocks][d][64]
     int32_t *cids = nullptr;        // [c_nblocks*64] bucket id per slot, -1 = padding
     int32_t c_nblocks = 0;
@@ -144,8 +149,6 @@ __device__ __forceinline__ int32_t key_id(uint64_t key) { return (int32_t)(uint3
 enum { MT_L2 = 0, MT_IP = 1, MT_L1 = 2 };
 constexpr unsigned kFull = 0xffffffffu;
 
-// One dimension's contribution to the distance (Sec. 2.1): squared
-// difference, product, or absolute difference.
 // Smallest power of two >= v (v >= 1).
 __host__ __device__ inline int pow2_ceil(int v) {
     int p = 1;
@@ -153,6 +156,8 @@ __host__ __device__ inline int pow2_ceil(int v) {
     return p;
 }
 
+// One dimension's contribution to the distance (Sec. 2.1): squared
+// difference, product, or absolute difference.
 template <int MET>
 __device__ __forceinline__ float term(float qv, float x, float acc) {
     if (MET == MT_L2) {

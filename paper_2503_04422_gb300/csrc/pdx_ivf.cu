@@ -197,7 +197,8 @@ cudaError_t launch_keys_to_parts(const uint64_t *topk, int64_t nq, int32_t nprob
 // BSA metadata. chk[t] = dimensions visited at the t-th prune check.
 // resid[b][t][lane] = sum_{j >= chk[t]} x[b][j][lane]^2 (unvisited energy of
 // each stored vector); qaux[q][t] = (sum_{j >= chk[t]} q_j^2, F(chk[t])) with
-// F(d) = sum_{j < d} var_j / sum_j var_j.
+// F(d) = sum_{j < d} var_j / sum_j var_j (1 without variances: the
+// Cauchy-Schwarz inner-product bound uses the norms alone).
 __global__ void bsa_resid_kernel(const float *__restrict__ data, int64_t nblocks, int32_t d,
                                  const int32_t *__restrict__ chk, int32_t nchk, float *__restrict__ resid) {
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -232,13 +233,14 @@ __global__ void bsa_qaux_kernel(const float *__restrict__ q, int64_t nq, int32_t
     if (r >= nq) return;
     const float *qr = q + r * d;
     float tot = 0.f;
-    for (int j = 0; j < d; ++j) tot += var[j];
+    if (var)
+        for (int j = 0; j < d; ++j) tot += var[j];
     float s1 = 0.f, sv = 0.f;
     int c = nchk - 1;
     for (int j = d - 1; j >= 0 && c >= 0; --j) {
         float v = qr[j];
         s1 = fmaf(v, v, s1);
-        sv += var[j];
+        if (var) sv += var[j];
         while (c >= 0 && chk[c] == j) {
             qaux[(r * nchk + c) * 2] = s1;                                   // ||q_r||^2
             qaux[(r * nchk + c) * 2 + 1] = tot > 0.f ? 1.f - sv / tot : 1.f;  // F(d): visited variance fraction

@@ -34,7 +34,7 @@
 
 namespace pdx {
 
-enum { PR_NONE = 0, PR_BOND = 1, PR_ADS = 2, PR_BSA = 3, PR_ADSB = 4 };
+enum { PR_NONE = 0, PR_BOND = 1, PR_ADS = 2, PR_BSA = 3, PR_ADSB = 4, PR_CSIP = 5 };
 
 // ---- storage types of the PDX blocks ----
 enum { ST_F32 = 0, ST_BF16 = 1, ST_FP8 = 2 };
@@ -333,9 +333,24 @@ __device__ __forceinline__ bool prune_test(float partial, float thr, int dv, int
         if (partial > thr) return true;
         float r = 1.f + eps0 * rsqrtf((float)dv);
         return partial > thr * sd2 * r * r;
+    } else if (PR == PR_CSIP) {
+        // inner product, any norms: partial is the visited sum of q_j x_j and
+        // rx2 the Cauchy-Schwarz margin from cs_margin; the unvisited part of
+        // -q.x is at least -||q_r|| ||x_r||
+        return -partial - rx2 > thr;
     } else {
         return false;
     }
+}
+
+// Margin of the Cauchy-Schwarz inner-product bound at a check point: the
+// largest value the unvisited dimensions can add to q.x, ||q_r|| ||x_r||, plus
+// the rounding of the FP32 sums (the visited partial is within D * 2^-24 of
+// sum |q_j x_j| <= ||q|| ||x||; the squared norms are sums of squares with
+// the same relative error). rx2, x2: the vector's unvisited and whole squared
+// norms; rq2, q2: the query's.
+__device__ __forceinline__ float cs_margin(float rx2, float x2, float rq2, float q2, float gamma) {
+    return sqrtf(rx2 * rq2) * (1.f + gamma) + gamma * sqrtf(x2 * q2);
 }
 
 // Resident CTAs per SM the register allocation is built for (OCC): 3 (80
@@ -561,6 +576,7 @@ __global__ void __launch_bounds__(256, OCC) pdxsearch_kernel(ScanParams a) {
         float tau_loc = __int_as_float(0x7f800000);
         const float *qaux = (PR == PR_BSA)    ? a.qaux + qi * a.nchk * 2
                             : (PR == PR_ADSB) ? a.qaux + (qi * (a.nslots / chunks) + pr) * (int64_t)a.nchk
+                            : (PR == PR_CSIP) ? a.qaux + qi * (a.nchk + 1) * 2
                                               : nullptr;
         // PDX-BOND skim of the first fetch step (4 dimensions). In exact search
         // nearly every block ends there: each of its vectors' partial over the
@@ -771,10 +787,18 @@ __global__ void __launch_bounds__(256, OCC) pdxsearch_kernel(ScanParams a) {
                     sd2 = qaux[chk * 2 + 1];
                 }
                 if (PR == PR_ADSB) sd2 = qaux[min(chk, a.nchk - 1)];
+                if (PR == PR_CSIP) {  // the query's unvisited and whole squared norms
+                    rq2 = qaux[(chk + 1) * 2];
+                    sd2 = qaux[0];
+                }
 #pragma unroll
                 for (int c = 0; c < 4; ++c) {
                     float rx2 = 0.f;
                     if (PR == PR_BSA) rx2 = a.resid[((int64_t)b * a.nchk + chk) * kBlock + 4 * sl + c];
+                    if (PR == PR_CSIP) {
+                        const float *rb = a.resid + (int64_t)b * (a.nchk + 1) * kBlock + 4 * sl + c;
+                        rx2 = cs_margin(rb[(chk + 1) * kBlock], rb[0], rq2, sd2, a.gamma);
+                    }
                     if (prune_test<PR>(sel4(f, c), thr, pos, D, a.eps0, rx2, rq2, sd2, a.bsa_m)) alive &= ~(1u << c);
                 }
                 ++chk;
@@ -884,6 +908,10 @@ __global__ void __launch_bounds__(256, OCC) pdxsearch_kernel(ScanParams a) {
                         if (m < nsurv) rx2 = a.resid[((int64_t)b * a.nchk + chk) * kBlock + my_v];
                     }
                     if (PR == PR_ADSB) sd2 = qaux[min(chk, a.nchk - 1)];
+                    if (PR == PR_CSIP && m < nsurv) {
+                        const float *rb = a.resid + (int64_t)b * (a.nchk + 1) * kBlock + my_v;
+                        rx2 = cs_margin(rb[(chk + 1) * kBlock], rb[0], qaux[(chk + 1) * 2], qaux[0], a.gamma);
+                    }
                     ++chk;
                     bool keep = (m < nsurv) && !prune_test<PR>(my_p, thr, pos, D, a.eps0, rx2, rq2, sd2, a.bsa_m);
                     unsigned km = __ballot_sync(kFull, keep && g == 0);   // one bit per survivor, at its lane m*G
@@ -1111,6 +1139,9 @@ cudaError_t launch_scan(int pruner, int metric, const ScanParams &p, int num_sms
         return launch_scan_t<PR_BSA, MT_L2, ST_F32>(p, num_sms, st);
     case PR_ADSB:
         return launch_scan_t<PR_ADSB, MT_L2, ST_F32>(p, num_sms, st);
+    case PR_CSIP:
+        if (metric != MT_IP) return cudaErrorInvalidValue;
+        return launch_scan_t<PR_CSIP, MT_IP, ST_F32>(p, num_sms, st);
     default:
         return cudaErrorInvalidValue;
     }

@@ -204,7 +204,10 @@ static pdx_status prepare_entry(pdx_server *s, int c, int bk) {
             float best = 1e30f;
             TuneRecord bt{o.ctas_per_sm, o.first_step, o.blocks_per_item, 0.f};
             const uint32_t ctas[] = {3, 4};
-            const uint32_t steps[] = {4, 8};
+            // a pruner with norms stored for one schedule keeps its first step
+            const bool fixed_step = o.pruner == PDX_PRUNE_CS_IP;
+            const std::vector<uint32_t> steps =
+                fixed_step ? std::vector<uint32_t>{o.first_step} : std::vector<uint32_t>{4u, 8u};
             std::vector<uint32_t> bpis;
             for (uint32_t b : item_sizes(ix, B, s->o.k, o, pl, s->sms))
                 if (plan_fits(s, ix, B, o, pl, b)) bpis.push_back(b);

@@ -21,7 +21,7 @@ LIB_PATH = os.path.join(_HERE, "_build", "libpdx.so")
 PDX_OK, PDX_ERR_ARG, PDX_ERR_OOM, PDX_ERR_CUDA, PDX_ERR_TIMEOUT, PDX_ERR_UNSUPPORTED = range(6)
 METRIC = {"l2": 0, "ip": 1, "l1": 2}
 DTYPE = {"f32": 0, "bf16": 1, "fp8": 2}
-PRUNER = {"none": 0, "bond": 1, "ads": 2, "adsampling": 2, "bsa": 3, "ads_bond": 4}
+PRUNER = {"none": 0, "bond": 1, "ads": 2, "adsampling": 2, "bsa": 3, "ads_bond": 4, "cs_ip": 5}
 ORDER = {"dist_to_means": 0, "decreasing": 1, "sequential": 2, "learned": 3}
 MEANS = {"block": 0, "collection": 1, "auto": 2}
 ENGINE = {"auto": 0, "scan": 1, "tensor": 2}
@@ -36,7 +36,8 @@ STATUS_NAMES = {0: "PDX_OK", 1: "PDX_ERR_ARG", 2: "PDX_ERR_OOM", 3: "PDX_ERR_CUD
 class pdx_build_opts(ctypes.Structure):
     _fields_ = [("struct_size", ctypes.c_uint32), ("metric", ctypes.c_int), ("storage", ctypes.c_int),
                 ("partition_size", ctypes.c_uint32), ("keep_rows", ctypes.c_int32),
-                ("dense_rows", ctypes.c_int32), ("keep_dsm", ctypes.c_int32), ("start_clusters", ctypes.c_int32)]
+                ("dense_rows", ctypes.c_int32), ("keep_dsm", ctypes.c_int32), ("start_clusters", ctypes.c_int32),
+                ("cs_first_step", ctypes.c_int32)]
 
 
 class pdx_ivf_opts(ctypes.Structure):
@@ -207,7 +208,7 @@ class Index:
 
 
 def build_opts(metric="l2", storage="f32", partition_size=10000, keep_rows=True,
-               dense_rows=False, keep_dsm=False, start_clusters=0) -> pdx_build_opts:
+               dense_rows=False, keep_dsm=False, start_clusters=0, cs_first_step=0) -> pdx_build_opts:
     o = pdx_build_opts()
     lib().pdx_default_build_opts(ctypes.byref(o))
     o.metric = METRIC[metric]
@@ -217,6 +218,7 @@ def build_opts(metric="l2", storage="f32", partition_size=10000, keep_rows=True,
     o.dense_rows = int(bool(dense_rows))
     o.keep_dsm = int(bool(keep_dsm))
     o.start_clusters = int(start_clusters)
+    o.cs_first_step = int(cs_first_step)
     return o
 
 
@@ -253,16 +255,18 @@ def search_opts(pruner="bond", order="dist_to_means", zone_dims=None, selection_
 
 
 def pdx_build_layout(x, metric="l2", partition_size=10000, storage="f32", stream=None,
-                     dense_rows=False, keep_dsm=False, keep_rows=True, start_clusters=0) -> Index:
+                     dense_rows=False, keep_dsm=False, keep_rows=True, start_clusters=0,
+                     cs_first_step=0) -> Index:
     """Exact-search index over x [n][d] (Sec. 3, Sec. 6.6); dense_rows also
     keeps the row-major FP32 vectors the tensor-core engine reads, keep_dsm a
-    fully dimension-major copy for the DSM layout scan."""
+    fully dimension-major copy for the DSM layout scan, cs_first_step (inner
+    product) the norms the Cauchy-Schwarz pruner "cs_ip" reads."""
     p, keep, cuda, shape = _ptr_f32(x, "x")
     if len(shape) != 2:
         raise ValueError("x must be [n][d]")
     h = ctypes.c_void_p()
     o = build_opts(metric, storage, partition_size, keep_rows=keep_rows, dense_rows=dense_rows, keep_dsm=keep_dsm,
-                   start_clusters=start_clusters)
+                   start_clusters=start_clusters, cs_first_step=cs_first_step)
     _check(lib().pdx_build_layout(p, shape[0], shape[1], ctypes.byref(o), _stream(cuda, stream), ctypes.byref(h)),
            "pdx_build_layout")
     del keep

@@ -75,6 +75,20 @@ def anisotropic_gaussian(n: int, d: int, nq: int, decay: float = 0.9, seed: int 
     return x, q
 
 
+def mips_vectors(n: int, d: int, nq: int, decay: float = 0.93, norm_spread: float = 1.0,
+                 seed: int = BASE_SEED + 9):
+    """Inner-product workload with varied norms: coordinates independent,
+    zero-mean Gaussian with standard deviation decay^j in storage order (the
+    energy sits in the leading coordinates, as after a PCA projection), and
+    each vector scaled by exp(u), u uniform in [-norm_spread, norm_spread].
+    Queries follow the same coordinates without the norm scaling."""
+    sig = (decay ** np.arange(d)).astype(np.float64)
+    scale = np.exp(_rng(seed, 2).uniform(-norm_spread, norm_spread, size=(n, 1)))
+    x = (_rng(seed, 0).standard_normal((n, d)) * sig * scale).astype(np.float32)
+    q = (_rng(seed, 1).standard_normal((nq, d)) * sig).astype(np.float32)
+    return x, q
+
+
 @dataclass
 class MixtureSpec:
     n: int

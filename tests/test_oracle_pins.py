@@ -350,3 +350,50 @@ def test_ads_bond_reduces_to_adsampling_without_reordering():
         for v in bond_only:
             assert ((x[v] - q) ** 2).sum() > tau
         assert {e[1] for e in b.prune_events} <= {e[1] for e in a.prune_events}
+
+
+def test_cs_ip_predicate_hand_worked_events():
+    # tests/golden/cs_ip_worked.json: the exact Cauchy-Schwarz bound for the
+    # inner product at a fixed tau. A flipped sign loses the result; ||q|| or
+    # ||x|| in place of the unvisited norms keeps x6 at d=3; an unvisited set
+    # that starts one dimension late prunes x7 at d=1.
+    g = _gold("cs_ip_worked.json")
+    x = np.array(g["vectors"], np.float64)
+    q = np.array(g["query"], np.float64)
+    d, i, st = ops.pdxearch(x, q, g["k"], [np.arange(x.shape[0])], pruner="cs_ip", metric="ip",
+                            first_step=g["first_step"], tau0=g["tau0"], tau_fixed=True)
+    assert [list(e) for e in st.prune_events] == g["prune_events"]
+    assert i.tolist() == g["top_ids"]
+    assert d.tolist() == g["top_dists"]
+
+
+@pytest.mark.parametrize("first_step,sel", [(1, 0.2), (4, 0.2), (2, 0.6)])
+def test_cs_ip_is_exact_for_any_norms(first_step, sel):
+    # the bound holds for every vector, so the pruned search returns the brute
+    # force inner-product top-k, with norms spread over two orders of magnitude
+    rng = np.random.default_rng(31)
+    n, d, k = 900, 20, 9
+    x = rng.standard_normal((n, d)) * (0.5 ** np.arange(d) * 3.0) * np.exp(rng.uniform(-2.3, 2.3, (n, 1)))
+    q = rng.standard_normal((4, d)) * (0.5 ** np.arange(d) * 3.0)
+    blocks = ops.partitions(n, 128)
+    tdist, truth = ok.knn(x.astype(np.float32), q.astype(np.float32), k, metric="ip")
+    for j in range(q.shape[0]):
+        dd, idx, st = ops.pdxearch(x.astype(np.float32), q[j].astype(np.float32), k, blocks, pruner="cs_ip",
+                                   metric="ip", first_step=first_step, selection_threshold=sel)
+        assert idx.tolist() == truth[j].tolist()
+        np.testing.assert_allclose(-dd, tdist[j], rtol=1e-12)
+        # energy decays with the dimension: most vectors end early
+        assert st.values_visited < 0.6 * n * d
+
+
+def test_cs_ip_with_a_query_zero_beyond_the_check_is_the_exact_test():
+    # ||q_r|| = 0 after the first check point: the bound equals -q.x, so a
+    # vector is pruned there exactly when its -q.x exceeds tau
+    rng = np.random.default_rng(32)
+    x = rng.standard_normal((200, 8))
+    q = np.array([1.5, -2.0, 0, 0, 0, 0, 0, 0])
+    tau = -1.0
+    _, _, st = ops.pdxearch(x, q, 3, [np.arange(200)], pruner="cs_ip", metric="ip", first_step=2, tau0=tau,
+                            tau_fixed=True)
+    pruned_at_2 = {e[1] for e in st.prune_events if e[2] == 2}
+    assert pruned_at_2 == {v for v in range(200) if -(x[v] @ q) > tau}
