@@ -40,6 +40,7 @@ WORKLOADS = {
     "learned_order_2m_d1536": dict(k=10, pruner="bond", metric="ip", nclusters=1024, traces=50_000),
     "serving_64_fp8": dict(k=100, pruner="bond", storage="fp8", batches=1000, max_batch=4096),
     "layouts": dict(k=10),
+    "mips_1m_d768": dict(k=10, pruner="cs_ip", metric="ip"),
 }
 PROFILE_TRAFFIC = os.path.join(ROOT, "profiles", "traffic.json")
 
@@ -259,7 +260,9 @@ def run_ours(args, rank, world, local_rank):
     pruner = args.pruner or spec["pruner"]
     engine = args.engine or ("tensor" if pruner == "none" else "auto")
     tensor = pruner == "none" and engine == "tensor"
-    ix = pdx.pdx_build_layout(torch.from_numpy(x).cuda(), storage=args.storage, dense_rows=tensor)
+    metric = spec.get("metric", "l2")
+    ix = pdx.pdx_build_layout(torch.from_numpy(x).cuda(), metric=metric, storage=args.storage, dense_rows=tensor,
+                              cs_first_step=4 if pruner == "cs_ip" else 0)
     torch.cuda.synchronize()
     torch.cuda.empty_cache()
     q_dev = torch.from_numpy(q).cuda()
@@ -350,7 +353,8 @@ def run_ours(args, rank, world, local_rank):
                     "launch_ms_avg": launch_ms, "bracket": "both GEMM launches and the select between them",
                     "per_unit": {"flop_per_query": 2.0 * n * d, "units_per_launch": nq}}
     else:
-        roofline = {"bound": "hbm", "kernel": f"pdxsearch_kernel<{pruner.upper()},L2,{args.storage.upper()}>",
+        roofline = {"bound": "hbm",
+                    "kernel": f"pdxsearch_kernel<{pruner.upper()},{metric.upper()},{args.storage.upper()}>",
                     "achieved": achieved,
                     "peak": peak, "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,
                     "traffic": traffic, "algorithmic_bytes_per_launch": bytes_per_launch,
@@ -415,10 +419,28 @@ def run_ours(args, rank, world, local_rank):
                "same_ids_as_pdx_bond": same}
         del ix_t
         torch.cuda.empty_cache()
+    elif pruner == "cs_ip" and not args.no_alt and not args.shard:
+        # the unpruned inner-product scan over the same index (same exact results)
+        opts_t = pdx.search_opts(pruner="none", engine="scan")
+        od_t = torch.empty_like(od)
+        oi_t = torch.empty_like(oi)
+        for _ in range(args.warmup):
+            pdx.pdx_search_exact(ix, q_dev, k, opts=opts_t, out=(od_t, oi_t))
+        ev_t = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+        torch.cuda.synchronize()
+        for i in range(K):
+            flush.zero_()
+            ev_t[i][0].record(stream)
+            pdx.pdx_search_exact(ix, q_dev, k, opts=opts_t, out=(od_t, oi_t))
+            ev_t[i][1].record(stream)
+        torch.cuda.synchronize()
+        t_ms = sum(a_.elapsed_time(b_) for a_, b_ in ev_t)
+        alt = {"engine": "pdx scan, no pruning (inner product)", "value": nq * world * K / (t_ms / 1e3),
+               "unit": "queries/s", "ms_per_step": t_ms / K, "same_ids_as_cs_ip": bool(torch.equal(oi_t, oi))}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        rate, thr, done = cpu_oracle_rate(x, q, k, budget_s=args.cpu_budget)
+        rate, thr, done = cpu_oracle_rate(x, q, k, budget_s=args.cpu_budget, metric=metric)
         cpu = {"value": rate, "unit": "queries/s", "cores": thr, "kind": "oracle",
                "sample": f"{done} queries against all {n} vectors, FP64 brute force with full sort"}
     if rank == 0:
@@ -434,11 +456,12 @@ def run_ours(args, rank, world, local_rank):
                                        "per-shard top-k, pdx_merge_topk on the device") if args.shard
                        else f"replicas{world}: every rank searches its own queries over the whole collection",
                        "pruner": pruner, "engine": "tensor (TF32 GEMM + FP32 rerank)" if tensor else "pdx scan",
-                       "order": "dist_to_means",
+                       "metric": metric,
+                       "order": "storage order (the stored norms fix it)" if pruner == "cs_ip" else "dist_to_means",
                        "means": "collection (automatic for exact search)", "zone_dims": "1 (automatic)",
                        "first_step": int(opts.first_step), "selection_threshold": round(float(opts.selection_threshold), 3),
                        "start": (f"start clusters: {min(1024, n // 4096)} k-means centroids x 64 member vectors, "
-                                 "the 2 nearest per query" if n >= 65536 and pruner != "none"
+                                 "the 2 nearest per query" if n >= 65536 and pruner not in ("none", "cs_ip")
                                  else f"the first {int(opts.start_vectors)} stored vectors"),
                        "ctas_per_sm": int(opts.ctas_per_sm) or "automatic (4 when four CTAs fit with 32 KB of L1, else 3)",
                        "l2": (f"collection {n * d * 4 / 1e9:.3g} GB; 256 MB L2 flush between timed steps "
@@ -933,7 +956,7 @@ def main():
     ap.add_argument("--n", type=int, default=None, help="smaller collection (profiling); default = workload size")
     ap.add_argument("--nq", type=int, default=None, help="queries per GPU; default = workload size")
     ap.add_argument("--storage", default="f32", choices=["f32", "bf16", "fp8"])
-    ap.add_argument("--pruner", default=None, choices=["none", "bond"],
+    ap.add_argument("--pruner", default=None, choices=["none", "bond", "cs_ip"],
                     help="exact workloads: override the workload's pruner")
     ap.add_argument("--engine", default=None, choices=["auto", "scan", "tensor"],
                     help="unpruned exact search: PDX scan or tensor-core GEMM (default tensor)")

@@ -237,6 +237,7 @@ WORKLOADS = {
     "bond_exact_1m_d768": dict(kind="mixture", n=1_000_000, d=768, nq=1_000, k=10),
     "ivf_1m_d960": dict(kind="mixture_rot", n=1_000_000, d=960, nq=10_000, k=10, nlist=1024),
     "learned_order_2m_d1536": dict(kind="embedding", n=2_000_000, d=1536, nq=5_000, k=10),
+    "mips_1m_d768": dict(kind="mips", n=1_000_000, d=768, nq=1_000, k=10),
 }
 
 
@@ -253,4 +254,6 @@ def make(name: str, n: int | None = None, nq: int | None = None):
         return gaussian_mixture(MixtureSpec(n=n, d=w["d"], nq=nq, seed=BASE_SEED + 2, rotate=True))
     if w["kind"] == "embedding":
         return embedding_like(n, w["d"], nq)
+    if w["kind"] == "mips":
+        return mips_vectors(n, w["d"], nq, decay=0.99, norm_spread=1.0)
     raise KeyError(name)
