@@ -769,6 +769,14 @@ pdx_status exact_plan(const pdx_index *ix, int64_t nq, int32_t k, const pdx_sear
     // (L2 ranking), else from the first start_vectors stored vectors
     ep->start_clusters = ep->start && ix->sc_c > 0 && pl.metric == PDX_L2;
     ep->sc_ld = ep->start_clusters ? ((int64_t)ix->sc_c + kBlock - 1) / kBlock * kBlock : 0;
+    // kStartProbe clusters, or enough for twice k members (k = 100: 4), at
+    // most 16 and at most all of them: the initial threshold is the k-th of
+    // the members' distances, which is loose when k is close to their count
+    ep->sc_probe = 0;
+    if (ep->start_clusters) {
+        const int want = (2 * k + ix->sc_m - 1) / ix->sc_m;
+        ep->sc_probe = std::min(std::min(16, ix->sc_c), std::max(kStartProbe, want));
+    }
     if (ep->start && !ep->start_clusters) {
         int64_t sv = std::max<int64_t>(o.start_vectors, k);
         ep->start_blk = (int)std::min<int64_t>(ix->nblocks, (sv + kBlock - 1) / kBlock);
@@ -784,8 +792,8 @@ pdx_status exact_plan(const pdx_index *ix, int64_t nq, int32_t k, const pdx_sear
                + rup((size_t)nq * kPoolCap * 4) + rup((size_t)nq * 4);  // shared candidate pools
     if (ep->start) b += rup((size_t)nq * ep->Lstart * 8) + rup((size_t)nq * k * 8);
     if (ep->start_clusters)
-        b += rup((size_t)nq * ep->sc_ld * 8) + rup((size_t)nq * kStartProbe * 8) +
-             rup((size_t)nq * kStartProbe * ix->sc_m * 8);
+        b += rup((size_t)nq * ep->sc_ld * 8) + rup((size_t)nq * ep->sc_probe * 8) +
+             rup((size_t)nq * ep->sc_probe * ix->sc_m * 8);
     if (o.tau_init) b += rup((size_t)nq * 4);
     if (pl.pruner == PDX_PRUNE_CS_IP) {
         if ((int)o.first_step != ix->cs_first_step) {
@@ -867,9 +875,9 @@ pdx_status exact_run(const pdx_index *ix, const float *qd, int64_t nq, int32_t k
     uint64_t *skeys = ep.start ? reinterpret_cast<uint64_t *>(take((size_t)nq * ep.Lstart * 8)) : nullptr;
     uint64_t *stopk = ep.start ? reinterpret_cast<uint64_t *>(take((size_t)nq * k * 8)) : nullptr;
     uint64_t *sc_keys = ep.start_clusters ? reinterpret_cast<uint64_t *>(take((size_t)nq * ep.sc_ld * 8)) : nullptr;
-    uint64_t *sc_near = ep.start_clusters ? reinterpret_cast<uint64_t *>(take((size_t)nq * kStartProbe * 8)) : nullptr;
+    uint64_t *sc_near = ep.start_clusters ? reinterpret_cast<uint64_t *>(take((size_t)nq * ep.sc_probe * 8)) : nullptr;
     uint64_t *sc_mkeys =
-        ep.start_clusters ? reinterpret_cast<uint64_t *>(take((size_t)nq * kStartProbe * ix->sc_m * 8)) : nullptr;
+        ep.start_clusters ? reinterpret_cast<uint64_t *>(take((size_t)nq * ep.sc_probe * ix->sc_m * 8)) : nullptr;
     unsigned char *mlp_ws = ep.mlp_bytes ? take(ep.mlp_bytes) : nullptr;
     float *tau_in = o.tau_init ? reinterpret_cast<float *>(take((size_t)nq * 4)) : nullptr;
     float *cs_q = pl.pruner == PDX_PRUNE_CS_IP
@@ -930,7 +938,7 @@ pdx_status exact_run(const pdx_index *ix, const float *qd, int64_t nq, int32_t k
         // START (Sec. 4) from the query's kStartProbe nearest start clusters:
         // exact distances to their members give every query an initial
         // k-th-best threshold of real vectors near it
-        const int P = kStartProbe, M = ix->sc_m;
+        const int P = ep.sc_probe, M = ix->sc_m;
         PDX_TRY(launch_dense_keys_rows(qd, nq, ix->sc_cent, ix->sc_c, d, ep.sc_ld, sc_keys, st));
         PDX_TRY(launch_select_k(sc_keys, nq, ep.sc_ld, P, sc_near, st));
         PDX_TRY(launch_member_keys(qd, nq, d, ix->xnary, ix->data, ix->slot_of, sc_near, P, ix->sc_members, M, sc_mkeys,

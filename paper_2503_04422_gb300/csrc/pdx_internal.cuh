@@ -18,7 +18,7 @@ constexpr int kMaxK = 1024;
 constexpr int kMaxD = 4096;
 constexpr int kMaxSortUnits = 256;  // zone keys a scan warp sorts in-kernel (8 per lane)
 constexpr int kPoolCap = 256;       // shared candidate distances per query (8 per lane)
-constexpr int kStartProbe = 2;      // start clusters a query's START reads
+constexpr int kStartProbe = 2;      // start clusters a query's START reads (at least; more for large k)
 constexpr int kMaxChecks = 16;      // prune check points of one fetch schedule (doubling: log2(d) + 1)
 constexpr int kStartMembers = 64;   // member vectors kept per start cluster
 
@@ -288,6 +288,7 @@ struct ExactPlan {
     int layout = 0;            // pdx_layout of an unpruned scan (0: the PDX scan path)
     bool start_clusters = false;  // START from the query's nearest start clusters
     int64_t sc_ld = 0;         // padded centroid count of the centroid keys
+    int32_t sc_probe = 0;      // start clusters read per query: enough members for k
     bool dense = false;        // tensor-core engine (pdx_dense.cu) instead of the scan
     int dense_cap = 0;         // its candidate entries per query
     size_t bytes = 0;

@@ -305,8 +305,30 @@ cudaError_t launch_select_k(const uint64_t *keys, int64_t rows, int64_t L, int32
 // threshold: tau[row] is the k-th distance of k real vectors found by the
 // scan, so the k smallest keys are all within slack(tau, gamma) (the slack
 // covers FP32 sums taken in another order, e.g. by START). Keys within it are
-// compacted into shared memory and sorted; a row with more of them than the
-// buffer holds falls back to the chunked sort of select_k_kernel.
+// compacted into shared memory and sorted. A row with more of them than the
+// buffer holds (a scan whose threshold tightened late, e.g. one query spread
+// over many work items in one wave) takes the k-th smallest of the sb keys it
+// kept as its new limit: that is the k-th distance of k real candidates, so it
+// still bounds the row's k-th from above, and the row is filtered again. If a
+// round brings no progress (ties) the chunked sort of select_k_kernel decides.
+__device__ __forceinline__ void block_bitonic(uint64_t *buf, int len, int tid, int nt) {
+    for (int size = 2; size <= len; size <<= 1) {
+        for (int stride = size >> 1; stride > 0; stride >>= 1) {
+            for (int i = tid; i < (len >> 1); i += nt) {
+                const int lo = 2 * i - (i & (stride - 1));
+                const int hi = lo + stride;
+                const bool asc = (lo & size) == 0;
+                const uint64_t x = buf[lo], y = buf[hi];
+                if ((x > y) == asc) {
+                    buf[lo] = y;
+                    buf[hi] = x;
+                }
+            }
+            __syncthreads();
+        }
+    }
+}
+
 __global__ void __launch_bounds__(512) select_k_tau_kernel(const uint64_t *__restrict__ keys, int64_t L, int32_t k,
                                                            const float *__restrict__ tau, float gamma, int32_t sb,
                                                            uint64_t *__restrict__ out) {
@@ -316,40 +338,43 @@ __global__ void __launch_bounds__(512) select_k_tau_kernel(const uint64_t *__res
     const uint64_t *src = keys + row * L;
     const int tid = threadIdx.x, nt = blockDim.x;
     const float t = o2f(reinterpret_cast<const uint32_t *>(tau)[row]);
-    const uint32_t lim = f2o(t + fabsf(t) * gamma);
-    if (tid == 0) count = 0;
-    __syncthreads();
-    for (int64_t i = tid; i < L; i += nt) {
-        const uint64_t key = src[i];
-        if (key != kEmptyKey && (uint32_t)(key >> 32) <= lim) {
-            const int pos = atomicAdd(&count, 1);
-            if (pos < sb) buf[pos] = key;
-        }
-    }
-    __syncthreads();
-    const int c = count;
-    if (c <= sb) {
-        int len = 1;
-        while (len < (c > k ? c : k)) len <<= 1;
-        for (int i = c + tid; i < len; i += nt) buf[i] = kEmptyKey;
+    uint32_t lim = f2o(t + fabsf(t) * gamma);
+    for (int round = 0; round < 4; ++round) {
+        if (tid == 0) count = 0;
         __syncthreads();
-        for (int size = 2; size <= len; size <<= 1) {
-            for (int stride = size >> 1; stride > 0; stride >>= 1) {
-                for (int i = tid; i < (len >> 1); i += nt) {
-                    const int lo = 2 * i - (i & (stride - 1));
-                    const int hi = lo + stride;
-                    const bool asc = (lo & size) == 0;
-                    const uint64_t x = buf[lo], y = buf[hi];
-                    if ((x > y) == asc) {
-                        buf[lo] = y;
-                        buf[hi] = x;
-                    }
+        // eight independent loads in flight per thread: a small batch leaves
+        // one CTA to read a long row (1 query: every work item's list)
+        for (int64_t base = tid; base < L; base += (int64_t)nt * 8) {
+            uint64_t kk[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const int64_t i = base + (int64_t)u * nt;
+                kk[u] = i < L ? src[i] : kEmptyKey;
+            }
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                if (kk[u] != kEmptyKey && (uint32_t)(kk[u] >> 32) <= lim) {
+                    const int pos = atomicAdd(&count, 1);
+                    if (pos < sb) buf[pos] = kk[u];
                 }
-                __syncthreads();
             }
         }
-        for (int i = tid; i < k; i += nt) out[row * k + i] = buf[i];
-        return;
+        __syncthreads();
+        const int c = count;
+        const int m = c < sb ? c : sb;
+        int len = 1;
+        while (len < (m > k ? m : k)) len <<= 1;   // <= sb: sb is a power of two >= 2 * pow2(k)
+        for (int i = m + tid; i < len; i += nt) buf[i] = kEmptyKey;
+        __syncthreads();
+        block_bitonic(buf, len, tid, nt);
+        if (c <= sb) {
+            for (int i = tid; i < k; i += nt) out[row * k + i] = buf[i];
+            return;
+        }
+        const uint32_t nl = (uint32_t)(buf[k - 1] >> 32);   // m = sb >= k real keys
+        __syncthreads();
+        if (nl >= lim) break;
+        lim = nl;
     }
     // fallback: running best kpad of all keys, chunks appended and sorted
     int kpad = 1;
@@ -360,21 +385,7 @@ __global__ void __launch_bounds__(512) select_k_tau_kernel(const uint64_t *__res
         __syncthreads();
         for (int i = tid; i < chunk; i += nt) buf[kpad + i] = (off + i < L) ? src[off + i] : kEmptyKey;
         __syncthreads();
-        for (int size = 2; size <= sb; size <<= 1) {
-            for (int stride = size >> 1; stride > 0; stride >>= 1) {
-                for (int i = tid; i < (sb >> 1); i += nt) {
-                    const int lo = 2 * i - (i & (stride - 1));
-                    const int hi = lo + stride;
-                    const bool asc = (lo & size) == 0;
-                    const uint64_t x = buf[lo], y = buf[hi];
-                    if ((x > y) == asc) {
-                        buf[lo] = y;
-                        buf[hi] = x;
-                    }
-                }
-                __syncthreads();
-            }
-        }
+        block_bitonic(buf, sb, tid, nt);
     }
     for (int i = tid; i < k; i += nt) out[row * k + i] = buf[i];
 }
