@@ -363,9 +363,10 @@ pdx_status pdx_ivf_build(const float *x, int64_t n, int32_t d, const pdx_ivf_opt
  * pdx_search_exact -- exact k-NN of nq queries q[nq][d] over an index built
  * by pdx_build_layout (Sec. 2.1; PDX-BOND, Sec. 5, is exact). Writes
  * out_dist[nq][k] (float32) and out_idx[nq][k] (int64 vector ids). opts may
- * be NULL (PDX-BOND, distance-to-means order). pruner must be NONE or BOND
- * (ADSampling/BSA are approximate and only offered over IVF). IP with BOND
- * requires a unit-norm index (it is searched as L2, the same ranking).
+ * be NULL (PDX-BOND, distance-to-means order). pruner must be NONE, BOND or
+ * CS_IP (ADSampling/BSA are approximate and only offered over IVF). IP with
+ * BOND requires a unit-norm index (it is searched as L2, the same ranking);
+ * CS_IP serves IP indexes of any norms built with cs_first_step.
  * Errors: PDX_ERR_ARG (NULL pointers, nq < 0, k outside [1,1024], bad opts),
  * PDX_ERR_UNSUPPORTED, PDX_ERR_OOM, PDX_ERR_CUDA. nq == 0 is a no-op.
  */
@@ -447,7 +448,7 @@ typedef struct pdx_server_opts {
     int32_t use_graphs;        /* capture each (collection, bucket) search in a CUDA graph  */
     int32_t autotune;          /* time candidate launch shapes on first use                 */
     const char *tune_cache;    /* optional JSON file of tuning results (read and written)   */
-    pdx_search_opts search;    /* base options; pruner NONE or BOND                         */
+    pdx_search_opts search;    /* base options; pruner NONE, BOND or CS_IP                 */
 } pdx_server_opts;
 
 typedef struct pdx_server_info_t {

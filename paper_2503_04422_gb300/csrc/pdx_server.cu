@@ -331,8 +331,9 @@ extern "C" pdx_status pdx_server_create(const pdx_index *const *indexes, int32_t
         set_error("pdx_server_create: k=%d max_batch=%d out of range", opts->k, opts->max_batch);
         return PDX_ERR_ARG;
     }
-    if (opts->search.pruner != PDX_PRUNE_NONE && opts->search.pruner != PDX_PRUNE_BOND) {
-        set_error("pdx_server_create: a server runs exact searches (pruner NONE or BOND)");
+    if (opts->search.pruner != PDX_PRUNE_NONE && opts->search.pruner != PDX_PRUNE_BOND &&
+        opts->search.pruner != PDX_PRUNE_CS_IP) {
+        set_error("pdx_server_create: a server runs exact searches (pruner NONE, BOND or CS_IP)");
         return PDX_ERR_ARG;
     }
     if (opts->search.tau_init || opts->search.tau_fixed) {
