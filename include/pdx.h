@@ -186,9 +186,9 @@ typedef struct pdx_build_opts {
                                   runs k-means over a sample and keeps, per centroid, the 64
                                   vectors nearest to it; a pruned L2 search then takes its
                                   initial threshold from exact distances to the members of
-                                  the query's 2 nearest centroids (real vectors near the
-                                  query) instead of from the first start_vectors stored
-                                  vectors. 0 = automatic (n/4096 centroids, at most 1024,
+                                  the query's 2 nearest centroids (more for k > 64: enough
+                                  for 2k members, at most 16; real vectors near the query)
+                                  instead of from the first start_vectors stored vectors. 0 = automatic (n/4096 centroids, at most 1024,
                                   for n >= 65536; none below), -1 = none                  */
     int32_t cs_first_step;     /* inner-product indexes: store, for the Cauchy-Schwarz bound
                                   of PDX_PRUNE_CS_IP, every vector's norm and the norms of
