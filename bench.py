@@ -272,7 +272,7 @@ def run_ours(args, rank, world, local_rank):
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")   # > 129 MB L2
     opts = pdx.search_opts(pruner=pruner, engine=engine if pruner == "none" else "auto",
                            first_step=args.first_step, ctas_per_sm=args.ctas_per_sm,
-                           start_vectors=args.start_vectors)
+                           start_vectors=args.start_vectors, selection_threshold=args.selection_threshold)
     stream = torch.cuda.current_stream()
 
     def step(ev_scan=None):
@@ -393,50 +393,40 @@ def run_ours(args, rank, world, local_rank):
         e2e = {"value": nq * K / (e_ms / 1e3), "unit": "queries/s", "h2d_bytes_per_step": nq * d * 4,
                "d2h_bytes_per_step": nq * k * 12}
 
-    # the other exact engine on the same workload: no pruning, the L2
-    # decomposition's q.x on the tensor cores (same exact results)
-    alt = None
-    if pruner == "bond" and args.storage == "f32" and not args.no_alt and not args.shard:
-        ix_t = pdx.pdx_build_layout(torch.from_numpy(x).cuda(), dense_rows=True)
-        torch.cuda.synchronize()
-        opts_t = pdx.search_opts(pruner="none", engine="tensor")
+    # the other exact engines on the same workload (same exact results): no
+    # pruning, q.x on the tensor cores (the L2 decomposition's, or the inner
+    # product itself), and for the inner-product pruner also the plain scan
+    def time_engine(index, opts_t):
         od_t = torch.empty_like(od)
         oi_t = torch.empty_like(oi)
         for _ in range(args.warmup):
-            pdx.pdx_search_exact(ix_t, q_dev, k, opts=opts_t, out=(od_t, oi_t))
+            pdx.pdx_search_exact(index, q_dev, k, opts=opts_t, out=(od_t, oi_t))
         ev_t = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
         torch.cuda.synchronize()
         for i in range(K):
             flush.zero_()
             ev_t[i][0].record(stream)
-            pdx.pdx_search_exact(ix_t, q_dev, k, opts=opts_t, out=(od_t, oi_t))
+            pdx.pdx_search_exact(index, q_dev, k, opts=opts_t, out=(od_t, oi_t))
             ev_t[i][1].record(stream)
         torch.cuda.synchronize()
         t_ms = sum(a_.elapsed_time(b_) for a_, b_ in ev_t)
-        same = bool(torch.equal(oi_t, oi))
+        return t_ms, bool(torch.equal(oi_t, oi))
+
+    alt = None
+    plain = None
+    if pruner in ("bond", "cs_ip") and args.storage == "f32" and not args.no_alt and not args.shard:
+        ix_t = pdx.pdx_build_layout(torch.from_numpy(x).cuda(), metric=metric, dense_rows=True)
+        torch.cuda.synchronize()
+        t_ms, same = time_engine(ix_t, pdx.search_opts(pruner="none", engine="tensor"))
         alt = {"engine": "tensor (no pruning; TF32 tcgen05 GEMM, proven margins, FP32 rerank)",
                "value": nq * world * K / (t_ms / 1e3), "unit": "queries/s", "ms_per_step": t_ms / K,
-               "same_ids_as_pdx_bond": same}
+               ("same_ids_as_pdx_bond" if pruner == "bond" else "same_ids_as_cs_ip"): same}
         del ix_t
         torch.cuda.empty_cache()
-    elif pruner == "cs_ip" and not args.no_alt and not args.shard:
-        # the unpruned inner-product scan over the same index (same exact results)
-        opts_t = pdx.search_opts(pruner="none", engine="scan")
-        od_t = torch.empty_like(od)
-        oi_t = torch.empty_like(oi)
-        for _ in range(args.warmup):
-            pdx.pdx_search_exact(ix, q_dev, k, opts=opts_t, out=(od_t, oi_t))
-        ev_t = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
-        torch.cuda.synchronize()
-        for i in range(K):
-            flush.zero_()
-            ev_t[i][0].record(stream)
-            pdx.pdx_search_exact(ix, q_dev, k, opts=opts_t, out=(od_t, oi_t))
-            ev_t[i][1].record(stream)
-        torch.cuda.synchronize()
-        t_ms = sum(a_.elapsed_time(b_) for a_, b_ in ev_t)
-        alt = {"engine": "pdx scan, no pruning (inner product)", "value": nq * world * K / (t_ms / 1e3),
-               "unit": "queries/s", "ms_per_step": t_ms / K, "same_ids_as_cs_ip": bool(torch.equal(oi_t, oi))}
+    if pruner == "cs_ip" and not args.no_alt and not args.shard:
+        t_ms, same = time_engine(ix, pdx.search_opts(pruner="none", engine="scan"))
+        plain = {"engine": "pdx scan, no pruning (inner product)", "value": nq * world * K / (t_ms / 1e3),
+                 "unit": "queries/s", "ms_per_step": t_ms / K, "same_ids_as_cs_ip": same}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -475,7 +465,7 @@ def run_ours(args, rank, world, local_rank):
             "gpu_launches_per_step": launches / K,
             "clocks": clk,
             "cpu_baseline": cpu,
-            "other_exact_engine": alt,
+            "other_exact_engine": alt, "plain_scan": plain,
         }
         print(json.dumps(line), flush=True)
     if dist:
@@ -970,6 +960,8 @@ def main():
     ap.add_argument("--no-alt", action="store_true", help="exact workload: skip the tensor-engine companion line")
     ap.add_argument("--ctas-per-sm", type=int, default=None, help="exact and IVF workloads: resident scan CTAs per SM")
     ap.add_argument("--start-vectors", type=int, default=None, help="exact workloads: START scan size (default 1024)")
+    ap.add_argument("--selection-threshold", type=float, default=None,
+                    help="exact workloads: survivor share below which a block enters PRUNE (default 0.2)")
     ap.add_argument("--shard", action="store_true",
                     help="exact workload: split the collection over the ranks by id range (strong scaling)")
     ap.add_argument("--layout-workload", default="plain_scan_10k_d128",
