@@ -403,8 +403,10 @@ __device__ __forceinline__ uint32_t pool_kth(const ScanParams &a, int64_t qi, in
 // aligned) lanes take 16-byte pieces i = lane, lane + 32, ... and issue
 // kRowUnroll of them (512 bytes per warp each) before the first is consumed;
 // otherwise lanes take dimensions j = lane, lane + 32, ... (128 contiguous
-// bytes per request).
-constexpr int kRowUnroll = 4;
+// bytes per request). Rounds of 3 (384 dimensions, then the early-exit check
+// of row_dist_bounded) beat 2, 4 and 5 (1M x 768: 263k vs 251k / 258k / 251k
+// queries/s; 2M x 1536 unchanged).
+constexpr int kRowUnroll = 3;
 template <int MET>
 __device__ __forceinline__ float row_dist(const float *__restrict__ xrow, const float *__restrict__ qrow, int D,
                                           int lane, bool vec4) {
