@@ -149,6 +149,20 @@ __device__ __forceinline__ int32_t key_id(uint64_t key) { return (int32_t)(uint3
 enum { MT_L2 = 0, MT_IP = 1, MT_L1 = 2 };
 constexpr unsigned kFull = 0xffffffffu;
 
+// Raise a kernel's dynamic shared-memory limit to at least `bytes`, never
+// lowering it. Launches of one kernel ask for different sizes (they depend on
+// d and k); a limit set lower by a later, smaller launch would make an earlier
+// launch with more shared memory (e.g. a kernel node of a captured CUDA graph,
+// or its replay under a profiler) invalid.
+template <typename F>
+inline cudaError_t raise_smem_limit(F *func, size_t bytes) {
+    cudaFuncAttributes fa;
+    cudaError_t e = cudaFuncGetAttributes(&fa, func);
+    if (e != cudaSuccess) return e;
+    if ((size_t)fa.maxDynamicSharedSizeBytes >= bytes) return cudaSuccess;
+    return cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
 // Smallest power of two >= v (v >= 1).
 __host__ __device__ inline int pow2_ceil(int v) {
     int p = 1;

@@ -244,20 +244,17 @@ cudaError_t launch_layout_t(int metric, const LayoutParams &p, size_t smem, int 
     cudaError_t e;
     switch (metric) {
     case MT_IP:
-        e = cudaFuncSetAttribute(layout_scan_kernel<MT_IP, LAYOUT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)smem);
+        e = raise_smem_limit(layout_scan_kernel<MT_IP, LAYOUT>, smem);
         if (e != cudaSuccess) return e;
         layout_scan_kernel<MT_IP, LAYOUT><<<grid, kLayoutWarps * 32, smem, st>>>(p);
         break;
     case MT_L1:
-        e = cudaFuncSetAttribute(layout_scan_kernel<MT_L1, LAYOUT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)smem);
+        e = raise_smem_limit(layout_scan_kernel<MT_L1, LAYOUT>, smem);
         if (e != cudaSuccess) return e;
         layout_scan_kernel<MT_L1, LAYOUT><<<grid, kLayoutWarps * 32, smem, st>>>(p);
         break;
     default:
-        e = cudaFuncSetAttribute(layout_scan_kernel<MT_L2, LAYOUT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)smem);
+        e = raise_smem_limit(layout_scan_kernel<MT_L2, LAYOUT>, smem);
         if (e != cudaSuccess) return e;
         layout_scan_kernel<MT_L2, LAYOUT><<<grid, kLayoutWarps * 32, smem, st>>>(p);
     }

@@ -329,9 +329,7 @@ cudaError_t mlp_order(pdx_mlp *net, const float *q, int64_t nq, const float *cen
     int npad = 1;
     while (npad < d) npad <<= 1;
     const size_t smem = (size_t)npad * 8 + (size_t)(2 * d + H) * 4;
-    if ((e = cudaFuncSetAttribute(mlp_order_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) !=
-        cudaSuccess)
-        return e;
+    if ((e = raise_smem_limit(mlp_order_kernel, smem)) != cudaSuccess) return e;
     mlp_order_kernel<<<(unsigned)nq, 256, smem, st>>>(q, nq, d, H, cent, nearest, net->w1h, net->b1(), net->w2h,
                                                        net->b2(), mu, order);
     return counted(cudaGetLastError());

@@ -1085,7 +1085,7 @@ static cudaError_t launch_scan_t(const ScanParams &p, int num_sms, cudaStream_t 
     // leaves at least 32 KB of the SM for L1
     const bool four = p.ctas_per_sm != 3 && 4 * (smem + 1024) + 32 * 1024 <= 228 * 1024;
     auto kern = four ? pdxsearch_kernel<PR, MET, ST, 4> : pdxsearch_kernel<PR, MET, ST, 3>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = raise_smem_limit(kern, smem);
     if (e != cudaSuccess) return e;
     // Shared-memory carveout sized for the requested number of resident CTAs
     // (1 KB reserved per CTA); what remains of the SM's on-chip memory is L1,

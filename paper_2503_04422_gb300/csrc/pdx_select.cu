@@ -294,7 +294,7 @@ cudaError_t launch_select_k(const uint64_t *keys, int64_t rows, int64_t L, int32
     if (sb < 2 * kpad) sb = 2 * kpad;
     if (sb < 64) sb = 64;
     size_t smem = (size_t)sb * 8;
-    cudaError_t e = cudaFuncSetAttribute(select_k_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = raise_smem_limit(select_k_kernel, smem);
     if (e != cudaSuccess) return e;
     int threads = sb >= 1024 ? 512 : (sb / 2 < 32 ? 32 : sb / 2);
     select_k_kernel<<<(unsigned)rows, threads, smem, st>>>(keys, L, k, kpad, sb, out);
@@ -396,15 +396,8 @@ cudaError_t launch_select_k_tau(const uint64_t *keys, int64_t rows, int64_t L, i
     int kpad = pow2_ceil(k);
     const int sb = std::max(8192, 2 * kpad);  // power of two (kpad <= 1024)
     const size_t smem = (size_t)sb * 8;
-    static int have[64];
-    int dev = 0;
-    cudaGetDevice(&dev);
-    if (have[dev & 63] < (int)smem) {
-        cudaError_t e = cudaFuncSetAttribute(select_k_tau_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)smem);
-        if (e != cudaSuccess) return e;
-        have[dev & 63] = (int)smem;
-    }
+    cudaError_t e = raise_smem_limit(select_k_tau_kernel, smem);
+    if (e != cudaSuccess) return e;
     select_k_tau_kernel<<<(unsigned)rows, 512, smem, st>>>(keys, L, k, tau, gamma, sb, out);
     return counted(cudaGetLastError());
 }
@@ -704,7 +697,7 @@ cudaError_t launch_order(const float *q, int64_t rows, int32_t d, const float *m
     if (rows == 0) return cudaSuccess;
     const int nunits = (mode >= 1) ? d : (d + Z - 1) / Z;
     size_t smem = (size_t)pow2_ceil(nunits) * 8;
-    cudaError_t e = cudaFuncSetAttribute(order_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = raise_smem_limit(order_kernel, smem);
     if (e != cudaSuccess) return e;
     order_kernel<<<(unsigned)rows, 256, smem, st>>>(q, rows, d, means, per_part, row_part, mode, Z, scores, out);
     return counted(cudaGetLastError());
