@@ -39,6 +39,7 @@ WORKLOADS = {
     "ivf_1m_d960": dict(k=10, pruner="ads", nlist=1024),
     "learned_order_2m_d1536": dict(k=10, pruner="bond", metric="ip", nclusters=1024, traces=50_000),
     "serving_64_fp8": dict(k=100, pruner="bond", storage="fp8", batches=1000, max_batch=4096),
+    "serving_batch1_fp8": dict(k=100, pruner="bond", storage="fp8"),
     "layouts": dict(k=10),
     "mips_1m_d768": dict(k=10, pruner="cs_ip", metric="ip"),
 }
@@ -868,6 +869,73 @@ def run_serving(args, rank, world, local_rank):
         pass
 
 
+def run_serving_batch1(args, rank, world, local_rank):
+    """Batch-1 latency through the serving runtime: the largest, the median and
+    the smallest of the 64 serving collections (FP8, exact top-100), one query
+    per call, graphs and the tuner on. Each collection takes --warmup calls
+    (tuning and graph capture happen there), then --steps timed calls, each
+    bracketed by CUDA events; the line gives the median device time per call
+    and queries/s at that median for the median collection."""
+    import numpy as np
+    import torch
+
+    import pdx_synth
+    from paper_2503_04422_gb300 import build as pbuild
+    pbuild.build()
+    from paper_2503_04422_gb300 import pdx
+
+    torch.cuda.set_device(local_rank)
+    spec = WORKLOADS[args.workload]
+    k = spec["k"]
+    colls = pdx_synth.serving_collections()
+    order = np.argsort([c.n for c in colls])
+    picks = {"largest": int(order[-1]), "median": int(order[len(order) // 2]), "smallest": int(order[0])}
+    if args.b1_collection != "all":
+        picks = {args.b1_collection: picks[args.b1_collection]}
+    nq = args.steps + args.warmup
+    ixs, qs = [], []
+    for ci in picks.values():
+        c = colls[ci]
+        x, q = pdx_synth.mixture_device(c.n, c.d, nq, c.seed)
+        ixs.append(pdx.pdx_build_layout(x, storage=spec["storage"]))
+        qs.append(q)
+        del x
+    torch.cuda.synchronize()
+    torch.cuda.empty_cache()
+    srv = pdx.Server(ixs, k=k, max_batch=4096, use_graphs=True, autotune=True, pruner=spec["pruner"])
+    out = (torch.empty((1, k), dtype=torch.float32, device="cuda"), torch.empty((1, k), dtype=torch.int64, device="cuda"))
+    st = torch.cuda.current_stream()
+    res = {}
+    launches = 0
+    clocks = ClockSampler(local_rank)
+    clocks.start()
+    for j, (name, ci) in enumerate(picks.items()):
+        for r in range(args.warmup):
+            srv.search(j, qs[j][r:r + 1], out=out)
+        torch.cuda.synchronize()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+        l0 = pdx.pdx_kernel_launches()
+        for r in range(args.steps):
+            ev[r][0].record(st)
+            srv.search(j, qs[j][args.warmup + r:args.warmup + r + 1], out=out)
+            ev[r][1].record(st)
+        torch.cuda.synchronize()
+        launches += pdx.pdx_kernel_launches() - l0
+        ms = sorted(a.elapsed_time(b) for a, b in ev)
+        c = colls[ci]
+        res[name] = {"collection": f"{c.n} x {c.d}", "median_ms": ms[len(ms) // 2], "min_ms": ms[0], "max_ms": ms[-1]}
+    clk = clocks.stop()
+    srv.free()
+    main = res.get("median") or next(iter(res.values()))
+    line = {"metric": METRIC, "value": 1e3 / main["median_ms"], "unit": "queries/s", "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": main["median_ms"], "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "fp8_e4m3 (FP32 accumulate, FP32 rerank)", "data": "synthetic",
+            "config": {"workload": args.workload, "k": k, "batch": 1, "collections": res, "graphs": True,
+                       "autotune": True, "timer": "CUDA events around each call (median over the timed calls)"},
+            "gpu_launches": int(launches), "clocks": clk}
+    print(json.dumps(line), flush=True)
+
+
 def run_layouts(args, rank, world, local_rank):
     """The layout comparison (Sec. 3 Fig. 3, Table 3's kernel study, N-ary +
     gather and DSM in Sec. 7) on one workload: exact top-k by a linear scan
@@ -956,6 +1024,8 @@ def main():
     ap.add_argument("--traces", type=int, default=None, help="learned-order workload: training queries")
     ap.add_argument("--epochs", type=int, default=30, help="learned-order workload: training epochs")
     ap.add_argument("--no-f32-compare", action="store_true", help="serving workload: skip the FP32-storage stream")
+    ap.add_argument("--b1-collection", default="all", choices=["all", "largest", "median", "smallest"],
+                    help="batch-1 serving workload: which collections")
     ap.add_argument("--first-step", type=int, default=None, help="exact and IVF workloads: first fetch step (default 4)")
     ap.add_argument("--no-alt", action="store_true", help="exact workload: skip the tensor-engine companion line")
     ap.add_argument("--ctas-per-sm", type=int, default=None, help="exact and IVF workloads: resident scan CTAs per SM")
@@ -979,6 +1049,8 @@ def main():
         run_ivf(args, rank, world, local_rank)
     elif args.workload.startswith("learned"):
         run_learned(args, rank, world, local_rank)
+    elif args.workload == "serving_batch1_fp8":
+        run_serving_batch1(args, rank, world, local_rank)
     elif args.workload.startswith("serving"):
         run_serving(args, rank, world, local_rank)
     elif args.workload == "layouts":
