@@ -795,6 +795,8 @@ pdx_status exact_plan(const pdx_index *ix, int64_t nq, int32_t k, const pdx_sear
         b += rup((size_t)nq * ep->sc_ld * 8) + rup((size_t)nq * ep->sc_probe * 8) +
              rup((size_t)nq * ep->sc_probe * ix->sc_m * 8);
     if (o.tau_init) b += rup((size_t)nq * 4);
+    if (nq <= kSplitSelectRows)  // the final selection's compact buffer and counters
+        b += rup((size_t)nq * kSplitSelectCap * 8) + rup((size_t)nq * 4);
     if (pl.pruner == PDX_PRUNE_CS_IP) {
         if ((int)o.first_step != ix->cs_first_step) {
             set_error("PDX_PRUNE_CS_IP: first_step %u differs from the index's stored schedule (%d)", o.first_step,
@@ -880,6 +882,9 @@ pdx_status exact_run(const pdx_index *ix, const float *qd, int64_t nq, int32_t k
         ep.start_clusters ? reinterpret_cast<uint64_t *>(take((size_t)nq * ep.sc_probe * ix->sc_m * 8)) : nullptr;
     unsigned char *mlp_ws = ep.mlp_bytes ? take(ep.mlp_bytes) : nullptr;
     float *tau_in = o.tau_init ? reinterpret_cast<float *>(take((size_t)nq * 4)) : nullptr;
+    uint64_t *sel_compact =
+        nq <= kSplitSelectRows ? reinterpret_cast<uint64_t *>(take((size_t)nq * kSplitSelectCap * 8)) : nullptr;
+    int32_t *sel_counts = nq <= kSplitSelectRows ? reinterpret_cast<int32_t *>(take((size_t)nq * 4)) : nullptr;
     float *cs_q = pl.pruner == PDX_PRUNE_CS_IP
                       ? reinterpret_cast<float *>(take((size_t)nq * (ix->cs_nchk + 1) * 2 * 4))
                       : nullptr;
@@ -1015,7 +1020,7 @@ pdx_status exact_run(const pdx_index *ix, const float *qd, int64_t nq, int32_t k
     PDX_TRY(launch_scan(pl.pruner, pl.metric, p, sms, st));
     if (o.scan_event_stop) PDX_TRY(cudaEventRecord(static_cast<cudaEvent_t>(o.scan_event_stop), st));
     PDX_TRY(mark(4));
-    PDX_TRY(launch_select_k_tau(cand, nq, (int64_t)ep.nslots * k, k, tau, p.gamma, topk, st));
+    PDX_TRY(launch_select_k_tau(cand, nq, (int64_t)ep.nslots * k, k, tau, p.gamma, topk, st, sel_compact, sel_counts));
     // canonical distances: from the contiguous rows when the index keeps them
     // (same lanes, order and reduction as from the blocks, so the same bits)
     if (ix->xnary && ix->metric != PDX_L1)

@@ -367,8 +367,13 @@ cudaError_t launch_select_k(const uint64_t *keys, int64_t rows, int64_t L, int32
                             cudaStream_t st);
 // The same over keys whose distance is within slack(tau[row], gamma), where
 // tau[row] is the row's final threshold (the k-th distance of k real vectors).
+// With scratch for at most kSplitSelectRows rows (compact: rows x kSplitSelectCap
+// keys, counts: rows ints) a small batch's long rows are first filtered by many
+// CTAs at once; null scratch keeps one CTA per row.
+constexpr int kSplitSelectRows = 16;
+constexpr int kSplitSelectCap = 8192;
 cudaError_t launch_select_k_tau(const uint64_t *keys, int64_t rows, int64_t L, int32_t k, const float *tau,
-                                float gamma, uint64_t *out, cudaStream_t st);
+                                float gamma, uint64_t *out, cudaStream_t st, uint64_t *compact, int32_t *counts);
 // tau[row] = min(tau[row], init[row]) on the ordered representation.
 cudaError_t launch_tau_min(float *tau, const float *init, int64_t rows, cudaStream_t st);
 // tau[row] = distance of the k-th key of each row (or +inf).

@@ -329,13 +329,54 @@ __device__ __forceinline__ void block_bitonic(uint64_t *buf, int len, int tid, i
     }
 }
 
+// Small batches: one row's keys are filtered by many CTAs (slices of the row)
+// into a compact per-row buffer of `cap` keys, with a per-row counter
+// (zeroed before the launch). A row whose keys within the limit exceed cap
+// is selected from its full row instead.
+__global__ void __launch_bounds__(512) filter_keys_kernel(const uint64_t *__restrict__ keys, int64_t L,
+                                                          const float *__restrict__ tau, float gamma, int32_t cap,
+                                                          uint64_t *__restrict__ compact, int32_t *__restrict__ counts) {
+    const int64_t row = blockIdx.y;
+    const int64_t per = (L + gridDim.x - 1) / gridDim.x;
+    const int64_t lo = (int64_t)blockIdx.x * per;
+    const int64_t hi = min(L, lo + per);
+    const uint64_t *src = keys + row * L;
+    const float t = o2f(reinterpret_cast<const uint32_t *>(tau)[row]);
+    const uint32_t lim = f2o(t + fabsf(t) * gamma);
+    const int nt = blockDim.x;
+    for (int64_t base = lo + threadIdx.x; base < hi; base += (int64_t)nt * 8) {
+        uint64_t kk[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const int64_t i = base + (int64_t)u * nt;
+            kk[u] = i < hi ? src[i] : kEmptyKey;
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            if (kk[u] != kEmptyKey && (uint32_t)(kk[u] >> 32) <= lim) {
+                const int pos = atomicAdd(counts + row, 1);
+                if (pos < cap) compact[row * cap + pos] = kk[u];
+            }
+        }
+    }
+}
+
 __global__ void __launch_bounds__(512) select_k_tau_kernel(const uint64_t *__restrict__ keys, int64_t L, int32_t k,
                                                            const float *__restrict__ tau, float gamma, int32_t sb,
+                                                           const uint64_t *__restrict__ compact,
+                                                           const int32_t *__restrict__ counts, int32_t cap,
                                                            uint64_t *__restrict__ out) {
     extern __shared__ __align__(16) uint64_t buf[];
     __shared__ int count;
     const int64_t row = blockIdx.x;
     const uint64_t *src = keys + row * L;
+    if (counts) {   // filtered by filter_keys_kernel: its compact keys, unless they overflowed
+        const int c = counts[row];
+        if (c <= cap) {
+            src = compact + row * cap;
+            L = c;
+        }
+    }
     const int tid = threadIdx.x, nt = blockDim.x;
     const float t = o2f(reinterpret_cast<const uint32_t *>(tau)[row]);
     uint32_t lim = f2o(t + fabsf(t) * gamma);
@@ -391,14 +432,26 @@ __global__ void __launch_bounds__(512) select_k_tau_kernel(const uint64_t *__res
 }
 
 cudaError_t launch_select_k_tau(const uint64_t *keys, int64_t rows, int64_t L, int32_t k, const float *tau,
-                                float gamma, uint64_t *out, cudaStream_t st) {
+                                float gamma, uint64_t *out, cudaStream_t st, uint64_t *compact, int32_t *counts) {
     if (rows == 0) return cudaSuccess;
     int kpad = pow2_ceil(k);
-    const int sb = std::max(8192, 2 * kpad);  // power of two (kpad <= 1024)
+    const int sb = std::max(kSplitSelectCap, 2 * kpad);  // power of two (kpad <= 1024)
     const size_t smem = (size_t)sb * 8;
     cudaError_t e = raise_smem_limit(select_k_tau_kernel, smem);
     if (e != cudaSuccess) return e;
-    select_k_tau_kernel<<<(unsigned)rows, 512, smem, st>>>(keys, L, k, tau, gamma, sb, out);
+    const bool split = compact && counts && rows <= kSplitSelectRows && L > 4096 && sb == kSplitSelectCap;
+    if (split) {
+        // 128 slices in all, whatever the batch (1 query: 128 CTAs over its row)
+        const int slices = (int)std::max<int64_t>(1, std::min<int64_t>(128 / rows, (L + 4095) / 4096));
+        e = cudaMemsetAsync(counts, 0, (size_t)rows * 4, st);
+        if (e != cudaSuccess) return e;
+        filter_keys_kernel<<<dim3((unsigned)slices, (unsigned)rows), 512, 0, st>>>(keys, L, tau, gamma,
+                                                                                   kSplitSelectCap, compact, counts);
+        e = counted(cudaGetLastError());
+        if (e != cudaSuccess) return e;
+    }
+    select_k_tau_kernel<<<(unsigned)rows, 512, smem, st>>>(keys, L, k, tau, gamma, sb, split ? compact : nullptr,
+                                                            split ? counts : nullptr, kSplitSelectCap, out);
     return counted(cudaGetLastError());
 }
 

@@ -297,3 +297,16 @@ def test_start_clusters_keep_bond_exact(P, torch, clusters):
         torch.cuda.synchronize()
         check_topk(x, q, k, dist, idx)
         assert st["start_values"] > 0
+
+
+@pytest.mark.parametrize("nq,k,pruner", [(1, 10, "bond"), (3, 100, "bond"), (16, 64, "bond"), (2, 50, "none")])
+def test_small_batches_with_long_item_lists(P, torch, nq, k, pruner):
+    # a batch of at most 16 queries spreads over many work items, whose lists
+    # the final selection filters with many CTAs into a compact buffer; the
+    # unpruned scan keeps tau = +inf, so every key passes and the compact buffer
+    # overflows into the full-row selection
+    x, q = pdx_synth.gaussian_mixture(pdx_synth.MixtureSpec(n=120000, d=32, nq=nq, n_centres=64, seed=61))
+    ix = P.pdx_build_layout(_dev(torch, x), partition_size=6000)
+    dist, idx = P.pdx_search_exact(ix, _dev(torch, q), k, pruner=pruner, engine="scan" if pruner == "none" else "auto")
+    torch.cuda.synchronize()
+    check_topk(x, q, k, dist, idx)
