@@ -295,6 +295,18 @@ typedef struct pdx_search_opts {
                                   counts (tests against a sequential implementation).    */
     pdx_layout layout;         /* unpruned exact search on the SCAN engine: which storage
                                   layout the linear scan reads (default PDX)               */
+    uint64_t *finished_log;    /* optional device array (a check of exactness, not for
+                                  speed): the PDXearch scan appends (query << 32) | id for
+                                  every vector it carries through all D dimensions (it was
+                                  pruned by no test), in no particular order. A pruned
+                                  exact search is exact iff every query's true top-k is
+                                  among its entries. FP32 blocks with PDX_PRUNE_BOND or
+                                  PDX_PRUNE_CS_IP only (else PDX_ERR_UNSUPPORTED); the
+                                  logging scan is a separate kernel instance, so searches
+                                  without a log run unchanged. NULL (default): no log     */
+    unsigned long long *finished_count; /* device counter the scan adds to (the caller zeroes
+                                  it); entries beyond finished_cap are counted, not stored */
+    uint64_t finished_cap;     /* capacity of finished_log in entries                      */
 } pdx_search_opts;
 
 typedef struct pdx_index_info {

@@ -621,6 +621,15 @@ pdx_status check_search_args(const pdx_index *ix, const float *q, int64_t nq, in
         set_error("%s: tau_fixed needs tau_init", fn);
         return PDX_ERR_ARG;
     }
+    if (o->finished_log &&
+        (!o->finished_count || !is_device_ptr(o->finished_log) || !is_device_ptr(o->finished_count))) {
+        set_error("%s: finished_log and finished_count must both be device pointers", fn);
+        return PDX_ERR_ARG;
+    }
+    if (o->finished_log && (ix->storage != PDX_F32 || (o->pruner != PDX_PRUNE_BOND && o->pruner != PDX_PRUNE_CS_IP))) {
+        set_error("%s: finished_log is kept by FP32 PDX-BOND and CS_IP scans", fn);
+        return PDX_ERR_UNSUPPORTED;
+    }
     if (o->order == PDX_ORDER_LEARNED && o->mlp->d != ix->d) {
         set_error("%s: the network was built for d=%d, the index has d=%d", fn, o->mlp->d, ix->d);
         return PDX_ERR_ARG;
@@ -1016,6 +1025,9 @@ pdx_status exact_run(const pdx_index *ix, const float *qd, int64_t nq, int32_t k
         p.resid = ix->cs_resid;
         p.nchk = ix->cs_nchk;
     }
+    p.fin_log = o.finished_log;
+    p.fin_count = o.finished_count;
+    p.fin_cap = o.finished_cap;
     if (o.scan_event_start) PDX_TRY(cudaEventRecord(static_cast<cudaEvent_t>(o.scan_event_start), st));
     PDX_TRY(launch_scan(pl.pruner, pl.metric, p, sms, st));
     if (o.scan_event_stop) PDX_TRY(cudaEventRecord(static_cast<cudaEvent_t>(o.scan_event_stop), st));
@@ -1672,6 +1684,9 @@ extern "C" pdx_status pdx_search_ivf(const pdx_index *ix, const float *q, int64_
     p.qorder_per_part = op.per_part;
     p.tau_fixed = o.tau_fixed ? 1 : 0;
     p.rows_vec4 = rows_vec4(ix, p.qrows);
+    p.fin_log = o.finished_log;
+    p.fin_count = o.finished_count;
+    p.fin_cap = o.finished_cap;
     if (o.scan_event_start) PDX_TRY(cudaEventRecord(static_cast<cudaEvent_t>(o.scan_event_start), st));
     // START (Sec. 4): the nearest bucket of every query, starting from tau = +inf
     p.slot0 = 0;

@@ -261,6 +261,9 @@ struct ScanParams {
     int32_t *pool_cnt;         // [nq]
     int32_t tau_fixed;         // thresholds stay at their initial values (no tightening)
     int32_t rows_vec4;         // d % 4 == 0 and xnary, qrows 16-byte aligned: rows read as float4
+    uint64_t *fin_log;         // optional: (query << 32) | id of every vector carried through all D
+    unsigned long long *fin_count;
+    uint64_t fin_cap;
 };
 
 

@@ -359,6 +359,15 @@ __device__ __forceinline__ float cs_margin(float rx2, float x2, float rq2, float
 // The launcher takes 4 when four CTAs' shared memory still leaves room for L1.
 
 
+// Exactness check (finished_log): lane 0 records a vector that passed every
+// prune test of the scan and reached the merge with all D dimensions.
+__device__ __forceinline__ void log_finished(const ScanParams &a, int64_t qi, int32_t id, int lane) {
+    if (lane == 0) {
+        const unsigned long long pos = atomicAdd(a.fin_count, 1ull);
+        if (pos < a.fin_cap) a.fin_log[pos] = ((uint64_t)qi << 32) | (uint32_t)id;
+    }
+}
+
 // Offer a full distance to the query's shared pool (lane 0 writes). The pool
 // is a ring: once full, new distances (only those below the current
 // threshold are offered) replace the oldest. Each (query, vector) pair is
@@ -508,7 +517,9 @@ __device__ __forceinline__ float row_dist_bounded(const float *__restrict__ xrow
 constexpr int kRowFinish = 8;
 constexpr int kPruneBudget = 8;
 
-template <int PR, int MET, int ST, int OCC>
+// LOG: the instance that records finished vectors (finished_log); the
+// searches' own instances carry none of its code or registers.
+template <int PR, int MET, int ST, int OCC, bool LOG = false>
 __global__ void __launch_bounds__(256, OCC) pdxsearch_kernel(ScanParams a) {
     using ET = typename Elem<ST>::T;
     constexpr bool kLB = (PR == PR_BOND || PR == PR_NONE);  // low-precision: prune on a lower bound
@@ -999,6 +1010,12 @@ __global__ void __launch_bounds__(256, OCC) pdxsearch_kernel(ScanParams a) {
                 unsigned m2 = __ballot_sync(kFull, alive & 4u) & 0xffffu;
                 unsigned m3 = __ballot_sync(kFull, alive & 8u) & 0xffffu;
                 nfinal = __popc(m0) + __popc(m1) + __popc(m2) + __popc(m3);
+                if (LOG) {  // every alive vector: lane l of the first half holds 4l..4l+3
+                    const unsigned mm[4] = {m0, m1, m2, m3};
+                    for (int c = 0; c < 4; ++c)
+                        for (unsigned am = mm[c]; am; am &= am - 1u)
+                            log_finished(a, qi, a.ids[(int64_t)b * kBlock + 4 * (__ffs(am) - 1) + c], lane);
+                }
             } else if (rows) {
                 int finished = 0;
                 // all survivors' ids in one round of loads (lane m: survivor m)
@@ -1013,6 +1030,7 @@ __global__ void __launch_bounds__(256, OCC) pdxsearch_kernel(ScanParams a) {
                     if (lane == 0) w.ctr[S_VALUES] += (unsigned long long)vis;
                     if (vis < D) continue;
                     ++finished;
+                    if (LOG) log_finished(a, qi, id, lane);
                     if (dd <= thr) {
                         topk_insert(w.topk, cnt, k, make_key(dd, id), lane);
                         if (lane == 0) w.ctr[S_CAND] += 1;
@@ -1024,6 +1042,10 @@ __global__ void __launch_bounds__(256, OCC) pdxsearch_kernel(ScanParams a) {
                 }
                 nfinal = finished;
             } else if (nsurv > 0) {
+                if (LOG) {
+                    const int myid = (lane < nsurv) ? a.ids[(int64_t)b * kBlock + my_v] : 0;
+                    for (int m = 0; m < nsurv; ++m) log_finished(a, qi, __shfl_sync(kFull, myid, m), lane);
+                }
                 float dist = rank_dist<MET>(my_p);
                 bool cand = (lane < nsurv) && (dist <= thr);
                 unsigned cm = __ballot_sync(kFull, cand);
@@ -1085,6 +1107,11 @@ static cudaError_t launch_scan_t(const ScanParams &p, int num_sms, cudaStream_t 
     // leaves at least 32 KB of the SM for L1
     const bool four = p.ctas_per_sm != 3 && 4 * (smem + 1024) + 32 * 1024 <= 228 * 1024;
     auto kern = four ? pdxsearch_kernel<PR, MET, ST, 4> : pdxsearch_kernel<PR, MET, ST, 3>;
+    if constexpr (ST == ST_F32 && (PR == PR_BOND || PR == PR_CSIP)) {
+        if (p.fin_log) kern = four ? pdxsearch_kernel<PR, MET, ST, 4, true> : pdxsearch_kernel<PR, MET, ST, 3, true>;
+    } else {
+        if (p.fin_log) return cudaErrorInvalidValue;  // the log exists for FP32 BOND and CS_IP scans
+    }
     cudaError_t e = raise_smem_limit(kern, smem);
     if (e != cudaSuccess) return e;
     // Shared-memory carveout sized for the requested number of resident CTAs

@@ -72,7 +72,8 @@ class pdx_search_opts(ctypes.Structure):
                 ("scan_event_stop", ctypes.c_void_p), ("means_scope", ctypes.c_int),
                 ("ctas_per_sm", ctypes.c_uint32), ("mlp", ctypes.c_void_p), ("mlp_centroids", ctypes.c_void_p),
                 ("mlp_ncentroids", ctypes.c_int32), ("engine", ctypes.c_int), ("tau_init", ctypes.c_void_p),
-                ("tau_fixed", ctypes.c_int32), ("layout", ctypes.c_int)]
+                ("tau_fixed", ctypes.c_int32), ("layout", ctypes.c_int), ("finished_log", ctypes.c_void_p),
+                ("finished_count", ctypes.c_void_p), ("finished_cap", ctypes.c_uint64)]
 
 
 class pdx_index_info(ctypes.Structure):
@@ -225,10 +226,14 @@ def build_opts(metric="l2", storage="f32", partition_size=10000, keep_rows=True,
 def search_opts(pruner="bond", order="dist_to_means", zone_dims=None, selection_threshold=None, eps0=None,
                 bsa_m=None, first_step=None, start_vectors=None, blocks_per_item=None,
                 means_scope=None, ctas_per_sm=None, mlp=None, mlp_centroids=None,
-                engine="auto", tau_init=None, tau_fixed=False, layout="pdx") -> pdx_search_opts:
+                engine="auto", tau_init=None, tau_fixed=False, layout="pdx", finished_log=None,
+                finished_count=None) -> pdx_search_opts:
     """Search options; tau_init (float32 [nq], host or device) seeds each
-    query's threshold and tau_fixed keeps it fixed (see include/pdx.h). The
-    returned struct keeps a reference to tau_init's storage."""
+    query's threshold and tau_fixed keeps it fixed (see include/pdx.h).
+    finished_log (int64 device tensor) and finished_count (one-element int64
+    device tensor, zeroed by the caller) receive (query << 32) | id of every
+    vector the scan carried through all dimensions. The returned struct keeps
+    references to these tensors."""
     o = pdx_search_opts()
     lib().pdx_default_search_opts(ctypes.byref(o))
     if tau_init is not None:
@@ -237,6 +242,13 @@ def search_opts(pruner="bond", order="dist_to_means", zone_dims=None, selection_
         o._tau_keep = tk
     o.tau_fixed = int(bool(tau_fixed))
     o.layout = LAYOUT[layout]
+    if finished_log is not None:
+        if finished_count is None or not finished_log.is_cuda or not finished_count.is_cuda:
+            raise ValueError("finished_log and finished_count must be CUDA tensors")
+        o.finished_log = finished_log.data_ptr()
+        o.finished_count = finished_count.data_ptr()
+        o.finished_cap = finished_log.numel()
+        o._fin_keep = (finished_log, finished_count)
     o.pruner = PRUNER[pruner]
     o.order = ORDER[order]
     o.engine = ENGINE[engine]

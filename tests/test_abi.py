@@ -55,7 +55,8 @@ def test_struct_layouts_match_c(tmp_path):
         " offsetof(pdx_ivf_opts, rotation_seed), offsetof(pdx_search_stats, phase_ns));"
         "printf(\"%zu %zu %zu\\n\", offsetof(pdx_search_opts, layout), offsetof(pdx_build_opts, keep_dsm),"
         " offsetof(pdx_build_opts, start_clusters));"
-        "printf(\"%zu\\n\", offsetof(pdx_build_opts, cs_first_step));return 0;}\n")
+        "printf(\"%zu %zu %zu\\n\", offsetof(pdx_build_opts, cs_first_step), offsetof(pdx_search_opts, finished_log),"
+        " offsetof(pdx_search_opts, finished_cap));return 0;}\n")
     exe = tmp_path / "sizes"
     subprocess.check_call(["gcc", "-I", os.path.join(ROOT, "include"), str(prog), "-o", str(exe)])
     got = [int(v) for v in subprocess.check_output([str(exe)]).split()]
@@ -67,7 +68,8 @@ def test_struct_layouts_match_c(tmp_path):
             P.pdx_search_stats.dense_fallbacks.offset, P.pdx_search_opts.tau_init.offset,
             P.pdx_search_opts.tau_fixed.offset, P.pdx_ivf_opts.rotation_seed.offset,
             P.pdx_search_stats.phase_ns.offset, P.pdx_search_opts.layout.offset, P.pdx_build_opts.keep_dsm.offset,
-            P.pdx_build_opts.start_clusters.offset, P.pdx_build_opts.cs_first_step.offset]
+            P.pdx_build_opts.start_clusters.offset, P.pdx_build_opts.cs_first_step.offset,
+            P.pdx_search_opts.finished_log.offset, P.pdx_search_opts.finished_cap.offset]
     assert got == want
 
 
