@@ -4,6 +4,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <mutex>
+
 #include "pdx.h"
 
 namespace pdx {
@@ -154,8 +156,15 @@ constexpr unsigned kFull = 0xffffffffu;
 // d and k); a limit set lower by a later, smaller launch would make an earlier
 // launch with more shared memory (e.g. a kernel node of a captured CUDA graph,
 // or its replay under a profiler) invalid.
+// One lock for all kernels: two host threads raising the same kernel's limit
+// to different sizes must not leave the smaller one in place.
+inline std::mutex &smem_limit_lock() {
+    static std::mutex m;
+    return m;
+}
 template <typename F>
 inline cudaError_t raise_smem_limit(F *func, size_t bytes) {
+    std::lock_guard<std::mutex> guard(smem_limit_lock());
     cudaFuncAttributes fa;
     cudaError_t e = cudaFuncGetAttributes(&fa, func);
     if (e != cudaSuccess) return e;
