@@ -242,8 +242,8 @@ typedef struct pdx_search_stats {
                                       orders, order-network inference
                                   [1] finding the nearest IVF buckets (0 for exact search)
                                   [2] START: the initial thresholds (exact: start clusters or
-                                      the first start_vectors; IVF: threshold set-up only, the
-                                      nearest bucket is scanned first inside phase [3])
+                                      the first start_vectors; IVF: the nearest bucket's scan,
+                                      unless a large batch runs it first inside phase [3])
                                   [3] WARMUP/PRUNE: the PDXearch scan (or the tensor engine)
                                   [4] merge of the per-item lists, canonical distances, output */
     uint64_t reserved[2];

@@ -1688,17 +1688,33 @@ extern "C" pdx_status pdx_search_ivf(const pdx_index *ix, const float *q, int64_
     p.fin_count = o.finished_count;
     p.fin_cap = o.finished_cap;
     if (o.scan_event_start) PDX_TRY(cudaEventRecord(static_cast<cudaEvent_t>(o.scan_event_start), st));
-    // START (Sec. 4) and WARMUP/PRUNE in one launch: items are numbered
-    // slot-major, so every query's nearest bucket (slot 0, its block groups)
-    // is handed out first, from tau = +inf, and the later buckets start from
-    // the thresholds it has produced by then. One launch leaves no idle tail
-    // between the phases (1M x 960, nprobe 4: ADS 749k -> 786k queries/s);
-    // START's time is therefore inside the scan phase.
+    // START (Sec. 4): every query's nearest bucket (slot 0, its block groups)
+    // from tau = +inf, then WARMUP/PRUNE over the other buckets from the
+    // thresholds it produced. When the START items fill at least two waves of
+    // the GPU's warps, both run in one launch: items are numbered slot-major,
+    // so the nearest buckets are handed out first and nearly all of them are
+    // done before a later bucket starts, and no idle tail separates the phases
+    // (1M x 960, 10,000 queries, nprobe 4: ADS 749k -> 786k queries/s; START's
+    // time is then inside the scan phase). With fewer, a later bucket would
+    // start before its query's START had a threshold: two launches.
+    const bool one_launch = nq * (int64_t)ivf_chunks >= 2 * (int64_t)sms * 32;
     p.slot0 = 0;
-    p.nitems = nq * (int64_t)nprobe * ivf_chunks;
     p.work_counter = work;
-    PDX_TRY(mark(3));
-    PDX_TRY(launch_scan(pl.pruner, pl.metric, p, sms, st));
+    if (one_launch) {
+        p.nitems = nq * (int64_t)nprobe * ivf_chunks;
+        PDX_TRY(mark(3));
+        PDX_TRY(launch_scan(pl.pruner, pl.metric, p, sms, st));
+    } else {
+        p.nitems = nq * (int64_t)ivf_chunks;
+        PDX_TRY(launch_scan(pl.pruner, pl.metric, p, sms, st));
+        PDX_TRY(mark(3));
+        if (nprobe > 1) {
+            p.slot0 = ivf_chunks;
+            p.nitems = nq * (int64_t)(nprobe - 1) * ivf_chunks;
+            p.work_counter = work + 2;
+            PDX_TRY(launch_scan(pl.pruner, pl.metric, p, sms, st));
+        }
+    }
     if (o.scan_event_stop) PDX_TRY(cudaEventRecord(static_cast<cudaEvent_t>(o.scan_event_stop), st));
     PDX_TRY(mark(4));
     PDX_TRY(launch_select_k(cand, nq, (int64_t)nslots * k, k, topk, st));
