@@ -614,8 +614,8 @@ def run_learned(args, rank, world, local_rank):
     1536 is trained on the GPU on traces of the plain method for separate
     training queries. The line reports queries/s with the learned order, next to
     the heuristic's, at identical exact results. Following the fallback rule,
-    the learned order is used only if it visits fewer values than the heuristic
-    on a validation split."""
+    the learned order is used only if it visits at least 1% fewer values than
+    the heuristic on a validation split."""
     import numpy as np
     import torch
 
@@ -670,7 +670,9 @@ def run_learned(args, rank, world, local_rank):
     _, iv_h, sv_h = pdx.pdx_search_exact(ix, q_val, k, opts=pdx.search_opts(pruner="bond"), stats=True)
     _, iv_l, sv_l = pdx.pdx_search_exact(ix, q_val, k, opts=pdx.search_opts(pruner="bond", order="learned", mlp=net,
                                                                              mlp_centroids=cent), stats=True)
-    use_learned = sv_l["values_visited"] < sv_h["values_visited"]
+    # (by at least 1%: the network's inference costs time, and a smaller
+    # difference is within what the split itself varies by)
+    use_learned = sv_l["values_visited"] < 0.99 * sv_h["values_visited"]
     od = torch.empty((nq, k), dtype=torch.float32, device="cuda")
     oi = torch.empty((nq, k), dtype=torch.int64, device="cuda")
     stats_dev = torch.zeros(16, dtype=torch.int64, device="cuda")
