@@ -6,47 +6,77 @@
 namespace pdx {
 
 // ---------------------------------------------------------------------------
-// y[r][i] = sum_j M[i][j] * (x[r][j] - shift[j])  (FP32, 64x64 output tiles,
-// 32-dimension k-chunks staged in shared memory, 4x4 outputs per thread)
+// y[r][i] = sum_j M[i][j] * (x[r][j] - shift[j])  (FP32, 128 x 64 output
+// tiles, 16-dimension k-chunks staged in shared memory with the next chunk
+// loaded into registers meanwhile, 8 x 4 outputs per thread; every output is
+// summed in dimension order)
 __global__ void __launch_bounds__(256) transform_kernel(const float *__restrict__ x, int64_t rows, int32_t d,
                                                         const float *__restrict__ M, const float *__restrict__ shift,
                                                         float *__restrict__ y) {
-    __shared__ __align__(16) float Xs[32][68];
-    __shared__ __align__(16) float Ms[32][68];
-    const int tid = threadIdx.x, ty = tid >> 4, tx = tid & 15;
-    const int64_t r0 = (int64_t)blockIdx.x * 64;
-    const int i0 = blockIdx.y * 64;
-    float acc[4][4] = {};
-    for (int j0 = 0; j0 < d; j0 += 32) {
-        for (int e = tid; e < 64 * 32; e += 256) {
-            int rr = e >> 5, jj = e & 31;
-            int64_t r = r0 + rr;
-            int j = j0 + jj;
-            float v = 0.f;
-            if (r < rows && j < d) v = x[r * d + j] - (shift ? shift[j] : 0.f);
-            Xs[jj][rr] = v;
-            int ii = i0 + rr;
-            Ms[jj][rr] = (ii < d && j < d) ? M[(int64_t)ii * d + j] : 0.f;
+    constexpr int TR = 128, TI = 64, KC = 16;
+    __shared__ __align__(16) float Xs[KC][TR + 4];
+    __shared__ __align__(16) float Ms[KC][TI + 4];
+    const int tid = threadIdx.x, ty = tid >> 4, tx = tid & 15;  // rows ty*8..+7, outputs tx*4..+3
+    const int64_t r0 = (int64_t)blockIdx.x * TR;
+    const int i0 = blockIdx.y * TI;
+    float acc[8][4];
+#pragma unroll
+    for (int u = 0; u < 8; ++u)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) acc[u][v] = 0.f;
+    float xpf[8], mpf[4];
+    auto load = [&](int j0) {
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const int e = tid + 256 * u;
+            const int rr = e >> 4, jj = e & 15;
+            const int64_t r = r0 + rr;
+            const int j = j0 + jj;
+            xpf[u] = (r < rows && j < d) ? x[r * d + j] - (shift ? shift[j] : 0.f) : 0.f;
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int e = tid + 256 * u;
+            const int ii = e >> 4, jj = e & 15;
+            const int i = i0 + ii, j = j0 + jj;
+            mpf[u] = (i < d && j < d) ? M[(int64_t)i * d + j] : 0.f;
+        }
+    };
+    load(0);
+    for (int j0 = 0; j0 < d; j0 += KC) {
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const int e = tid + 256 * u;
+            Xs[e & 15][e >> 4] = xpf[u];
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int e = tid + 256 * u;
+            Ms[e & 15][e >> 4] = mpf[u];
         }
         __syncthreads();
-        for (int jj = 0; jj < 32; ++jj) {
-            float4 a = *reinterpret_cast<const float4 *>(&Xs[jj][ty * 4]);
-            float4 b = *reinterpret_cast<const float4 *>(&Ms[jj][tx * 4]);
-            float aa[4] = {a.x, a.y, a.z, a.w}, bb[4] = {b.x, b.y, b.z, b.w};
+        if (j0 + KC < d) load(j0 + KC);
+        const int jn = min(KC, d - j0);
+        for (int jj = 0; jj < jn; ++jj) {
+            const float4 a0 = *reinterpret_cast<const float4 *>(&Xs[jj][ty * 8]);
+            const float4 a1 = *reinterpret_cast<const float4 *>(&Xs[jj][ty * 8 + 4]);
+            const float4 bv = *reinterpret_cast<const float4 *>(&Ms[jj][tx * 4]);
+            const float aa[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+            const float bb[4] = {bv.x, bv.y, bv.z, bv.w};
 #pragma unroll
-            for (int u = 0; u < 4; ++u)
+            for (int u = 0; u < 8; ++u)
 #pragma unroll
                 for (int v = 0; v < 4; ++v) acc[u][v] = fmaf(aa[u], bb[v], acc[u][v]);
         }
         __syncthreads();
     }
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {
-        int64_t r = r0 + ty * 4 + u;
+    for (int u = 0; u < 8; ++u) {
+        const int64_t r = r0 + ty * 8 + u;
         if (r >= rows) continue;
 #pragma unroll
         for (int v = 0; v < 4; ++v) {
-            int i = i0 + tx * 4 + v;
+            const int i = i0 + tx * 4 + v;
             if (i < d) y[r * d + i] = acc[u][v];
         }
     }
@@ -55,7 +85,7 @@ __global__ void __launch_bounds__(256) transform_kernel(const float *__restrict_
 cudaError_t launch_transform(const float *x, int64_t rows, int32_t d, const float *M, const float *shift, float *y,
                              cudaStream_t st) {
     if (rows == 0) return cudaSuccess;
-    dim3 grid((unsigned)((rows + 63) / 64), (unsigned)((d + 63) / 64));
+    dim3 grid((unsigned)((rows + 127) / 128), (unsigned)((d + 63) / 64));
     transform_kernel<<<grid, 256, 0, st>>>(x, rows, d, M, shift, y);
     return counted(cudaGetLastError());
 }

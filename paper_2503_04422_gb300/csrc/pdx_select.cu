@@ -9,44 +9,64 @@
 namespace pdx {
 
 // ---------------------------------------------------------------------------
-// START (Sec. 4, PHASE 0) for exact search: exact distances of a tile of 64
-// queries to one 64-vector block, fully over D, written as (distance, id) keys.
-// Each thread owns 4 queries x 4 vectors; the block's dimension slices are
-// already dimension-major in PDX order and are staged 32 dimensions at a time.
+// START (Sec. 4, PHASE 0) for exact search and the IVF bucket search: exact
+// distances of a tile of 128 queries to one 64-vector block, fully over D,
+// written as (distance, id) keys. Each thread owns 8 queries x 4 vectors; the
+// block's dimension slices are already dimension-major in PDX order and are
+// staged 16 dimensions at a time, the next 16 loaded into registers while the
+// current ones are used. Every distance is summed in dimension order.
 template <int MET>
 __global__ void __launch_bounds__(256) dense_keys_kernel(const float *__restrict__ q, int64_t nq,
                                                          const float *__restrict__ data,
                                                          const int32_t *__restrict__ ids, int32_t d, int32_t nblk,
                                                          uint64_t *__restrict__ keys) {
-    __shared__ __align__(16) float Qs[32][68];  // padded rows: fewer bank conflicts on the transposed store
-    __shared__ __align__(16) float Xs[32][64];
+    constexpr int TQ = 128, KC = 16;
+    __shared__ __align__(16) float Qs[KC][TQ + 4];  // [dimension][query], padded rows
+    __shared__ __align__(16) float Xs[KC][kBlock];  // [dimension][vector]: the block's own layout
     const int tid = threadIdx.x;
-    const int64_t q0 = (int64_t)blockIdx.x * 64;
+    const int64_t q0 = (int64_t)blockIdx.x * TQ;
     const int b = blockIdx.y;
-    const int ty = tid >> 4, tx = tid & 15;
-    float acc[4][4];
+    const int ty = tid >> 4, tx = tid & 15;  // queries ty*8..+7, vectors tx*4..+3
+    float acc[8][4];
 #pragma unroll
-    for (int i = 0; i < 4; ++i)
+    for (int i = 0; i < 8; ++i)
 #pragma unroll
         for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
     const float *xb = data + (int64_t)b * d * kBlock;
-    for (int j0 = 0; j0 < d; j0 += 32) {
-        for (int e = tid; e < 32 * 64; e += 256) {
-            int jj = e >> 6, t = e & 63;
-            Xs[jj][t] = (j0 + jj < d) ? xb[(int64_t)(j0 + jj) * kBlock + t] : 0.f;
-            int qq = e >> 5, j2 = e & 31;
-            int64_t qi = q0 + qq;
-            Qs[j2][qq] = (qi < nq && j0 + j2 < d) ? q[qi * d + j0 + j2] : 0.f;
-        }
-        __syncthreads();
-        const int jn = min(32, d - j0);
-        for (int jj = 0; jj < jn; ++jj) {
-            float4 av = *reinterpret_cast<const float4 *>(&Qs[jj][ty * 4]);
-            float4 bv = *reinterpret_cast<const float4 *>(&Xs[jj][tx * 4]);
-            float aa[4] = {av.x, av.y, av.z, av.w};
-            float bb[4] = {bv.x, bv.y, bv.z, bv.w};
+    // the next chunk is loaded into registers while the current one is used
+    float qpf[8];
+    float4 xpf;
+    auto load = [&](int j0) {
 #pragma unroll
-            for (int i = 0; i < 4; ++i)
+        for (int u = 0; u < 8; ++u) {
+            const int e = tid + 256 * u;
+            const int qq = e >> 4, jj = e & 15;
+            const int64_t qi = q0 + qq;
+            qpf[u] = (qi < nq && j0 + jj < d) ? q[qi * d + j0 + jj] : 0.f;
+        }
+        const int jj = tid >> 4;
+        xpf = (j0 + jj < d) ? *reinterpret_cast<const float4 *>(xb + (int64_t)(j0 + jj) * kBlock + (tid & 15) * 4)
+                            : make_float4(0.f, 0.f, 0.f, 0.f);
+    };
+    load(0);
+    for (int j0 = 0; j0 < d; j0 += KC) {
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const int e = tid + 256 * u;
+            Qs[e & 15][e >> 4] = qpf[u];
+        }
+        *reinterpret_cast<float4 *>(&Xs[tid >> 4][(tid & 15) * 4]) = xpf;
+        __syncthreads();
+        if (j0 + KC < d) load(j0 + KC);
+        const int jn = min(KC, d - j0);
+        for (int jj = 0; jj < jn; ++jj) {
+            const float4 a0 = *reinterpret_cast<const float4 *>(&Qs[jj][ty * 8]);
+            const float4 a1 = *reinterpret_cast<const float4 *>(&Qs[jj][ty * 8 + 4]);
+            const float4 bv = *reinterpret_cast<const float4 *>(&Xs[jj][tx * 4]);
+            const float aa[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+            const float bb[4] = {bv.x, bv.y, bv.z, bv.w};
+#pragma unroll
+            for (int i = 0; i < 8; ++i)
 #pragma unroll
                 for (int j = 0; j < 4; ++j) acc[i][j] = term<MET>(aa[i], bb[j], acc[i][j]);
         }
@@ -54,13 +74,13 @@ __global__ void __launch_bounds__(256) dense_keys_kernel(const float *__restrict
     }
     const int64_t L = (int64_t)nblk * kBlock;
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
-        int64_t qi = q0 + ty * 4 + i;
+    for (int i = 0; i < 8; ++i) {
+        const int64_t qi = q0 + ty * 8 + i;
         if (qi >= nq) continue;
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
-            int v = tx * 4 + j;
-            int32_t id = ids[(int64_t)b * kBlock + v];
+            const int v = tx * 4 + j;
+            const int32_t id = ids[(int64_t)b * kBlock + v];
             keys[qi * L + (int64_t)b * kBlock + v] = (id >= 0) ? make_key(rank_dist<MET>(acc[i][j]), id) : kEmptyKey;
         }
     }
@@ -198,7 +218,7 @@ cudaError_t launch_member_keys(const float *q, int64_t nq, int32_t d, const floa
 cudaError_t launch_dense_keys(const float *q, int64_t nq, const float *data, const int32_t *ids, int32_t d,
                               int32_t nblk, int metric, uint64_t *keys, cudaStream_t st) {
     if (nq == 0 || nblk == 0) return cudaSuccess;
-    dim3 grid((unsigned)((nq + 63) / 64), (unsigned)nblk);
+    dim3 grid((unsigned)((nq + 127) / 128), (unsigned)nblk);
     if (metric == MT_IP)
         dense_keys_kernel<MT_IP><<<grid, 256, 0, st>>>(q, nq, data, ids, d, nblk, keys);
     else if (metric == MT_L1)
